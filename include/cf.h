@@ -1,0 +1,188 @@
+/*
+ * cf.h -- C ABI of libcf: GB300 (sm_103a) dense LU with tournament pivoting
+ * and Cholesky, after COnfLUX / COnfCHOX (Kwasniewski et al., "On the
+ * Parallel I/O Optimality of Linear Algebra Kernels: Near-Optimal Matrix
+ * Factorizations", SC'21, arXiv 2108.09337).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are column-major: element (i, j) of X with leading dimension
+ *    ldx is X[i + j*ldx].  ld >= max(1, rows).  Sizes may be 0 (no-op).
+ *  - Pointers are DEVICE pointers unless a parameter says "host".  The
+ *    caller owns all memory.  Calls that need scratch take (work, lwork);
+ *    the matching *_workspace_size() gives the bytes; lwork smaller than
+ *    that returns CF_ERR_WORKSPACE before anything is enqueued.  The library
+ *    never allocates device memory inside a call.
+ *  - Every call enqueues its work on `stream` and returns without waiting,
+ *    except where a parameter says it synchronises.
+ *  - ipiv is int32, 1-based, LAPACK order: row i was interchanged with row
+ *    ipiv[i]-1, for i = 0..n-1 in increasing order.
+ *  - info is a device int32: 0 on success; k > 0 when U(k-1,k-1) is exactly
+ *    zero (LU; the factorization still completes, as LAPACK dgetrf does), or
+ *    when the leading minor of order k is not positive definite (Cholesky;
+ *    the factorization stops there).
+ *  - Return value (host): CF_OK, -i when argument i (1-based) is invalid, or
+ *    one of the CF_ERR_* codes below.
+ *  - Not thread-safe for concurrent calls that share a work buffer.
+ */
+#ifndef CF_H
+#define CF_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CF_OK = 0,
+    CF_ERR_CUDA = -100,          /* a CUDA call failed; see cf_last_cuda_error */
+    CF_ERR_WORKSPACE = -101,     /* lwork below the size *_workspace_size gave */
+    CF_ERR_NOT_CONVERGED = -102, /* refinement stopped above the tolerance */
+    CF_ERR_TIMEOUT = -103,       /* a bounded device-side wait ran out */
+    CF_ERR_UNSUPPORTED = -104    /* valid but unsupported configuration */
+};
+
+typedef enum {
+    CF_F64 = 0,
+    CF_F32 = 1,
+    CF_BF16 = 2,
+    CF_F16 = 3,
+    CF_FP8E4M3 = 4
+} cf_prec;
+
+/* Tunables.  Pass NULL for the defaults (in brackets).  The pivot sequence
+ * is a function of (v, leaf_h, arity) only; the oracle takes the same three. */
+typedef struct {
+    int v;             /* block size of a step, 1..128 [128] (Sec. 7.2, "Block size v") */
+    int leaf_h;        /* tournament leaf height, 1..128 [128] */
+    int arity;         /* children per playoff node, 2..4 [2] */
+    int outer_V;       /* mixed LU/Cholesky: depth of the deferred update, multiple of v [0 = auto] */
+    int lookahead;     /* mixed paths: overlap panel t+1 with update t [1] */
+    double tol;        /* refinement stop: max backward error [1e-14] */
+    int max_iter;      /* refinement iterations [30] */
+    int gmres_restart; /* GMRES-IR Krylov dimension [30] */
+} cf_options;
+
+void cf_default_options(cf_options *opt /* host */);
+
+/* Statistics of a refined solve.  Written to host memory by the mixed
+ * solvers (they synchronise `stream` once per refinement step). */
+typedef struct {
+    int iterations;    /* refinement steps taken (residual evaluations - 1) */
+    int solver;        /* 0 = LU-IR / Cholesky-IR, 1 = GMRES-IR */
+    int converged;     /* 1 if eta <= tol */
+    int info;          /* info of the low-precision factorization */
+    double eta;        /* final max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) */
+    double eta0;       /* backward error of the unrefined solution */
+    double shift;      /* diagonal shift added before factoring (0 if none) */
+    double factor_ms;  /* device time of the factorization */
+    double refine_ms;  /* device time of the refinement */
+} cf_refine_stats;
+
+const char *cf_status_string(int status);
+int cf_last_cuda_error(void);   /* last cudaError_t seen by the library */
+
+/* ------------------------------------------------------------------------
+ * LU-1  TournPivot on one panel (Alg. 1 step 2; Sec. 7.3, "Tournament
+ * Pivoting" / "Pivoting in COnfLUX").  Exposed for testing the selection
+ * rule alone.
+ *   panel   m x w FP64, ld ldp (read only)
+ *   winners device int[min(m,w)]: 0-based panel rows of the pivots, in
+ *           pivot order
+ * Leaves are leaf_h consecutive rows; each playoff node stacks the winners
+ * of `arity` adjacent children (original panel values) and keeps min(rows, w)
+ * by partial-pivoting elimination; ties go to the smallest stacked position.
+ * w <= 128, 1 <= leaf_h <= 128, 2 <= arity <= 4.
+ * ------------------------------------------------------------------------ */
+size_t cf_tourn_workspace_size(int m, int w, int leaf_h, int arity);
+int cf_tourn_select(int m, int w, const double *panel, int ldp, int leaf_h,
+                    int arity, int *winners, void *work, size_t lwork,
+                    cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * cf_getrf -- FP64 LU with tournament pivoting, in place (Alg. 1; Sec. 7.2
+ * routines TournPivot, Factorize A00/A10/A01/A11; Table 2).
+ *   A     n x n FP64, lda: overwritten by L (unit, strictly below the
+ *         diagonal) and U (upper) of P A = L U.
+ *   ipiv  device int[n], 1-based interchanges (see above).
+ *   info  device int[1].
+ * ------------------------------------------------------------------------ */
+size_t cf_getrf_workspace_size(int n, const cf_options *opt);
+int cf_getrf(int n, double *A, int lda, int *ipiv, int *info, void *work,
+             size_t lwork, const cf_options *opt, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * cf_potrf -- FP64 Cholesky, lower, in place (Listing "Cholesky
+ * Factorization", Sec. 6.2; COnfCHOX, Sec. 7.5 and Table 2: potrf on A00,
+ * trsm on the panel, triangular update of A11).  Only the lower triangle is
+ * read or written.
+ * ------------------------------------------------------------------------ */
+size_t cf_potrf_workspace_size(int n, const cf_options *opt);
+int cf_potrf(int n, double *A, int lda, int *info, void *work, size_t lwork,
+             const cf_options *opt, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * S-1  Solves with the FP64 factors (paper silent; LAPACK getrs / potrs).
+ *   B  n x nrhs FP64, ldb: overwritten by the solution.
+ * cf_getrs needs work of cf_getrs_workspace_size(n, nrhs) bytes (the row
+ * order and a permuted copy of B).
+ * ------------------------------------------------------------------------ */
+size_t cf_getrs_workspace_size(int n, int nrhs);
+int cf_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv,
+             double *B, int ldb, void *work, size_t lwork,
+             cudaStream_t stream);
+int cf_potrs(int n, int nrhs, const double *L, int lda, double *B, int ldb,
+             cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * R-1  FP64 residual R = B - A X (A m x n; X n x nrhs; B, R m x nrhs).
+ * R may alias B.
+ * ------------------------------------------------------------------------ */
+int cf_residual(int m, int n, int nrhs, const double *A, int lda,
+                const double *X, int ldx, const double *B, int ldb, double *R,
+                int ldr, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * LU-5 / CH-3 building block, exposed for testing: C -= A_lp * B_lp^T on the
+ * tensor cores (tcgen05, TMEM accumulators, TMA-fed), FP32 accumulate.
+ *   A_lp  m x k low-precision, K-major: element (i, p) at A_lp[i*lda_k + p]
+ *   B_lp  n x k low-precision, K-major: element (j, p) at B_lp[j*ldb_k + p]
+ *   C     m x n FP32 column-major, ldc.
+ *   prec  CF_BF16 or CF_F16.  lower != 0: only tiles on or below the
+ *         diagonal of C are updated, and inside diagonal tiles only i >= j.
+ * k must be a multiple of 64; lda_k, ldb_k multiples of 8 elements; both
+ * operand pointers 16-byte aligned.
+ * ------------------------------------------------------------------------ */
+int cf_schur_update_lp(int m, int n, int k, const void *A_lp, int lda_k,
+                       const void *B_lp, int ldb_k, float *C, int ldc,
+                       cf_prec prec, int lower, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Mixed-precision refined solves (north star; the paper cites GPU mixed
+ * LU + refinement as related work, Sec. 11).  A and B are never modified.
+ *   factor_prec  CF_BF16 or CF_F16 (CF_FP8E4M3 for cf_posv_mixed)
+ *   X            n x nrhs FP64 solution, ldx
+ *   info         device int[1], info of the low-precision factorization
+ *   stats        host cf_refine_stats (may be NULL)
+ * Returns CF_ERR_NOT_CONVERGED when max_iter steps leave eta > tol (X then
+ * holds the best iterate).
+ * ------------------------------------------------------------------------ */
+size_t cf_gesv_mixed_workspace_size(int n, int nrhs, cf_prec factor_prec,
+                                    const cf_options *opt);
+int cf_gesv_mixed(int n, int nrhs, const double *A, int lda, const double *B,
+                  int ldb, double *X, int ldx, cf_prec factor_prec, int *info,
+                  cf_refine_stats *stats, void *work, size_t lwork,
+                  const cf_options *opt, cudaStream_t stream);
+size_t cf_posv_mixed_workspace_size(int n, int nrhs, cf_prec factor_prec,
+                                    const cf_options *opt);
+int cf_posv_mixed(int n, int nrhs, const double *A, int lda, const double *B,
+                  int ldb, double *X, int ldx, cf_prec factor_prec, int *info,
+                  cf_refine_stats *stats, void *work, size_t lwork,
+                  const cf_options *opt, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CF_H */

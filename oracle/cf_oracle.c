@@ -39,7 +39,9 @@
  * Readings of points the paper leaves open (each is also listed in the
  * design notes of the repository):
  *   - argmax ties: the candidate with the smallest position in the stacked
- *     block (its position before any elimination) wins;
+ *     block (its position before any elimination) wins; a NaN entry ranks
+ *     below every number (NaN inputs are outside the contract; this only
+ *     keeps the selection well defined);
  *   - tree: leaves are h consecutive rows of the current panel (the last leaf
  *     is shorter); each playoff node stacks the winners of `arity` adjacent
  *     children in child order; a group with a single child passes through;
@@ -81,6 +83,7 @@ static int gepp_select(int r, int w, double *S, int lds, int *order,
         for (int i = 0; i < r; ++i) {
             if (used[i]) continue;
             double a = fabs(S[IX(i, j, lds)]);
+            if (a != a) a = -0.5;       /* NaN ranks below every number */
             if (a > bestv) {            /* strict: ties keep the smaller i */
                 second = bestv;
                 bestv = a;

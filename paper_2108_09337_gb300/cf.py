@@ -1,0 +1,274 @@
+"""ctypes binding of libcf (include/cf.h): argument marshalling only.
+
+Every computation happens in libcf's CUDA kernels; torch provides device
+memory and the current stream.  Matrices are column-major torch tensors:
+an m x n matrix is a tensor of shape (m, n) with stride (1, ld), ld >= m
+(e.g. ``fortran_empty(m, n)`` or ``t.t().contiguous().t()``).
+
+Importing this module loads libcf.so and raises if it is missing: there is no
+CPU or PyTorch fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcf.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "cf.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libcf.so is not built (run __graft_entry__.build() or "
+                      "python -m paper_2108_09337_gb300.build)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+CF_OK = 0
+CF_ERR_CUDA = -100
+CF_ERR_WORKSPACE = -101
+CF_ERR_NOT_CONVERGED = -102
+CF_ERR_TIMEOUT = -103
+CF_ERR_UNSUPPORTED = -104
+CF_F64, CF_F32, CF_BF16, CF_F16, CF_FP8E4M3 = range(5)
+PREC = {"f64": CF_F64, "f32": CF_F32, "bf16": CF_BF16, "f16": CF_F16,
+        "fp8": CF_FP8E4M3, "fp8e4m3": CF_FP8E4M3}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("v", ctypes.c_int), ("leaf_h", ctypes.c_int), ("arity", ctypes.c_int),
+                ("outer_V", ctypes.c_int), ("lookahead", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int)]
+
+
+class RefineStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("solver", ctypes.c_int), ("converged", ctypes.c_int),
+                ("info", ctypes.c_int), ("eta", ctypes.c_double), ("eta0", ctypes.c_double),
+                ("shift", ctypes.c_double), ("factor_ms", ctypes.c_double),
+                ("refine_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_I, _P, _S, _D = ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_double
+_OPT = ctypes.POINTER(Options)
+_SIG = {
+    "cf_default_options": (None, [_OPT]),
+    "cf_status_string": (ctypes.c_char_p, [_I]),
+    "cf_last_cuda_error": (_I, []),
+    "cf_tourn_workspace_size": (_S, [_I, _I, _I, _I]),
+    "cf_tourn_select": (_I, [_I, _I, _P, _I, _I, _I, _P, _P, _S, _P]),
+    "cf_getrf_workspace_size": (_S, [_I, _OPT]),
+    "cf_getrf": (_I, [_I, _P, _I, _P, _P, _P, _S, _OPT, _P]),
+    "cf_potrf_workspace_size": (_S, [_I, _OPT]),
+    "cf_potrf": (_I, [_I, _P, _I, _P, _P, _S, _OPT, _P]),
+    "cf_getrs_workspace_size": (_S, [_I, _I]),
+    "cf_getrs": (_I, [_I, _I, _P, _I, _P, _P, _I, _P, _S, _P]),
+    "cf_potrs": (_I, [_I, _I, _P, _I, _P, _I, _P]),
+    "cf_residual": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P]),
+    "cf_schur_update_lp": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
+    "cf_gesv_mixed_workspace_size": (_S, [_I, _I, _I, _OPT]),
+    "cf_gesv_mixed": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _P, ctypes.POINTER(RefineStats),
+                           _P, _S, _OPT, _P]),
+    "cf_posv_mixed_workspace_size": (_S, [_I, _I, _I, _OPT]),
+    "cf_posv_mixed": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _P, ctypes.POINTER(RefineStats),
+                           _P, _S, _OPT, _P]),
+}
+for _name, (_res, _args) in _SIG.items():
+    if hasattr(_lib, _name):
+        _f = getattr(_lib, _name)
+        _f.restype = _res
+        _f.argtypes = _args
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/cf.h declares."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cf_[a-z0-9_]+)\s*\(", txt)))
+
+
+class CfError(RuntimeError):
+    def __init__(self, fn, status):
+        msg = _lib.cf_status_string(status).decode()
+        if status == CF_ERR_CUDA:
+            msg += " (cudaError %d)" % _lib.cf_last_cuda_error()
+        super().__init__("%s returned %d: %s" % (fn, status, msg))
+        self.status = status
+
+
+def _check(fn, st):
+    if st != CF_OK:
+        raise CfError(fn, st)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _ld(t: torch.Tensor, name: str) -> int:
+    """Leading dimension of a column-major CUDA tensor (checked)."""
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dim() == 1:
+        if t.shape[0] > 1 and t.stride(0) != 1:
+            raise ValueError("%s must be contiguous" % name)
+        return max(t.shape[0], 1)
+    if t.dim() != 2:
+        raise ValueError("%s must be 1-D or 2-D" % name)
+    m, n = t.shape
+    if m > 1 and t.stride(0) != 1:
+        raise ValueError("%s must be column-major (stride (1, ld))" % name)
+    if n > 1:
+        if t.stride(1) < m:
+            raise ValueError("%s: leading dimension below the row count" % name)
+        return max(t.stride(1), 1)
+    return max(m, 1)
+
+
+def fortran_empty(m: int, n: int, dtype=torch.float64, device="cuda"):
+    return torch.empty((n, m), dtype=dtype, device=device).t()
+
+
+def to_fortran(t: torch.Tensor) -> torch.Tensor:
+    return t.t().contiguous().t()
+
+
+def options(**kw) -> Options:
+    o = Options()
+    _lib.cf_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+# --------------------------------------------------------------------------
+def tourn_select(panel: torch.Tensor, leaf_h: int = 128, arity: int = 2) -> torch.Tensor:
+    assert panel.dtype == torch.float64
+    m, w = panel.shape
+    ld = _ld(panel, "panel")
+    win = torch.empty(max(min(m, w), 1), dtype=torch.int32, device=panel.device)
+    ws = _workspace(_lib.cf_tourn_workspace_size(m, w, leaf_h, arity), panel.device)
+    _check("cf_tourn_select", _lib.cf_tourn_select(m, w, _ptr(panel), ld, leaf_h, arity, _ptr(win),
+                                                   _ptr(ws), ws.numel(), _stream()))
+    return win[:min(m, w)]
+
+
+def getrf(A: torch.Tensor, v=None, leaf_h=None, arity=None, work=None):
+    """In-place LU with tournament pivoting.  Returns (ipiv, info) device
+    int32 tensors (ipiv 1-based)."""
+    assert A.dtype == torch.float64
+    n = A.shape[0]
+    assert A.shape == (n, n)
+    lda = _ld(A, "A")
+    opt = options(v=v, leaf_h=leaf_h, arity=arity)
+    ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    need = _lib.cf_getrf_workspace_size(n, ctypes.byref(opt))
+    ws = work if work is not None else _workspace(need, A.device)
+    _check("cf_getrf", _lib.cf_getrf(n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(ws), ws.numel(),
+                                     ctypes.byref(opt), _stream()))
+    return ipiv[:n], info
+
+
+def potrf(A: torch.Tensor, v=None):
+    assert A.dtype == torch.float64
+    n = A.shape[0]
+    lda = _ld(A, "A")
+    opt = options(v=v)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    ws = _workspace(_lib.cf_potrf_workspace_size(n, ctypes.byref(opt)), A.device)
+    _check("cf_potrf", _lib.cf_potrf(n, _ptr(A), lda, _ptr(info), _ptr(ws), ws.numel(),
+                                     ctypes.byref(opt), _stream()))
+    return info
+
+
+def getrs(LU: torch.Tensor, ipiv: torch.Tensor, B: torch.Tensor):
+    n = LU.shape[0]
+    nrhs = B.shape[1] if B.dim() == 2 else 1
+    ws = _workspace(_lib.cf_getrs_workspace_size(n, nrhs), LU.device)
+    _check("cf_getrs", _lib.cf_getrs(n, nrhs, _ptr(LU), _ld(LU, "LU"), _ptr(ipiv), _ptr(B), _ld(B, "B"),
+                                     _ptr(ws), ws.numel(), _stream()))
+    return B
+
+
+def potrs(L: torch.Tensor, B: torch.Tensor):
+    n = L.shape[0]
+    nrhs = B.shape[1] if B.dim() == 2 else 1
+    _check("cf_potrs", _lib.cf_potrs(n, nrhs, _ptr(L), _ld(L, "L"), _ptr(B), _ld(B, "B"), _stream()))
+    return B
+
+
+def residual(A: torch.Tensor, X: torch.Tensor, B: torch.Tensor, R: torch.Tensor | None = None):
+    m, n = A.shape
+    nrhs = X.shape[1] if X.dim() == 2 else 1
+    if R is None:
+        R = fortran_empty(m, nrhs, device=A.device)
+    _check("cf_residual", _lib.cf_residual(m, n, nrhs, _ptr(A), _ld(A, "A"), _ptr(X), _ld(X, "X"),
+                                           _ptr(B), _ld(B, "B"), _ptr(R), _ld(R, "R"), _stream()))
+    return R
+
+
+def schur_update_lp(A_lp: torch.Tensor, B_lp: torch.Tensor, C: torch.Tensor, lower: bool = False):
+    """C -= A_lp @ B_lp^T on the tensor cores; A_lp (m x k) and B_lp (n x k)
+    row-major (K-major) bf16/fp16 tensors, C float32 column-major."""
+    m, k = A_lp.shape
+    n = B_lp.shape[0]
+    prec = {torch.bfloat16: CF_BF16, torch.float16: CF_F16}[A_lp.dtype]
+    _check("cf_schur_update_lp", _lib.cf_schur_update_lp(m, n, k, _ptr(A_lp), A_lp.stride(0), _ptr(B_lp),
+                                                         B_lp.stride(0), _ptr(C), _ld(C, "C"), prec,
+                                                         int(lower), _stream()))
+    return C
+
+
+def _mixed(fn, wsfn, A, B, prec, opt_kw, work=None):
+    n = A.shape[0]
+    nrhs = B.shape[1] if B.dim() == 2 else 1
+    X = fortran_empty(n, nrhs, device=A.device)
+    info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    opt = options(**opt_kw)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    need = wsfn(n, nrhs, p, ctypes.byref(opt))
+    ws = work if work is not None else _workspace(need, A.device)
+    stats = RefineStats()
+    st = fn(n, nrhs, _ptr(A), _ld(A, "A"), _ptr(B), _ld(B, "B"), _ptr(X), _ld(X, "X"), p, _ptr(info),
+            ctypes.byref(stats), _ptr(ws), ws.numel(), ctypes.byref(opt), _stream())
+    if st not in (CF_OK, CF_ERR_NOT_CONVERGED):
+        raise CfError(fn.__name__, st)
+    return X, info, stats, st
+
+
+def gesv_mixed(A, B, prec="bf16", work=None, **opt_kw):
+    """Mixed-precision LU solve with FP64 refinement; A, B unchanged.
+    Returns (X, info, stats, status)."""
+    return _mixed(_lib.cf_gesv_mixed, _lib.cf_gesv_mixed_workspace_size, A, B, prec, opt_kw, work)
+
+
+def posv_mixed(A, B, prec="bf16", work=None, **opt_kw):
+    """Mixed-precision Cholesky solve with FP64 refinement."""
+    return _mixed(_lib.cf_posv_mixed, _lib.cf_posv_mixed_workspace_size, A, B, prec, opt_kw, work)
+
+
+def gesv_mixed_workspace_size(n, nrhs, prec="bf16", **opt_kw):
+    opt = options(**opt_kw)
+    return _lib.cf_gesv_mixed_workspace_size(n, nrhs, PREC[prec], ctypes.byref(opt))
+
+
+def posv_mixed_workspace_size(n, nrhs, prec="bf16", **opt_kw):
+    opt = options(**opt_kw)
+    return _lib.cf_posv_mixed_workspace_size(n, nrhs, PREC[prec], ctypes.byref(opt))
+
+
+def lib():
+    return _lib

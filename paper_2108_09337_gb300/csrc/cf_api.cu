@@ -1,0 +1,287 @@
+// cf_api.cu -- C ABI of the FP64 path: cf_getrf, cf_potrf, cf_getrs, cf_potrs,
+// cf_residual, options and status strings.
+//
+// The host loop of cf_getrf follows COnfLUX's outer loop (Alg. 1) on one
+// GPU: per step t of width v, TournPivot on the current panel (LU-1), the row
+// interchanges (LU-2; the paper masks rows instead because its matrix is
+// replicated over c layers -- a single copy swaps in O(vN) per step), the LU
+// of the selected rows A00, the two triangular solves (LU-3, LU-4) and the
+// Schur update of A11 (LU-5).  The paper's scatters and reductions between
+// ranks (steps 1, 3-6, 8, 10) have no counterpart on one device.
+#include <atomic>
+#include <cstring>
+
+#include "cf_common.cuh"
+#include "cf_kernels.cuh"
+
+namespace cf {
+
+static std::atomic<int> g_last_cuda_error{0};
+void set_cuda_error(cudaError_t e) { g_last_cuda_error.store((int)e); }
+
+int launch_trsm_left_f64(bool lower, bool unit, bool trans, double *X, int ldx, int w, int cols, const double *Tm,
+                         int ldt, cudaStream_t st);
+int launch_gemm_f64_sub_t(int m, int n, int k, const double *A, int lda, bool trans_a, const double *B, int ldb,
+                          bool trans_b, double *C, int ldc, bool lower, const int *skip, cudaStream_t st);
+
+int resolve_options(const cf_options *in, Opts *o) {
+    *o = Opts();
+    if (in == nullptr) return CF_OK;
+    if (in->v != 0) o->v = in->v;
+    if (in->leaf_h != 0) o->leaf_h = in->leaf_h;
+    if (in->arity != 0) o->arity = in->arity;
+    o->outer_V = in->outer_V;
+    o->lookahead = in->lookahead;
+    if (in->tol > 0) o->tol = in->tol;
+    if (in->max_iter > 0) o->max_iter = in->max_iter;
+    if (in->gmres_restart > 0) o->gmres_restart = in->gmres_restart;
+    if (o->v < 1 || o->v > kMaxV) return CF_ERR_UNSUPPORTED;
+    if (o->leaf_h < 1 || o->leaf_h > kMaxV) return CF_ERR_UNSUPPORTED;
+    if (o->arity < 2 || o->arity > 4) return CF_ERR_UNSUPPORTED;
+    if (o->outer_V < 0 || (o->outer_V % o->v) != 0) return CF_ERR_UNSUPPORTED;
+    return CF_OK;
+}
+
+// ipiv (1-based interchanges) -> row order: perm[i] = original row now at i.
+__global__ void k_ipiv_to_perm(int n, const int *ipiv, int *perm) {
+    extern __shared__ int sp[];
+    const bool use_smem = (size_t)n * sizeof(int) <= 200 * 1024;
+    int *p = use_smem ? sp : perm;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n; ++i) {
+            const int j = ipiv[i] - 1;
+            if (j != i) { const int t = p[i]; p[i] = p[j]; p[j] = t; }
+        }
+    }
+    __syncthreads();
+    if (use_smem)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = p[i];
+}
+
+// Out[i, c] = In[perm[i], c]
+__global__ void k_gather_rows(int n, int nrhs, const int *perm, const double *In, int ldi, double *Out, int ldo) {
+    const size_t tot = (size_t)n * nrhs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), c = (int)(e / n);
+        Out[(size_t)i + (size_t)c * ldo] = In[(size_t)perm[i] + (size_t)c * ldi];
+    }
+}
+
+}  // namespace cf
+
+using namespace cf;
+
+extern "C" void cf_default_options(cf_options *opt) {
+    if (opt == nullptr) return;
+    Opts o;
+    opt->v = o.v;
+    opt->leaf_h = o.leaf_h;
+    opt->arity = o.arity;
+    opt->outer_V = o.outer_V;
+    opt->lookahead = o.lookahead;
+    opt->tol = o.tol;
+    opt->max_iter = o.max_iter;
+    opt->gmres_restart = o.gmres_restart;
+}
+
+extern "C" const char *cf_status_string(int s) {
+    switch (s) {
+        case CF_OK: return "ok";
+        case CF_ERR_CUDA: return "CUDA error";
+        case CF_ERR_WORKSPACE: return "workspace too small";
+        case CF_ERR_NOT_CONVERGED: return "refinement did not reach the tolerance";
+        case CF_ERR_TIMEOUT: return "bounded device wait timed out";
+        case CF_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return s < 0 ? "invalid argument" : "unknown status";
+    }
+}
+
+extern "C" int cf_last_cuda_error(void) { return g_last_cuda_error.load(); }
+
+// ------------------------------------------------------------------- getrf
+extern "C" size_t cf_getrf_workspace_size(int n, const cf_options *opt) {
+    Opts o;
+    if (resolve_options(opt, &o) != CF_OK) return 0;
+    return tourn_ws_bytes(n > 0 ? n : 1, o.leaf_h, o.arity);
+}
+
+extern "C" int cf_getrf(int n, double *A, int lda, int *ipiv, int *info, void *work, size_t lwork,
+                        const cf_options *opt, cudaStream_t st) {
+    if (n < 0) return -1;
+    if (n > 0 && A == nullptr) return -2;
+    if (lda < (n > 1 ? n : 1)) return -3;
+    if (n > 0 && ipiv == nullptr) return -4;
+    if (info == nullptr) return -5;
+    Opts o;
+    int rc = resolve_options(opt, &o);
+    if (rc != CF_OK) return rc;
+    CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
+    if (n == 0) return CF_OK;
+    if (work == nullptr || lwork < cf_getrf_workspace_size(n, opt)) return CF_ERR_WORKSPACE;
+    TournWS ws{};
+    TournEpilogue ep{};
+    rc = tourn_ws_carve(work, n, o.leaf_h, o.arity, &ws, &ep);
+    if (rc != CF_OK) return rc;
+    CF_CUDA_TRY(cudaMemsetAsync(ws.counter, 0, ws.counter_bytes, st));
+    const size_t ld = (size_t)lda;
+    for (int k0 = 0; k0 < n; k0 += o.v) {
+        const int w = o.v < n - k0 ? o.v : n - k0;
+        const int m = n - k0;
+        double *A00 = A + k0 + k0 * ld;
+        ep.ipiv = ipiv;
+        ep.k0 = k0;
+        // LU-1 TournPivot on A[k0:n, k0:k0+w]
+        if ((rc = launch_tourn<double>(A00, lda, m, w, o.leaf_h, o.arity, ws, ep, st))) return rc;
+        // LU-2 interchanges on all n columns
+        if ((rc = launch_apply_swaps<double>(A, lda, n, k0, ep, nullptr, st))) return rc;
+        // A00 = L00 U00 (no further pivoting)
+        if ((rc = launch_getf2_nopiv<double>(A00, lda, w, k0, info, st))) return rc;
+        // LU-3 A10 <- A10 U00^{-1}
+        if ((rc = launch_trsm_right_upper<double>(A00 + w, lda, m - w, w, A00, lda, false, nullptr, st))) return rc;
+        // LU-4 A01 <- L00^{-1} A01
+        if ((rc = launch_trsm_left_lower_unit<double>(A00 + w * ld, lda, w, n - k0 - w, A00, lda, st))) return rc;
+        // LU-5 A11 <- A11 - A10 A01
+        if ((rc = launch_gemm_f64_sub(m - w, n - k0 - w, w, A00 + w, lda, A00 + w * ld, lda, false,
+                                      A00 + w + w * ld, lda, false, nullptr, st)))
+            return rc;
+    }
+    return CF_OK;
+}
+
+// ------------------------------------------------------------------- potrf
+extern "C" size_t cf_potrf_workspace_size(int n, const cf_options *opt) {
+    (void)n;
+    (void)opt;
+    return 0;
+}
+
+extern "C" int cf_potrf(int n, double *A, int lda, int *info, void *work, size_t lwork, const cf_options *opt,
+                        cudaStream_t st) {
+    (void)work;
+    (void)lwork;
+    if (n < 0) return -1;
+    if (n > 0 && A == nullptr) return -2;
+    if (lda < (n > 1 ? n : 1)) return -3;
+    if (info == nullptr) return -4;
+    Opts o;
+    int rc = resolve_options(opt, &o);
+    if (rc != CF_OK) return rc;
+    CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
+    const size_t ld = (size_t)lda;
+    for (int k0 = 0; k0 < n; k0 += o.v) {
+        const int w = o.v < n - k0 ? o.v : n - k0;
+        const int m = n - k0;
+        double *A00 = A + k0 + k0 * ld;
+        // CH-1 L00 = chol(A00)
+        if ((rc = launch_potf2<double>(A00, lda, w, k0, info, st))) return rc;
+        // CH-2 L10 <- A10 L00^{-T}
+        if ((rc = launch_trsm_right_upper<double>(A00 + w, lda, m - w, w, A00, lda, true, info, st))) return rc;
+        // CH-3 A11 <- A11 - L10 L10^T (lower)
+        if ((rc = launch_gemm_f64_sub(m - w, m - w, w, A00 + w, lda, A00 + w, lda, true, A00 + w + w * ld, lda,
+                                      true, info, st)))
+            return rc;
+    }
+    return CF_OK;
+}
+
+// ------------------------------------------------------------------- solves
+extern "C" size_t cf_getrs_workspace_size(int n, int nrhs) {
+    Carver cv(nullptr);
+    cv.take<int>(n > 0 ? n : 1);
+    cv.take<double>((size_t)(n > 0 ? n : 1) * (nrhs > 0 ? nrhs : 1));
+    return cv.size();
+}
+
+extern "C" int cf_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, double *B, int ldb, void *work,
+                        size_t lwork, cudaStream_t st) {
+    if (n < 0) return -1;
+    if (nrhs < 0) return -2;
+    if (n > 0 && LU == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (n > 0 && ipiv == nullptr) return -5;
+    if (n > 0 && nrhs > 0 && B == nullptr) return -6;
+    if (ldb < (n > 1 ? n : 1)) return -7;
+    if (n == 0 || nrhs == 0) return CF_OK;
+    if (work == nullptr || lwork < cf_getrs_workspace_size(n, nrhs)) return CF_ERR_WORKSPACE;
+    Carver cv(work);
+    int *perm = cv.take<int>(n);
+    double *T = cv.take<double>((size_t)n * nrhs);
+    const size_t smem = (size_t)n * sizeof(int) <= 200 * 1024 ? (size_t)n * sizeof(int) : 0;
+    if (smem > 48 * 1024) CF_CUDA_TRY(cudaFuncSetAttribute(k_ipiv_to_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_ipiv_to_perm<<<1, 1024, smem, st>>>(n, ipiv, perm);
+    CF_LAUNCH_CHECK();
+    k_gather_rows<<<1024, 256, 0, st>>>(n, nrhs, perm, B, ldb, T, n);
+    CF_LAUNCH_CHECK();
+    int rc;
+    const size_t ld = (size_t)lda;
+    const int v = kMaxV;
+    for (int k0 = 0; k0 < n; k0 += v) {                 // L y = P b
+        const int w = v < n - k0 ? v : n - k0;
+        if ((rc = launch_trsm_left_f64(true, true, false, T + k0, n, w, nrhs, LU + k0 + k0 * ld, lda, st))) return rc;
+        if ((rc = launch_gemm_f64_sub_t(n - k0 - w, nrhs, w, LU + (k0 + w) + k0 * ld, lda, false, T + k0, n, false,
+                                        T + k0 + w, n, false, nullptr, st)))
+            return rc;
+    }
+    const int nb = (n + v - 1) / v;
+    for (int b = nb - 1; b >= 0; --b) {                 // U x = y
+        const int k0 = b * v;
+        const int w = v < n - k0 ? v : n - k0;
+        if ((rc = launch_trsm_left_f64(false, false, false, T + k0, n, w, nrhs, LU + k0 + k0 * ld, lda, st))) return rc;
+        if ((rc = launch_gemm_f64_sub_t(k0, nrhs, w, LU + k0 * ld, lda, false, T + k0, n, false, T, n, false, nullptr,
+                                        st)))
+            return rc;
+    }
+    CF_CUDA_TRY(cudaMemcpy2DAsync(B, sizeof(double) * ldb, T, sizeof(double) * n, sizeof(double) * n, nrhs,
+                                  cudaMemcpyDeviceToDevice, st));
+    return CF_OK;
+}
+
+extern "C" int cf_potrs(int n, int nrhs, const double *L, int lda, double *B, int ldb, cudaStream_t st) {
+    if (n < 0) return -1;
+    if (nrhs < 0) return -2;
+    if (n > 0 && L == nullptr) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (n > 0 && nrhs > 0 && B == nullptr) return -5;
+    if (ldb < (n > 1 ? n : 1)) return -6;
+    if (n == 0 || nrhs == 0) return CF_OK;
+    int rc;
+    const size_t ld = (size_t)lda, lb = (size_t)ldb;
+    const int v = kMaxV;
+    for (int k0 = 0; k0 < n; k0 += v) {                 // L y = b
+        const int w = v < n - k0 ? v : n - k0;
+        if ((rc = launch_trsm_left_f64(true, false, false, B + k0, ldb, w, nrhs, L + k0 + k0 * ld, lda, st))) return rc;
+        if ((rc = launch_gemm_f64_sub_t(n - k0 - w, nrhs, w, L + (k0 + w) + k0 * ld, lda, false, B + k0, ldb, false,
+                                        B + k0 + w, ldb, false, nullptr, st)))
+            return rc;
+    }
+    const int nb = (n + v - 1) / v;
+    for (int b = nb - 1; b >= 0; --b) {                 // L^T x = y
+        const int k0 = b * v;
+        const int w = v < n - k0 ? v : n - k0;
+        if ((rc = launch_trsm_left_f64(false, false, true, B + k0, ldb, w, nrhs, L + k0 + k0 * ld, lda, st))) return rc;
+        // B[0:k0] -= (L[k0:k0+w, 0:k0])^T B[k0:k0+w]
+        if ((rc = launch_gemm_f64_sub_t(k0, nrhs, w, L + k0, lda, true, B + k0, ldb, false, B, ldb, false, nullptr,
+                                        st)))
+            return rc;
+    }
+    (void)lb;
+    return CF_OK;
+}
+
+extern "C" int cf_residual(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
+                           const double *B, int ldb, double *R, int ldr, cudaStream_t st) {
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (m > 0 && n > 0 && A == nullptr) return -4;
+    if (lda < (m > 1 ? m : 1)) return -5;
+    if (n > 0 && nrhs > 0 && X == nullptr) return -6;
+    if (ldx < (n > 1 ? n : 1)) return -7;
+    if (m > 0 && nrhs > 0 && B == nullptr) return -8;
+    if (ldb < (m > 1 ? m : 1)) return -9;
+    if (m > 0 && nrhs > 0 && R == nullptr) return -10;
+    if (ldr < (m > 1 ? m : 1)) return -11;
+    return launch_residual_f64(m, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, st);
+}

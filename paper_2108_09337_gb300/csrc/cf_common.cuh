@@ -1,0 +1,68 @@
+// cf_common.cuh -- shared definitions of the libcf CUDA sources (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/cf.h"
+
+namespace cf {
+
+// Largest block size / leaf height / candidates per tree node handled by the
+// shared-memory tournament tiles.
+constexpr int kMaxV = 128;
+
+// Records the last CUDA error seen by the library (cf_last_cuda_error()).
+void set_cuda_error(cudaError_t e);
+
+#define CF_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t cf_e_ = (expr);                         \
+        if (cf_e_ != cudaSuccess) {                         \
+            ::cf::set_cuda_error(cf_e_);                    \
+            return CF_ERR_CUDA;                             \
+        }                                                   \
+    } while (0)
+
+#define CF_LAUNCH_CHECK() CF_CUDA_TRY(cudaGetLastError())
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves aligned sub-buffers out of a caller-provided workspace; with a null
+// base it only measures.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base((char *)b) {}
+    template <typename T>
+    T *take(size_t count, size_t align = 256) {
+        off = align_up(off, align);
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+    size_t size() const { return align_up(off, 256); }
+};
+
+// Options with defaults filled in and ranges checked.
+struct Opts {
+    int v = 128, leaf_h = 128, arity = 2, outer_V = 0, lookahead = 1;
+    double tol = 1e-14;
+    int max_iter = 30, gmres_restart = 30;
+};
+// Returns 0 or a negative status for an out-of-range field.
+int resolve_options(const cf_options *in, Opts *out);
+
+// Exactly rounded product and difference (no FMA contraction), so that the
+// tournament, the diagonal-block factorization and the panel solves round
+// exactly like the FP64 oracle.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+
+}  // namespace cf

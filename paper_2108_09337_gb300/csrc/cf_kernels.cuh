@@ -1,0 +1,75 @@
+// cf_kernels.cuh -- launchers shared between the libcf translation units.
+#pragma once
+
+#include "cf_common.cuh"
+
+namespace cf {
+
+constexpr int kMaxLevels = 32;
+
+// Shape of one tournament: levels of the reduction tree.
+struct TournPlan {
+    int m, w, h, arity;
+    int nleaves;
+    int nlevels;              // including the leaf level
+    int cnt[kMaxLevels];      // nodes per level
+    int off[kMaxLevels];      // first node index of each level
+    int total_nodes;
+};
+
+// Device scratch of a tournament.
+struct TournWS {
+    int *node_win;            // [total_nodes][kMaxV] panel rows chosen by each node
+    int *node_cnt;            // [total_nodes]
+    int *counter;             // [total_nodes] arrivals; zero before and after
+    int *root_win;            // [kMaxV] winners in pivot order
+    size_t counter_bytes;
+};
+
+// Root-node outputs used by the LU driver (ipiv == nullptr: none).
+struct TournEpilogue {
+    int *ipiv;
+    int k0;
+    int *swap_cnt;            // [1] number of moved rows
+    int *swap_dst;            // [2*kMaxV] destination positions (relative to k0)
+    int *swap_src;            // [2*kMaxV] source positions (relative to k0)
+};
+
+int make_tourn_plan(int m, int w, int h, int arity, TournPlan *plan);
+size_t tourn_ws_bytes(int m, int h, int arity);
+int tourn_ws_carve(void *work, int m, int h, int arity, TournWS *ws, TournEpilogue *ep);
+
+template <typename T>
+int launch_tourn(const T *P, int ldp, int m, int w, int h, int arity, const TournWS &ws, const TournEpilogue &ep,
+                 cudaStream_t st);
+template <typename T>
+int launch_apply_swaps(T *A, int lda, int ncols, int k0, const TournEpilogue &ep, int *perm, cudaStream_t st);
+
+// ---- panel kernels (cf_panel.cu)
+// LU of the w x w diagonal block without pivoting (S1/S2 of Fig. "prog_rep").
+template <typename T>
+int launch_getf2_nopiv(T *A00, int lda, int w, int kglob, int *info, cudaStream_t st);
+// A10 <- A10 * U^{-1}: rows x w block X, U upper non-unit w x w (or, with
+// trans_lower, U = L^T for a lower L).  Optional low-precision copy of the
+// result, K-major: lp[(r) * ldlp + c].
+template <typename T>
+int launch_trsm_right_upper(T *X, int ldx, int rows, int w, const T *U, int ldu, bool trans_lower,
+                            const int *skip_if_nonzero, cudaStream_t st);
+// A01 <- L^{-1} * A01: w x cols block X, L unit lower w x w.
+template <typename T>
+int launch_trsm_left_lower_unit(T *X, int ldx, int w, int cols, const T *L, int ldl, cudaStream_t st);
+// Cholesky of the w x w diagonal block (lower), Listing "Cholesky".
+template <typename T>
+int launch_potf2(T *A00, int lda, int w, int kglob, int *info, cudaStream_t st);
+
+// ---- FP64 GEMM / SYRK (cf_gemm64.cu)
+// C -= A * op(B); op(B)(p, j) = trans_b ? B[j + p*ldb] : B[p + j*ldb].
+// lower: only entries with i >= j are touched.  skip_if_nonzero: device int
+// whose nonzero value turns the launch into a no-op (Cholesky breakdown).
+int launch_gemm_f64_sub(int m, int n, int k, const double *A, int lda, const double *B, int ldb, bool trans_b,
+                        double *C, int ldc, bool lower, const int *skip_if_nonzero, cudaStream_t st);
+// R = B - A X for a thin X (nrhs columns).
+int launch_residual_f64(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
+                        int ldb, double *R, int ldr, cudaStream_t st);
+
+}  // namespace cf

@@ -1,0 +1,70 @@
+"""CPU-only checks of the C-ABI library: it builds, loads, exports every
+function include/cf.h declares, and its host-side logic (options, status
+strings, workspace sizes, argument validation) behaves without a GPU.  No
+call here reaches a kernel."""
+import ctypes
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2108_09337_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def _header_functions():
+    import re
+    txt = open(os.path.join(ROOT, "include", "cf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cf_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_function(lib):
+    names = _header_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_default_options_and_status_strings(lib):
+    from paper_2108_09337_gb300 import cf
+    o = cf.options()
+    assert (o.v, o.leaf_h, o.arity, o.lookahead, o.max_iter) == (128, 128, 2, 1, 30)
+    assert o.tol == 1e-14
+    lib.cf_status_string.restype = ctypes.c_char_p
+    assert lib.cf_status_string(0) == b"ok"
+    assert b"workspace" in lib.cf_status_string(-101)
+    assert b"invalid" in lib.cf_status_string(-3)
+
+
+def test_workspace_sizes_are_host_only(lib):
+    from paper_2108_09337_gb300 import cf
+    L = cf.lib()
+    o = cf.options()
+    s1 = L.cf_getrf_workspace_size(2048, ctypes.byref(o))
+    s2 = L.cf_getrf_workspace_size(32768, ctypes.byref(o))
+    assert 0 < s1 < s2 < 64 << 20
+    assert L.cf_getrs_workspace_size(1000, 4) >= 1000 * 4 * 8 + 4000
+    bad = cf.options(v=200)
+    assert L.cf_getrf_workspace_size(100, ctypes.byref(bad)) == 0
+
+
+def test_argument_validation_returns_before_any_cuda_call(lib):
+    from paper_2108_09337_gb300 import cf
+    L = cf.lib()
+    null = ctypes.c_void_p(0)
+    # negative n -> -1 ; lda too small -> -3
+    assert L.cf_getrf(-1, null, 1, null, null, null, 0, None, null) == -1
+    assert L.cf_getrf(10, ctypes.c_void_p(16), 5, ctypes.c_void_p(16), ctypes.c_void_p(16), null, 0,
+                      None, null) == -3
+    assert L.cf_potrf(-2, null, 1, null, null, 0, None, null) == -1
+    assert L.cf_tourn_select(10, 200, ctypes.c_void_p(16), 10, 128, 2, null, null, 0, null) == -2
+    assert L.cf_tourn_select(10, 4, ctypes.c_void_p(16), 10, 0, 2, null, null, 0, null) == -5
+    assert L.cf_tourn_select(10, 4, ctypes.c_void_p(16), 10, 8, 7, null, null, 0, null) == -6
+    assert L.cf_residual(-1, 1, 1, null, 1, null, 1, null, 1, null, 1, null) == -1
+    assert L.cf_getrs(4, 1, ctypes.c_void_p(16), 2, null, null, 4, null, 0, null) == -4
