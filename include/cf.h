@@ -159,6 +159,11 @@ int cf_schur_update_lp(int m, int n, int k, const void *A_lp, int lda_k,
                        const void *B_lp, int ldb_k, float *C, int ldc,
                        cf_prec prec, int lower, cudaStream_t stream);
 
+/* Synchronises `stream` and returns, then clears, the status word of the
+ * library's bounded device-side waits: CF_OK, or CF_ERR_TIMEOUT if a wait in
+ * a tensor-core kernel ran out since the last call. */
+int cf_device_status(cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * Mixed-precision refined solves (north star; the paper cites GPU mixed
  * LU + refinement as related work, Sec. 11).  A and B are never modified.

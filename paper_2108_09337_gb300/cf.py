@@ -69,6 +69,7 @@ _SIG = {
     "cf_potrs": (_I, [_I, _I, _P, _I, _P, _I, _P]),
     "cf_residual": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P]),
     "cf_schur_update_lp": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
+    "cf_device_status": (_I, [_P]),
     "cf_gesv_mixed_workspace_size": (_S, [_I, _I, _I, _OPT]),
     "cf_gesv_mixed": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _P, ctypes.POINTER(RefineStats),
                            _P, _S, _OPT, _P]),
@@ -230,6 +231,11 @@ def schur_update_lp(A_lp: torch.Tensor, B_lp: torch.Tensor, C: torch.Tensor, low
                                                          B_lp.stride(0), _ptr(C), _ld(C, "C"), prec,
                                                          int(lower), _stream()))
     return C
+
+
+def device_status() -> int:
+    """Synchronises the current stream; CF_OK or CF_ERR_TIMEOUT (then cleared)."""
+    return _lib.cf_device_status(_stream())
 
 
 def _mixed(fn, wsfn, A, B, prec, opt_kw, work=None):

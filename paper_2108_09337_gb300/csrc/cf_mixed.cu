@@ -3,10 +3,6 @@
 #include "cf_common.cuh"
 #include "cf_kernels.cuh"
 
-extern "C" int cf_schur_update_lp(int, int, int, const void *, int, const void *, int, float *, int, cf_prec, int,
-                                  cudaStream_t) {
-    return CF_ERR_UNSUPPORTED;
-}
 extern "C" size_t cf_gesv_mixed_workspace_size(int, int, cf_prec, const cf_options *) { return 0; }
 extern "C" int cf_gesv_mixed(int, int, const double *, int, const double *, int, double *, int, cf_prec, int *,
                              cf_refine_stats *, void *, size_t, const cf_options *, cudaStream_t) {

@@ -1,0 +1,414 @@
+// cf_tc.cu -- LU-5 / CH-3 on the 5th-generation tensor cores:
+//     C[m x n] -= A[m x k] * B[n x k]^T     (FP32 C, column-major)
+// with A and B in BF16 or FP16, K-major (row i of A holds its k values
+// contiguously), FP32 accumulation in tensor memory.
+//
+// This is Alg. 1 step 11 ("Factorize A11", Table 2's local gemm) and, with
+// `lower`, COnfCHOX's triangular gemmt -- the dominant cost of both methods
+// (Sec. 7.5).  Design for sm_103a:
+//   * persistent CTAs, one per SM, walking 128 x 256 output tiles;
+//   * warp 0 issues TMA loads (128-byte swizzle) into a 4-stage ring of
+//     shared-memory stages, warp 1 (one elected lane) issues tcgen05.mma
+//     (kind::f16, M=128, N=256, K=16) into one of two TMEM accumulators,
+//     warps 2-5 drain the other accumulator with tcgen05.ld and apply
+//     C -= acc with coalesced column accesses, so the epilogue of tile i
+//     overlaps the MMAs of tile i+1;
+//   * every mbarrier wait is bounded; on expiry the kernel records
+//     CF_ERR_TIMEOUT in a device status word, drains its own copies and
+//     MMAs (again bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "cf_common.cuh"
+#include "cf_kernels.cuh"
+#include "cf_tc.cuh"
+
+namespace cf {
+
+__device__ int g_tc_status = 0;       // 0 or CF_ERR_TIMEOUT
+
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int UMMA_K = 16;
+constexpr int kThreads = 192;         // 6 warps
+constexpr uint32_t kStageA = BM * BK * 2;     // 16 KB
+constexpr uint32_t kStageB = BN * BK * 2;     // 32 KB
+constexpr uint32_t kStageBytes = kStageA + kStageB;
+constexpr uint32_t kTmemCols = 2 * BN;        // two accumulators
+constexpr long long kSpinLimit = 1ll << 22;   // bounded: ~0.5-4 s with backoff
+
+struct Smem {
+    uint64_t full[STAGES];
+    uint64_t empty[STAGES];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait.  Returns false if the kernel is aborting (another role gave
+// up) or the limit expired (then this role starts the abort).
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    for (long long i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (i > 64) __nanosleep(64);
+    }
+    *abort_flag = 1;
+    atomicExch(&g_tc_status, CF_ERR_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile whose rows are 128
+// bytes, written by TMA with the 128-byte swizzle; 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t make_sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                      // descriptor version (sm_100 family)
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = BF16 (1) or F16 (0),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(bool bf16, int M, int N) {
+    return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+#define TMEM_LD32(taddr, r)                                                                                   \
+    asm volatile(                                                                                             \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                    \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),     \
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), \
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),          \
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),          \
+          "=r"(r[30]), "=r"(r[31])                                                                            \
+        : "r"(taddr))
+
+struct Problem {
+    int m, n, k;
+    float *C;
+    int ldc;
+    int lower;
+    int tiles_m, tiles_n, ntiles;
+};
+
+// Tile t -> (bm, bn), M fastest so consecutive CTAs share a B tile in L2.
+__device__ __forceinline__ bool tile_coords(const Problem &p, int t, int &m0, int &n0) {
+    m0 = (t % p.tiles_m) * BM;
+    n0 = (t / p.tiles_m) * BN;
+    if (p.lower && n0 > m0 + BM - 1) return false;   // strictly above the diagonal
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Problem p,
+           uint32_t idesc) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *stageA = base;
+    uint8_t *stageB = base + STAGES * kStageA;
+    Smem &s = *reinterpret_cast<Smem *>(base + STAGES * kStageBytes);
+    volatile int *abort_flag = &s.abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkb = p.k / BK;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) { mbar_init(&s.full[i], 1); mbar_init(&s.empty[i], 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&s.acc_full[i], 1); mbar_init(&s.acc_empty[i], 4); }
+        mbar_init(&s.drain, 1);
+        s.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = s.tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+                int m0, n0;
+                if (!tile_coords(p, t, m0, n0)) continue;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int st = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!wait_bounded(&s.empty[st], ph ^ 1u, abort_flag)) { ok = false; break; }
+                    mbar_arrive_expect_tx(&s.full[st], kStageBytes);
+                    tma_load_2d(stageA + st * kStageA, &tmA, &s.full[st], kb * BK, m0);
+                    tma_load_2d(stageB + st * kStageB, &tmB, &s.full[st], kb * BK, n0);
+                }
+            }
+            if (!ok) {
+                // Drain: every issued stage's copy must land before the CTA exits.
+                for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j) {
+                    const int st = j % STAGES;
+                    const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
+                    for (long long i = 0; i < kSpinLimit && !mbar_try_wait(&s.full[st], ph); ++i) __nanosleep(64);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int it = 0, tcount = 0;
+            bool ok = true, issued = false;
+            for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+                int m0, n0;
+                if (!tile_coords(p, t, m0, n0)) continue;
+                const int b = tcount & 1;
+                const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
+                if (!wait_bounded(&s.acc_empty[b], aph ^ 1u, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int st = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!wait_bounded(&s.full[st], ph, abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t ad = make_sw128_desc(smem_u32(stageA + st * kStageA));
+                    const uint64_t bd = make_sw128_desc(smem_u32(stageB + st * kStageB));
+#pragma unroll
+                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                        // advance 16 elements = 32 bytes inside the swizzled row
+                        umma_f16(d_tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    issued = true;
+                    umma_commit(&s.empty[st]);
+                }
+                if (!ok) break;
+                umma_commit(&s.acc_full[b]);
+                ++tcount;
+            }
+            if (issued) {
+                // Let every MMA this CTA issued finish before TMEM is freed.
+                umma_commit(&s.drain);
+                for (long long i = 0; i < kSpinLimit && !mbar_try_wait(&s.drain, 0); ++i) __nanosleep(64);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..5)
+        const int quarter = warp & 3;                 // TMEM lanes 32*quarter ..
+        int tcount = 0;
+        for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+            int m0, n0;
+            if (!tile_coords(p, t, m0, n0)) continue;
+            const int b = tcount & 1;
+            const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
+            bool ok = true;
+            if (lane == 0) ok = wait_bounded(&s.acc_full[b], aph, abort_flag);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            tc_fence_after();
+            const int row = m0 + quarter * 32 + lane;
+            const bool row_ok = row < p.m;
+            float *crow = p.C + row;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                const int colbase = n0 + c0;
+                float cv[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = colbase + j;
+                    const bool ok2 = row_ok && col < p.n && (!p.lower || row >= col);
+                    cv[j] = ok2 ? crow[(size_t)col * p.ldc] : 0.f;
+                }
+                uint32_t r[32];
+                const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0);
+                TMEM_LD32(taddr, r);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = colbase + j;
+                    const bool ok2 = row_ok && col < p.n && (!p.lower || row >= col);
+                    if (ok2) crow[(size_t)col * p.ldc] = cv[j] - __uint_as_float(r[j]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s.acc_empty[b]);
+            ++tcount;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static int get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_encode ? CF_OK : CF_ERR_CUDA;
+}
+
+// 2-D K-major operand: rows x k elements of 2 bytes, row pitch ld elements.
+static int make_operand_map(CUtensorMap *map, const void *ptr, int rows, int k, int ld, int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? CF_OK : CF_ERR_CUDA;
+}
+
+static int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+int launch_schur_tc(int m, int n, int k, const void *A, int lda_k, const void *B, int ldb_k, float *C, int ldc,
+                    bool bf16, bool lower, cudaStream_t st, int max_ctas) {
+    if (m <= 0 || n <= 0 || k <= 0) return CF_OK;
+    if (k % tc::BK != 0 || lda_k % 8 != 0 || ldb_k % 8 != 0 || lda_k < k || ldb_k < k) return CF_ERR_UNSUPPORTED;
+    if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return CF_ERR_UNSUPPORTED;
+    int rc = get_encoder();
+    if (rc) return rc;
+    CUtensorMap ta, tb;
+    if ((rc = make_operand_map(&ta, A, m, k, lda_k, tc::BM))) return rc;
+    if ((rc = make_operand_map(&tb, B, n, k, ldb_k, tc::BN))) return rc;
+    tc::Problem p;
+    p.m = m; p.n = n; p.k = k; p.C = C; p.ldc = ldc; p.lower = lower ? 1 : 0;
+    p.tiles_m = ceil_div(m, tc::BM);
+    p.tiles_n = ceil_div(n, tc::BN);
+    p.ntiles = p.tiles_m * p.tiles_n;
+    const size_t smem = 1024 + tc::STAGES * tc::kStageBytes + sizeof(tc::Smem);
+    CF_CUDA_TRY(cudaFuncSetAttribute(tc::k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = num_sms();
+    if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+    if (grid > p.ntiles) grid = p.ntiles;
+    tc::k_schur_tc<<<grid, tc::kThreads, smem, st>>>(ta, tb, p, tc::make_idesc(bf16, tc::BM, tc::BN));
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+int tc_take_status(cudaStream_t st, int *status) {
+    int h = 0;
+    CF_CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    CF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h != 0) {
+        const int zero = 0;
+        CF_CUDA_TRY(cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+        CF_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    *status = h;
+    return CF_OK;
+}
+
+}  // namespace cf
+
+extern "C" int cf_schur_update_lp(int m, int n, int k, const void *A_lp, int lda_k, const void *B_lp, int ldb_k,
+                                  float *C, int ldc, cf_prec prec, int lower, cudaStream_t stream) {
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (k < 0 || k % 64 != 0) return -3;
+    if (m > 0 && k > 0 && A_lp == nullptr) return -4;
+    if (lda_k < k || lda_k % 8 != 0) return -5;
+    if (n > 0 && k > 0 && B_lp == nullptr) return -6;
+    if (ldb_k < k || ldb_k % 8 != 0) return -7;
+    if (m > 0 && n > 0 && C == nullptr) return -8;
+    if (ldc < (m > 1 ? m : 1)) return -9;
+    if (prec != CF_BF16 && prec != CF_F16) return -10;
+    return cf::launch_schur_tc(m, n, k, A_lp, lda_k, B_lp, ldb_k, C, ldc, prec == CF_BF16, lower != 0, stream, 0);
+}
+
+extern "C" int cf_device_status(cudaStream_t stream) {
+    int s = 0;
+    int rc = cf::tc_take_status(stream, &s);
+    if (rc != CF_OK) return rc;
+    return s;
+}

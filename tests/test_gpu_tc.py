@@ -1,0 +1,68 @@
+"""GPU checks of the tensor-core Schur update C -= A B^T (tcgen05, TMA,
+TMEM) through cf_schur_update_lp.
+
+Reference: the same BF16/FP16 operands widened to FP64 on the host, C - A B^T
+in FP64 (a plain definition of the operation).  Bound per entry: the FP32
+accumulation of k products and the final FP32 subtraction,
+|err| <= 2 (k + 2) 2^-24 (|A| |B|^T + |C|).
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cf():
+    assert torch.cuda.is_available()
+    from paper_2108_09337_gb300 import cf as _cf
+    return _cf
+
+
+def _run(cf, m, n, k, dtype, lower=False, ldc_pad=0, seed=0):
+    g = torch.Generator().manual_seed(seed)
+    A = torch.randn((m, k), generator=g).to(dtype)
+    B = torch.randn((n, k), generator=g).to(dtype)
+    C = torch.randn((m, n), generator=g, dtype=torch.float32)
+    dC = torch.zeros((n, m + ldc_pad), dtype=torch.float32)
+    dC[:, :m] = C.t()
+    dC = dC.cuda().t()[:m, :]
+    cf.schur_update_lp(A.cuda(), B.cuda(), dC, lower=lower)
+    assert cf.device_status() == 0
+    got = dC.cpu().double().numpy()
+    Ad, Bd, Cd = A.double().numpy(), B.double().numpy(), C.double().numpy()
+    ref = Cd - Ad @ Bd.T
+    bound = 2 * (k + 2) * 2.0 ** -24 * (np.abs(Ad) @ np.abs(Bd).T + np.abs(Cd))
+    if lower:
+        il = np.tril(np.ones((m, n), dtype=bool))
+        assert np.all(np.abs(got - ref)[il] <= bound[il])
+        assert np.array_equal(got[~il], Cd[~il])      # upper part untouched
+    else:
+        assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 256, 64), (128, 256, 128), (256, 512, 64), (300, 500, 192),
+                                   (1, 1, 64), (129, 257, 64), (1000, 700, 1024), (4096, 4096, 128)])
+def test_schur_update_bf16(cf, m, n, k):
+    _run(cf, m, n, k, torch.bfloat16, seed=m + n + k)
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 256, 64), (333, 777, 256)])
+def test_schur_update_fp16(cf, m, n, k):
+    _run(cf, m, n, k, torch.float16, seed=k)
+
+
+@pytest.mark.parametrize("m,k", [(128, 64), (600, 128), (1000, 256)])
+def test_schur_update_lower(cf, m, k):
+    _run(cf, m, m, k, torch.bfloat16, lower=True, seed=m)
+
+
+def test_schur_update_ldc(cf):
+    _run(cf, 200, 300, 128, torch.bfloat16, ldc_pad=40)
+
+
+def test_schur_update_many_tiles_persistent(cf):
+    """More tiles than SMs: every CTA walks several tiles and reuses both
+    TMEM accumulators."""
+    _run(cf, 2048, 8192, 128, torch.bfloat16, seed=5)
