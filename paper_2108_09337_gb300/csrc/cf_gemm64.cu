@@ -1,4 +1,5 @@
-// cf_gemm64.cu -- FP64 Schur-complement update and FP64 residual.
+// cf_gemm64.cu -- SIMT Schur-complement update (FP64; FP32 for the solves of
+// the mixed path) and the FP64 residual.
 //
 //   LU-5 (FP64 path)  A11 <- A11 - A10 A01      (Alg. 1 step 11; Table 2 gemm)
 //   CH-3 (FP64 path)  A11 <- A11 - L10 L10^T    (Table 2 gemmt, lower only)
@@ -21,23 +22,23 @@ constexpr int kGemmThreads = 256;
 // C[m x n] -= op(A)[m x k] * op(B)[k x n]
 //   op(A)(i, p) = TA ? A[p + i*lda] : A[i + p*lda]
 //   op(B)(p, j) = TB ? B[j + p*ldb] : B[p + j*ldb]
-template <bool TA, bool TB, bool LOWER>
+template <typename T, bool TA, bool TB, bool LOWER>
 __global__ void __launch_bounds__(kGemmThreads)
-k_gemm_f64_sub(int m, int n, int k, const double *__restrict__ A, int lda, const double *__restrict__ B, int ldb,
-               double *__restrict__ C, int ldc, const int *skip) {
+k_gemm_sub(int m, int n, int k, const T *__restrict__ A, int lda, const T *__restrict__ B, int ldb,
+           T *__restrict__ C, int ldc, const int *skip) {
     if (skip != nullptr && *skip != 0) return;
     const int bm = blockIdx.x * kBM, bn = blockIdx.y * kBN;
     if (LOWER && bn > bm + kBM - 1) return;      // tile strictly above the diagonal
-    __shared__ __align__(16) double As[kBK][kBM + 2];
-    __shared__ __align__(16) double Bs[kBK][kBN + 2];
+    __shared__ __align__(16) T As[kBK][kBM + 2];
+    __shared__ __align__(16) T Bs[kBK][kBN + 2];
     const int tid = threadIdx.x;
     const int tm = (tid & 15) * 4;               // 4 rows
     const int tn = (tid >> 4) * 4;               // 4 columns
-    double acc[4][4];
+    T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
     for (int p0 = 0; p0 < k; p0 += kBK) {
 #pragma unroll
@@ -46,7 +47,7 @@ k_gemm_f64_sub(int m, int n, int k, const double *__restrict__ A, int lda, const
             int i, p;
             if (!TA) { i = idx % kBM; p = idx / kBM; } else { p = idx % kBK; i = idx / kBK; }
             const int gi = bm + i, gp = p0 + p;
-            double v = 0.0;
+            T v = T(0);
             if (gi < m && gp < k) v = TA ? A[(size_t)gp + (size_t)gi * lda] : A[(size_t)gi + (size_t)gp * lda];
             As[p][i] = v;
         }
@@ -56,14 +57,14 @@ k_gemm_f64_sub(int m, int n, int k, const double *__restrict__ A, int lda, const
             int j, p;
             if (!TB) { p = idx % kBK; j = idx / kBK; } else { j = idx % kBN; p = idx / kBN; }
             const int gj = bn + j, gp = p0 + p;
-            double v = 0.0;
+            T v = T(0);
             if (gj < n && gp < k) v = TB ? B[(size_t)gj + (size_t)gp * ldb] : B[(size_t)gp + (size_t)gj * ldb];
             Bs[p][j] = v;
         }
         __syncthreads();
 #pragma unroll
         for (int p = 0; p < kBK; ++p) {
-            double a[4], b[4];
+            T a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[p][tm + i];
 #pragma unroll
@@ -84,22 +85,23 @@ k_gemm_f64_sub(int m, int n, int k, const double *__restrict__ A, int lda, const
             const int gi = bm + tm + i;
             if (gi >= m) continue;
             if (LOWER && gi < gj) continue;
-            double *c = C + (size_t)gi + (size_t)gj * ldc;
+            T *c = C + (size_t)gi + (size_t)gj * ldc;
             *c = *c - acc[i][j];
         }
     }
 }
 
-int launch_gemm_f64_sub_t(int m, int n, int k, const double *A, int lda, bool trans_a, const double *B, int ldb,
-                          bool trans_b, double *C, int ldc, bool lower, const int *skip, cudaStream_t st) {
+template <typename T>
+int launch_gemm_sub_t(int m, int n, int k, const T *A, int lda, bool trans_a, const T *B, int ldb, bool trans_b,
+                      T *C, int ldc, bool lower, const int *skip, cudaStream_t st) {
     if (m <= 0 || n <= 0 || k <= 0) return CF_OK;
     dim3 grid(ceil_div(m, kBM), ceil_div(n, kBN));
     if (grid.y > 65535) return CF_ERR_UNSUPPORTED;
-#define CF_GEMM_CASE(TA, TB, LO)                                                                         \
-    if (trans_a == TA && trans_b == TB && lower == LO) {                                                 \
-        k_gemm_f64_sub<TA, TB, LO><<<grid, kGemmThreads, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, skip); \
-        CF_LAUNCH_CHECK();                                                                               \
-        return CF_OK;                                                                                    \
+#define CF_GEMM_CASE(TA, TB, LO)                                                                            \
+    if (trans_a == TA && trans_b == TB && lower == LO) {                                                    \
+        k_gemm_sub<T, TA, TB, LO><<<grid, kGemmThreads, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, skip);   \
+        CF_LAUNCH_CHECK();                                                                                  \
+        return CF_OK;                                                                                       \
     }
     CF_GEMM_CASE(false, false, false)
     CF_GEMM_CASE(false, true, true)
@@ -107,6 +109,15 @@ int launch_gemm_f64_sub_t(int m, int n, int k, const double *A, int lda, bool tr
     CF_GEMM_CASE(true, false, false)
 #undef CF_GEMM_CASE
     return CF_ERR_UNSUPPORTED;
+}
+template int launch_gemm_sub_t<double>(int, int, int, const double *, int, bool, const double *, int, bool, double *,
+                                       int, bool, const int *, cudaStream_t);
+template int launch_gemm_sub_t<float>(int, int, int, const float *, int, bool, const float *, int, bool, float *, int,
+                                      bool, const int *, cudaStream_t);
+
+int launch_gemm_f64_sub_t(int m, int n, int k, const double *A, int lda, bool trans_a, const double *B, int ldb,
+                          bool trans_b, double *C, int ldc, bool lower, const int *skip, cudaStream_t st) {
+    return launch_gemm_sub_t<double>(m, n, k, A, lda, trans_a, B, ldb, trans_b, C, ldc, lower, skip, st);
 }
 
 int launch_gemm_f64_sub(int m, int n, int k, const double *A, int lda, const double *B, int ldb, bool trans_b,

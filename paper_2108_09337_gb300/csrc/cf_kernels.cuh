@@ -68,6 +68,14 @@ int launch_potf2(T *A00, int lda, int w, int kglob, int *info, cudaStream_t st);
 // whose nonzero value turns the launch into a no-op (Cholesky breakdown).
 int launch_gemm_f64_sub(int m, int n, int k, const double *A, int lda, const double *B, int ldb, bool trans_b,
                         double *C, int ldc, bool lower, const int *skip_if_nonzero, cudaStream_t st);
+// Generic SIMT form: C -= op(A) op(B) for T = double or float.
+template <typename T>
+int launch_gemm_sub_t(int m, int n, int k, const T *A, int lda, bool trans_a, const T *B, int ldb, bool trans_b,
+                      T *C, int ldc, bool lower, const int *skip, cudaStream_t st);
+// Left triangular solve X <- M^{-1} X (w <= 128) for the solves.
+template <typename T>
+int launch_trsm_left(bool lower, bool unit, bool trans, T *X, int ldx, int w, int cols, const T *Tm, int ldt,
+                     cudaStream_t st);
 // R = B - A X for a thin X (nrhs columns).
 int launch_residual_f64(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
                         int ldb, double *R, int ldr, cudaStream_t st);

@@ -266,13 +266,21 @@ int launch_trsm_left_lower_unit(T *X, int ldx, int w, int cols, const T *L, int 
     return launch_trsm_left_t<T, true, true, false>(X, ldx, w, cols, L, ldl, st);
 }
 
+template <typename T>
+int launch_trsm_left(bool lower, bool unit, bool trans, T *X, int ldx, int w, int cols, const T *Tm, int ldt,
+                     cudaStream_t st) {
+    if (lower && unit && !trans) return launch_trsm_left_t<T, true, true, false>(X, ldx, w, cols, Tm, ldt, st);
+    if (lower && !unit && !trans) return launch_trsm_left_t<T, true, false, false>(X, ldx, w, cols, Tm, ldt, st);
+    if (!lower && !unit && !trans) return launch_trsm_left_t<T, false, false, false>(X, ldx, w, cols, Tm, ldt, st);
+    if (!lower && !unit && trans) return launch_trsm_left_t<T, false, false, true>(X, ldx, w, cols, Tm, ldt, st);
+    return CF_ERR_UNSUPPORTED;
+}
+template int launch_trsm_left<double>(bool, bool, bool, double *, int, int, int, const double *, int, cudaStream_t);
+template int launch_trsm_left<float>(bool, bool, bool, float *, int, int, int, const float *, int, cudaStream_t);
+
 int launch_trsm_left_f64(bool lower, bool unit, bool trans, double *X, int ldx, int w, int cols, const double *Tm,
                          int ldt, cudaStream_t st) {
-    if (lower && unit && !trans) return launch_trsm_left_t<double, true, true, false>(X, ldx, w, cols, Tm, ldt, st);
-    if (lower && !unit && !trans) return launch_trsm_left_t<double, true, false, false>(X, ldx, w, cols, Tm, ldt, st);
-    if (!lower && !unit && !trans) return launch_trsm_left_t<double, false, false, false>(X, ldx, w, cols, Tm, ldt, st);
-    if (!lower && !unit && trans) return launch_trsm_left_t<double, false, false, true>(X, ldx, w, cols, Tm, ldt, st);
-    return CF_ERR_UNSUPPORTED;
+    return launch_trsm_left<double>(lower, unit, trans, X, ldx, w, cols, Tm, ldt, st);
 }
 
 template int launch_getf2_nopiv<double>(double *, int, int, int, int *, cudaStream_t);

@@ -1,0 +1,87 @@
+"""GPU checks of the mixed-precision refined solves through the C ABI
+(cf_gesv_mixed, cf_posv_mixed): BF16 / FP16 tensor-core Schur updates on FP32
+working storage, FP64 refinement.
+
+Bar (the benchmark spec): backward error eta = max_j ||b_j - A x_j||_inf /
+(||A||_inf ||x_j||_inf + ||b_j||_inf) <= 1e-14, computed here on the host by
+the oracle's compensated residual from the returned x; the forward error
+against the oracle's FP64 solution is bounded by kappa_inf(A) * eta * 4.
+A and B must come back unchanged.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2108_09337_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cf():
+    assert torch.cuda.is_available()
+    from paper_2108_09337_gb300 import cf as _cf
+    return _cf
+
+
+def _dev(A):
+    return torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+
+
+def _check_solution(A, B, X, eta_tol=1e-14):
+    eta = oracle.backward_error(A, X, B).max()
+    assert eta <= eta_tol, eta
+    Xs = np.linalg.solve(A, B)
+    kappa = np.linalg.cond(A, np.inf)
+    fwd = np.abs(X - Xs).max() / np.abs(Xs).max()
+    assert fwd <= 4 * kappa * max(eta, 1e-16) + 1e-13
+    return eta
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+@pytest.mark.parametrize("n,nrhs,V", [(1, 1, 0), (37, 2, 0), (129, 3, 0), (512, 16, 256), (1000, 4, 256),
+                                      (2048, 16, 0)])
+def test_gesv_mixed_well_conditioned(cf, prec, n, nrhs, V):
+    A = inputs.uniform_pm1(n, seed=0, shift=2 * np.sqrt(n))
+    B = inputs.rhs_normal(n, nrhs, seed=3)
+    dA, dB = _dev(A), _dev(B)
+    X, info, stats, st = cf.gesv_mixed(dA, dB, prec=prec, outer_V=V)
+    assert st == cf.CF_OK, stats.as_dict()
+    assert int(info.item()) == 0 and stats.converged == 1
+    np.testing.assert_array_equal(dA.cpu().numpy(), A)
+    np.testing.assert_array_equal(dB.cpu().numpy(), B)
+    _check_solution(A, B, X.cpu().numpy())
+    assert stats.iterations <= 20
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+@pytest.mark.parametrize("n,nrhs,V", [(1, 1, 0), (300, 2, 128), (1024, 8, 256), (2048, 8, 0)])
+def test_posv_mixed(cf, prec, n, nrhs, V):
+    S = inputs.spd_gram(n, seed=1)
+    B = inputs.rhs_normal(n, nrhs, seed=4)
+    dS, dB = _dev(S), _dev(B)
+    X, info, stats, st = cf.posv_mixed(dS, dB, prec=prec, outer_V=V)
+    assert st == cf.CF_OK, stats.as_dict()
+    assert stats.converged == 1
+    np.testing.assert_array_equal(dS.cpu().numpy(), S)
+    _check_solution(S, B, X.cpu().numpy())
+
+
+def test_gesv_mixed_unshifted_uniform_small(cf):
+    """s = 0 (kappa ~ 1e3 at n = 256): FP16 factors still let classical
+    refinement converge."""
+    n = 256
+    A = inputs.uniform_pm1(n, seed=0)
+    B = inputs.rhs_normal(n, 2, seed=3)
+    X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec="f16")
+    assert st == cf.CF_OK, stats.as_dict()
+    _check_solution(A, B, X.cpu().numpy())
+
+
+def test_gesv_mixed_workspace_error(cf):
+    A = _dev(inputs.uniform_pm1(64, seed=1, shift=16.0))
+    B = _dev(inputs.rhs_normal(64, 1))
+    with pytest.raises(cf.CfError) as e:
+        cf.gesv_mixed(A, B, work=torch.empty(16, dtype=torch.uint8, device="cuda"))
+    assert e.value.status == cf.CF_ERR_WORKSPACE
