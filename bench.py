@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark: TFLOP/s of mixed-precision LU and Cholesky solves refined to
+1e-14 backward error at N = 32768 on one GB300, next to this project's FP64
+path and the CPU oracle.
+
+One step = cf_gesv_mixed (LU with tournament pivoting, BF16 tensor-core
+Schur updates, FP64 refinement; A = U[-1,1] + 2 sqrt(N) I, 16 right-hand
+sides) + cf_posv_mixed (Cholesky, BF16 updates, FP64 refinement;
+A = G G^T / N + alpha I with kappa ~ 1e2, 8 right-hand sides).  value =
+(2N^3/3 + N^3/3) / step time.  A step counts only if every right-hand side
+reaches eta <= 1e-14 (checked here with an FP64 residual).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cf|reference]
+
+For N > 1 (torchrun) every rank solves its own replica (the factorization
+of one matrix does not shard): value = flops of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TFLOP/s for LU/Cholesky at N=32768, mixed+refine vs FP64, at 1e-14 backward err"
+UNIT = "TFLOP/s"
+TOL = 1e-14
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; ~2 DFMA/clk/SM x 152 SMs x 2.07 GHz)
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cf", "reference"], default="cf")
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "f16"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                     "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5).stdout
+                parts = [p.strip() for p in out.strip().split(",")]
+                if len(parts) >= 8:
+                    self.samples.append(parts)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for nm, v in zip(names, s[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ oracle
+def _oracle_sample(n_sample: int):
+    """The FP64 oracle as it stands on this host's cores: LU (v = h = 128)
+    and Cholesky at n_sample with the same generators.  Returns (TFLOP/s,
+    seconds, threads)."""
+    import oracle
+    from paper_2108_09337_gb300 import inputs
+    A = inputs.uniform_pm1(n_sample, seed=0, shift=2 * math.sqrt(n_sample))
+    S = inputs.spd_gram(n_sample, seed=1)
+    t0 = time.perf_counter()
+    oracle.getrf(A, v=128, h=128, arity=2)
+    oracle.potrf(S)
+    dt = time.perf_counter() - t0
+    fl = oracle.lu_flops(n_sample) + oracle.chol_flops(n_sample)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return fl / dt / 1e12, dt, threads
+
+
+def run_reference(args, rank: int):
+    """--impl reference: the oracle, timed on the host cores, each step a
+    bounded sample (N = 2048 LU + Cholesky) of the benchmark workload."""
+    if rank != 0:
+        return
+    n_s = 2048
+    for _ in range(args.warmup):
+        _oracle_sample(n_s)
+    times, rates = [], []
+    for _ in range(args.steps):
+        r, dt, threads = _oracle_sample(n_s)
+        times.append(dt)
+        rates.append(r)
+    value = statistics.median(rates)
+    sample = "oracle LU (tournament, v=h=128) + Cholesky at N=%d per step, same generators" % n_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "CPU oracle sample of the N=32768 LU/Cholesky workload", "n_sample": n_s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def _gen_inputs(n, device):
+    import torch
+    from paper_2108_09337_gb300 import inputs
+    A_lu = inputs.uniform_pm1_torch(n, seed=0, shift=2.0 * math.sqrt(n), device=device)
+    B_lu = inputs.rhs_normal_torch(n, 16, seed=3, device=device)
+    A_ch = inputs.spd_gram_torch(n, seed=1, alpha=0.0, device=device)
+    # alpha = lambda_max / (kappa - 1), kappa = 1e2; lambda_max by power iteration
+    g = torch.Generator(device=device)
+    g.manual_seed(5)
+    x = torch.randn(n, 1, generator=g, device=device, dtype=torch.float64)
+    lam = 0.0
+    for _ in range(30):
+        y = A_ch @ x
+        lam = float(torch.linalg.vector_norm(y) / torch.linalg.vector_norm(x))
+        x = y / torch.linalg.vector_norm(y)
+    alpha = lam / (1e2 - 1.0)
+    A_ch.diagonal().add_(alpha)
+    B_ch = inputs.rhs_normal_torch(n, 8, seed=4, device=device)
+    return A_lu, B_lu, A_ch, B_ch, {"lambda_max_est": lam, "alpha": alpha}
+
+
+def _eta(A, X, B):
+    import torch
+    R = B - A @ X
+    an = torch.linalg.matrix_norm(A, ord=float("inf"))
+    num = R.abs().amax(dim=0)
+    den = an * X.abs().amax(dim=0) + B.abs().amax(dim=0)
+    return float((num / den).max())
+
+
+def run_gpu(args, rank: int, world: int, local_rank: int):
+    import numpy as np  # noqa: F401
+    import torch
+    import torch.distributed as dist
+    from paper_2108_09337_gb300 import cf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    prec = args.prec
+    lu_fl = 2.0 * n ** 3 / 3.0
+    ch_fl = n ** 3 / 3.0
+
+    A_lu, B_lu, A_ch, B_ch, gen_info = _gen_inputs(n, dev)
+    ws_lu = torch.empty(cf.gesv_mixed_workspace_size(n, 16, prec), dtype=torch.uint8, device=dev)
+    ws_ch = torch.empty(cf.posv_mixed_workspace_size(n, 8, prec), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        X1, info1, st1, s1 = cf.gesv_mixed(A_lu, B_lu, prec=prec, work=ws_lu)
+        X2, info2, st2, s2 = cf.posv_mixed(A_ch, B_ch, prec=prec, work=ws_ch)
+        return (X1, st1, s1), (X2, st2, s2)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per_step = []
+    stats_lu, stats_ch = [], []
+    launches0 = cf.kernel_launches()
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            (X1, st1, S1), (X2, st2, S2) = step()
+            s1.record(stream)
+            per_step.append((s0, s1))
+            stats_lu.append(S1.as_dict())
+            stats_ch.append(S2.as_dict())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = cf.kernel_launches() - launches0
+    total_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * (lu_fl + ch_fl) / (ms_step * 1e-3) / 1e12
+
+    # verify the last step's solutions independently (FP64 residual in torch)
+    eta_lu = _eta(A_lu, X1, B_lu)
+    eta_ch = _eta(A_ch, X2, B_ch)
+    ok = (eta_lu <= TOL) and (eta_ch <= TOL) and st1 == cf.CF_OK and st2 == cf.CF_OK
+
+    # ---- dominant kernel and its roofline (device time measured inside the steps)
+    res_ms = sum(s["residual_ms"] for s in stats_lu + stats_ch)
+    res_n = sum(s["residual_launches"] for s in stats_lu + stats_ch)
+    res_fl = sum(2.0 * n * n * k * s["residual_launches"] for s, k in
+                 [(s, 16) for s in stats_lu] + [(s, 8) for s in stats_ch])
+    upd_ms = sum(s["update_ms"] for s in stats_lu + stats_ch)
+    upd_n = sum(s["update_launches"] for s in stats_lu + stats_ch)
+    upd_fl = sum(s["update_flops"] for s in stats_lu + stats_ch)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if res_ms >= upd_ms and res_n > 0:
+        ach = (res_fl / res_n) / (res_ms / res_n * 1e-3) / 1e12
+        roof = {"kernel": "k_residual_f64 (R-1, FP64 r = b - A x)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (~2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
+                "launches": res_n, "avg_ms": res_ms / res_n}
+    else:
+        pk = peaks.get("bf16_tflops_sustained") or 1700.0
+        ach = (upd_fl / max(upd_n, 1)) / (upd_ms / max(upd_n, 1) * 1e-3) / 1e12 if upd_n else 0.0
+        roof = {"kernel": "k_schur_tc (LU-5/CH-3, K=V tcgen05 update)", "bound": "tensor", "achieved": ach,
+                "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks
+                else "fallback 1.7 PFLOP/s sustained",
+                "launches": upd_n, "avg_ms": upd_ms / max(upd_n, 1)}
+    kernels = {
+        "residual_f64": {"ms_per_step": res_ms / args.steps, "launches_per_step": res_n / args.steps,
+                         "tflops": (res_fl / (res_ms * 1e-3) / 1e12) if res_ms else None},
+        "schur_tc_KV": {"ms_per_step": upd_ms / args.steps, "launches_per_step": upd_n / args.steps,
+                        "tflops": (upd_fl / (upd_ms * 1e-3) / 1e12) if upd_ms else None},
+    }
+    parts = {
+        "lu": {"factor_ms": statistics.median(s["factor_ms"] for s in stats_lu),
+               "refine_ms": statistics.median(s["refine_ms"] for s in stats_lu),
+               "iterations": stats_lu[-1]["iterations"], "eta": eta_lu, "eta0": stats_lu[-1]["eta0"]},
+        "chol": {"factor_ms": statistics.median(s["factor_ms"] for s in stats_ch),
+                 "refine_ms": statistics.median(s["refine_ms"] for s in stats_ch),
+                 "iterations": stats_ch[-1]["iterations"], "eta": eta_ch, "eta0": stats_ch[-1]["eta0"],
+                 "shift": stats_ch[-1]["shift"]},
+    }
+    for k in parts:
+        p = parts[k]
+        fl = lu_fl if k == "lu" else ch_fl
+        p["tflops"] = fl / ((p["factor_ms"] + p["refine_ms"]) * 1e-3) / 1e12
+
+    # ---- e2e: same step through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hA_lu = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        hA_lu.copy_(A_lu)
+        hB_lu = torch.empty((16, n), dtype=torch.float64, pin_memory=True).t()
+        hB_lu.copy_(B_lu)
+        hA_ch = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        hA_ch.copy_(A_ch)
+        hB_ch = torch.empty((8, n), dtype=torch.float64, pin_memory=True).t()
+        hB_ch.copy_(B_ch)
+        hX1 = torch.empty((16, n), dtype=torch.float64, pin_memory=True).t()
+        hX2 = torch.empty((8, n), dtype=torch.float64, pin_memory=True).t()
+        dA1, dB1, dA2, dB2 = torch.empty_like(A_lu), torch.empty_like(B_lu), torch.empty_like(A_ch), \
+            torch.empty_like(B_ch)
+        del A_lu, A_ch
+        torch.cuda.empty_cache()
+
+        def e2e_step():
+            dA1.copy_(hA_lu, non_blocking=True)
+            dB1.copy_(hB_lu, non_blocking=True)
+            X1_, _, _, _ = cf.gesv_mixed(dA1, dB1, prec=prec, work=ws_lu)
+            hX1.copy_(X1_, non_blocking=True)
+            dA2.copy_(hA_ch, non_blocking=True)
+            dB2.copy_(hB_ch, non_blocking=True)
+            X2_, _, _, _ = cf.posv_mixed(dA2, dB2, prec=prec, work=ws_ch)
+            hX2.copy_(X2_, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(1, min(args.steps, 3))
+        barrier()
+        e0.record(stream)
+        for _ in range(k2):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms2 = e0.elapsed_time(e1) / k2
+        if world > 1:
+            t = torch.tensor([ms2], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms2 = float(t.item())
+        h2d = 2 * n * n * 8 + (16 + 8) * n * 8
+        d2h = (16 + 8) * n * 8
+        e2e = {"value": world * (lu_fl + ch_fl) / (ms2 * 1e-3) / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms2}
+        del hA_lu, hA_ch, dA1, dA2
+        torch.cuda.empty_cache()
+
+    # ---- this project's FP64 path on the same matrices (one run each)
+    fp64 = None
+    if not args.no_fp64:
+        from paper_2108_09337_gb300 import inputs
+        A64 = inputs.uniform_pm1_torch(n, seed=0, shift=2.0 * math.sqrt(n), device=dev)
+        A64 = A64.t().contiguous().t() if A64.stride(0) != 1 else A64
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ipiv, info = cf.getrf(A64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lu_ms = e0.elapsed_time(e1)
+        del A64, ipiv
+        S64 = inputs.spd_gram_torch(n, seed=1, alpha=gen_info["alpha"], device=dev)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cf.potrf(S64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ch_ms = e0.elapsed_time(e1)
+        del S64
+        fp64 = {"lu_ms": lu_ms, "chol_ms": ch_ms, "lu_tflops": lu_fl / (lu_ms * 1e-3) / 1e12,
+                "chol_tflops": ch_fl / (ch_ms * 1e-3) / 1e12,
+                "tflops": (lu_fl + ch_fl) / ((lu_ms + ch_ms) * 1e-3) / 1e12,
+                "note": "factorization only (FP64 path; its solve adds O(N^2))"}
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu:
+        r, dt, threads = _oracle_sample(4096)
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "FP64 oracle LU (tournament, v=h=128) + Cholesky at N=4096, same generators, "
+                         "%.1f s on this host" % dt}
+    line = {
+        "metric": METRIC, "value": value if ok else 0.0, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": "mixed LU solve (N=32768, 16 RHS, A=U[-1,1]+2sqrt(N)I) + mixed Cholesky solve "
+                               "(N=32768, 8 RHS, A=GG^T/N+alpha I, kappa~1e2), %s tensor-core updates, FP64 "
+                               "refinement to 1e-14" % prec,
+                   "n": n, "v": 128, "leaf_h": 128, "arity": 2, "outer_V": 1024, "factor_prec": prec,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (A is 8.6 GB per matrix)", "inputs": gen_info},
+        "converged": ok, "eta": {"lu": eta_lu, "chol": eta_ch},
+        "parts": parts, "kernels": kernels,
+        "clocks": clk.summary(),
+        "e2e": e2e, "gpu_launches": launches,
+        "roofline": roof, "cpu_baseline": cpu, "fp64_path": fp64,
+        "speedup_vs_fp64": (value / fp64["tflops"]) if (fp64 and ok) else None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_gpu(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

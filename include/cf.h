@@ -79,10 +79,18 @@ typedef struct {
     double shift;      /* diagonal shift added before factoring (0 if none) */
     double factor_ms;  /* device time of the factorization */
     double refine_ms;  /* device time of the refinement */
+    double residual_ms;     /* device time inside the FP64 residual launches */
+    double update_ms;       /* device time inside the K = V tensor-core updates */
+    double update_flops;    /* algorithmic flops of those updates */
+    int residual_launches;
+    int update_launches;
 } cf_refine_stats;
 
 const char *cf_status_string(int status);
 int cf_last_cuda_error(void);   /* last cudaError_t seen by the library */
+/* Number of kernel launches the library has enqueued in this process so far
+ * (a captured graph counts each of its kernels at every replay). */
+long long cf_kernel_launches(void);
 
 /* ------------------------------------------------------------------------
  * LU-1  TournPivot on one panel (Alg. 1 step 2; Sec. 7.3, "Tournament

@@ -46,7 +46,9 @@ class RefineStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("solver", ctypes.c_int), ("converged", ctypes.c_int),
                 ("info", ctypes.c_int), ("eta", ctypes.c_double), ("eta0", ctypes.c_double),
                 ("shift", ctypes.c_double), ("factor_ms", ctypes.c_double),
-                ("refine_ms", ctypes.c_double)]
+                ("refine_ms", ctypes.c_double), ("residual_ms", ctypes.c_double),
+                ("update_ms", ctypes.c_double), ("update_flops", ctypes.c_double),
+                ("residual_launches", ctypes.c_int), ("update_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -58,6 +60,7 @@ _SIG = {
     "cf_default_options": (None, [_OPT]),
     "cf_status_string": (ctypes.c_char_p, [_I]),
     "cf_last_cuda_error": (_I, []),
+    "cf_kernel_launches": (ctypes.c_longlong, []),
     "cf_tourn_workspace_size": (_S, [_I, _I, _I, _I]),
     "cf_tourn_select": (_I, [_I, _I, _P, _I, _I, _I, _P, _P, _S, _P]),
     "cf_getrf_workspace_size": (_S, [_I, _OPT]),
@@ -274,6 +277,11 @@ def gesv_mixed_workspace_size(n, nrhs, prec="bf16", **opt_kw):
 def posv_mixed_workspace_size(n, nrhs, prec="bf16", **opt_kw):
     opt = options(**opt_kw)
     return _lib.cf_posv_mixed_workspace_size(n, nrhs, PREC[prec], ctypes.byref(opt))
+
+
+def kernel_launches() -> int:
+    """Kernel launches libcf has enqueued in this process so far."""
+    return int(_lib.cf_kernel_launches())
 
 
 def lib():

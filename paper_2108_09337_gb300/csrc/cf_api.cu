@@ -17,7 +17,9 @@
 namespace cf {
 
 static std::atomic<int> g_last_cuda_error{0};
+static std::atomic<long long> g_launches{0};
 void set_cuda_error(cudaError_t e) { g_last_cuda_error.store((int)e); }
+void count_launches(long long n) { g_launches.fetch_add(n); }
 
 int launch_trsm_left_f64(bool lower, bool unit, bool trans, double *X, int ldx, int w, int cols, const double *Tm,
                          int ldt, cudaStream_t st);
@@ -99,6 +101,8 @@ extern "C" const char *cf_status_string(int s) {
 }
 
 extern "C" int cf_last_cuda_error(void) { return g_last_cuda_error.load(); }
+
+extern "C" long long cf_kernel_launches(void) { return g_launches.load(); }
 
 // ------------------------------------------------------------------- getrf
 extern "C" size_t cf_getrf_workspace_size(int n, const cf_options *opt) {

@@ -15,6 +15,8 @@ constexpr int kMaxV = 128;
 
 // Records the last CUDA error seen by the library (cf_last_cuda_error()).
 void set_cuda_error(cudaError_t e);
+// Counts enqueued kernel launches (cf_kernel_launches()).
+void count_launches(long long n);
 
 #define CF_CUDA_TRY(expr)                                   \
     do {                                                    \
@@ -25,7 +27,11 @@ void set_cuda_error(cudaError_t e);
         }                                                   \
     } while (0)
 
-#define CF_LAUNCH_CHECK() CF_CUDA_TRY(cudaGetLastError())
+#define CF_LAUNCH_CHECK()              \
+    do {                               \
+        ::cf::count_launches(1);       \
+        CF_CUDA_TRY(cudaGetLastError()); \
+    } while (0)
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -213,6 +213,38 @@ static int grid_for(size_t tot) {
     return (int)g;
 }
 
+// Event pairs around selected launches on one stream; read after a sync.
+struct Timer {
+    std::vector<cudaEvent_t> ev;
+    double flops = 0.0;
+    int launches = 0;
+    int begin(cudaStream_t st) {
+        cudaEvent_t e;
+        CF_CUDA_TRY(cudaEventCreate(&e));
+        ev.push_back(e);
+        CF_CUDA_TRY(cudaEventRecord(e, st));
+        return CF_OK;
+    }
+    int end(cudaStream_t st, double fl) {
+        int rc = begin(st);
+        flops += fl;
+        ++launches;
+        return rc;
+    }
+    double ms() const {   // after the stream has been synchronised
+        double t = 0;
+        for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+            float x = 0;
+            cudaEventElapsedTime(&x, ev[i], ev[i + 1]);
+            t += x;
+        }
+        return t;
+    }
+    ~Timer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
 template <typename LP>
 static int cvt_rows(int rows, int k, int kpad, const float *src, int lds, void *dst, int ldk, cudaStream_t st) {
     if (rows <= 0) return CF_OK;
@@ -235,7 +267,7 @@ static int cvt_cols(int k, int cols, int kpad, const float *src, int lds, void *
 // Schur updates.
 // ---------------------------------------------------------------------------
 template <typename LP>
-static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st) {
+static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu) {
     const bool bf16 = std::is_same<LP, __nv_bfloat16>::value;
     const int v = o.v, V = pick_V(n, o);
     const size_t ld = (size_t)w.ldw;
@@ -278,8 +310,10 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             const int Vs = JE - J0, Vp = (Vs + 63) / 64 * 64, mr = n - JE;
             if ((rc = cvt_rows<LP>(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Lb, Vp, st))) return rc;
             if ((rc = cvt_cols<LP>(Vs, mr, Vp, W + J0 + JE * ld, w.ldw, w.Ub, Vp, st))) return rc;
+            if (tu && (rc = tu->begin(st))) return rc;
             if ((rc = launch_schur_tc(mr, mr, Vp, w.Lb, Vp, w.Ub, Vp, W + JE + JE * ld, w.ldw, bf16, false, st, 0)))
                 return rc;
+            if (tu && (rc = tu->end(st, 2.0 * mr * (double)mr * Vs))) return rc;
         }
     }
     return CF_OK;
@@ -289,7 +323,7 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
 // Mixed Cholesky of W (lower, in place).
 // ---------------------------------------------------------------------------
 template <typename LP>
-static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st) {
+static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu) {
     const bool bf16 = std::is_same<LP, __nv_bfloat16>::value;
     const int v = o.v, V = pick_V(n, o);
     const size_t ld = (size_t)w.ldw;
@@ -316,8 +350,11 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
         if (JE < n) {
             const int Vs = JE - J0, Vp = (Vs + 63) / 64 * 64, mr = n - JE;
             if ((rc = cvt_rows<LP>(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Lb, Vp, st))) return rc;
+            if (tu && (rc = tu->begin(st))) return rc;
             if ((rc = launch_schur_tc(mr, mr, Vp, w.Lb, Vp, w.Lb, Vp, W + JE + JE * ld, w.ldw, bf16, true, st, 0)))
                 return rc;
+            // algorithmic flops of the triangular update: m (m + 1) K
+            if (tu && (rc = tu->end(st, (double)mr * (mr + 1.0) * Vs))) return rc;
         }
     }
     return CF_OK;
@@ -366,6 +403,7 @@ static int solve_f32(int n, int nrhs, const MixedWS &w, bool lu, cudaStream_t st
 // step instead of ~4 n/v); falls back to direct launches if capture fails.
 struct SolveGraph {
     cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
     ~SolveGraph() {
         if (exec) cudaGraphExecDestroy(exec);
     }
@@ -378,7 +416,10 @@ static int build_solve_graph(int n, int nrhs, const MixedWS &w, bool lu, cudaStr
         cudaGetLastError();
         return CF_OK;
     }
+    const long long before = cf_kernel_launches();
     int rc = solve_f32(n, nrhs, w, lu, st);
+    g->kernels = cf_kernel_launches() - before;
+    count_launches(-g->kernels);       // captured, not yet launched
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (rc != CF_OK || e != cudaSuccess || graph == nullptr) {
@@ -415,12 +456,13 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     // ---- factorization (Cholesky retries with a diagonal shift on breakdown)
     double shift = 0.0;
     int hinfo = 0;
+    Timer tupd, tres;
     const double u_lp = std::is_same<LP, __nv_bfloat16>::value ? 0x1p-8 : 0x1p-11;
     for (int attempt = 0; attempt < 4; ++attempt) {
         k_f64_to_f32<<<grid_for((size_t)n * n), 256, 0, st>>>(n, n, A, lda, w.W, w.ldw, shift);
         CF_LAUNCH_CHECK();
         CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
-        rc = lu ? mixed_getrf<LP>(n, w, info, o, st) : mixed_potrf<LP>(n, w, info, o, st);
+        rc = lu ? mixed_getrf<LP>(n, w, info, o, st, &tupd) : mixed_potrf<LP>(n, w, info, o, st, &tupd);
         if (rc) return rc;
         CF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
         CF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -477,7 +519,9 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     bool converged = false;
     for (;; ++it) {
         if (it > 0) {
+            if ((rc = tres.begin(st))) return rc;
             if ((rc = launch_residual_f64(n, n, nrhs, A, lda, X, ldx, B, ldb, w.R, ldr, st))) return rc;
+            if ((rc = tres.end(st, 2.0 * n * (double)n * nrhs))) return rc;
         }
         CF_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(unsigned long long) * 2 * nrhs, st));
         k_col_absmax<<<dim3(grid_for(n), nrhs), 256, 0, st>>>(n, nrhs, w.R, ldr, nR);
@@ -515,6 +559,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
         CF_LAUNCH_CHECK();
         if (graph.exec) {
             CF_CUDA_TRY(cudaGraphLaunch(graph.exec, st));
+            count_launches(graph.kernels);
         } else if ((rc = solve_f32(n, nrhs, w, lu, st))) {
             return rc;
         }
@@ -535,6 +580,11 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     S.eta = eta;
     S.factor_ms = f_ms;
     S.refine_ms = r_ms;
+    S.residual_ms = tres.ms();
+    S.residual_launches = tres.launches;
+    S.update_ms = tupd.ms();
+    S.update_flops = tupd.flops;
+    S.update_launches = tupd.launches;
     if (stats) *stats = S;
     return converged ? CF_OK : CF_ERR_NOT_CONVERGED;
 }

@@ -410,6 +410,7 @@ static int launch_tourn_cl(const T *P, int ldp, const TournPlan &plan, const Tou
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     CF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tourn<T, CL>, P, ldp, plan, ws, ep));
+    count_launches(1);
     return CF_OK;
 }
 
