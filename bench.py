@@ -219,7 +219,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             s0 = torch.cuda.Event(enable_timing=True)
             s1 = torch.cuda.Event(enable_timing=True)
             s0.record(stream)
-            (X1, st1, S1), (X2, st2, S2) = step()
+            (X1, S1, st1), (X2, S2, st2) = step()
             s1.record(stream)
             per_step.append((s0, s1))
             stats_lu.append(S1.as_dict())

@@ -57,7 +57,7 @@ typedef enum {
 typedef struct {
     int v;             /* block size of a step, 1..128 [128] (Sec. 7.2, "Block size v") */
     int leaf_h;        /* tournament leaf height, 1..128 [128] */
-    int arity;         /* children per playoff node, 2..4 [2] */
+    int arity;         /* children per playoff node, 2..4 [2]; the mixed paths use 2 */
     int outer_V;       /* mixed LU/Cholesky: depth of the deferred update, multiple of v [0 = auto] */
     int lookahead;     /* mixed paths: overlap panel t+1 with update t [1] */
     double tol;        /* refinement stop: max backward error [1e-14] */
@@ -108,6 +108,14 @@ size_t cf_tourn_workspace_size(int m, int w, int leaf_h, int arity);
 int cf_tourn_select(int m, int w, const double *panel, int ldp, int leaf_h,
                     int arity, int *winners, void *work, size_t lwork,
                     cudaStream_t stream);
+
+/* The same selection on an FP32 panel, as the mixed-precision solvers run
+ * it (elimination in FP32 with fused multiply-add; one register row per
+ * thread).  Same arguments and workspace as cf_tourn_select, except that
+ * 1 <= leaf_h <= 256 and arity must be 2. */
+int cf_tourn_select_f32(int m, int w, const float *panel, int ldp, int leaf_h,
+                        int arity, int *winners, void *work, size_t lwork,
+                        cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * cf_getrf -- FP64 LU with tournament pivoting, in place (Alg. 1; Sec. 7.2

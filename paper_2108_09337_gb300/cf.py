@@ -63,6 +63,7 @@ _SIG = {
     "cf_kernel_launches": (ctypes.c_longlong, []),
     "cf_tourn_workspace_size": (_S, [_I, _I, _I, _I]),
     "cf_tourn_select": (_I, [_I, _I, _P, _I, _I, _I, _P, _P, _S, _P]),
+    "cf_tourn_select_f32": (_I, [_I, _I, _P, _I, _I, _I, _P, _P, _S, _P]),
     "cf_getrf_workspace_size": (_S, [_I, _OPT]),
     "cf_getrf": (_I, [_I, _P, _I, _P, _P, _P, _S, _OPT, _P]),
     "cf_potrf_workspace_size": (_S, [_I, _OPT]),
@@ -159,13 +160,16 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
 
 # --------------------------------------------------------------------------
 def tourn_select(panel: torch.Tensor, leaf_h: int = 128, arity: int = 2) -> torch.Tensor:
-    assert panel.dtype == torch.float64
+    """TournPivot on a column-major FP64 (cf_tourn_select) or FP32
+    (cf_tourn_select_f32) panel; returns the winners' row indices."""
+    assert panel.dtype in (torch.float64, torch.float32)
     m, w = panel.shape
     ld = _ld(panel, "panel")
     win = torch.empty(max(min(m, w), 1), dtype=torch.int32, device=panel.device)
     ws = _workspace(_lib.cf_tourn_workspace_size(m, w, leaf_h, arity), panel.device)
-    _check("cf_tourn_select", _lib.cf_tourn_select(m, w, _ptr(panel), ld, leaf_h, arity, _ptr(win),
-                                                   _ptr(ws), ws.numel(), _stream()))
+    fn, name = ((_lib.cf_tourn_select, "cf_tourn_select") if panel.dtype == torch.float64
+                else (_lib.cf_tourn_select_f32, "cf_tourn_select_f32"))
+    _check(name, fn(m, w, _ptr(panel), ld, leaf_h, arity, _ptr(win), _ptr(ws), ws.numel(), _stream()))
     return win[:min(m, w)]
 
 

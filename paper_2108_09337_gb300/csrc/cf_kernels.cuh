@@ -76,6 +76,26 @@ int launch_gemm_sub_t(int m, int n, int k, const T *A, int lda, bool trans_a, co
 template <typename T>
 int launch_trsm_left(bool lower, bool unit, bool trans, T *X, int ldx, int w, int cols, const T *Tm, int ldt,
                      cudaStream_t st);
+// ---- FP32 panel kernels of the mixed path (cf_tourn32.cu, cf_panel32.cu)
+int launch_tourn32(const float *P, int ldp, int m, int w, int h, int arity, const TournWS &ws, const TournEpilogue &ep,
+                   cudaStream_t st);
+int launch_a00_lu32(float *A00, int lda, int w, int kglob, int *info, cudaStream_t st);
+int launch_a00_chol32(float *A00, int lda, int w, int kglob, int *info, cudaStream_t st);
+template <typename LP>
+int launch_rtrsm32(float *X, int ldx, int rows, int w, const float *M00, int ldm, bool trans_lower, LP *lp, int ldk,
+                   int kpad, const int *skip, cudaStream_t st);
+template <typename LP>
+int launch_ltrsm32(float *X, int ldx, int w, int cols, const float *L00, int ldl, LP *lp, int ldk, int kpad,
+                   cudaStream_t st);
+
+// ---- thin triangular solves with FP32 factors (cf_trsv.cu)
+// mode: 0 unit lower (L of LU), 1 upper (U), 2 lower (Cholesky L), 3 L^T.
+size_t trsv_ws_bytes(int n);
+size_t diag_inverse_floats(int n);
+int launch_diag_inverse(int mode, int n, const float *T, int ldt, float *Dinv, cudaStream_t st);
+int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
+                    int *sync_ws, cudaStream_t st);
+int trsv_take_status(cudaStream_t st, int *status);
 // R = B - A X for a thin X (nrhs columns).
 int launch_residual_f64(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
                         int ldb, double *R, int ldr, cudaStream_t st);

@@ -164,6 +164,8 @@ struct MixedWS {
     TournEpilogue tep{};
     double *R = nullptr, *scale = nullptr, *rowsum = nullptr;
     float *Rf = nullptr;
+    float *DinvL = nullptr, *DinvU = nullptr;   // inverses of the 64 x 64 diagonal blocks
+    int *trsv_sync = nullptr;
     unsigned long long *norms = nullptr;   // [0..nrhs) |R|, [nrhs..2nrhs) |X|, [2nrhs..3nrhs) |B|, [3nrhs] ||A||
     size_t bytes = 0;
 };
@@ -201,6 +203,9 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->scale = cv.take<double>(nrhs + 1);
     w->rowsum = cv.take<double>(n + 1);
     w->Rf = cv.take<float>((size_t)n * nrhs + 1);
+    w->DinvL = cv.take<float>(diag_inverse_floats(n));
+    w->DinvU = lu ? cv.take<float>(diag_inverse_floats(n)) : nullptr;
+    w->trsv_sync = cv.take<int>(trsv_ws_bytes(n) / sizeof(int) + 1);
     w->norms = cv.take<unsigned long long>(3 * nrhs + 2);
     w->bytes = cv.size();
     return CF_OK;
@@ -284,18 +289,18 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             float *A00 = W + k0 + k0 * ld;
             w.tep.ipiv = w.ipiv;
             w.tep.k0 = k0;
-            if ((rc = launch_tourn<float>(A00, w.ldw, m, wd, o.leaf_h, o.arity, w.tws, w.tep, st))) return rc;
+            if ((rc = launch_tourn32(A00, w.ldw, m, wd, o.leaf_h, o.arity, w.tws, w.tep, st))) return rc;
             if ((rc = launch_apply_swaps<float>(W, w.ldw, n, k0, w.tep, w.perm, st))) return rc;
-            if ((rc = launch_getf2_nopiv<float>(A00, w.ldw, wd, k0, info, st))) return rc;
+            if ((rc = launch_a00_lu32(A00, w.ldw, wd, k0, info, st))) return rc;
             const int below = m - wd, right = n - k0 - wd;
-            if ((rc = launch_trsm_right_upper<float>(A00 + wd, w.ldw, below, wd, A00, w.ldw, false, nullptr, st)))
+            // LU-3 / LU-4; they also write the K-major low-precision operands
+            // of the updates.
+            if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, false, (LP *)w.Ab, kMaxV, kMaxV,
+                                         nullptr, st)))
                 return rc;
-            if ((rc = launch_trsm_left_lower_unit<float>(A00 + wd * ld, w.ldw, wd, right, A00, w.ldw, st))) return rc;
+            if ((rc = launch_ltrsm32<LP>(A00 + wd * ld, w.ldw, wd, right, A00, w.ldw, (LP *)w.Bb, kMaxV, kMaxV, st)))
+                return rc;
             if (below <= 0 || right <= 0) continue;
-            // K = v updates: the slab columns right of the panel (all rows below)
-            // and the slab's remaining rows in the columns beyond the slab.
-            if ((rc = cvt_rows<LP>(below, wd, kMaxV, A00 + wd, w.ldw, w.Ab, kMaxV, st))) return rc;
-            if ((rc = cvt_cols<LP>(wd, right, kMaxV, A00 + wd * ld, w.ldw, w.Bb, kMaxV, st))) return rc;
             const int nslab = JE - (k0 + wd), nout = n - JE;
             float *C = A00 + wd + wd * ld;
             if (nslab > 0 &&
@@ -335,14 +340,15 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             const int wd = v < JE - k0 ? v : JE - k0;
             const int m = n - k0;
             float *A00 = W + k0 + k0 * ld;
-            if ((rc = launch_potf2<float>(A00, w.ldw, wd, k0, info, st))) return rc;
+            if ((rc = launch_a00_chol32(A00, w.ldw, wd, k0, info, st))) return rc;
             const int below = m - wd;
             if (below <= 0) continue;
-            if ((rc = launch_trsm_right_upper<float>(A00 + wd, w.ldw, below, wd, A00, w.ldw, true, info, st)))
+            // CH-2: L10 = A10 L00^{-T}, with its K-major low-precision copy
+            if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, true, (LP *)w.Ab, kMaxV, kMaxV, info,
+                                         st)))
                 return rc;
             const int nslab = JE - (k0 + wd);
             if (nslab <= 0) continue;
-            if ((rc = cvt_rows<LP>(below, wd, kMaxV, A00 + wd, w.ldw, w.Ab, kMaxV, st))) return rc;
             if ((rc = launch_schur_tc(below, nslab, kMaxV, w.Ab, kMaxV, w.Ab, kMaxV, A00 + wd + wd * ld, w.ldw, bf16,
                                       true, st, 0)))
                 return rc;
@@ -360,79 +366,12 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
     return CF_OK;
 }
 
-// Correction solve with the FP32 factors: Rf <- W^{-1} P Rf.
+// Correction solve with the FP32 factors: Rf <- W^{-1} P Rf, two sync-free
+// blocked triangular solves.
 static int solve_f32(int n, int nrhs, const MixedWS &w, bool lu, cudaStream_t st) {
-    const int v = kMaxV;
-    const size_t ld = (size_t)w.ldw;
-    const int ldf = n;
-    float *Rf = w.Rf;
-    const float *W = w.W;
     int rc;
-    for (int k0 = 0; k0 < n; k0 += v) {
-        const int wd = v < n - k0 ? v : n - k0;
-        if ((rc = launch_trsm_left<float>(true, lu, false, Rf + k0, ldf, wd, nrhs, W + k0 + k0 * ld, w.ldw, st)))
-            return rc;
-        if ((rc = launch_gemm_sub_t<float>(n - k0 - wd, nrhs, wd, W + (k0 + wd) + k0 * ld, w.ldw, false, Rf + k0, ldf,
-                                           false, Rf + k0 + wd, ldf, false, nullptr, st)))
-            return rc;
-    }
-    const int nb = (n + v - 1) / v;
-    for (int b = nb - 1; b >= 0; --b) {
-        const int k0 = b * v;
-        const int wd = v < n - k0 ? v : n - k0;
-        if (lu) {
-            if ((rc = launch_trsm_left<float>(false, false, false, Rf + k0, ldf, wd, nrhs, W + k0 + k0 * ld, w.ldw,
-                                              st)))
-                return rc;
-            if ((rc = launch_gemm_sub_t<float>(k0, nrhs, wd, W + k0 * ld, w.ldw, false, Rf + k0, ldf, false, Rf, ldf,
-                                               false, nullptr, st)))
-                return rc;
-        } else {
-            if ((rc = launch_trsm_left<float>(false, false, true, Rf + k0, ldf, wd, nrhs, W + k0 + k0 * ld, w.ldw,
-                                              st)))
-                return rc;
-            if ((rc = launch_gemm_sub_t<float>(k0, nrhs, wd, W + k0, w.ldw, true, Rf + k0, ldf, false, Rf, ldf,
-                                               false, nullptr, st)))
-                return rc;
-        }
-    }
-    return CF_OK;
-}
-
-// Captures the correction solve into a CUDA graph (one launch per refinement
-// step instead of ~4 n/v); falls back to direct launches if capture fails.
-struct SolveGraph {
-    cudaGraphExec_t exec = nullptr;
-    long long kernels = 0;
-    ~SolveGraph() {
-        if (exec) cudaGraphExecDestroy(exec);
-    }
-};
-
-static int build_solve_graph(int n, int nrhs, const MixedWS &w, bool lu, cudaStream_t st, SolveGraph *g) {
-    cudaStreamCaptureStatus cs;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return CF_OK;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaGetLastError();
-        return CF_OK;
-    }
-    const long long before = cf_kernel_launches();
-    int rc = solve_f32(n, nrhs, w, lu, st);
-    g->kernels = cf_kernel_launches() - before;
-    count_launches(-g->kernels);       // captured, not yet launched
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(st, &graph);
-    if (rc != CF_OK || e != cudaSuccess || graph == nullptr) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        return CF_OK;
-    }
-    if (cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
-        g->exec = nullptr;
-        cudaGetLastError();
-    }
-    cudaGraphDestroy(graph);
-    return CF_OK;
+    if ((rc = launch_trsv_f32(lu ? 0 : 2, n, nrhs, w.W, w.ldw, w.DinvL, w.Rf, n, w.trsv_sync, st))) return rc;
+    return launch_trsv_f32(lu ? 1 : 3, n, nrhs, w.W, w.ldw, lu ? w.DinvU : w.DinvL, w.Rf, n, w.trsv_sync, st);
 }
 
 template <typename LP>
@@ -509,8 +448,10 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     k_copy_cols<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, B, ldb, w.R, ldr);
     CF_LAUNCH_CHECK();
 
-    SolveGraph graph;
-    if (S.info == 0) build_solve_graph(n, nrhs, w, lu, st, &graph);
+    if (S.info == 0) {
+        if ((rc = launch_diag_inverse(lu ? 0 : 2, n, w.W, w.ldw, w.DinvL, st))) return rc;
+        if (lu && (rc = launch_diag_inverse(1, n, w.W, w.ldw, w.DinvU, st))) return rc;
+    }
 
     std::vector<unsigned long long> hn(3 * nrhs + 2);
     std::vector<double> hscale(nrhs);
@@ -557,17 +498,14 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
         k_gather_scale<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, lu ? w.perm : nullptr, w.R, ldr, w.scale,
                                                                   w.Rf, n);
         CF_LAUNCH_CHECK();
-        if (graph.exec) {
-            CF_CUDA_TRY(cudaGraphLaunch(graph.exec, st));
-            count_launches(graph.kernels);
-        } else if ((rc = solve_f32(n, nrhs, w, lu, st))) {
-            return rc;
-        }
+        if ((rc = solve_f32(n, nrhs, w, lu, st))) return rc;
         k_axpy_update<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, w.Rf, n, w.scale, X, ldx);
         CF_LAUNCH_CHECK();
     }
     CF_CUDA_TRY(cudaEventRecord(e2, st));
     CF_CUDA_TRY(cudaEventSynchronize(e2));
+    if ((rc = trsv_take_status(st, &tstat))) return rc;
+    if (tstat != 0) return CF_ERR_TIMEOUT;
     float f_ms = 0, r_ms = 0;
     cudaEventElapsedTime(&f_ms, e0, e1);
     cudaEventElapsedTime(&r_ms, e1, e2);

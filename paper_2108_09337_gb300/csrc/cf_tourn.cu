@@ -453,7 +453,8 @@ template int launch_apply_swaps<float>(float *, int, int, int, const TournEpilog
 // ---------------------------------------------------------------------------
 extern "C" size_t cf_tourn_workspace_size(int m, int w, int leaf_h, int arity) {
     (void)w;
-    return cf::tourn_ws_bytes(m > 0 ? m : 1, leaf_h, arity);
+    (void)leaf_h;   // sized for the most leaves (h = 1), valid for every leaf height
+    return cf::tourn_ws_bytes(m > 0 ? m : 1, 1, arity < 2 ? 2 : arity);
 }
 
 extern "C" int cf_tourn_select(int m, int w, const double *panel, int ldp, int leaf_h, int arity, int *winners,
@@ -470,7 +471,7 @@ extern "C" int cf_tourn_select(int m, int w, const double *panel, int ldp, int l
     if (lwork < cf_tourn_workspace_size(m, w, leaf_h, arity) || work == nullptr) return CF_ERR_WORKSPACE;
     TournWS ws{};
     TournEpilogue ep{};
-    int rc = tourn_ws_carve(work, m, leaf_h, arity, &ws, &ep);
+    int rc = tourn_ws_carve(work, m, 1, arity, &ws, &ep);
     if (rc != CF_OK) return rc;
     ep.ipiv = nullptr;
     CF_CUDA_TRY(cudaMemsetAsync(ws.counter, 0, ws.counter_bytes, stream));

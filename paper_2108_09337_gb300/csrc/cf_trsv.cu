@@ -1,0 +1,216 @@
+// cf_trsv.cu -- S-1 for the refinement loop: triangular solves with the FP32
+// factors and a thin right-hand side (nrhs <= 16), one launch per solve.
+//
+// Block rows of 64 are processed by CTAs that take a ticket in launch order
+// (atomic counter), so every block a CTA depends on belongs to a CTA that
+// started earlier and never waits on a later one.  A CTA subtracts the
+// contributions of the finished blocks as their flags appear, applies the
+// precomputed inverse of its diagonal block, publishes its block of the
+// solution and raises its flag.  The factor is read exactly once; the chain
+// of dependent work is one 64 x 64 tile product per block.  Waits on flags
+// are bounded: after the limit the kernel records CF_ERR_TIMEOUT and goes
+// on (results are then wrong, never hung).
+#include "cf_common.cuh"
+#include "cf_kernels.cuh"
+
+namespace cf {
+
+__device__ int g_trsv_status = 0;
+
+constexpr int kSB = 64;                // block size
+constexpr long long kFlagSpin = 1ll << 22;
+
+// Effective matrix M (n x n) seen by a solve:
+//   0: M = L, unit lower (forward)       1: M = U, upper (backward)
+//   2: M = L, lower (forward)            3: M = L^T (backward)
+template <int MODE>
+__device__ __forceinline__ float m_elem(const float *T, int ldt, int i, int k) {
+    return (MODE == 3) ? T[(size_t)k + (size_t)i * ldt] : T[(size_t)i + (size_t)k * ldt];
+}
+
+// Inverse of each 64 x 64 diagonal block of M, stored block after block,
+// column-major (Dinv[b*64*64 + i + 64*j]).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_diag_inverse(int n, const float *__restrict__ T, int ldt, float *Dinv) {
+    __shared__ float Ms[kSB][kSB + 1];   // Ms[i][k] = M(b0+i, b0+k)
+    __shared__ float Xs[kSB][kSB + 1];   // Xs[i][j] = inverse
+    const int b = blockIdx.x, b0 = b * kSB, nbk = min(kSB, n - b0);
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kSB * kSB; e += 256) {
+        const int i = e % kSB, k = e / kSB;
+        float v = 0.f;
+        if (i < nbk && k < nbk) v = m_elem<MODE>(T, ldt, b0 + i, b0 + k);
+        if (i >= nbk || k >= nbk) v = (i == k) ? 1.f : 0.f;
+        if (MODE == 0 && i == k) v = 1.f;
+        Ms[i][k] = v;
+        Xs[i][k] = (i == k) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    const bool lower = (MODE != 1);
+    // Solve M X = I column-parallel: thread owns column j = tid % 64 and rows
+    // i = tid / 64 + 4 t.
+    const int j = tid % kSB, i0 = tid / kSB;
+    for (int s = 0; s < kSB; ++s) {
+        const int k = lower ? s : kSB - 1 - s;
+        if (MODE != 0 && i0 == 0) Xs[k][j] = Xs[k][j] / Ms[k][k];
+        __syncthreads();
+        const float xk = Xs[k][j];
+        for (int i = i0; i < kSB; i += 4) {
+            if ((lower && i > k) || (!lower && i < k)) Xs[i][j] = fmaf(-Ms[i][k], xk, Xs[i][j]);
+        }
+        __syncthreads();
+    }
+    float *D = Dinv + (size_t)b * kSB * kSB;
+    for (int e = tid; e < kSB * kSB; e += 256) D[e] = Xs[e % kSB][e / kSB];
+}
+
+template <int MODE, int NR>
+__global__ void __launch_bounds__(256)
+k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const float *__restrict__ Dinv, float *X,
+               int ldx, int *flags, int *ticket) {
+    __shared__ float Ts[kSB][kSB + 1];
+    __shared__ float Ys[kSB][NR + 1];
+    __shared__ int s_ticket;
+    constexpr bool fwd = (MODE == 0 || MODE == 2);
+    constexpr int CPT = (NR + 3) / 4;            // right-hand sides per thread
+    const int nb = (n + kSB - 1) / kSB;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_ticket = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int s = s_ticket;
+    if (s >= nb) return;
+    const int b = fwd ? s : nb - 1 - s;
+    const int r0 = b * kSB, rb = min(kSB, n - r0);
+    const int i = tid % kSB, q = tid / kSB;      // row, rhs group
+    float acc[CPT];
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+        const int c = q + 4 * t;
+        acc[t] = (i < rb && c < nrhs) ? X[(size_t)(r0 + i) + (size_t)c * ldx] : 0.f;
+    }
+    for (int step = 0; step < s; ++step) {
+        const int cb = fwd ? step : nb - 1 - step;
+        const int c0 = cb * kSB, cbk = min(kSB, n - c0);
+        if (tid == 0) {
+            volatile int *f = flags + cb;
+            long long it = 0;
+            while (*f == 0 && it < kFlagSpin) {
+                ++it;
+                if (it > 32) __nanosleep(32);
+            }
+            if (it >= kFlagSpin) atomicExch(&g_trsv_status, CF_ERR_TIMEOUT);
+            __threadfence();
+        }
+        __syncthreads();
+        for (int e = tid; e < kSB * kSB; e += 256) {
+            // coalesced along the stored matrix's columns in both layouts
+            const int ii = (MODE == 3) ? e / kSB : e % kSB, kk = (MODE == 3) ? e % kSB : e / kSB;
+            Ts[ii][kk] = (ii < rb && kk < cbk) ? m_elem<MODE>(T, ldt, r0 + ii, c0 + kk) : 0.f;
+        }
+        for (int e = tid; e < kSB * NR; e += 256) {
+            const int kk = e % kSB, c = e / kSB;
+            Ys[kk][c] = (kk < cbk && c < nrhs) ? __ldcg(X + (size_t)(c0 + kk) + (size_t)c * ldx) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kSB; ++kk) {
+            const float m = Ts[i][kk];
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) acc[t] = fmaf(-m, Ys[kk][q + 4 * t], acc[t]);
+        }
+        __syncthreads();
+    }
+    // y_b = Dinv_b acc
+#pragma unroll
+    for (int t = 0; t < CPT; ++t)
+        if (q + 4 * t < NR) Ys[i][q + 4 * t] = acc[t];
+    const float *D = Dinv + (size_t)b * kSB * kSB;
+    for (int e = tid; e < kSB * kSB; e += 256) {
+        const int ii = e % kSB, kk = e / kSB;
+        // MODE 3 uses the inverse of L_bb transposed: (L^T)_bb^{-1} = (L_bb^{-1})^T
+        Ts[ii][kk] = (MODE == 3) ? D[kk + kSB * ii] : D[ii + kSB * kk];
+    }
+    __syncthreads();
+    float y[CPT];
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) y[t] = 0.f;
+#pragma unroll 8
+    for (int kk = 0; kk < kSB; ++kk) {
+        const float d = Ts[i][kk];
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) y[t] = fmaf(d, Ys[kk][q + 4 * t], y[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+        const int c = q + 4 * t;
+        if (i < rb && c < nrhs) X[(size_t)(r0 + i) + (size_t)c * ldx] = y[t];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicExch(flags + b, 1);
+}
+
+size_t trsv_ws_bytes(int n) {
+    const int nb = (n + kSB - 1) / kSB;
+    return sizeof(int) * (size_t)(nb + 1);
+}
+
+size_t diag_inverse_floats(int n) {
+    const int nb = (n + kSB - 1) / kSB;
+    return (size_t)nb * kSB * kSB;
+}
+
+// mode: 0 unit lower, 1 upper, 2 lower, 3 lower transposed (see m_elem).
+int launch_diag_inverse(int mode, int n, const float *T, int ldt, float *Dinv, cudaStream_t st) {
+    if (n <= 0) return CF_OK;
+    const int nb = (n + kSB - 1) / kSB;
+    switch (mode) {
+        case 0: k_diag_inverse<0><<<nb, 256, 0, st>>>(n, T, ldt, Dinv); break;
+        case 1: k_diag_inverse<1><<<nb, 256, 0, st>>>(n, T, ldt, Dinv); break;
+        case 2: k_diag_inverse<2><<<nb, 256, 0, st>>>(n, T, ldt, Dinv); break;
+        default: return CF_ERR_UNSUPPORTED;
+    }
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+template <int MODE>
+static int launch_trsv_mode(int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
+                            int *sync_ws, cudaStream_t st) {
+    const int nb = (n + kSB - 1) / kSB;
+    CF_CUDA_TRY(cudaMemsetAsync(sync_ws, 0, sizeof(int) * (size_t)(nb + 1), st));
+    int *flags = sync_ws, *ticket = sync_ws + nb;
+    if (nrhs <= 4) k_trsv_blocked<MODE, 4><<<nb, 256, 0, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    else if (nrhs <= 8) k_trsv_blocked<MODE, 8><<<nb, 256, 0, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    else k_trsv_blocked<MODE, 16><<<nb, 256, 0, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+// X <- M^{-1} X for nrhs <= 16 columns; sync_ws holds trsv_ws_bytes(n).
+int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
+                    int *sync_ws, cudaStream_t st) {
+    if (n <= 0 || nrhs <= 0) return CF_OK;
+    if (nrhs > 16) return CF_ERR_UNSUPPORTED;
+    switch (mode) {
+        case 0: return launch_trsv_mode<0>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 1: return launch_trsv_mode<1>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 2: return launch_trsv_mode<2>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 3: return launch_trsv_mode<3>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        default: return CF_ERR_UNSUPPORTED;
+    }
+}
+
+int trsv_take_status(cudaStream_t st, int *status) {
+    int h = 0;
+    CF_CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, g_trsv_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    CF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h != 0) {
+        const int zero = 0;
+        CF_CUDA_TRY(cudaMemcpyToSymbolAsync(g_trsv_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+    }
+    *status = h;
+    return CF_OK;
+}
+
+}  // namespace cf

@@ -85,3 +85,31 @@ def test_gesv_mixed_workspace_error(cf):
     with pytest.raises(cf.CfError) as e:
         cf.gesv_mixed(A, B, work=torch.empty(16, dtype=torch.uint8, device="cuda"))
     assert e.value.status == cf.CF_ERR_WORKSPACE
+
+
+# ---------------------------------------------------------- LU-1 in FP32
+@pytest.mark.parametrize("m,w,h,arity", [(128, 128, 128, 2), (1000, 128, 128, 2), (777, 100, 50, 2),
+                                         (5000, 128, 256, 2), (300, 17, 128, 2), (50, 128, 128, 2),
+                                         (256, 128, 256, 2), (32768, 128, 128, 2)])
+def test_tourn_select_f32_gap_audited(cf, m, w, h, arity):
+    """FP32 panel values (exact in FP64): where the FP64 oracle's gaps are all
+    >= 1e-3 the FP32 elimination must pick the same rows in the same order;
+    otherwise the selection must still be min(m, w) distinct rows."""
+    P = inputs.uniform_pm1(m, seed=m + 7 * w, m=w).astype(np.float32).astype(np.float64)
+    win_o, gap = oracle.tourn_select(P, h=h, arity=arity)
+    dP = torch.from_numpy(np.ascontiguousarray(P.T.astype(np.float32))).cuda().t()
+    win = cf.tourn_select(dP, leaf_h=h, arity=arity).cpu().numpy()
+    assert len(win) == min(m, w) and len(set(win.tolist())) == len(win)
+    assert win.min() >= 0 and win.max() < m
+    if gap >= 1e-3:
+        np.testing.assert_array_equal(win, win_o)
+
+
+def test_tourn_select_f32_constructed_gepp(cf):
+    """Single leaf (GEPP mode) on a constructed P^T L U: pivots are P."""
+    n = 128
+    A, perm, L, U = inputs.constructed_plu(n, seed=3)
+    dP = torch.from_numpy(np.ascontiguousarray(A.T.astype(np.float32))).cuda().t()
+    win = cf.tourn_select(dP, leaf_h=128, arity=2).cpu().numpy()
+    # GEPP on the first w columns selects perm[0..w) in order
+    np.testing.assert_array_equal(win, perm[:n])
