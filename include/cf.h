@@ -129,6 +129,25 @@ size_t cf_getrf_workspace_size(int n, const cf_options *opt);
 int cf_getrf(int n, double *A, int lda, int *ipiv, int *info, void *work,
              size_t lwork, const cf_options *opt, cudaStream_t stream);
 
+/* cf_getrf_noalloc -- cf_getrf for callers that cannot allocate device
+ * memory (code running under stream capture, plugins inside a framework
+ * whose allocator owns the device memory, callers with memory partitioned up
+ * front).  The paper has no counterpart; this is a deployment convenience.
+ * Same arguments, results and kernels as cf_getrf, but the tournament
+ * scratch lives in a 2 MiB array that the library places on every GPU that
+ * loads it and holds until the process exits; nothing is allocated.
+ *   - The scratch needed grows like n / leaf_h: n up to 131072 fits with
+ *     leaf_h = 128 and arity 2 (65536 with leaf_h = 64).  Larger requests
+ *     return CF_ERR_WORKSPACE before anything is enqueued.
+ *   - The first call on a device looks up the array's device address (once,
+ *     with that device current); make that first call before any stream
+ *     capture on that device.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and corrupt each other.  The
+ *     arrival counters are cleared at the start of every call. */
+int cf_getrf_noalloc(int n, double *A, int lda, int *ipiv, int *info,
+                     const cf_options *opt, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * cf_potrf -- FP64 Cholesky, lower, in place (Listing "Cholesky
  * Factorization", Sec. 6.2; COnfCHOX, Sec. 7.5 and Table 2: potrf on A00,

@@ -66,6 +66,7 @@ _SIG = {
     "cf_tourn_select_f32": (_I, [_I, _I, _P, _I, _I, _I, _P, _P, _S, _P]),
     "cf_getrf_workspace_size": (_S, [_I, _OPT]),
     "cf_getrf": (_I, [_I, _P, _I, _P, _P, _P, _S, _OPT, _P]),
+    "cf_getrf_noalloc": (_I, [_I, _P, _I, _P, _P, _OPT, _P]),
     "cf_potrf_workspace_size": (_S, [_I, _OPT]),
     "cf_potrf": (_I, [_I, _P, _I, _P, _P, _S, _OPT, _P]),
     "cf_getrs_workspace_size": (_S, [_I, _I]),
@@ -187,6 +188,23 @@ def getrf(A: torch.Tensor, v=None, leaf_h=None, arity=None, work=None):
     ws = work if work is not None else _workspace(need, A.device)
     _check("cf_getrf", _lib.cf_getrf(n, _ptr(A), lda, _ptr(ipiv), _ptr(info), _ptr(ws), ws.numel(),
                                      ctypes.byref(opt), _stream()))
+    return ipiv[:n], info
+
+
+def getrf_noalloc(A: torch.Tensor, v=None, leaf_h=None, arity=None, ipiv=None, info=None):
+    """cf_getrf_noalloc: the LU of getrf with the library's fixed scratch
+    instead of a work buffer (see include/cf.h).  ipiv and info may be passed
+    in so that the call itself allocates nothing."""
+    assert A.dtype == torch.float64
+    n = A.shape[0]
+    lda = _ld(A, "A")
+    opt = options(v=v, leaf_h=leaf_h, arity=arity)
+    if ipiv is None:
+        ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check("cf_getrf_noalloc", _lib.cf_getrf_noalloc(n, _ptr(A), lda, _ptr(ipiv), _ptr(info),
+                                                     ctypes.byref(opt), _stream()))
     return ipiv[:n], info
 
 
