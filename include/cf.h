@@ -179,6 +179,22 @@ int cf_residual(int m, int n, int nrhs, const double *A, int lda,
                 const double *X, int ldx, const double *B, int ldb, double *R,
                 int ldr, cudaStream_t stream);
 
+/* R-1 on the FP32 pipes (an alternative to cf_residual, not used by the
+ * mixed solvers): R = B - A X with A and X split into pairs of FP32 arrays
+ * (hi = fl32(v), lo = fl32(v - hi)); products are formed exactly as FP32
+ * pairs and summed with error-free transformations, restarting from zero
+ * every 32 terms into an FP64 accumulator.  Accuracy: the pair carries 48
+ * bits relative to its running value, so the error is about 2^-48 times the
+ * largest partial sums of a row (measured 4e-15 to 8e-15 of
+ * ||A||_inf ||x||_inf + ||b||_inf on diagonally dominant matrices, against
+ * 1e-16 for cf_residual); about 1.8x the throughput of FP64 on this part.
+ * work: cf_residual_pair_workspace_size(m, n, nrhs) bytes. */
+size_t cf_residual_pair_workspace_size(int m, int n, int nrhs);
+int cf_residual_pair(int m, int n, int nrhs, const double *A, int lda,
+                     const double *X, int ldx, const double *B, int ldb,
+                     double *R, int ldr, void *work, size_t lwork,
+                     cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * LU-5 / CH-3 building block, exposed for testing: C -= A_lp * B_lp^T on the
  * tensor cores (tcgen05, TMEM accumulators, TMA-fed), FP32 accumulate.
@@ -202,6 +218,8 @@ int cf_device_status(cudaStream_t stream);
 /* ------------------------------------------------------------------------
  * Mixed-precision refined solves (north star; the paper cites GPU mixed
  * LU + refinement as related work, Sec. 11).  A and B are never modified.
+ * cf_posv_mixed factors the lower triangle but forms residuals with all of
+ * A, which must hold both triangles.
  *   factor_prec  CF_BF16 or CF_F16 (CF_FP8E4M3 for cf_posv_mixed)
  *   X            n x nrhs FP64 solution, ldx
  *   info         device int[1], info of the low-precision factorization

@@ -289,3 +289,38 @@ extern "C" int cf_residual(int m, int n, int nrhs, const double *A, int lda, con
     if (ldr < (m > 1 ? m : 1)) return -11;
     return launch_residual_f64(m, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, st);
 }
+
+extern "C" size_t cf_residual_pair_workspace_size(int m, int n, int nrhs) {
+    Carver cv(nullptr);
+    const size_t mm = m > 0 ? m : 1, nn = n > 0 ? n : 1, rr = nrhs > 0 ? nrhs : 1;
+    cv.take<float>(mm * nn);
+    cv.take<float>(mm * nn);
+    cv.take<float>(nn * rr);
+    cv.take<float>(nn * rr);
+    return cv.size();
+}
+
+extern "C" int cf_residual_pair(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
+                                const double *B, int ldb, double *R, int ldr, void *work, size_t lwork,
+                                cudaStream_t st) {
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0) return -3;
+    if (m > 0 && n > 0 && A == nullptr) return -4;
+    if (lda < (m > 1 ? m : 1)) return -5;
+    if (n > 0 && nrhs > 0 && X == nullptr) return -6;
+    if (ldx < (n > 1 ? n : 1)) return -7;
+    if (m > 0 && nrhs > 0 && B == nullptr) return -8;
+    if (ldb < (m > 1 ? m : 1)) return -9;
+    if (m > 0 && nrhs > 0 && R == nullptr) return -10;
+    if (ldr < (m > 1 ? m : 1)) return -11;
+    if (m == 0 || nrhs == 0) return CF_OK;
+    if (work == nullptr || lwork < cf_residual_pair_workspace_size(m, n, nrhs)) return CF_ERR_WORKSPACE;
+    Carver cv(work);
+    float *Ahi = cv.take<float>((size_t)m * n), *Alo = cv.take<float>((size_t)m * n);
+    float *Xhi = cv.take<float>((size_t)n * nrhs), *Xlo = cv.take<float>((size_t)n * nrhs);
+    int rc;
+    if ((rc = launch_split_f64(m, n, A, lda, Ahi, Alo, m, nullptr, 0, 0.0, st))) return rc;
+    if ((rc = launch_split_f64(n, nrhs, X, ldx, Xhi, Xlo, n, nullptr, 0, 0.0, st))) return rc;
+    return launch_residual_df(m, n, nrhs, Ahi, Alo, m, Xhi, Xlo, n, B, ldb, R, ldr, st);
+}

@@ -33,17 +33,6 @@ namespace cf {
 // ---------------------------------------------------------------------------
 // Element-wise kernels
 // ---------------------------------------------------------------------------
-__global__ void k_f64_to_f32(int m, int n, const double *__restrict__ A, int lda, float *__restrict__ W, int ldw,
-                             double shift) {
-    const size_t tot = (size_t)m * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % m), j = (int)(e / m);
-        double a = A[(size_t)i + (size_t)j * lda];
-        if (i == j) a += shift;
-        W[(size_t)i + (size_t)j * ldw] = (float)a;
-    }
-}
-
 template <typename LP>
 __device__ __forceinline__ LP to_lp(float x);
 template <>
@@ -398,8 +387,8 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     Timer tupd, tres;
     const double u_lp = std::is_same<LP, __nv_bfloat16>::value ? 0x1p-8 : 0x1p-11;
     for (int attempt = 0; attempt < 4; ++attempt) {
-        k_f64_to_f32<<<grid_for((size_t)n * n), 256, 0, st>>>(n, n, A, lda, w.W, w.ldw, shift);
-        CF_LAUNCH_CHECK();
+        // W = fl32(A) (+ shift on the diagonal)
+        if ((rc = launch_split_f64(n, n, A, lda, nullptr, nullptr, w.ldw, w.W, w.ldw, shift, st))) return rc;
         CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
         rc = lu ? mixed_getrf<LP>(n, w, info, o, st, &tupd) : mixed_potrf<LP>(n, w, info, o, st, &tupd);
         if (rc) return rc;

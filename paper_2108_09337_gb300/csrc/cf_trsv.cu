@@ -64,15 +64,49 @@ __global__ void __launch_bounds__(256) k_diag_inverse(int n, const float *__rest
     for (int e = tid; e < kSB * kSB; e += 256) D[e] = Xs[e % kSB][e / kSB];
 }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int kTLD = kSB + 4;          // smem leading dimension (16-byte rows)
+
+// Stages the STORED 64 x 64 tile whose top-left element is (i0, j0) of T
+// (column-major, ld ldt) into St[col * kTLD + row] with 16-byte async copies
+// when the whole tile is inside the matrix and aligned; element by element
+// otherwise (zero outside).
+__device__ __forceinline__ void stage_tile(float *St, const float *T, int ldt, int n, int i0, int j0, bool fast) {
+    const int tid = threadIdx.x;
+    if (fast) {
+        for (int e = tid; e < kSB * kSB / 4; e += 256) {
+            const int r4 = e % (kSB / 4), c = e / (kSB / 4);
+            cp_async16(St + c * kTLD + 4 * r4, T + (size_t)(i0 + 4 * r4) + (size_t)(j0 + c) * ldt);
+        }
+    } else {
+        for (int e = tid; e < kSB * kSB; e += 256) {
+            const int r = e % kSB, c = e / kSB;
+            St[c * kTLD + r] = (i0 + r < n && j0 + c < n) ? T[(size_t)(i0 + r) + (size_t)(j0 + c) * ldt] : 0.f;
+        }
+    }
+}
+
 template <int MODE, int NR>
 __global__ void __launch_bounds__(256)
 k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const float *__restrict__ Dinv, float *X,
                int ldx, int *flags, int *ticket) {
-    __shared__ float Ts[kSB][kSB + 1];
-    __shared__ float Ys[kSB][NR + 1];
+    extern __shared__ __align__(16) float sm[];
+    float *St0 = sm;                               // two tile buffers
+    float *St1 = sm + kSB * kTLD;
+    float *Ds = sm + 2 * kSB * kTLD;               // inverse of the diagonal block
+    float *Ys = sm + 3 * kSB * kTLD;               // [kSB][NR + 1]
     __shared__ int s_ticket;
     constexpr bool fwd = (MODE == 0 || MODE == 2);
-    constexpr int CPT = (NR + 3) / 4;            // right-hand sides per thread
+    constexpr int CPT = (NR + 3) / 4;              // right-hand sides per thread
+    constexpr int YLD = NR + 1;
     const int nb = (n + kSB - 1) / kSB;
     const int tid = threadIdx.x;
     if (tid == 0) s_ticket = atomicAdd(ticket, 1);
@@ -81,14 +115,43 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const floa
     if (s >= nb) return;
     const int b = fwd ? s : nb - 1 - s;
     const int r0 = b * kSB, rb = min(kSB, n - r0);
-    const int i = tid % kSB, q = tid / kSB;      // row, rhs group
+    const int i = tid % kSB, q = tid / kSB;        // row, rhs group
+    const bool aligned = ((ldt & 3) == 0) && ((((uintptr_t)T) & 15) == 0);
+    // the diagonal block's inverse does not depend on anyone: fetch it now
+    {
+        const float *D = Dinv + (size_t)b * kSB * kSB;
+        for (int e = tid; e < kSB * kSB; e += 256) {
+            const int ii = e % kSB, kk = e / kSB;
+            // MODE 3 uses (L_bb^{-1})^T
+            Ds[kk * kTLD + ii] = (MODE == 3) ? D[kk + kSB * ii] : D[ii + kSB * kk];
+        }
+    }
     float acc[CPT];
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
         const int c = q + 4 * t;
         acc[t] = (i < rb && c < nrhs) ? X[(size_t)(r0 + i) + (size_t)c * ldx] : 0.f;
     }
+    // Stored tile that holds M(block b, block cb): for MODE 3 it is L(cb, b).
+    auto tile_origin = [&](int cb, int &ti, int &tj) {
+        if (MODE == 3) { ti = cb * kSB; tj = r0; } else { ti = r0; tj = cb * kSB; }
+    };
+    if (s > 0) {
+        const int cb = fwd ? 0 : nb - 1;
+        int ti, tj;
+        tile_origin(cb, ti, tj);
+        stage_tile(St0, T, ldt, n, ti, tj, aligned && ti + kSB <= n && tj + kSB <= n);
+        cp_async_commit();
+    }
     for (int step = 0; step < s; ++step) {
+        float *St = (step & 1) ? St1 : St0;
+        if (step + 1 < s) {                        // prefetch the next tile
+            const int cb = fwd ? step + 1 : nb - 2 - step;
+            int ti, tj;
+            tile_origin(cb, ti, tj);
+            stage_tile((step & 1) ? St0 : St1, T, ldt, n, ti, tj, aligned && ti + kSB <= n && tj + kSB <= n);
+        }
+        cp_async_commit();
         const int cb = fwd ? step : nb - 1 - step;
         const int c0 = cb * kSB, cbk = min(kSB, n - c0);
         if (tid == 0) {
@@ -96,49 +159,40 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const floa
             long long it = 0;
             while (*f == 0 && it < kFlagSpin) {
                 ++it;
-                if (it > 32) __nanosleep(32);
+                if (it > 64) __nanosleep(20);
             }
             if (it >= kFlagSpin) atomicExch(&g_trsv_status, CF_ERR_TIMEOUT);
             __threadfence();
         }
         __syncthreads();
-        for (int e = tid; e < kSB * kSB; e += 256) {
-            // coalesced along the stored matrix's columns in both layouts
-            const int ii = (MODE == 3) ? e / kSB : e % kSB, kk = (MODE == 3) ? e % kSB : e / kSB;
-            Ts[ii][kk] = (ii < rb && kk < cbk) ? m_elem<MODE>(T, ldt, r0 + ii, c0 + kk) : 0.f;
-        }
         for (int e = tid; e < kSB * NR; e += 256) {
             const int kk = e % kSB, c = e / kSB;
-            Ys[kk][c] = (kk < cbk && c < nrhs) ? __ldcg(X + (size_t)(c0 + kk) + (size_t)c * ldx) : 0.f;
+            Ys[kk * YLD + c] = (kk < cbk && c < nrhs) ? __ldcg(X + (size_t)(c0 + kk) + (size_t)c * ldx) : 0.f;
         }
+        cp_async_wait<1>();                        // this step's tile has landed
         __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < kSB; ++kk) {
-            const float m = Ts[i][kk];
+            const float m = (MODE == 3) ? St[i * kTLD + kk] : St[kk * kTLD + i];
 #pragma unroll
-            for (int t = 0; t < CPT; ++t) acc[t] = fmaf(-m, Ys[kk][q + 4 * t], acc[t]);
+            for (int t = 0; t < CPT; ++t) acc[t] = fmaf(-m, Ys[kk * YLD + q + 4 * t], acc[t]);
         }
         __syncthreads();
     }
+    cp_async_wait<0>();
     // y_b = Dinv_b acc
 #pragma unroll
     for (int t = 0; t < CPT; ++t)
-        if (q + 4 * t < NR) Ys[i][q + 4 * t] = acc[t];
-    const float *D = Dinv + (size_t)b * kSB * kSB;
-    for (int e = tid; e < kSB * kSB; e += 256) {
-        const int ii = e % kSB, kk = e / kSB;
-        // MODE 3 uses the inverse of L_bb transposed: (L^T)_bb^{-1} = (L_bb^{-1})^T
-        Ts[ii][kk] = (MODE == 3) ? D[kk + kSB * ii] : D[ii + kSB * kk];
-    }
+        if (q + 4 * t < NR) Ys[i * YLD + q + 4 * t] = acc[t];
     __syncthreads();
     float y[CPT];
 #pragma unroll
     for (int t = 0; t < CPT; ++t) y[t] = 0.f;
 #pragma unroll 8
     for (int kk = 0; kk < kSB; ++kk) {
-        const float d = Ts[i][kk];
+        const float d = Ds[kk * kTLD + i];
 #pragma unroll
-        for (int t = 0; t < CPT; ++t) y[t] = fmaf(d, Ys[kk][q + 4 * t], y[t]);
+        for (int t = 0; t < CPT; ++t) y[t] = fmaf(d, Ys[kk * YLD + q + 4 * t], y[t]);
     }
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
@@ -180,9 +234,17 @@ static int launch_trsv_mode(int n, int nrhs, const float *T, int ldt, const floa
     const int nb = (n + kSB - 1) / kSB;
     CF_CUDA_TRY(cudaMemsetAsync(sync_ws, 0, sizeof(int) * (size_t)(nb + 1), st));
     int *flags = sync_ws, *ticket = sync_ws + nb;
-    if (nrhs <= 4) k_trsv_blocked<MODE, 4><<<nb, 256, 0, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
-    else if (nrhs <= 8) k_trsv_blocked<MODE, 8><<<nb, 256, 0, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
-    else k_trsv_blocked<MODE, 16><<<nb, 256, 0, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    const size_t smem = sizeof(float) * (3 * (size_t)kSB * kTLD + (size_t)kSB * 17);
+    if (nrhs <= 4) {
+        CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<MODE, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_trsv_blocked<MODE, 4><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    } else if (nrhs <= 8) {
+        CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<MODE, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_trsv_blocked<MODE, 8><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    } else {
+        CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<MODE, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_trsv_blocked<MODE, 16><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    }
     CF_LAUNCH_CHECK();
     return CF_OK;
 }

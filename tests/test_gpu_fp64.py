@@ -296,3 +296,18 @@ def test_config_n2048_lu_and_cholesky(cf):
     assert int(info.item()) == 0
     assert np.abs(L - Lo).max() <= 1e-12 * np.abs(Lo).max()
     assert oracle.chol_residual(S, L) <= 20.0
+
+
+def test_residual_pair_accuracy(cf):
+    """cf_residual_pair (FP32-pipe residual) against the compensated oracle
+    residual: error below 2e-14 of ||A|| ||x|| + ||b|| (its documented floor is
+    ~2^-48 times a row's largest partial sums)."""
+    for n, nrhs in ((129, 3), (1000, 8), (2000, 17)):
+        A = inputs.uniform_pm1(n, seed=n, shift=2 * np.sqrt(n))
+        rng = np.random.default_rng(n)
+        X = np.asfortranarray(rng.standard_normal((n, nrhs)) * 0.1)
+        B = np.asfortranarray(A @ X + 1e-12 * rng.standard_normal((n, nrhs)))
+        Ro = oracle.residual(A, X, B)
+        Rp = _host(cf.residual_pair(_dev(A), _dev(X), _dev(B)))
+        den = np.abs(A).sum(1).max() * np.abs(X).max(0) + np.abs(B).max(0)
+        assert (np.abs(Rp - Ro).max(0) / den).max() <= 2e-14
