@@ -216,6 +216,53 @@ int cf_schur_update_lp(int m, int n, int k, const void *A_lp, int lda_k,
 int cf_device_status(cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * BAT-1  Batched uneven factorizations in one persistent launch (north star;
+ * the paper's small-N regime, Sec. 9).  All per-matrix arguments are DEVICE
+ * arrays of length batch: n[i] (0 <= n[i] <= 512), lda[i], A[i] (device
+ * pointer to an n x n column-major matrix), ipiv[i] (device int[n[i]]),
+ * info[i].  kind[i] = 0 for LU (tournament rule with one leaf per panel, i.e.
+ * partial pivoting, block size min(v, 32)), 1 for Cholesky (lower); kind ==
+ * NULL means every matrix has default_kind.  One CTA factors one matrix at a
+ * time; matrices are taken longest-first (decreasing n).  info[i] = -1 for
+ * n[i] > 512.  Capturable in a CUDA graph (no host synchronisation).
+ * ------------------------------------------------------------------------ */
+size_t cf_factor_batched_workspace_size(int batch);
+int cf_factor_batched(int batch, const int *kind, int default_kind,
+                      const int *n, double *const *A, const int *lda,
+                      int *const *ipiv, int *info, void *work, size_t lwork,
+                      const cf_options *opt, cudaStream_t stream);
+size_t cf_getrf_batched_workspace_size(int batch);
+int cf_getrf_batched(int batch, const int *n, double *const *A,
+                     const int *lda, int *const *ipiv, int *info, void *work,
+                     size_t lwork, const cf_options *opt, cudaStream_t stream);
+size_t cf_potrf_batched_workspace_size(int batch);
+int cf_potrf_batched(int batch, const int *n, double *const *A,
+                     const int *lda, int *info, void *work, size_t lwork,
+                     const cf_options *opt, cudaStream_t stream);
+
+/* Batched mixed-precision solve A_i x_i = b_i (one right-hand side each):
+ * each matrix is factored in FP32 (same rule as above) in the CTA's own
+ * scratch and its solution refined in FP64 (residual b - A x in FP64,
+ * eta = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf)) until
+ * eta <= opt->tol.  If the FP32 factorization breaks down, or eta does not
+ * at least halve in one step, or opt->max_iter steps pass, that matrix is
+ * refactored in FP64 and refined on (at most opt->max_iter more steps), the
+ * per-matrix form of LAPACK dsgesv's fallback.  All in one launch.
+ * A_i, b_i are not modified; X[i] (device double[n[i]]) receives x_i;
+ * iters[i], eta[i] (device) the refinement steps and final backward error
+ * (eta[i] > tol means not converged); info[i] = k > 0 if the FP64
+ * factorization met a zero (LU) or non-positive (Cholesky) pivot at step k,
+ * -1 if n[i] > 512.  solver (device, may be NULL): 32 or 64, the precision
+ * of the factors that produced x_i. */
+size_t cf_solve_batched_mixed_workspace_size(int batch);
+int cf_solve_batched_mixed(int batch, const int *kind, int default_kind,
+                           const int *n, const double *const *A,
+                           const int *lda, const double *const *B,
+                           double *const *X, int *info, int *iters,
+                           double *eta, int *solver, void *work, size_t lwork,
+                           const cf_options *opt, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Mixed-precision refined solves (north star; the paper cites GPU mixed
  * LU + refinement as related work, Sec. 11).  A and B are never modified.
  * cf_posv_mixed factors the lower triangle but forms residuals with all of

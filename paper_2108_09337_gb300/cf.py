@@ -77,6 +77,14 @@ _SIG = {
     "cf_residual_pair": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _S, _P]),
     "cf_schur_update_lp": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
     "cf_device_status": (_I, [_P]),
+    "cf_factor_batched_workspace_size": (_S, [_I]),
+    "cf_factor_batched": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P, _S, _OPT, _P]),
+    "cf_getrf_batched_workspace_size": (_S, [_I]),
+    "cf_getrf_batched": (_I, [_I, _P, _P, _P, _P, _P, _P, _S, _OPT, _P]),
+    "cf_potrf_batched_workspace_size": (_S, [_I]),
+    "cf_potrf_batched": (_I, [_I, _P, _P, _P, _P, _P, _S, _OPT, _P]),
+    "cf_solve_batched_mixed_workspace_size": (_S, [_I]),
+    "cf_solve_batched_mixed": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _S, _OPT, _P]),
     "cf_gesv_mixed_workspace_size": (_S, [_I, _I, _I, _OPT]),
     "cf_gesv_mixed": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _P, ctypes.POINTER(RefineStats),
                            _P, _S, _OPT, _P]),
@@ -314,6 +322,83 @@ def gesv_mixed_workspace_size(n, nrhs, prec="bf16", **opt_kw):
 def posv_mixed_workspace_size(n, nrhs, prec="bf16", **opt_kw):
     opt = options(**opt_kw)
     return _lib.cf_posv_mixed_workspace_size(n, nrhs, PREC[prec], ctypes.byref(opt))
+
+
+class Batch:
+    """A batch of column-major matrices packed in one device buffer, with the
+    device pointer / size arrays the batched C entry points take."""
+
+    def __init__(self, sizes, device="cuda", dtype=torch.float64, kinds=None):
+        self.sizes = [int(x) for x in sizes]
+        offs, o = [], 0
+        for n in self.sizes:
+            offs.append(o)
+            o += max(n * n, 1)
+            o = (o + 31) // 32 * 32          # 256-byte alignment of every matrix
+        self.offsets = offs
+        self.data = torch.zeros(max(o, 1), dtype=dtype, device=device)
+        el = self.data.element_size()
+        base = self.data.data_ptr()
+        self.n = torch.tensor(self.sizes, dtype=torch.int32, device=device)
+        self.lda = torch.tensor([max(n, 1) for n in self.sizes], dtype=torch.int32, device=device)
+        self.ptrs = torch.tensor([base + el * q for q in offs], dtype=torch.int64, device=device)
+        self.kind = None if kinds is None else torch.tensor(list(kinds), dtype=torch.int32, device=device)
+        po, p = [], 0
+        for n in self.sizes:
+            po.append(p)
+            p += max(n, 1)
+        self.vec_offsets = po
+        self.vec_total = max(p, 1)
+
+    def matrix(self, i):
+        n = self.sizes[i]
+        return self.data[self.offsets[i]:self.offsets[i] + n * n].view(n, n).t()
+
+    def vec_ptrs(self, buf):
+        el = buf.element_size()
+        return torch.tensor([buf.data_ptr() + el * q for q in self.vec_offsets], dtype=torch.int64,
+                            device=buf.device)
+
+
+def factor_batched(batch: "Batch", default_kind=0, v=None, work=None):
+    """In-place FP64 LU / Cholesky of every matrix (cf_factor_batched).
+    Returns (ipiv buffer, ipiv pointer array, info)."""
+    nb = len(batch.sizes)
+    ipiv = torch.zeros(batch.vec_total, dtype=torch.int32, device=batch.data.device)
+    iptr = batch.vec_ptrs(ipiv)
+    info = torch.zeros(max(nb, 1), dtype=torch.int32, device=batch.data.device)
+    opt = options(v=v)
+    ws = work if work is not None else _workspace(_lib.cf_factor_batched_workspace_size(nb), batch.data.device)
+    kind = _ptr(batch.kind) if batch.kind is not None else ctypes.c_void_p(0)
+    _check("cf_factor_batched", _lib.cf_factor_batched(nb, kind, default_kind, _ptr(batch.n), _ptr(batch.ptrs),
+                                                       _ptr(batch.lda), _ptr(iptr), _ptr(info), _ptr(ws),
+                                                       ws.numel(), ctypes.byref(opt), _stream()))
+    return ipiv, iptr, info
+
+
+def solve_batched_mixed(batch: "Batch", B: torch.Tensor, default_kind=0, tol=None, max_iter=None, work=None):
+    """FP32 factors + FP64 refinement for every A_i x_i = b_i
+    (cf_solve_batched_mixed); B packed like batch.vec_offsets.  Returns
+    (X, info, iters, eta, solver), solver[i] = 32 or 64 (the precision of
+    the factors that produced x_i)."""
+    nb = len(batch.sizes)
+    dev = batch.data.device
+    X = torch.zeros(batch.vec_total, dtype=torch.float64, device=dev)
+    info = torch.zeros(max(nb, 1), dtype=torch.int32, device=dev)
+    iters = torch.zeros(max(nb, 1), dtype=torch.int32, device=dev)
+    eta = torch.zeros(max(nb, 1), dtype=torch.float64, device=dev)
+    solver = torch.zeros(max(nb, 1), dtype=torch.int32, device=dev)
+    opt = options(tol=tol, max_iter=max_iter)
+    ws = work if work is not None else _workspace(_lib.cf_solve_batched_mixed_workspace_size(nb), dev)
+    kind = _ptr(batch.kind) if batch.kind is not None else ctypes.c_void_p(0)
+    bptr = batch.vec_ptrs(B)      # keep the pointer arrays alive across the call
+    xptr = batch.vec_ptrs(X)
+    _check("cf_solve_batched_mixed",
+           _lib.cf_solve_batched_mixed(nb, kind, default_kind, _ptr(batch.n), _ptr(batch.ptrs), _ptr(batch.lda),
+                                       _ptr(bptr), _ptr(xptr), _ptr(info), _ptr(iters), _ptr(eta), _ptr(solver),
+                                       _ptr(ws), ws.numel(), ctypes.byref(opt), _stream()))
+    torch.cuda.current_stream().synchronize()
+    return X, info, iters, eta, solver
 
 
 def kernel_launches() -> int:

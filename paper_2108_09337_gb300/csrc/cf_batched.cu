@@ -1,0 +1,724 @@
+// cf_batched.cu -- BAT-1: thousands of independent, uneven factorizations in
+// one persistent launch (north star; the paper's small-N motivation is its
+// Sec. 9.3 discussion of small matrices on many nodes).
+//
+// One CTA factors one matrix at a time.  CTAs pull matrix indices from an
+// atomic queue ordered by decreasing n^3 (longest processing time first), so
+// the few large matrices start early and the many small ones fill the tail.
+// Each matrix uses the same blocked algorithm as cf_getrf / cf_potrf (Alg. 1
+// with block size vb; the tournament with one leaf covering the panel, i.e.
+// leaf height >= n, which is partial pivoting), run by one CTA out of L2:
+// the panel copy for the pivot search and the diagonal block live in shared
+// memory, the trailing update streams through registers.  Matrices up to
+// n = 512 (the panel copy is 512 x vb).
+//
+// The mixed variant (cf_solve_batched_mixed) factors an FP32 copy held in
+// the CTA's own scratch and refines each solution in FP64 to the tolerance
+// (falling back to FP64 factors for a matrix the FP32 ones cannot serve),
+// all inside the same launch; nothing returns to the host between matrices,
+// so the whole batch can be captured in a CUDA graph.
+#include <climits>
+#include <cmath>
+
+#include "cf_common.cuh"
+#include "cf_kernels.cuh"
+
+namespace cf {
+
+constexpr int kBT = 256;                // threads per CTA
+constexpr int kBMaxN = 512;             // largest matrix
+constexpr int kBMaxV = 32;              // largest block size
+
+template <typename T>
+struct BSmem {
+    T P[kBMaxN * kBMaxV];               // panel copy (pivot search) / L10 block
+    T D[kBMaxV * (kBMaxV + 1)];         // diagonal block
+    T redv[kBT / 32];
+    int redi[kBT / 32];
+    int used[kBMaxN];
+    int order[kBMaxV];
+    int lab[kBMaxN];
+    int where_[kBMaxN];
+    int fail;
+};
+
+template <typename T>
+__device__ __forceinline__ T bkey(T a) {
+    T x = fabs(a);
+    return (x != x) ? T(-0.5) : x;
+}
+
+template <typename T>
+__device__ __forceinline__ void bbetter(T &bv, int &bi, T ov, int oi) {
+    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+}
+
+// CTA-wide argmax (value, index) with the tie rule of the tournament.
+template <typename T>
+__device__ void cta_argmax(BSmem<T> &s, T &bv, int &bi) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        bbetter(bv, bi, ov, oi);
+    }
+    if (lane == 0) { s.redv[warp] = bv; s.redi[warp] = bi; }
+    __syncthreads();
+    bv = s.redv[0];
+    bi = s.redi[0];
+#pragma unroll
+    for (int q = 1; q < kBT / 32; ++q) bbetter(bv, bi, s.redv[q], s.redi[q]);
+    __syncthreads();
+}
+
+// C (mm x nn, ldc) -= A (mm x kk, lda) * B (kk x nn, ldb), kk <= kBMaxV; if
+// lower, only i >= j (relative indices, diagonal aligned).  A may be shared.
+template <typename T>
+__device__ void cta_gemm_sub(int mm, int nn, int kk, const T *A, int lda, const T *B, int ldb, T *C, int ldc,
+                             bool lower) {
+    const int tid = threadIdx.x;
+    const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;      // 64 x 64 tiles, 4 x 4 per thread
+    for (int j0 = 0; j0 < nn; j0 += 64) {
+        for (int i0 = 0; i0 < mm; i0 += 64) {
+            if (lower && j0 > i0 + 63) continue;
+            T acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+            for (int p = 0; p < kk; ++p) {
+                T av[4], bv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int i = i0 + tr + a;
+                    av[a] = i < mm ? A[(size_t)i + (size_t)p * lda] : T(0);
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int j = j0 + tc + b;
+                    bv[b] = j < nn ? B[(size_t)p + (size_t)j * ldb] : T(0);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int j = j0 + tc + b;
+                if (j >= nn) continue;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int i = i0 + tr + a;
+                    if (i >= mm || (lower && i < j)) continue;
+                    T *c = C + (size_t)i + (size_t)j * ldc;
+                    *c = *c - acc[a][b];
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// In-place LU of one n x n matrix (n <= kBMaxN) with the pivot rule of the
+// tournament for a single leaf (partial pivoting, ties to the smallest
+// position), block size vb.  Same step structure as cf_getrf.
+template <typename T>
+__device__ void cta_getrf(BSmem<T> &s, T *A, int n, int lda, int *ipiv, int *info, int vb) {
+    const int tid = threadIdx.x;
+    for (int k0 = 0; k0 < n; k0 += vb) {
+        const int w = min(vb, n - k0), m = n - k0;
+        T *A00 = A + k0 + (size_t)k0 * lda;
+        // ---- LU-1: partial-pivoting selection on a copy of the panel
+        for (int e = tid; e < m * w; e += kBT) {
+            const int r = e % m, c = e / m;
+            s.P[c * m + r] = A00[r + (size_t)c * lda];
+        }
+        for (int r = tid; r < m; r += kBT) s.used[r] = 0;
+        __syncthreads();
+        for (int j = 0; j < w; ++j) {
+            T bv = T(-1);
+            int bi = INT_MAX;
+            for (int r = tid; r < m; r += kBT)
+                if (!s.used[r]) bbetter(bv, bi, bkey(s.P[j * m + r]), r);
+            cta_argmax(s, bv, bi);
+            if (tid == 0) { s.order[j] = bi; s.used[bi] = 1; }
+            __syncthreads();
+            const T piv = s.P[j * m + bi];
+            if (piv != T(0)) {
+                for (int r = tid; r < m; r += kBT) {
+                    if (s.used[r]) continue;
+                    const T l = s.P[j * m + r] / piv;
+                    for (int c = j + 1; c < w; ++c) s.P[c * m + r] = s.P[c * m + r] - l * s.P[c * m + bi];
+                }
+            }
+            __syncthreads();
+        }
+        // ---- LU-2: interchanges (positions of the winners, as cf_getrf)
+        if (tid == 0) {
+            for (int r = 0; r < m; ++r) { s.lab[r] = r; s.where_[r] = r; }
+            for (int j = 0; j < w; ++j) {
+                const int lab = s.order[j], p = s.where_[lab];
+                ipiv[k0 + j] = k0 + p + 1;
+                if (p != j) {
+                    const int lj = s.lab[j];
+                    s.lab[j] = lab; s.where_[lab] = j;
+                    s.lab[p] = lj;  s.where_[lj] = p;
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = tid; c < n; c += kBT) {
+            T *col = A + (size_t)c * lda;
+            for (int j = 0; j < w; ++j) {
+                const int p = ipiv[k0 + j] - 1;
+                if (p != k0 + j) { const T t = col[k0 + j]; col[k0 + j] = col[p]; col[p] = t; }
+            }
+        }
+        __syncthreads();
+        // ---- A00 = L00 U00 (no pivoting) in shared memory
+        for (int e = tid; e < w * w; e += kBT) {
+            const int r = e % w, c = e / w;
+            s.D[c * (kBMaxV + 1) + r] = A00[r + (size_t)c * lda];
+        }
+        __syncthreads();
+        for (int k = 0; k < w; ++k) {
+            const T piv = s.D[k * (kBMaxV + 1) + k];
+            if (piv == T(0) && tid == 0) atomicCAS(info, 0, k0 + k + 1);
+            __syncthreads();
+            for (int e = tid; e < (w - k - 1); e += kBT) {
+                const int r = k + 1 + e;
+                if (piv != T(0)) s.D[k * (kBMaxV + 1) + r] = s.D[k * (kBMaxV + 1) + r] / piv;
+            }
+            __syncthreads();
+            const int rem = w - k - 1;
+            for (int e = tid; e < rem * rem; e += kBT) {
+                const int r = k + 1 + e % rem, c = k + 1 + e / rem;
+                s.D[c * (kBMaxV + 1) + r] -= s.D[k * (kBMaxV + 1) + r] * s.D[c * (kBMaxV + 1) + k];
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < w * w; e += kBT) {
+            const int r = e % w, c = e / w;
+            A00[r + (size_t)c * lda] = s.D[c * (kBMaxV + 1) + r];
+        }
+        // ---- LU-3: A10 <- A10 U00^{-1} (one row per thread)
+        for (int r = w + tid; r < m; r += kBT) {
+            T *row = A00 + r;
+            for (int k = 0; k < w; ++k) {
+                const T ukk = s.D[k * (kBMaxV + 1) + k];
+                T x = row[(size_t)k * lda];
+                if (ukk != T(0)) x = x / ukk;
+                row[(size_t)k * lda] = x;
+                for (int j = k + 1; j < w; ++j) row[(size_t)j * lda] -= x * s.D[j * (kBMaxV + 1) + k];
+            }
+        }
+        // ---- LU-4: A01 <- L00^{-1} A01 (one column per thread)
+        for (int c = w + tid; c < m; c += kBT) {
+            T *col = A00 + (size_t)c * lda;
+            for (int k = 0; k < w; ++k) {
+                const T xk = col[k];
+                for (int i = k + 1; i < w; ++i) col[i] -= s.D[k * (kBMaxV + 1) + i] * xk;
+            }
+        }
+        __syncthreads();
+        // ---- LU-5: A11 <- A11 - A10 A01
+        if (m > w) cta_gemm_sub<T>(m - w, m - w, w, A00 + w, lda, A00 + (size_t)w * lda, lda,
+                                   A00 + w + (size_t)w * lda, lda, false);
+        __syncthreads();
+    }
+}
+
+// In-place Cholesky (lower) of one matrix, block size vb.  Returns nonzero
+// (and sets *info) on a non-positive pivot.
+template <typename T>
+__device__ int cta_potrf(BSmem<T> &s, T *A, int n, int lda, int *info, int vb) {
+    const int tid = threadIdx.x;
+    if (tid == 0) s.fail = 0;
+    __syncthreads();
+    for (int k0 = 0; k0 < n; k0 += vb) {
+        const int w = min(vb, n - k0), m = n - k0;
+        T *A00 = A + k0 + (size_t)k0 * lda;
+        for (int e = tid; e < w * w; e += kBT) {
+            const int r = e % w, c = e / w;
+            if (r >= c) s.D[c * (kBMaxV + 1) + r] = A00[r + (size_t)c * lda];
+        }
+        __syncthreads();
+        for (int k = 0; k < w; ++k) {
+            const T d = s.D[k * (kBMaxV + 1) + k];
+            if (!(d > T(0))) {
+                if (tid == 0) { s.fail = 1; atomicCAS(info, 0, k0 + k + 1); }
+                __syncthreads();
+                return 1;
+            }
+            const T lkk = sqrt(d);
+            __syncthreads();
+            if (tid == 0) s.D[k * (kBMaxV + 1) + k] = lkk;
+            for (int r = k + 1 + tid; r < w; r += kBT) s.D[k * (kBMaxV + 1) + r] /= lkk;
+            __syncthreads();
+            const int rem = w - k - 1;
+            for (int e = tid; e < rem * rem; e += kBT) {
+                const int r = k + 1 + e % rem, c = k + 1 + e / rem;
+                if (r >= c) s.D[c * (kBMaxV + 1) + r] -= s.D[k * (kBMaxV + 1) + r] * s.D[k * (kBMaxV + 1) + c];
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < w * w; e += kBT) {
+            const int r = e % w, c = e / w;
+            if (r >= c) A00[r + (size_t)c * lda] = s.D[c * (kBMaxV + 1) + r];
+        }
+        // CH-2: L10 <- A10 L00^{-T} (one row per thread)
+        for (int r = w + tid; r < m; r += kBT) {
+            T *row = A00 + r;
+            for (int k = 0; k < w; ++k) {
+                T x = row[(size_t)k * lda] / s.D[k * (kBMaxV + 1) + k];
+                row[(size_t)k * lda] = x;
+                for (int j = k + 1; j < w; ++j) row[(size_t)j * lda] -= x * s.D[k * (kBMaxV + 1) + j];
+            }
+        }
+        __syncthreads();
+        // CH-3: A11 <- A11 - L10 L10^T (lower); B operand = L10^T read from A
+        if (m > w) {
+            // stage L10^T? read directly: B(p, j) = L10(j, p) = A00[w + j + p*lda]
+            const int mm = m - w;
+            T *C = A00 + w + (size_t)w * lda;
+            const int tr = (tid & 15) * 4, tc = (tid >> 4) * 4;
+            for (int j0 = 0; j0 < mm; j0 += 64)
+                for (int i0 = j0; i0 < mm; i0 += 64) {
+                    T acc[4][4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+                    for (int p = 0; p < w; ++p) {
+                        T av[4], bv[4];
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const int i = i0 + tr + a;
+                            av[a] = i < mm ? A00[w + i + (size_t)p * lda] : T(0);
+                        }
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int j = j0 + tc + b;
+                            bv[b] = j < mm ? A00[w + j + (size_t)p * lda] : T(0);
+                        }
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int j = j0 + tc + b;
+                        if (j >= mm) continue;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const int i = i0 + tr + a;
+                            if (i >= mm || i < j) continue;
+                            C[(size_t)i + (size_t)j * lda] -= acc[a][b];
+                        }
+                    }
+                }
+        }
+        __syncthreads();
+    }
+    return 0;
+}
+
+// Per-CTA scratch of the mixed solve: the n x n factors (FP64 room), r, d
+// and the pivots, rounded to 1 KiB.
+__host__ __device__ constexpr size_t batched_scratch_bytes_per_cta() {
+    return ((sizeof(double) * ((size_t)kBMaxN * kBMaxN + 2 * kBMaxN) + sizeof(int) * kBMaxN) + 1023) / 1024 * 1024;
+}
+
+struct BatchArgs {
+    int batch;
+    const int *kind;          // per matrix: 0 LU, 1 Cholesky (null: all default_kind)
+    int default_kind;
+    const int *n;
+    const int *lda;
+    double *const *A;
+    int *const *ipiv;         // LU only (may be null for all-Cholesky batches)
+    int *info;
+    const int *order;         // processing order
+    int *queue;               // atomic counter, zero before the launch
+    int vb;
+    // mixed solve
+    const double *const *B;
+    double *const *X;
+    int *iters;
+    double *eta;
+    int *solver;              // optional: 32 or 64, precision of the factors used
+    double *scratch;          // per CTA: batched_scratch_bytes_per_cta()
+    double tol;
+    int max_iter;
+};
+
+// ---------------------------------------------------------------------------
+// FP64 factorizations in place.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBT, 1) k_factor_batched(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BSmem<double> &s = *reinterpret_cast<BSmem<double> *>(smem_raw);
+    __shared__ int s_idx;
+    while (true) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int q = s_idx;
+        __syncthreads();
+        if (q >= a.batch) return;
+        const int i = a.order ? a.order[q] : q;
+        const int n = a.n[i];
+        const int kind = a.kind ? a.kind[i] : a.default_kind;
+        if (threadIdx.x == 0) a.info[i] = 0;
+        __syncthreads();
+        if (n <= 0 || n > kBMaxN) {
+            if (threadIdx.x == 0 && n > kBMaxN) a.info[i] = -1;
+            continue;
+        }
+        if (kind == 0) cta_getrf<double>(s, a.A[i], n, a.lda[i], a.ipiv[i], a.info + i, a.vb);
+        else cta_potrf<double>(s, a.A[i], n, a.lda[i], a.info + i, a.vb);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed solve per matrix: FP32 factors in the CTA's scratch, FP64 refinement;
+// if the FP32 factors cannot bring eta to the tolerance (factorization
+// breakdown, contraction of eta slower than 1/2 per step, or max_iter), the
+// matrix is refactored in FP64 in the same scratch and refinement continues
+// from the current iterate (the fallback of LAPACK's dsgesv, per matrix).
+// ---------------------------------------------------------------------------
+__device__ double cta_max(double v, double *s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    v = s_red[0];
+#pragma unroll
+    for (int q = 1; q < kBT / 32; ++q) v = fmax(v, s_red[q]);
+    __syncthreads();
+    return v;
+}
+
+// r = b - A x (FP64, one row per thread); returns the componentwise-normwise
+// backward error ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf).
+__device__ double cta_residual_eta(int n, const double *A, int lda, const double *b, const double *x, double *r,
+                                   double an, double bn, double *s_red) {
+    const int tid = threadIdx.x;
+    double rn = 0.0, xn = 0.0;
+    for (int row = tid; row < n; row += kBT) {
+        double sum = 0.0;
+        for (int c = 0; c < n; ++c) sum = fma(A[(size_t)row + (size_t)c * lda], x[c], sum);
+        r[row] = b[row] - sum;
+        rn = fmax(rn, fabs(r[row]));
+    }
+    for (int row = tid; row < n; row += kBT) xn = fmax(xn, fabs(x[row]));
+    rn = cta_max(rn, s_red);
+    xn = cta_max(xn, s_red);
+    const double den = an * xn + bn;
+    if (rn != rn) return rn;                       // NaN stays NaN (never converged)
+    return den > 0.0 ? rn / den : (rn > 0.0 ? 1.0 : 0.0);
+}
+
+// x += (P^T L U)^{-1} r (kind 0) or (L L^T)^{-1} r (kind 1), the solve in the
+// factor precision T on r scaled by 1/||r||_inf; serial substitution with the
+// inner updates spread over the CTA.
+template <typename T>
+__device__ void cta_correct(int kind, int n, const T *W, const int *piv, const double *r, T *d, double *x,
+                            double *s_red) {
+    const int tid = threadIdx.x;
+    double rn = 0.0;
+    for (int row = tid; row < n; row += kBT) rn = fmax(rn, fabs(r[row]));
+    rn = cta_max(rn, s_red);
+    const double sc = rn > 0.0 ? rn : 1.0;
+    for (int row = tid; row < n; row += kBT) d[row] = (T)(r[row] / sc);
+    __syncthreads();
+    if (kind == 0 && tid == 0) {
+        for (int j = 0; j < n; ++j) {                // row interchanges, in order
+            const int p = piv[j] - 1;
+            if (p != j) { const T t = d[j]; d[j] = d[p]; d[p] = t; }
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {                    // L y = d (unit diagonal for LU)
+        if (kind == 1 && tid == 0) d[k] = d[k] / W[k + (size_t)k * n];
+        __syncthreads();
+        const T dk = d[k];
+        for (int row = k + 1 + tid; row < n; row += kBT) d[row] = fma(-W[row + (size_t)k * n], dk, d[row]);
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {               // U z = y (LU) or L^T z = y (Cholesky)
+        if (tid == 0) d[k] = d[k] / W[k + (size_t)k * n];
+        __syncthreads();
+        const T dk = d[k];
+        for (int row = tid; row < k; row += kBT) {
+            const T u = (kind == 0) ? W[row + (size_t)k * n] : W[k + (size_t)row * n];
+            d[row] = fma(-u, dk, d[row]);
+        }
+        __syncthreads();
+    }
+    for (int row = tid; row < n; row += kBT) x[row] += sc * (double)d[row];
+    __syncthreads();
+}
+
+// Factors fl_T(A) into W (ld n).  Returns nonzero on breakdown; *info gets
+// the first bad pivot (1-based) as the FP64 routines report it.
+template <typename T>
+__device__ int cta_factor_copy(unsigned char *smem_raw, int kind, int n, const double *A, int lda, T *W, int *piv,
+                               int *info, int vb) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < n * n; e += kBT) W[e] = (T)A[(size_t)(e % n) + (size_t)(e / n) * lda];
+    if (tid == 0) *info = 0;
+    __syncthreads();
+    BSmem<T> &s = *reinterpret_cast<BSmem<T> *>(smem_raw);
+    int fail = 0;
+    if (kind == 0) cta_getrf<T>(s, W, n, n, piv, info, vb);
+    else fail = cta_potrf<T>(s, W, n, n, info, vb);
+    __syncthreads();
+    return fail || *info != 0;
+}
+
+// Refinement steps with factors W until eta <= tol (returns 0), it reaches
+// it_end, or eta fails to halve in one step (returns 1).  r and eta hold the
+// residual of x on entry and on exit.
+template <typename T>
+__device__ int cta_refine(int kind, int n, const double *A, int lda, const double *b, double *x, const T *W,
+                          const int *piv, double *r, T *d, double an, double bn, double tol, int &it, int it_end,
+                          double &eta, double *s_red) {
+    double prev = -1.0;
+    while (true) {
+        if (eta <= tol) return 0;
+        if (it >= it_end) return 1;
+        if (prev >= 0.0 && !(eta <= 0.5 * prev)) return 1;      // stalled (or NaN)
+        cta_correct<T>(kind, n, W, piv, r, d, x, s_red);
+        ++it;
+        prev = eta;
+        eta = cta_residual_eta(n, A, lda, b, x, r, an, bn, s_red);
+    }
+}
+
+__global__ void __launch_bounds__(kBT, 1) k_solve_batched_mixed(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_idx;
+    __shared__ int s_info;
+    __shared__ double s_red[kBT / 32];
+    unsigned char *base = reinterpret_cast<unsigned char *>(a.scratch) + batched_scratch_bytes_per_cta() * blockIdx.x;
+    void *W = base;                                                          // n x n, FP32 or FP64
+    double *r = reinterpret_cast<double *>(base + sizeof(double) * kBMaxN * kBMaxN);
+    void *d = r + kBMaxN;                                                    // kBMaxN of FP32 or FP64
+    int *piv = reinterpret_cast<int *>(r + 2 * kBMaxN);
+    const int tid = threadIdx.x;
+    while (true) {
+        if (tid == 0) s_idx = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int q = s_idx;
+        __syncthreads();
+        if (q >= a.batch) return;
+        const int i = a.order ? a.order[q] : q;
+        const int n = a.n[i], lda = a.lda[i];
+        const int kind = a.kind ? a.kind[i] : a.default_kind;
+        const double *A = a.A[i];
+        const double *b = a.B[i];
+        double *x = a.X[i];
+        if (tid == 0) {
+            a.info[i] = 0; a.iters[i] = 0; a.eta[i] = 0.0;
+            if (a.solver) a.solver[i] = 32;
+        }
+        __syncthreads();
+        if (n <= 0 || n > kBMaxN) {
+            if (tid == 0 && n > kBMaxN) a.info[i] = -1;
+            continue;
+        }
+        // ||A||_inf and ||b||_inf
+        double an = 0.0, bn = 0.0;
+        for (int row = tid; row < n; row += kBT) {
+            double sum = 0.0;
+            for (int c = 0; c < n; ++c) sum += fabs(A[(size_t)row + (size_t)c * lda]);
+            an = fmax(an, sum);
+            bn = fmax(bn, fabs(b[row]));
+        }
+        an = cta_max(an, s_red);
+        bn = cta_max(bn, s_red);
+        for (int row = tid; row < n; row += kBT) x[row] = 0.0;
+        __syncthreads();
+        double eta = cta_residual_eta(n, A, lda, b, x, r, an, bn, s_red);
+        int it = 0;
+        int bad = cta_factor_copy<float>(smem_raw, kind, n, A, lda, static_cast<float *>(W), piv, &s_info, a.vb);
+        if (!bad)
+            bad = cta_refine<float>(kind, n, A, lda, b, x, static_cast<const float *>(W), piv, r,
+                                    static_cast<float *>(d), an, bn, a.tol, it, a.max_iter, eta, s_red);
+        if (bad) {
+            // FP64 factors; refinement resumes from the current iterate unless
+            // it is not finite
+            if (tid == 0 && a.solver) a.solver[i] = 64;
+            if (!(eta < 1.0)) {
+                for (int row = tid; row < n; row += kBT) x[row] = 0.0;
+                __syncthreads();
+                eta = cta_residual_eta(n, A, lda, b, x, r, an, bn, s_red);
+            }
+            if (cta_factor_copy<double>(smem_raw, kind, n, A, lda, static_cast<double *>(W), piv, &s_info, a.vb)) {
+                if (tid == 0) a.info[i] = s_info;
+            } else {
+                cta_refine<double>(kind, n, A, lda, b, x, static_cast<const double *>(W), piv, r,
+                                   static_cast<double *>(d), an, bn, a.tol, it, it + a.max_iter, eta, s_red);
+            }
+        }
+        if (tid == 0) { a.iters[i] = it; a.eta[i] = eta; }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: LPT order (sort by decreasing n, counting sort over n <= 512)
+// ---------------------------------------------------------------------------
+__global__ void k_lpt_histogram(int batch, const int *n, int *hist) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch; i += gridDim.x * blockDim.x) {
+        int v = n[i];
+        v = v < 0 ? 0 : (v > kBMaxN ? kBMaxN : v);
+        atomicAdd(hist + (kBMaxN - v), 1);           // bucket 0 = largest n
+    }
+}
+
+__global__ void k_lpt_scan(int *hist, int *cursor) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int sum = 0;
+        for (int b = 0; b <= kBMaxN; ++b) { cursor[b] = sum; sum += hist[b]; }
+    }
+}
+
+__global__ void k_lpt_scatter(int batch, const int *n, int *cursor, int *order) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch; i += gridDim.x * blockDim.x) {
+        int v = n[i];
+        v = v < 0 ? 0 : (v > kBMaxN ? kBMaxN : v);
+        order[atomicAdd(cursor + (kBMaxN - v), 1)] = i;
+    }
+}
+
+struct BatchWS {
+    int *order, *queue, *hist, *cursor;
+    double *scratch;
+    size_t bytes;
+};
+
+static int batch_grid(int vb) {
+    (void)vb;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;    // one CTA per SM (the panel copy needs most of the shared memory)
+}
+
+
+static int carve_batch(void *work, int batch, bool mixed, BatchWS *w) {
+    Carver cv(work);
+    w->order = cv.take<int>(batch > 0 ? batch : 1);
+    w->queue = cv.take<int>(1);
+    w->hist = cv.take<int>(kBMaxN + 1);
+    w->cursor = cv.take<int>(kBMaxN + 1);
+    w->scratch = mixed ? cv.take<double>(batched_scratch_bytes_per_cta() / sizeof(double) * batch_grid(32), 1024)
+                       : nullptr;
+    w->bytes = cv.size();
+    return CF_OK;
+}
+
+static int enqueue_order(int batch, const int *n, BatchWS &w, cudaStream_t st) {
+    CF_CUDA_TRY(cudaMemsetAsync(w.hist, 0, sizeof(int) * (kBMaxN + 1), st));
+    CF_CUDA_TRY(cudaMemsetAsync(w.queue, 0, sizeof(int), st));
+    k_lpt_histogram<<<ceil_div(batch, 256) < 1024 ? ceil_div(batch, 256) : 1024, 256, 0, st>>>(batch, n, w.hist);
+    CF_LAUNCH_CHECK();
+    k_lpt_scan<<<1, 32, 0, st>>>(w.hist, w.cursor);
+    CF_LAUNCH_CHECK();
+    k_lpt_scatter<<<ceil_div(batch, 256) < 1024 ? ceil_div(batch, 256) : 1024, 256, 0, st>>>(batch, n, w.cursor,
+                                                                                          w.order);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+}  // namespace cf
+
+using namespace cf;
+
+extern "C" size_t cf_factor_batched_workspace_size(int batch) {
+    BatchWS w{};
+    carve_batch(nullptr, batch, false, &w);
+    return w.bytes;
+}
+
+extern "C" int cf_factor_batched(int batch, const int *kind, int default_kind, const int *n, double *const *A,
+                                 const int *lda, int *const *ipiv, int *info, void *work, size_t lwork,
+                                 const cf_options *opt, cudaStream_t st) {
+    if (batch < 0) return -1;
+    if (default_kind != 0 && default_kind != 1) return -3;
+    if (batch > 0 && (n == nullptr || A == nullptr || lda == nullptr || info == nullptr)) return -4;
+    Opts o;
+    int rc = resolve_options(opt, &o);
+    if (rc) return rc;
+    if (batch == 0) return CF_OK;
+    if (work == nullptr || lwork < cf_factor_batched_workspace_size(batch)) return CF_ERR_WORKSPACE;
+    BatchWS w{};
+    carve_batch(work, batch, false, &w);
+    if ((rc = enqueue_order(batch, n, w, st))) return rc;
+    BatchArgs a{};
+    a.batch = batch; a.kind = kind; a.default_kind = default_kind; a.n = n; a.lda = lda; a.A = A;
+    a.ipiv = ipiv; a.info = info; a.order = w.order; a.queue = w.queue;
+    a.vb = o.v < kBMaxV ? o.v : kBMaxV;
+    const size_t smem = sizeof(BSmem<double>);
+    CF_CUDA_TRY(cudaFuncSetAttribute(k_factor_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_factor_batched<<<batch_grid(a.vb), kBT, smem, st>>>(a);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+extern "C" size_t cf_getrf_batched_workspace_size(int batch) { return cf_factor_batched_workspace_size(batch); }
+extern "C" size_t cf_potrf_batched_workspace_size(int batch) { return cf_factor_batched_workspace_size(batch); }
+
+extern "C" int cf_getrf_batched(int batch, const int *n, double *const *A, const int *lda, int *const *ipiv,
+                                int *info, void *work, size_t lwork, const cf_options *opt, cudaStream_t st) {
+    if (batch > 0 && ipiv == nullptr) return -5;
+    return cf_factor_batched(batch, nullptr, 0, n, A, lda, ipiv, info, work, lwork, opt, st);
+}
+
+extern "C" int cf_potrf_batched(int batch, const int *n, double *const *A, const int *lda, int *info, void *work,
+                                size_t lwork, const cf_options *opt, cudaStream_t st) {
+    return cf_factor_batched(batch, nullptr, 1, n, A, lda, nullptr, info, work, lwork, opt, st);
+}
+
+extern "C" size_t cf_solve_batched_mixed_workspace_size(int batch) {
+    BatchWS w{};
+    carve_batch(nullptr, batch, true, &w);
+    return w.bytes;
+}
+
+extern "C" int cf_solve_batched_mixed(int batch, const int *kind, int default_kind, const int *n,
+                                      const double *const *A, const int *lda, const double *const *B,
+                                      double *const *X, int *info, int *iters, double *eta, int *solver,
+                                      void *work, size_t lwork, const cf_options *opt, cudaStream_t st) {
+    if (batch < 0) return -1;
+    if (default_kind != 0 && default_kind != 1) return -3;
+    if (batch > 0 && (n == nullptr || A == nullptr || lda == nullptr || B == nullptr || X == nullptr ||
+                      info == nullptr || iters == nullptr || eta == nullptr))
+        return -4;
+    Opts o;
+    int rc = resolve_options(opt, &o);
+    if (rc) return rc;
+    if (batch == 0) return CF_OK;
+    if (work == nullptr || lwork < cf_solve_batched_mixed_workspace_size(batch)) return CF_ERR_WORKSPACE;
+    BatchWS w{};
+    carve_batch(work, batch, true, &w);
+    if ((rc = enqueue_order(batch, n, w, st))) return rc;
+    BatchArgs a{};
+    a.batch = batch; a.kind = kind; a.default_kind = default_kind; a.n = n; a.lda = lda;
+    a.A = const_cast<double *const *>(A);
+    a.info = info; a.order = w.order; a.queue = w.queue;
+    a.vb = o.v < kBMaxV ? o.v : kBMaxV;
+    a.B = B; a.X = X; a.iters = iters; a.eta = eta; a.solver = solver; a.scratch = w.scratch;
+    a.tol = o.tol; a.max_iter = o.max_iter;
+    const size_t smem = sizeof(BSmem<double>);      // holds BSmem<float> too
+    CF_CUDA_TRY(cudaFuncSetAttribute(k_solve_batched_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_solve_batched_mixed<<<batch_grid(a.vb), kBT, smem, st>>>(a);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}

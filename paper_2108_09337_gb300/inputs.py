@@ -112,6 +112,23 @@ def integer_l0(n: int, seed: int):
 # --------------------------------------------------------------------------
 # Device-side variants for large n (torch Philox; torch is plumbing here).
 # --------------------------------------------------------------------------
+def prescribed_cond(n: int, cond: float, seed: int, spd: bool = False) -> np.ndarray:
+    """Q1 diag(s) Q2^T with Q1, Q2 Haar-random orthogonal (QR of Gaussian
+    matrices, sign-fixed) and s geometric from 1 down to 1/cond; spd=True
+    takes Q2 = Q1 (symmetric positive definite, condition number cond)."""
+    g = _rng(seed)
+    def haar():
+        q, r = np.linalg.qr(g.standard_normal((n, n)))
+        return q * np.sign(np.diag(r))
+    q1 = haar()
+    q2 = q1 if spd else haar()
+    s = np.geomspace(1.0, 1.0 / cond, n) if n > 1 else np.ones(1)
+    A = (q1 * s) @ q2.T
+    if spd:
+        A = 0.5 * (A + A.T)
+    return np.asfortranarray(A)
+
+
 def uniform_pm1_torch(n: int, seed: int = 0, shift: float = 0.0,
                       device="cuda", dtype=None):
     import torch
