@@ -44,6 +44,7 @@ def _args():
     ap.add_argument("--impl", choices=["cf", "reference"], default="cf")
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--prec", default="bf16", choices=["bf16", "f16"])
+    ap.add_argument("--leaf-h", type=int, default=256, help="tournament leaf height of the mixed LU")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
@@ -188,12 +189,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     ch_fl = n ** 3 / 3.0
 
     A_lu, B_lu, A_ch, B_ch, gen_info = _gen_inputs(n, dev)
-    ws_lu = torch.empty(cf.gesv_mixed_workspace_size(n, 16, prec), dtype=torch.uint8, device=dev)
+    ws_lu = torch.empty(cf.gesv_mixed_workspace_size(n, 16, prec, leaf_h=args.leaf_h), dtype=torch.uint8, device=dev)
     ws_ch = torch.empty(cf.posv_mixed_workspace_size(n, 8, prec), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
     def step():
-        X1, info1, st1, s1 = cf.gesv_mixed(A_lu, B_lu, prec=prec, work=ws_lu)
+        X1, info1, st1, s1 = cf.gesv_mixed(A_lu, B_lu, prec=prec, work=ws_lu, leaf_h=args.leaf_h)
         X2, info2, st2, s2 = cf.posv_mixed(A_ch, B_ch, prec=prec, work=ws_ch)
         return (X1, st1, s1), (X2, st2, s2)
 
@@ -309,7 +310,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         def e2e_step():
             dA1.copy_(hA_lu, non_blocking=True)
             dB1.copy_(hB_lu, non_blocking=True)
-            X1_, _, _, _ = cf.gesv_mixed(dA1, dB1, prec=prec, work=ws_lu)
+            X1_, _, _, _ = cf.gesv_mixed(dA1, dB1, prec=prec, work=ws_lu, leaf_h=args.leaf_h)
             hX1.copy_(X1_, non_blocking=True)
             dA2.copy_(hA_ch, non_blocking=True)
             dB2.copy_(hB_ch, non_blocking=True)
@@ -380,7 +381,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "config": {"workload": "mixed LU solve (N=32768, 16 RHS, A=U[-1,1]+2sqrt(N)I) + mixed Cholesky solve "
                                "(N=32768, 8 RHS, A=GG^T/N+alpha I, kappa~1e2), %s tensor-core updates, FP64 "
                                "refinement to 1e-14" % prec,
-                   "n": n, "v": 128, "leaf_h": 128, "arity": 2, "outer_V": 1024, "factor_prec": prec,
+                   "n": n, "v": 128, "leaf_h": args.leaf_h, "arity": 2, "outer_V": 1024, "factor_prec": prec,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (A is 8.6 GB per matrix)", "inputs": gen_info},
         "converged": ok, "eta": {"lu": eta_lu, "chol": eta_ch},

@@ -56,7 +56,9 @@ typedef enum {
  * is a function of (v, leaf_h, arity) only; the oracle takes the same three. */
 typedef struct {
     int v;             /* block size of a step, 1..128 [128] (Sec. 7.2, "Block size v") */
-    int leaf_h;        /* tournament leaf height, 1..128 [128] */
+    int leaf_h;        /* tournament leaf height [128]: 1..128 for the FP64
+                          routines, 1..256 for the mixed solvers (whose FP32
+                          tournament takes arity 2 only) */
     int arity;         /* children per playoff node, 2..4 [2]; the mixed paths use 2 */
     int outer_V;       /* mixed LU/Cholesky: depth of the deferred update, multiple of v [0 = auto] */
     int lookahead;     /* mixed paths: overlap panel t+1 with update t [1] */

@@ -38,7 +38,7 @@ int resolve_options(const cf_options *in, Opts *o) {
     if (in->max_iter > 0) o->max_iter = in->max_iter;
     if (in->gmres_restart > 0) o->gmres_restart = in->gmres_restart;
     if (o->v < 1 || o->v > kMaxV) return CF_ERR_UNSUPPORTED;
-    if (o->leaf_h < 1 || o->leaf_h > kMaxV) return CF_ERR_UNSUPPORTED;
+    if (o->leaf_h < 1 || o->leaf_h > 2 * kMaxV) return CF_ERR_UNSUPPORTED;   // FP64 tournament: <= kMaxV
     if (o->arity < 2 || o->arity > 4) return CF_ERR_UNSUPPORTED;
     if (o->outer_V < 0 || (o->outer_V % o->v) != 0) return CF_ERR_UNSUPPORTED;
     return CF_OK;

@@ -338,7 +338,7 @@ k_apply_swaps(T *__restrict__ A, int lda, int ncols, int k0, const int *swap_cnt
 // Host side
 // ---------------------------------------------------------------------------
 int make_tourn_plan(int m, int w, int h, int arity, TournPlan *plan) {
-    if (m < 0 || w < 0 || w > kMaxV || h < 1 || h > kMaxV || arity < 2 || arity > 4) return CF_ERR_UNSUPPORTED;
+    if (m < 0 || w < 0 || w > kMaxV || h < 1 || h > 2 * kMaxV || arity < 2 || arity > 4) return CF_ERR_UNSUPPORTED;
     TournPlan p{};
     p.m = m; p.w = w; p.h = h; p.arity = arity;
     p.nleaves = m > 0 ? ceil_div(m, h) : 0;
@@ -417,6 +417,7 @@ static int launch_tourn_cl(const T *P, int ldp, const TournPlan &plan, const Tou
 template <typename T>
 int launch_tourn(const T *P, int ldp, int m, int w, int h, int arity, const TournWS &ws, const TournEpilogue &ep,
                  cudaStream_t st) {
+    if (h > kMaxV) return CF_ERR_UNSUPPORTED;      // a leaf is one tile of kMaxV rows at most
     TournPlan plan{};
     int rc = make_tourn_plan(m, w, h, arity, &plan);
     if (rc != CF_OK) return rc;

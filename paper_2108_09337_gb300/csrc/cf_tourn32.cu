@@ -5,13 +5,13 @@
 // playoff nodes on the original panel values of the stacked candidates, ties
 // to the smallest stacked position), built for latency:
 //   * one CTA of 256 threads is a whole leaf (h <= 256) or a whole node
-//     (2 x 128 candidates); each thread holds one row in registers;
-//   * after column j a thread shifts its row left while it updates it
-//     (a[t-1] = a[t] - l p[t]), so the current column is always a[0] and all
+//     (2 x 128 candidates); each thread holds one row in registers, indexed
+//     relative to the current block of 8 columns (cf_regrow.cuh), so all
 //     register indices are compile-time constants;
-//   * one barrier per column: every warp's best row is published (float4
-//     stores) before the barrier, every thread picks the CTA winner after it
-//     and reads the winner's row with float4 loads;
+//   * per column: a warp maximum of integer keys (one redux.sync and a
+//     ballot), eight packed 64-bit warp keys in shared memory, and only the
+//     winning row is written to shared memory (its live part), so the
+//     shared-memory traffic per column is one row, not one per warp;
 //   * the CTA that finishes a node second climbs to the parent (atomic
 //     counter), so no CTA waits for another.
 // FP32 with FMA: the mixed path's pivots are reported, not held to bit
@@ -28,9 +28,9 @@ constexpr int kT2 = 256;                 // rows per unit = threads per CTA
 constexpr int kT2Warps = kT2 / 32;
 
 struct T2Smem {
-    float4 cand[2][kT2Warps][kMaxV / 4];  // each warp's best row, by column parity
-    float redv[2][kT2Warps];
-    int redi[2][kT2Warps];
+    float4 prow[kMaxV / 4];               // the current pivot row (relative to the block start)
+    unsigned wkey[kT2Warps];              // each warp's largest key
+    float rinv;                           // 1 / pivot
     int order[kMaxV];
     int rows[kT2];
     int nrows;
@@ -39,62 +39,70 @@ struct T2Smem {
     int where_[2 * kMaxV];
 };
 
-__device__ __forceinline__ float key32(float a) {
+// Candidate key as an unsigned integer with the selection order
+// used < NaN < |a| (non-negative floats order like their bit patterns), so a
+// maximum is one redux.sync.
+__device__ __forceinline__ unsigned key32u(float a, bool used) {
     const float x = fabsf(a);
-    return (x != x) ? -0.5f : x;
-}
-
-__device__ __forceinline__ void better32(float &bv, int &bi, float ov, int oi) {
-    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    return used ? 0u : ((x != x) ? 1u : __float_as_uint(x) + 2u);
 }
 
 // Masked partial-pivoting selection on the rows held by this CTA's threads
 // (thread r holds stacked row r if r < s.nrows).  s.order[0..npiv) = stacked
-// indices of the pivots.  One barrier per column.
+// indices of the pivots.  Per column:
+//   warp maximum of the keys (redux.sync) and its smallest lane (ballot);
+//   barrier; every warp takes the maximum of the eight warp keys the same
+//   way (lane q reads warp q's key), so ties go to the smallest warp, then
+//   the smallest lane: the smallest stacked row;
+//   the winner publishes the live part of its row and 1 / pivot; barrier;
+//   every remaining row applies the rank-1 update with l = a * (1 / pivot)
+//   (FP32 selection only: the factors are recomputed from the original rows).
 struct TournStep {
     T2Smem &s;
-    float (&a)[kMaxV];
+    float2 (&a)[kPairs];
     int w, r, lane, warp;
     bool used;
     template <int U>
     __device__ __forceinline__ void step(int j0) {
-        const int j = j0 + U, par = j & 1;
-        float bv = used ? -1.f : key32(a[U]);
-        int bi = used ? INT_MAX : r;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            better32(bv, bi, ov, oi);
-        }
-        if (lane == 0) { s.redv[par][warp] = bv; s.redi[par][warp] = bi; }
-        if (bi == r) store_row4(s.cand[par][warp], a);     // this warp's best row
+        const int j = j0 + U;
+        const float aj = pair_elem<U>(a);
+        const unsigned k = key32u(aj, used);
+        const unsigned m = __reduce_max_sync(0xffffffffu, k);
+        const int wl = __ffs(__ballot_sync(0xffffffffu, k == m)) - 1;
+        if (lane == 0) s.wkey[warp] = m;
         __syncthreads();
-        float gv = s.redv[par][0];
-        int gi = s.redi[par][0];
-#pragma unroll
-        for (int q = 1; q < kT2Warps; ++q) better32(gv, gi, s.redv[par][q], s.redi[par][q]);
-        if (r == 0) s.order[j] = gi;
-        if (gi == r) used = true;
+        const unsigned kk = s.wkey[lane & (kT2Warps - 1)];
+        const unsigned gm = __reduce_max_sync(0xffffffffu, kk);
+        const int wb = __ffs(__ballot_sync(0xffffffffu, kk == gm)) - 1;
+        if (warp == wb && lane == wl) {
+            store_live_pairs<U>(s.prow, a, w - j0);
+            s.rinv = aj != 0.f ? 1.0f / aj : 0.f;      // zero pivot: no elimination
+            s.order[j] = r;
+            used = true;
+        }
+        __syncthreads();
         if (!used) {
-            const float4 *p4 = s.cand[par][gi >> 5];
-            const float piv = reinterpret_cast<const float *>(p4)[U];
-            if (piv != 0.f) rank1_from<U>(a, a[U] / piv, p4, w - j0);
+            const float ri = s.rinv;
+            if (ri != 0.f) rank1_pairs<U>(a, aj * ri, s.prow, w - j0);
         }
     }
 };
 
-__device__ void gepp_select_t2(T2Smem &s, float (&a)[kMaxV], int w, int npiv) {
+__device__ void gepp_select_t2(T2Smem &s, float2 (&a)[kPairs], int w, int npiv) {
     const int r = threadIdx.x;
     TournStep body{s, a, w, r, r & 31, r >> 5, !(r < s.nrows)};
-    for_blocks(a, npiv, body);
+    for_blocks_pairs(a, npiv, w, body);
     __syncthreads();
 }
 
-__device__ __forceinline__ void load_row32(float (&a)[kMaxV], const float *__restrict__ P, int ldp, int row, int w,
+__device__ __forceinline__ void load_row32(float2 (&a)[kPairs], const float *__restrict__ P, int ldp, int row, int w,
                                            bool valid) {
 #pragma unroll
-    for (int k = 0; k < kMaxV; ++k) a[k] = (valid && k < w) ? P[(size_t)row + (size_t)k * ldp] : 0.f;
+    for (int k = 0; k < kPairs; ++k) {
+        const float x = (valid && 2 * k < w) ? P[(size_t)row + (size_t)(2 * k) * ldp] : 0.f;
+        const float y = (valid && 2 * k + 1 < w) ? P[(size_t)row + (size_t)(2 * k + 1) * ldp] : 0.f;
+        a[k] = make_float2(x, y);
+    }
 }
 
 __device__ void root_epilogue_t2(T2Smem &s, const int *win, int np, const TournEpilogue &ep) {
@@ -128,7 +136,7 @@ k_tourn32(const float *__restrict__ P, int ldp, TournPlan plan, TournWS ws, Tour
     __shared__ T2Smem s;
     const int tid = threadIdx.x;
     const int w = plan.w;
-    float a[kMaxV];
+    float2 a[kPairs];
 
     // ---- leaf
     const int leaf = blockIdx.x;

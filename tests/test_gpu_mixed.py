@@ -105,6 +105,22 @@ def test_tourn_select_f32_gap_audited(cf, m, w, h, arity):
         np.testing.assert_array_equal(win, win_o)
 
 
+def test_tourn_select_f32_ties_zeros_nan(cf):
+    """Exact ties (ties to the smallest stacked row), zero columns and a NaN
+    (ranks below every number) in FP32, with values whose elimination is
+    exact, so the pivots must equal the oracle's."""
+    P = np.zeros((300, 8))
+    P[::3, :] = 1.0
+    P[7, 0] = -1.0
+    P[5, 0] = np.nan
+    win_o, _ = oracle.tourn_select(P, h=16, arity=2)
+    dP = torch.from_numpy(np.ascontiguousarray(P.T.astype(np.float32))).cuda().t()
+    for h in (16, 256):
+        win_o, _ = oracle.tourn_select(P, h=h, arity=2)
+        win = cf.tourn_select(dP, leaf_h=h, arity=2).cpu().numpy()
+        np.testing.assert_array_equal(win, win_o)
+
+
 def test_tourn_select_f32_constructed_gepp(cf):
     """Single leaf (GEPP mode) on a constructed P^T L U: pivots are P."""
     n = 128
