@@ -64,7 +64,7 @@ typedef struct {
     int lookahead;     /* mixed paths: overlap panel t+1 with update t [1] */
     double tol;        /* refinement stop: max backward error [1e-14] */
     int max_iter;      /* refinement iterations [30] */
-    int gmres_restart; /* GMRES-IR Krylov dimension [30] */
+    int gmres_restart; /* GMRES-IR Krylov dimension per correction, 1..256 [30] */
 } cf_options;
 
 void cf_default_options(cf_options *opt /* host */);
@@ -73,7 +73,9 @@ void cf_default_options(cf_options *opt /* host */);
  * solvers (they synchronise `stream` once per refinement step). */
 typedef struct {
     int iterations;    /* refinement steps taken (residual evaluations - 1) */
-    int solver;        /* 0 = LU-IR / Cholesky-IR, 1 = GMRES-IR */
+    int solver;        /* 0 = LU-IR / Cholesky-IR throughout, 1 = switched to
+                          GMRES-IR (classical refinement failed to halve eta
+                          in one step) */
     int converged;     /* 1 if eta <= tol */
     int info;          /* info of the low-precision factorization */
     double eta;        /* final max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) */
@@ -84,8 +86,9 @@ typedef struct {
     double residual_ms;     /* device time inside the FP64 residual launches */
     double update_ms;       /* device time inside the K = V tensor-core updates */
     double update_flops;    /* algorithmic flops of those updates */
-    int residual_launches;
+    int residual_launches;  /* FP64 products with A (residuals and GMRES steps) */
     int update_launches;
+    int gmres_iterations;   /* inner GMRES steps over all GMRES-IR corrections */
 } cf_refine_stats;
 
 const char *cf_status_string(int status);
@@ -273,8 +276,13 @@ int cf_solve_batched_mixed(int batch, const int *kind, int default_kind,
  *   X            n x nrhs FP64 solution, ldx
  *   info         device int[1], info of the low-precision factorization
  *   stats        host cf_refine_stats (may be NULL)
- * Returns CF_ERR_NOT_CONVERGED when max_iter steps leave eta > tol (X then
- * holds the best iterate).
+ * Refinement: classical (x += M^{-1} r with the FP32 factors M) while eta at
+ * least halves per step; after the first step that fails to, GMRES-IR
+ * (left-preconditioned GMRES with M, restart opt->gmres_restart, products
+ * with A in FP64) for every remaining step.
+ * Returns CF_ERR_NOT_CONVERGED when max_iter steps, or two GMRES-IR steps in
+ * a row that fail to halve eta, leave eta > tol (X then holds the best
+ * iterate and stats->eta its backward error).
  * ------------------------------------------------------------------------ */
 size_t cf_gesv_mixed_workspace_size(int n, int nrhs, cf_prec factor_prec,
                                     const cf_options *opt);

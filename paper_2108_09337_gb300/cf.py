@@ -48,7 +48,8 @@ class RefineStats(ctypes.Structure):
                 ("shift", ctypes.c_double), ("factor_ms", ctypes.c_double),
                 ("refine_ms", ctypes.c_double), ("residual_ms", ctypes.c_double),
                 ("update_ms", ctypes.c_double), ("update_flops", ctypes.c_double),
-                ("residual_launches", ctypes.c_int), ("update_launches", ctypes.c_int)]
+                ("residual_launches", ctypes.c_int), ("update_launches", ctypes.c_int),
+                ("gmres_iterations", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -41,6 +41,7 @@ int resolve_options(const cf_options *in, Opts *o) {
     if (o->leaf_h < 1 || o->leaf_h > 2 * kMaxV) return CF_ERR_UNSUPPORTED;   // FP64 tournament: <= kMaxV
     if (o->arity < 2 || o->arity > 4) return CF_ERR_UNSUPPORTED;
     if (o->outer_V < 0 || (o->outer_V % o->v) != 0) return CF_ERR_UNSUPPORTED;
+    if (o->gmres_restart < 1 || o->gmres_restart > 256) return CF_ERR_UNSUPPORTED;
     return CF_OK;
 }
 

@@ -126,7 +126,7 @@ int launch_gemm_f64_sub(int m, int n, int k, const double *A, int lda, const dou
 }
 
 // ---------------------------------------------------------------------------
-// R = B - A X, X thin (NR >= nrhs columns).  CTA: 64 rows; 16 row groups of 4
+// R = B - A X (B null: R = A X), X thin (NR >= nrhs columns).  CTA: 64 rows; 16 row groups of 4
 // rows x 16 lanes along k; the 16 k-partial sums are combined in shared
 // memory at the end.  Reads A once, coalesced along the columns.
 // ---------------------------------------------------------------------------
@@ -168,7 +168,7 @@ k_residual_f64(int m, int n, int nrhs, const double *__restrict__ A, int lda, co
         double s = 0.0;
 #pragma unroll
         for (int q = 0; q < 16; ++q) s += red[((size_t)q * 64 + rl) * NR + c];
-        R[(size_t)row + (size_t)c * ldr] = B[(size_t)row + (size_t)c * ldb] - s;
+        R[(size_t)row + (size_t)c * ldr] = B ? B[(size_t)row + (size_t)c * ldb] - s : s;   // B null: R = A X
     }
 }
 
@@ -188,7 +188,7 @@ int launch_residual_f64(int m, int n, int nrhs, const double *A, int lda, const 
     for (int c0 = 0; c0 < nrhs; c0 += 16) {
         const int nc = min(16, nrhs - c0);
         const double *Xc = X + (size_t)c0 * ldx;
-        const double *Bc = B + (size_t)c0 * ldb;
+        const double *Bc = B ? B + (size_t)c0 * ldb : nullptr;
         double *Rc = R + (size_t)c0 * ldr;
         int rc;
         if (nc == 1) rc = launch_residual_nr<1>(m, n, nc, A, lda, Xc, ldx, Bc, ldb, Rc, ldr, st);
@@ -291,7 +291,7 @@ k_residual_df(int m, int n, int nrhs, const float *__restrict__ Ahi, const float
         double s = 0.0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) s += red[((size_t)q * 64 + rl) * NR + c];
-        R[(size_t)row + (size_t)c * ldr] = B[(size_t)row + (size_t)c * ldb] - s;
+        R[(size_t)row + (size_t)c * ldr] = B ? B[(size_t)row + (size_t)c * ldb] - s : s;   // B null: R = A X
     }
 }
 

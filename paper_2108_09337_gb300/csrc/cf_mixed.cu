@@ -142,6 +142,91 @@ __global__ void k_copy_cols(int n, int nrhs, const double *S, int lds, double *D
 }
 
 // ---------------------------------------------------------------------------
+// GMRES-IR kernels.  Vectors are n x nrhs FP64 blocks (ld n), one Krylov
+// sequence per right-hand side; basis block i sits at V + i * n * nrhs.
+// ---------------------------------------------------------------------------
+constexpr int kDotRows = 2048;         // rows per partial-dot block
+constexpr double kGmresTol = 1e-8;     // inner GMRES: stop at ||g_k|| <= tol ||M^{-1} r||
+
+// part[(chunk * nv + i) * nrhs + c] = sum over the chunk's rows of V_i[r, c] * W[r, c]
+__global__ void __launch_bounds__(256) k_dots_partial(int n, int nrhs, const double *__restrict__ V,
+                                                      const double *__restrict__ W, double *part) {
+    __shared__ double red[8];
+    const int chunk = blockIdx.x, i = blockIdx.y, nv = gridDim.y;
+    const int r0 = chunk * kDotRows, r1 = min(n, r0 + kDotRows);
+    const double *Vi = V + (size_t)i * n * nrhs;
+    for (int c = 0; c < nrhs; ++c) {
+        double acc = 0.0;
+        for (int r = r0 + threadIdx.x; r < r1; r += 256)
+            acc = fma(Vi[(size_t)r + (size_t)c * n], W[(size_t)r + (size_t)c * n], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q) t += red[q];
+            part[((size_t)chunk * nv + i) * nrhs + c] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[j] (+)= sum over chunks of part[chunk * cnt + j], in chunk order
+__global__ void k_dots_final(int nchunks, int cnt, const double *part, double *out, int accumulate) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < nchunks; ++q) t += part[(size_t)q * cnt + j];
+        out[j] = accumulate ? out[j] + t : t;
+    }
+}
+
+// O[r, c] -= sum_{i < nv} coef[i * nrhs + c] * V_i[r, c]
+__global__ void k_block_axpy(int n, int nrhs, int nv, const double *__restrict__ V, const double *__restrict__ coef,
+                             double *O, int ldo) {
+    const size_t tot = (size_t)n * nrhs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % n), c = (int)(e / n);
+        double t = O[(size_t)r + (size_t)c * ldo];
+        for (int i = 0; i < nv; ++i) t = fma(-coef[i * nrhs + c], V[(size_t)i * tot + e], t);
+        O[(size_t)r + (size_t)c * ldo] = t;
+    }
+}
+
+// nrm[c] = sqrt(sq[c]); O[:, c] = W[:, c] / nrm[c] (zero if nrm[c] == 0)
+__global__ void k_normalize(int n, int nrhs, const double *sq, double *nrm, const double *W, double *O) {
+    const size_t tot = (size_t)n * nrhs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const double h = sqrt(sq[c]);
+        O[e] = h > 0.0 ? W[e] / h : 0.0;
+        if (e % n == 0) nrm[c] = h;
+    }
+}
+
+// Rf[i, c] = (float)(Y[perm[i], c] / s_c), s_c = max_i |Y[i, c]| (1 if 0),
+// with s_c read from the bit patterns k_col_absmax leaves.
+__global__ void k_gather_scale_bits(int n, int nrhs, const int *perm, const double *Y, const unsigned long long *sbits,
+                                    float *Rf) {
+    const size_t tot = (size_t)n * nrhs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), c = (int)(e / n);
+        const double sc = __longlong_as_double((long long)sbits[c]);
+        const int src = perm ? perm[i] : i;
+        Rf[e] = (float)(Y[(size_t)src + (size_t)c * n] / (sc > 0.0 ? sc : 1.0));
+    }
+}
+
+// Z[:, c] = s_c * Df[:, c]
+__global__ void k_scale_out_bits(int n, int nrhs, const float *Df, const unsigned long long *sbits, double *Z) {
+    const size_t tot = (size_t)n * nrhs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const double sc = __longlong_as_double((long long)sbits[c]);
+        Z[e] = (sc > 0.0 ? sc : 1.0) * (double)Df[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Workspace
 // ---------------------------------------------------------------------------
 struct MixedWS {
@@ -156,6 +241,16 @@ struct MixedWS {
     float *DinvL = nullptr, *DinvU = nullptr;   // inverses of the 64 x 64 diagonal blocks
     int *trsv_sync = nullptr;
     unsigned long long *norms = nullptr;   // [0..nrhs) |R|, [nrhs..2nrhs) |X|, [2nrhs..3nrhs) |B|, [3nrhs] ||A||
+    // GMRES-IR
+    int m = 0;                             // Krylov dimension
+    double *V = nullptr;                   // (m + 1) blocks of n x nrhs
+    double *Y = nullptr, *Wv = nullptr;    // n x nrhs each
+    double *part = nullptr;                // partial dots
+    double *hcol = nullptr;                // (m + 2) x nrhs: one Hessenberg column per right-hand side
+    double *coef = nullptr;                // (m + 1) x nrhs
+    double *sq = nullptr;                  // nrhs squared norms
+    unsigned long long *sbits = nullptr;   // preconditioner input scales
+    double *Xbest = nullptr;               // best iterate so far
     size_t bytes = 0;
 };
 
@@ -170,7 +265,9 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     Carver cv(work);
     w->ldw = (n + 31) / 32 * 32;
     w->W = cv.take<float>((size_t)w->ldw * (n > 0 ? n : 1), 1024);
-    w->Ab = cv.take<uint16_t>((size_t)(n + 1) * kMaxV, 1024);
+    // Ab: the K-major left operand of one step (rows x kMaxV), also the
+    // pivot rows' slab operand (kMaxV x Vp) of the left-looking update
+    w->Ab = cv.take<uint16_t>((size_t)((n > Vp ? n : Vp) + 1) * kMaxV, 1024);
     w->Bb = cv.take<uint16_t>((size_t)(n + 1) * kMaxV, 1024);
     w->Lb = cv.take<uint16_t>((size_t)(n + 1) * Vp, 1024);
     w->Ub = lu ? cv.take<uint16_t>((size_t)(n + 1) * Vp, 1024) : nullptr;
@@ -196,6 +293,17 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->DinvU = lu ? cv.take<float>(diag_inverse_floats(n)) : nullptr;
     w->trsv_sync = cv.take<int>(trsv_ws_bytes(n) / sizeof(int) + 1);
     w->norms = cv.take<unsigned long long>(3 * nrhs + 2);
+    w->m = o.gmres_restart;
+    const size_t blk = (size_t)n * nrhs;
+    w->V = cv.take<double>(blk * (w->m + 1) + 1);
+    w->Y = cv.take<double>(blk + 1);
+    w->Wv = cv.take<double>(blk + 1);
+    w->part = cv.take<double>((size_t)ceil_div(n > 0 ? n : 1, kDotRows) * (w->m + 1) * nrhs + 1);
+    w->hcol = cv.take<double>((size_t)(w->m + 2) * nrhs);
+    w->coef = cv.take<double>((size_t)(w->m + 1) * nrhs);
+    w->sq = cv.take<double>(nrhs + 1);
+    w->sbits = cv.take<unsigned long long>(nrhs + 1);
+    w->Xbest = cv.take<double>(blk + 1);
     w->bytes = cv.size();
     return CF_OK;
 }
@@ -264,6 +372,7 @@ template <typename LP>
 static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu) {
     const bool bf16 = std::is_same<LP, __nv_bfloat16>::value;
     const int v = o.v, V = pick_V(n, o);
+    const int Vpad = (V + 63) / 64 * 64;        // K stride of the slab's U operand
     const size_t ld = (size_t)w.ldw;
     float *W = w.W;
     int rc;
@@ -282,30 +391,47 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             if ((rc = launch_apply_swaps<float>(W, w.ldw, n, k0, w.tep, w.perm, st))) return rc;
             if ((rc = launch_a00_lu32(A00, w.ldw, wd, k0, info, st))) return rc;
             const int below = m - wd, right = n - k0 - wd;
+            const int off = k0 - J0, nout = n - JE;
+            // The part of the new pivot rows right of the slab has not yet
+            // received this slab's earlier steps (they are deferred for every
+            // row still below, and a pivot row may have come from anywhere
+            // below): apply them now, A[k0:k0+wd, JE:] -= L[k0:k0+wd, J0:k0]
+            // U[J0:k0, JE:] (left-looking, K = off).
+            if (off > 0 && nout > 0) {
+                const int Kp = (off + 63) / 64 * 64;
+                if ((rc = cvt_rows<LP>(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Ab, Kp, st))) return rc;
+                if ((rc = launch_schur_tc(wd, nout, Kp, w.Ab, Kp, w.Ub, Vpad, W + k0 + JE * ld, w.ldw, bf16, false,
+                                          st, 0)))
+                    return rc;
+            }
             // LU-3 / LU-4; they also write the K-major low-precision operands
-            // of the updates.
+            // of the updates inside the slab.
             if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, false, (LP *)w.Ab, kMaxV, kMaxV,
                                          nullptr, st)))
                 return rc;
             if ((rc = launch_ltrsm32<LP>(A00 + wd * ld, w.ldw, wd, right, A00, w.ldw, (LP *)w.Bb, kMaxV, kMaxV, st)))
                 return rc;
+            // U rows of this step right of the slab -> K-major operand of the
+            // slab's deferred update (K rows off .. off + wd, zeros up to the
+            // next multiple of 64)
+            if (nout > 0) {
+                const int kp = (off + wd + 63) / 64 * 64 - off;
+                if ((rc = cvt_cols<LP>(wd, nout, kp, W + k0 + JE * ld, w.ldw, (LP *)w.Ub + off, Vpad, st))) return rc;
+            }
             if (below <= 0 || right <= 0) continue;
-            const int nslab = JE - (k0 + wd), nout = n - JE;
+            // A11 restricted to the slab's remaining columns (every row below)
+            const int nslab = JE - (k0 + wd);
             float *C = A00 + wd + wd * ld;
             if (nslab > 0 &&
                 (rc = launch_schur_tc(below, nslab, kMaxV, w.Ab, kMaxV, w.Bb, kMaxV, C, w.ldw, bf16, false, st, 0)))
                 return rc;
-            if (nslab > 0 && nout > 0 &&
-                (rc = launch_schur_tc(nslab, nout, kMaxV, w.Ab, kMaxV, (const LP *)w.Bb + (size_t)nslab * kMaxV,
-                                      kMaxV, C + (size_t)nslab * ld, w.ldw, bf16, false, st, 0)))
-                return rc;
         }
         if (JE < n) {
+            // deferred update of everything right of and below the slab
             const int Vs = JE - J0, Vp = (Vs + 63) / 64 * 64, mr = n - JE;
             if ((rc = cvt_rows<LP>(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Lb, Vp, st))) return rc;
-            if ((rc = cvt_cols<LP>(Vs, mr, Vp, W + J0 + JE * ld, w.ldw, w.Ub, Vp, st))) return rc;
             if (tu && (rc = tu->begin(st))) return rc;
-            if ((rc = launch_schur_tc(mr, mr, Vp, w.Lb, Vp, w.Ub, Vp, W + JE + JE * ld, w.ldw, bf16, false, st, 0)))
+            if ((rc = launch_schur_tc(mr, mr, Vp, w.Lb, Vp, w.Ub, Vpad, W + JE + JE * ld, w.ldw, bf16, false, st, 0)))
                 return rc;
             if (tu && (rc = tu->end(st, 2.0 * mr * (double)mr * Vs))) return rc;
         }
@@ -361,6 +487,141 @@ static int solve_f32(int n, int nrhs, const MixedWS &w, bool lu, cudaStream_t st
     int rc;
     if ((rc = launch_trsv_f32(lu ? 0 : 2, n, nrhs, w.W, w.ldw, w.DinvL, w.Rf, n, w.trsv_sync, st))) return rc;
     return launch_trsv_f32(lu ? 1 : 3, n, nrhs, w.W, w.ldw, lu ? w.DinvU : w.DinvL, w.Rf, n, w.trsv_sync, st);
+}
+
+// ---------------------------------------------------------------------------
+// GMRES-IR correction (Carson and Higham, SISC 2017/2018; the preconditioner
+// applied in FP32 as in the multi-precision GMRES-IR analysis of Amestoy et
+// al., 2021): for every column of r = w.R, left-preconditioned restarted
+// GMRES on M^{-1} A d = M^{-1} r with M = the low-precision factors, the
+// products with A in FP64 on the untouched A, classical Gram-Schmidt with one
+// reorthogonalisation, Givens rotations of the small Hessenberg systems on
+// the host; then X += d.  All right-hand sides advance together (one FP64
+// product A [v_1 .. v_nrhs] per step).
+// ---------------------------------------------------------------------------
+// Z = M^{-1} Y through the FP32 factors, Y scaled per column into FP32.
+static int apply_precond(int n, int nrhs, const double *Yin, double *Z, MixedWS &w, bool lu, cudaStream_t st) {
+    const size_t blk = (size_t)n * nrhs;
+    CF_CUDA_TRY(cudaMemsetAsync(w.sbits, 0, sizeof(unsigned long long) * nrhs, st));
+    k_col_absmax<<<dim3(grid_for(n), nrhs), 256, 0, st>>>(n, nrhs, Yin, n, w.sbits);
+    CF_LAUNCH_CHECK();
+    k_gather_scale_bits<<<grid_for(blk), 256, 0, st>>>(n, nrhs, lu ? w.perm : nullptr, Yin, w.sbits, w.Rf);
+    CF_LAUNCH_CHECK();
+    int rc = solve_f32(n, nrhs, w, lu, st);
+    if (rc) return rc;
+    k_scale_out_bits<<<grid_for(blk), 256, 0, st>>>(n, nrhs, w.Rf, w.sbits, Z);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+// out[i * nrhs + c] (+)= <V_i[:, c], W[:, c]> for i < nv, fixed summation order.
+static int block_dots(int n, int nrhs, const double *V, int nv, const double *W, double *out, int accumulate,
+                      MixedWS &w, cudaStream_t st) {
+    const int nch = ceil_div(n, kDotRows);
+    k_dots_partial<<<dim3(nch, nv), 256, 0, st>>>(n, nrhs, V, W, w.part);
+    CF_LAUNCH_CHECK();
+    const int cnt = nv * nrhs;
+    k_dots_final<<<ceil_div(cnt, 256), 256, 0, st>>>(nch, cnt, w.part, out, accumulate);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+static int gmres_correct(int n, int nrhs, const double *A, int lda, double *X, int ldx, MixedWS &w, bool lu,
+                         double tau, cudaStream_t st, Timer &tres, int *inner) {
+    const size_t blk = (size_t)n * nrhs;
+    const int m = w.m;
+    int rc;
+    *inner = 0;
+    // z0 = M^{-1} r, beta = ||z0||_2, v_0 = z0 / beta
+    if ((rc = apply_precond(n, nrhs, w.R, w.Wv, w, lu, st))) return rc;
+    if ((rc = block_dots(n, nrhs, w.Wv, 1, w.Wv, w.sq, 0, w, st))) return rc;
+    k_normalize<<<grid_for(blk), 256, 0, st>>>(n, nrhs, w.sq, w.hcol, w.Wv, w.V);
+    CF_LAUNCH_CHECK();
+    std::vector<double> beta(nrhs);
+    CF_CUDA_TRY(cudaMemcpyAsync(beta.data(), w.hcol, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    CF_CUDA_TRY(cudaStreamSynchronize(st));
+
+    // per column: R (upper triangle of the rotated Hessenberg, column-major
+    // (m+1) x m), rotations, rotated right-hand side g
+    const int ldh = m + 1;
+    std::vector<double> R((size_t)nrhs * ldh * m, 0.0), cs((size_t)nrhs * m, 1.0), sn((size_t)nrhs * m, 0.0);
+    std::vector<double> g((size_t)nrhs * ldh, 0.0);
+    std::vector<int> kdim(nrhs, 0);
+    std::vector<char> done(nrhs, 0);
+    for (int c = 0; c < nrhs; ++c) {
+        g[(size_t)c * ldh] = beta[c];
+        done[c] = !(beta[c] > 0.0);
+    }
+    std::vector<double> h1((size_t)(m + 2) * nrhs), h2((size_t)(m + 1) * nrhs);
+    int k = 0;
+    for (; k < m; ++k) {
+        bool all = true;
+        for (int c = 0; c < nrhs; ++c) all = all && done[c];
+        if (all) break;
+        const double *Vk = w.V + (size_t)k * blk;
+        if ((rc = tres.begin(st))) return rc;
+        if ((rc = launch_residual_f64(n, n, nrhs, A, lda, Vk, n, nullptr, 0, w.Y, n, st))) return rc;   // Y = A v_k
+        if ((rc = tres.end(st, 2.0 * n * (double)n * nrhs))) return rc;
+        if ((rc = apply_precond(n, nrhs, w.Y, w.Wv, w, lu, st))) return rc;                          // w = M^{-1} Y
+        if ((rc = block_dots(n, nrhs, w.V, k + 1, w.Wv, w.hcol, 0, w, st))) return rc;               // CGS pass 1
+        k_block_axpy<<<grid_for(blk), 256, 0, st>>>(n, nrhs, k + 1, w.V, w.hcol, w.Wv, n);
+        CF_LAUNCH_CHECK();
+        if ((rc = block_dots(n, nrhs, w.V, k + 1, w.Wv, w.coef, 0, w, st))) return rc;               // CGS pass 2
+        k_block_axpy<<<grid_for(blk), 256, 0, st>>>(n, nrhs, k + 1, w.V, w.coef, w.Wv, n);
+        CF_LAUNCH_CHECK();
+        if ((rc = block_dots(n, nrhs, w.Wv, 1, w.Wv, w.sq, 0, w, st))) return rc;
+        k_normalize<<<grid_for(blk), 256, 0, st>>>(n, nrhs, w.sq, w.hcol + (size_t)(k + 1) * nrhs, w.Wv,
+                                                   w.V + (size_t)(k + 1) * blk);
+        CF_LAUNCH_CHECK();
+        CF_CUDA_TRY(cudaMemcpyAsync(h1.data(), w.hcol, sizeof(double) * (k + 2) * nrhs, cudaMemcpyDeviceToHost, st));
+        CF_CUDA_TRY(cudaMemcpyAsync(h2.data(), w.coef, sizeof(double) * (k + 1) * nrhs, cudaMemcpyDeviceToHost, st));
+        CF_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int c = 0; c < nrhs; ++c) {
+            if (done[c]) continue;
+            double *col = &R[((size_t)c * m + k) * ldh];
+            for (int i = 0; i <= k; ++i) col[i] = h1[(size_t)i * nrhs + c] + h2[(size_t)i * nrhs + c];
+            col[k + 1] = h1[(size_t)(k + 1) * nrhs + c];
+            const bool breakdown = !(col[k + 1] > 0.0);
+            double *csc = &cs[(size_t)c * m], *snc = &sn[(size_t)c * m], *gc = &g[(size_t)c * ldh];
+            for (int i = 0; i < k; ++i) {
+                const double t = csc[i] * col[i] + snc[i] * col[i + 1];
+                col[i + 1] = -snc[i] * col[i] + csc[i] * col[i + 1];
+                col[i] = t;
+            }
+            const double rr = std::hypot(col[k], col[k + 1]);
+            csc[k] = rr > 0.0 ? col[k] / rr : 1.0;
+            snc[k] = rr > 0.0 ? col[k + 1] / rr : 0.0;
+            col[k] = rr;
+            col[k + 1] = 0.0;
+            gc[k + 1] = -snc[k] * gc[k];
+            gc[k] = csc[k] * gc[k];
+            kdim[c] = k + 1;
+            if (breakdown || std::fabs(gc[k + 1]) <= tau * beta[c]) done[c] = 1;
+        }
+    }
+    *inner = k;
+    // y = R^{-1} g per column; X += V y
+    int nv = 0;
+    std::vector<double> cy((size_t)(m + 1) * nrhs, 0.0);
+    for (int c = 0; c < nrhs; ++c) {
+        const int kc = kdim[c];
+        nv = kc > nv ? kc : nv;
+        std::vector<double> y(kc > 0 ? kc : 1);
+        for (int i = kc - 1; i >= 0; --i) {
+            double t = g[(size_t)c * ldh + i];
+            for (int q = i + 1; q < kc; ++q) t -= R[((size_t)c * m + q) * ldh + i] * y[q];
+            const double d = R[((size_t)c * m + i) * ldh + i];
+            y[i] = d != 0.0 ? t / d : 0.0;
+        }
+        for (int i = 0; i < kc; ++i) cy[(size_t)i * nrhs + c] = -y[i];
+    }
+    if (nv > 0) {
+        CF_CUDA_TRY(cudaMemcpyAsync(w.coef, cy.data(), sizeof(double) * nv * nrhs, cudaMemcpyHostToDevice, st));
+        k_block_axpy<<<grid_for(blk), 256, 0, st>>>(n, nrhs, nv, w.V, w.coef, X, ldx);
+        CF_LAUNCH_CHECK();
+        CF_CUDA_TRY(cudaStreamSynchronize(st));    // cy is host memory that goes out of scope
+    }
+    return CF_OK;
 }
 
 template <typename LP>
@@ -444,8 +705,8 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
 
     std::vector<unsigned long long> hn(3 * nrhs + 2);
     std::vector<double> hscale(nrhs);
-    double eta_prev = HUGE_VAL, eta = HUGE_VAL;
-    int it = 0, stall = 0;
+    double eta_prev = HUGE_VAL, eta = HUGE_VAL, eta_best = HUGE_VAL;
+    int it = 0, stall = 0, solver = 0;
     bool converged = false;
     for (;; ++it) {
         if (it > 0) {
@@ -476,20 +737,39 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
         }
         if (it == 1) S.eta0 = eta;
         if (eta <= o.tol) { converged = true; break; }
+        if (eta < eta_best) {          // keep the best iterate
+            eta_best = eta;
+            k_copy_cols<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, X, ldx, w.Xbest, n);
+            CF_LAUNCH_CHECK();
+        }
         if (it >= o.max_iter || S.info != 0) break;
-        if (it >= 2 && eta > 0.5 * eta_prev) {
-            if (++stall >= 2) break;
+        // eta must at least halve per step: classical refinement that fails
+        // this hands over to GMRES-IR; GMRES-IR that fails it twice stops.
+        if (it >= 1 && !(eta <= 0.5 * eta_prev)) {
+            if (solver == 0) solver = 1;
+            else if (++stall >= 2) break;
         } else {
             stall = 0;
         }
-        eta_prev = eta < eta_prev ? eta : eta_prev;
-        CF_CUDA_TRY(cudaMemcpyAsync(w.scale, hscale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-        k_gather_scale<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, lu ? w.perm : nullptr, w.R, ldr, w.scale,
-                                                                  w.Rf, n);
+        eta_prev = eta;
+        if (solver == 0) {
+            CF_CUDA_TRY(cudaMemcpyAsync(w.scale, hscale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+            k_gather_scale<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, lu ? w.perm : nullptr, w.R, ldr,
+                                                                      w.scale, w.Rf, n);
+            CF_LAUNCH_CHECK();
+            if ((rc = solve_f32(n, nrhs, w, lu, st))) return rc;
+            k_axpy_update<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, w.Rf, n, w.scale, X, ldx);
+            CF_LAUNCH_CHECK();
+        } else {
+            int inner = 0;
+            if ((rc = gmres_correct(n, nrhs, A, lda, X, ldx, w, lu, kGmresTol, st, tres, &inner))) return rc;
+            S.gmres_iterations += inner;
+        }
+    }
+    if (!converged && eta_best < eta) {   // hand back the best iterate
+        k_copy_cols<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, w.Xbest, n, X, ldx);
         CF_LAUNCH_CHECK();
-        if ((rc = solve_f32(n, nrhs, w, lu, st))) return rc;
-        k_axpy_update<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, w.Rf, n, w.scale, X, ldx);
-        CF_LAUNCH_CHECK();
+        eta = eta_best;
     }
     CF_CUDA_TRY(cudaEventRecord(e2, st));
     CF_CUDA_TRY(cudaEventSynchronize(e2));
@@ -502,7 +782,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
     S.iterations = it;
-    S.solver = 0;
+    S.solver = solver;
     S.converged = converged ? 1 : 0;
     S.eta = eta;
     S.factor_ms = f_ms;

@@ -79,6 +79,56 @@ def test_gesv_mixed_unshifted_uniform_small(cf):
     _check_solution(A, B, X.cpu().numpy())
 
 
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_gesv_mixed_unshifted_uniform_gmres(cf, prec):
+    """s = 0 at n = 2048 (kappa_inf ~ 1e5): classical refinement with BF16
+    factors cannot contract (kappa u_f >> 1), so the solver must hand over to
+    GMRES-IR and still reach eta <= 1e-14 with all 16 right-hand sides."""
+    n = 2048
+    A = inputs.uniform_pm1(n, seed=0)
+    B = inputs.rhs_normal(n, 16, seed=3)
+    X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec=prec)
+    d = stats.as_dict()
+    assert st == cf.CF_OK, d
+    assert d["converged"] == 1
+    if prec == "bf16":
+        assert d["solver"] == 1 and d["gmres_iterations"] > 0, d
+    _check_solution(A, B, X.cpu().numpy())
+
+
+@pytest.mark.parametrize("spd", [False, True])
+def test_mixed_prescribed_condition(cf, spd):
+    """Haar-random A with geometrically spaced singular values, kappa_2 =
+    1e4 (n = 512), FP16 factors: refinement (classical, then GMRES-IR if
+    needed) reaches eta <= 1e-14.  (BF16 factors leave kappa(M^{-1} A) ~ 1e4
+    on this spectrum and restarted GMRES stagnates: a CPU emulation of the
+    same algorithm stalls near eta ~ 2e-4, so that case is not asked for.)"""
+    n = 512
+    A = inputs.prescribed_cond(n, 1e4, seed=21, spd=spd)
+    B = inputs.rhs_normal(n, 4, seed=5)
+    fn = cf.posv_mixed if spd else cf.gesv_mixed
+    X, info, stats, st = fn(_dev(A), _dev(B), prec="f16")
+    d = stats.as_dict()
+    assert st == cf.CF_OK, d
+    _check_solution(A, B, X.cpu().numpy())
+
+
+def test_gesv_mixed_not_converged_returns_best(cf):
+    """An unreachable tolerance (1e-30): the call reports
+    CF_ERR_NOT_CONVERGED after max_iter steps (or two failed GMRES-IR steps)
+    and hands back the iterate with the smallest backward error seen, which
+    is at the FP64 floor here."""
+    n = 256
+    A = inputs.uniform_pm1(n, seed=4, shift=2 * np.sqrt(n))
+    B = inputs.rhs_normal(n, 2, seed=6)
+    X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec="bf16", tol=1e-30, max_iter=8)
+    assert st == cf.CF_ERR_NOT_CONVERGED and stats.converged == 0
+    Xh = X.cpu().numpy()
+    assert np.isfinite(Xh).all()
+    eta = oracle.backward_error(A, Xh, B).max()
+    assert stats.eta <= 1e-15 and eta <= 2 * stats.eta + 1e-16, (eta, stats.as_dict())
+
+
 def test_gesv_mixed_workspace_error(cf):
     A = _dev(inputs.uniform_pm1(64, seed=1, shift=16.0))
     B = _dev(inputs.rhs_normal(64, 1))
