@@ -34,6 +34,7 @@ METRIC = "TFLOP/s for LU/Cholesky at N=32768, mixed+refine vs FP64, at 1e-14 bac
 UNIT = "TFLOP/s"
 TOL = 1e-14
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; ~2 DFMA/clk/SM x 152 SMs x 2.07 GHz)
+RESID_TRAFFIC_8192 = 542.2e6   # k_residual_f64 DRAM bytes per launch at N = 8192 (ncu)
 
 
 def _args():
@@ -257,8 +258,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         pass
     if res_ms >= upd_ms and res_n > 0:
         ach = (res_fl / res_n) / (res_ms / res_n * 1e-3) / 1e12
+        # DRAM bytes per launch from one ncu capture at N = 8192, 16 RHS
+        # (profiles/k_residual_f64_n8192.md: 539.1 MB read + 3.2 MB written),
+        # scaled to this N by the N^2 elements of A each launch streams once
+        traffic = RESID_TRAFFIC_8192 * (n / 8192.0) ** 2
         roof = {"kernel": "k_residual_f64 (R-1, FP64 r = b - A x)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": traffic, "traffic_note": "bytes per launch, ncu capture at N=8192 scaled by N^2",
                 "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (~2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
                 "launches": res_n, "avg_ms": res_ms / res_n}
     else:
