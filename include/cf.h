@@ -215,6 +215,36 @@ int cf_schur_update_lp(int m, int n, int k, const void *A_lp, int lda_k,
                        const void *B_lp, int ldb_k, float *C, int ldc,
                        cf_prec prec, int lower, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * CH-3 / LU-5 with FP8 operands (spec: trailing SYRK/GEMM in FP8 e4m3
+ * with per-128 x 128-tile FP32 scales, FP32 accumulation; the paper has no
+ * low-precision update), exposed for testing.
+ *
+ * cf_quantize_e4m3: src is a rows x k FP32 block, column-major (lds).  For
+ * every tile of 128 rows x 128 columns (K-block), scale = amax / 448 (1 for
+ * an all-zero tile) and each element becomes the e4m3 code of x * (448 /
+ * amax), rounded to nearest even and saturated to +-448.
+ *   q       device bytes, K-major: code of (i, p) at q[i*ldq + p]; columns
+ *           k .. kpad-1 (kpad = k rounded up to 128) are written as 0;
+ *           ldq >= kpad, a multiple of 16
+ *   scales  device float, scale of tile (rb, kb) at scales[rb*ld_scales + kb]
+ *
+ * cf_schur_update_fp8: C -= sum over K-blocks kb of
+ *   sA[i/128, kb] * sB[j/128, kb] * (qA_kb qB_kb^T)
+ * on the tensor cores (tcgen05 kind::f8f6f4, one TMEM accumulator per
+ * K-block, promoted into FP32 with its tile-pair scale).  k a multiple of
+ * 128; ldqa, ldqb multiples of 16 bytes; qA, qB 16-byte aligned; lower as
+ * in cf_schur_update_lp.  A device wait that expires is reported by
+ * cf_device_status.
+ * ------------------------------------------------------------------------ */
+int cf_quantize_e4m3(int rows, int k, const float *src, int lds, void *q,
+                     int ldq, float *scales, int ld_scales,
+                     cudaStream_t stream);
+int cf_schur_update_fp8(int m, int n, int k, const void *qA, int ldqa,
+                        const float *sA, int ldsa, const void *qB, int ldqb,
+                        const float *sB, int ldsb, float *C, int ldc,
+                        int lower, cudaStream_t stream);
+
 /* Synchronises `stream` and returns, then clears, the status word of the
  * library's bounded device-side waits: CF_OK, or CF_ERR_TIMEOUT if a wait in
  * a tensor-core kernel ran out since the last call. */

@@ -86,6 +86,8 @@ _SIG = {
     "cf_potrf_batched": (_I, [_I, _P, _P, _P, _P, _P, _S, _OPT, _P]),
     "cf_solve_batched_mixed_workspace_size": (_S, [_I]),
     "cf_solve_batched_mixed": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _S, _OPT, _P]),
+    "cf_quantize_e4m3": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P]),
+    "cf_schur_update_fp8": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _I, _I, _P]),
     "cf_gesv_mixed_workspace_size": (_S, [_I, _I, _I, _OPT]),
     "cf_gesv_mixed": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _I, _P, ctypes.POINTER(RefineStats),
                            _P, _S, _OPT, _P]),
@@ -279,6 +281,30 @@ def schur_update_lp(A_lp: torch.Tensor, B_lp: torch.Tensor, C: torch.Tensor, low
     _check("cf_schur_update_lp", _lib.cf_schur_update_lp(m, n, k, _ptr(A_lp), A_lp.stride(0), _ptr(B_lp),
                                                          B_lp.stride(0), _ptr(C), _ld(C, "C"), prec,
                                                          int(lower), _stream()))
+    return C
+
+
+def quantize_e4m3(src: torch.Tensor):
+    """Per-128x128-tile e4m3 quantization of a column-major float32 block
+    (cf_quantize_e4m3).  Returns (q uint8 rows x kpad K-major, scales float32
+    ceil(rows/128) x kpad/128)."""
+    rows, k = src.shape
+    kpad = (k + 127) // 128 * 128
+    q = torch.empty((rows, kpad), dtype=torch.uint8, device=src.device)
+    sc = torch.empty((max((rows + 127) // 128, 1), kpad // 128), dtype=torch.float32, device=src.device)
+    _check("cf_quantize_e4m3", _lib.cf_quantize_e4m3(rows, k, _ptr(src), _ld(src, "src"), _ptr(q), kpad, _ptr(sc),
+                                                     kpad // 128, _stream()))
+    return q, sc
+
+
+def schur_update_fp8(qA, sA, qB, sB, C: torch.Tensor, lower: bool = False):
+    """C -= sum_kb sA sB (qA qB^T)_kb on the tensor cores (cf_schur_update_fp8);
+    qA (m x k), qB (n x k) uint8 e4m3 codes, K-major; sA, sB tile scales."""
+    m, k = qA.shape
+    n = qB.shape[0]
+    _check("cf_schur_update_fp8", _lib.cf_schur_update_fp8(m, n, k, _ptr(qA), qA.stride(0), _ptr(sA), sA.stride(0),
+                                                           _ptr(qB), qB.stride(0), _ptr(sB), sB.stride(0), _ptr(C),
+                                                           _ld(C, "C"), int(lower), _stream()))
     return C
 
 
