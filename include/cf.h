@@ -74,8 +74,8 @@ void cf_default_options(cf_options *opt /* host */);
 typedef struct {
     int iterations;    /* refinement steps taken (residual evaluations - 1) */
     int solver;        /* 0 = LU-IR / Cholesky-IR throughout, 1 = switched to
-                          GMRES-IR (classical refinement failed to halve eta
-                          in one step) */
+                          GMRES-IR (a classical step cut eta by less than
+                          0.3x) */
     int converged;     /* 1 if eta <= tol */
     int info;          /* info of the low-precision factorization */
     double eta;        /* final max_j ||r_j||_inf / (||A||_inf ||x_j||_inf + ||b_j||_inf) */
@@ -306,8 +306,8 @@ int cf_solve_batched_mixed(int batch, const int *kind, int default_kind,
  *   X            n x nrhs FP64 solution, ldx
  *   info         device int[1], info of the low-precision factorization
  *   stats        host cf_refine_stats (may be NULL)
- * Refinement: classical (x += M^{-1} r with the FP32 factors M) while eta at
- * least halves per step; after the first step that fails to, GMRES-IR
+ * Refinement: classical (x += M^{-1} r with the FP32 factors M) while each
+ * step cuts eta by at least 0.3x; after the first step that does not, GMRES-IR
  * (left-preconditioned GMRES with M, restart opt->gmres_restart, products
  * with A in FP64) for every remaining step.
  * Returns CF_ERR_NOT_CONVERGED when max_iter steps, or two GMRES-IR steps in

@@ -30,6 +30,9 @@
 
 namespace cf {
 
+// Factor-precision tag of the FP8 Cholesky (e4m3 operands, per-tile scales).
+struct fp8_e4m3 {};
+
 // ---------------------------------------------------------------------------
 // Element-wise kernels
 // ---------------------------------------------------------------------------
@@ -147,6 +150,7 @@ __global__ void k_copy_cols(int n, int nrhs, const double *S, int lds, double *D
 // ---------------------------------------------------------------------------
 constexpr int kDotRows = 2048;         // rows per partial-dot block
 constexpr double kGmresTol = 1e-8;     // inner GMRES: stop at ||g_k|| <= tol ||M^{-1} r||
+constexpr double kSwitchRate = 0.3;    // classical refinement must cut eta at least this much per step
 
 // part[(chunk * nv + i) * nrhs + c] = sum over the chunk's rows of V_i[r, c] * W[r, c]
 __global__ void __launch_bounds__(256) k_dots_partial(int n, int nrhs, const double *__restrict__ V,
@@ -250,6 +254,7 @@ struct MixedWS {
     double *coef = nullptr;                // (m + 1) x nrhs
     double *sq = nullptr;                  // nrhs squared norms
     unsigned long long *sbits = nullptr;   // preconditioner input scales
+    float *sc8 = nullptr;                  // FP8 tile scales: slab (rows/128 x V/128), then one step
     double *Xbest = nullptr;               // best iterate so far
     size_t bytes = 0;
 };
@@ -304,6 +309,7 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->sq = cv.take<double>(nrhs + 1);
     w->sbits = cv.take<unsigned long long>(nrhs + 1);
     w->Xbest = cv.take<double>(blk + 1);
+    w->sc8 = cv.take<float>((size_t)(ceil_div(n > 0 ? n : 1, 128) + 1) * (Vp / 128 + 2));
     w->bytes = cv.size();
     return CF_OK;
 }
@@ -434,6 +440,57 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             if ((rc = launch_schur_tc(mr, mr, Vp, w.Lb, Vp, w.Ub, Vpad, W + JE + JE * ld, w.ldw, bf16, false, st, 0)))
                 return rc;
             if (tu && (rc = tu->end(st, 2.0 * mr * (double)mr * Vs))) return rc;
+        }
+    }
+    return CF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed Cholesky with FP8 e4m3 updates: the same two-level loop as below,
+// with every trailing update's operand (the FP32 L10 block) quantized to e4m3
+// with one FP32 scale per 128 x 128 tile, and the updates run by the FP8
+// tensor-core kernel, which applies the tile scales per K-block of 128.
+// Requires V to be a multiple of 128.
+// ---------------------------------------------------------------------------
+static int mixed_potrf_fp8(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu) {
+    const int v = o.v, V = pick_V(n, o);
+    if (V % 128 != 0) return CF_ERR_UNSUPPORTED;
+    const size_t ld = (size_t)w.ldw;
+    float *W = w.W;
+    const int nrb = ceil_div(n, 128);
+    float *sc_slab = w.sc8;                                  // nrb x (V / 128)
+    float *sc_step = w.sc8 + (size_t)nrb * (V / 128);        // nrb x 1
+    int rc;
+    for (int J0 = 0; J0 < n; J0 += V) {
+        const int JE = J0 + V < n ? J0 + V : n;
+        for (int k0 = J0; k0 < JE; k0 += v) {
+            const int wd = v < JE - k0 ? v : JE - k0;
+            const int m = n - k0;
+            float *A00 = W + k0 + k0 * ld;
+            if ((rc = launch_a00_chol32(A00, w.ldw, wd, k0, info, st))) return rc;
+            const int below = m - wd;
+            if (below <= 0) continue;
+            // CH-2 in FP32 (no low-precision copy: the FP8 operand needs the
+            // whole tile's amax first)
+            if ((rc = launch_rtrsm32<__nv_bfloat16>(A00 + wd, w.ldw, below, wd, A00, w.ldw, true, nullptr, kMaxV,
+                                                    kMaxV, info, st)))
+                return rc;
+            const int nslab = JE - (k0 + wd);
+            if (nslab <= 0) continue;
+            if ((rc = launch_quant_e4m3(below, wd, 128, A00 + wd, w.ldw, w.Ab, 128, sc_step, 1, st))) return rc;
+            if ((rc = launch_schur_fp8(below, nslab, 128, w.Ab, 128, sc_step, 1, w.Ab, 128, sc_step, 1,
+                                       A00 + wd + wd * ld, w.ldw, true, st)))
+                return rc;
+        }
+        if (JE < n) {
+            const int Vs = JE - J0, Vp8 = (Vs + 127) / 128 * 128, mr = n - JE;
+            if ((rc = launch_quant_e4m3(mr, Vs, Vp8, W + JE + J0 * ld, w.ldw, w.Lb, Vp8, sc_slab, Vp8 / 128, st)))
+                return rc;
+            if (tu && (rc = tu->begin(st))) return rc;
+            if ((rc = launch_schur_fp8(mr, mr, Vp8, w.Lb, Vp8, sc_slab, Vp8 / 128, w.Lb, Vp8, sc_slab, Vp8 / 128,
+                                       W + JE + JE * ld, w.ldw, true, st)))
+                return rc;
+            if (tu && (rc = tu->end(st, (double)mr * (mr + 1.0) * Vs))) return rc;
         }
     }
     return CF_OK;
@@ -646,12 +703,17 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     double shift = 0.0;
     int hinfo = 0;
     Timer tupd, tres;
-    const double u_lp = std::is_same<LP, __nv_bfloat16>::value ? 0x1p-8 : 0x1p-11;
+    const double u_lp = std::is_same<LP, __nv_bfloat16>::value ? 0x1p-8
+                        : std::is_same<LP, fp8_e4m3>::value   ? 0x1p-4
+                                                              : 0x1p-11;
     for (int attempt = 0; attempt < 4; ++attempt) {
         // W = fl32(A) (+ shift on the diagonal)
         if ((rc = launch_split_f64(n, n, A, lda, nullptr, nullptr, w.ldw, w.W, w.ldw, shift, st))) return rc;
         CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
-        rc = lu ? mixed_getrf<LP>(n, w, info, o, st, &tupd) : mixed_potrf<LP>(n, w, info, o, st, &tupd);
+        if constexpr (std::is_same<LP, fp8_e4m3>::value)
+            rc = lu ? CF_ERR_UNSUPPORTED : mixed_potrf_fp8(n, w, info, o, st, &tupd);
+        else
+            rc = lu ? mixed_getrf<LP>(n, w, info, o, st, &tupd) : mixed_potrf<LP>(n, w, info, o, st, &tupd);
         if (rc) return rc;
         CF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
         CF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -675,6 +737,8 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     CF_CUDA_TRY(cudaEventRecord(e1, st));
     int tstat = 0;
     if ((rc = tc_take_status(st, &tstat))) return rc;
+    if (tstat != 0) return CF_ERR_TIMEOUT;
+    if ((rc = fp8_take_status(st, &tstat))) return rc;
     if (tstat != 0) return CF_ERR_TIMEOUT;
     S.info = hinfo;
 
@@ -743,11 +807,14 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             CF_LAUNCH_CHECK();
         }
         if (it >= o.max_iter || S.info != 0) break;
-        // eta must at least halve per step: classical refinement that fails
-        // this hands over to GMRES-IR; GMRES-IR that fails it twice stops.
-        if (it >= 1 && !(eta <= 0.5 * eta_prev)) {
-            if (solver == 0) solver = 1;
-            else if (++stall >= 2) break;
+        // Classical refinement that fails to cut eta by kSwitchRate in one
+        // step hands over to GMRES-IR (at that rate the remaining classical
+        // steps would each cost as much as an inner GMRES step and converge
+        // slower); GMRES-IR that fails to halve eta twice in a row stops.
+        if (solver == 0 && it >= 1 && !(eta <= kSwitchRate * eta_prev)) {
+            solver = 1;
+        } else if (solver == 1 && !(eta <= 0.5 * eta_prev)) {
+            if (++stall >= 2) break;
         } else {
             stall = 0;
         }
@@ -806,7 +873,7 @@ static int check_mixed_args(int n, int nrhs, const double *A, int lda, const dou
     if (ldb < (n > 1 ? n : 1)) return -6;
     if (n > 0 && nrhs > 0 && X == nullptr) return -7;
     if (ldx < (n > 1 ? n : 1)) return -8;
-    if (prec != CF_BF16 && prec != CF_F16) return -9;
+    if (prec != CF_BF16 && prec != CF_F16 && prec != CF_FP8E4M3) return -9;
     if (info == nullptr) return -10;
     return CF_OK;
 }
@@ -837,6 +904,11 @@ static int mixed_entry(int n, int nrhs, const double *A, int lda, const double *
     }
     if (prec == CF_BF16)
         return mixed_solve<__nv_bfloat16>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, st);
+    if (prec == CF_FP8E4M3) {
+        if (lu) return -9;                     // FP8 updates: Cholesky only
+        if (pick_V(n, o) % 128 != 0) return CF_ERR_UNSUPPORTED;
+        return mixed_solve<fp8_e4m3>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, st);
+    }
     return mixed_solve<__half>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, st);
 }
 

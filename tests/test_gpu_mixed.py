@@ -129,6 +129,44 @@ def test_gesv_mixed_not_converged_returns_best(cf):
     assert stats.eta <= 1e-15 and eta <= 2 * stats.eta + 1e-16, (eta, stats.as_dict())
 
 
+@pytest.mark.parametrize("n,nrhs,V", [(1, 1, 0), (300, 2, 128), (1024, 8, 256), (2048, 8, 0)])
+def test_posv_mixed_fp8(cf, n, nrhs, V):
+    """FP8 e4m3 trailing updates with per-tile scales: refinement (classical,
+    GMRES-IR once that stalls, a diagonal shift on breakdown) reaches
+    eta <= 1e-14."""
+    S = inputs.spd_gram(n, seed=1)
+    B = inputs.rhs_normal(n, nrhs, seed=4)
+    dS, dB = _dev(S), _dev(B)
+    X, info, stats, st = cf.posv_mixed(dS, dB, prec="fp8", outer_V=V)
+    assert st == cf.CF_OK, stats.as_dict()
+    np.testing.assert_array_equal(dS.cpu().numpy(), S)
+    _check_solution(S, B, X.cpu().numpy())
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4])
+def test_posv_mixed_fp8_conditioned(cf, kappa):
+    """The N = 65536 configuration's matrix family at n = 2048:
+    A = G G^T / n + alpha I with alpha = lambda_max / (kappa - 1)
+    (lambda_max of G G^T / n from the dense eigensolver), 8 right-hand sides,
+    FP8 updates."""
+    n = 2048
+    S0 = inputs.spd_gram(n, seed=1, alpha=0.0)
+    lam = np.linalg.eigvalsh(S0)[-1]
+    S = S0 + (lam / (kappa - 1.0)) * np.eye(n)
+    B = inputs.rhs_normal(n, 8, seed=4)
+    X, info, stats, st = cf.posv_mixed(_dev(S), _dev(B), prec="fp8")
+    assert st == cf.CF_OK, stats.as_dict()
+    _check_solution(S, B, X.cpu().numpy())
+
+
+def test_gesv_mixed_fp8_refused(cf):
+    A = _dev(inputs.uniform_pm1(64, seed=1, shift=16.0))
+    B = _dev(inputs.rhs_normal(64, 1))
+    with pytest.raises(cf.CfError) as e:
+        cf.gesv_mixed(A, B, prec="fp8")
+    assert e.value.status == -9
+
+
 def test_gesv_mixed_workspace_error(cf):
     A = _dev(inputs.uniform_pm1(64, seed=1, shift=16.0))
     B = _dev(inputs.rhs_normal(64, 1))
