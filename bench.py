@@ -3,12 +3,15 @@
 1e-14 backward error at N = 32768 on one GB300, next to this project's FP64
 path and the CPU oracle.
 
-One step = cf_gesv_mixed (LU with tournament pivoting, BF16 tensor-core
-Schur updates, FP64 refinement; A = U[-1,1] + 2 sqrt(N) I, 16 right-hand
-sides) + cf_posv_mixed (Cholesky, BF16 updates, FP64 refinement;
-A = G G^T / N + alpha I with kappa ~ 1e2, 8 right-hand sides).  value =
-(2N^3/3 + N^3/3) / step time.  A step counts only if every right-hand side
-reaches eta <= 1e-14 (checked here with an FP64 residual).
+One step = cf_gesv_mixed (LU with tournament pivoting, FP16 tensor-core
+Schur updates with FP32 accumulation, FP64 refinement; A = U[-1,1] +
+2 sqrt(N) I, 16 right-hand sides) + cf_posv_mixed (Cholesky, FP16 updates,
+FP64 refinement; A = G G^T / N + alpha I with kappa ~ 1e2, 8 right-hand
+sides).  value = (2N^3/3 + N^3/3) / step time.  A step counts only if every
+right-hand side reaches eta <= 1e-14 (checked here with an FP64 residual).
+--prec bf16 times the same step with BF16 updates; by default the BF16 and
+split-BF16 solves, the unshifted LU (s = 0) and the N = 65536 Cholesky with
+FP8 updates run once after the timed step ("variants").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cf|reference]
 
@@ -44,11 +47,14 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cf", "reference"], default="cf")
     ap.add_argument("--n", type=int, default=32768)
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "f16"])
+    ap.add_argument("--prec", default="f16", choices=["bf16", "f16", "bf16x3"],
+                    help="update precision of the timed step (the other 16-bit one runs once as a variant)")
     ap.add_argument("--leaf-h", type=int, default=256, help="tournament leaf height of the mixed LU")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the once-run legs (FP16, s = 0 LU, FP8 Cholesky at N = 65536)")
     return ap.parse_args()
 
 
@@ -165,6 +171,78 @@ def _gen_inputs(n, device):
     A_ch.diagonal().add_(alpha)
     B_ch = inputs.rhs_normal_torch(n, 8, seed=4, device=device)
     return A_lu, B_lu, A_ch, B_ch, {"lambda_max_est": lam, "alpha": alpha}
+
+
+def _timed(fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def _run_variants(args, n, dev, A_lu, B_lu, A_ch, B_ch):
+    """One timed run each of the configurations the headline does not cover:
+    the other 16-bit and the split-BF16 updates at N = 32768 (LU and
+    Cholesky); the unshifted
+    LU (s = 0) with split BF16, BF16 and FP16 updates (GMRES-IR; BF16 / FP16
+    escalate to split BF16); Cholesky at N = 65536 with FP8 e4m3 updates and
+    per-tile scales, kappa = 1e2 and 1e4.  Every result is checked with an
+    independent FP64 residual."""
+    import torch
+    from paper_2108_09337_gb300 import cf, inputs
+    out = {}
+
+    def rec(name, fn, A, B, fl):
+        (X, info, S, st), ms = _timed(fn)
+        d = S.as_dict()
+        out[name] = {"ms": ms, "tflops": fl / (ms * 1e-3) / 1e12, "status": int(st),
+                     "eta": _eta(A, X, B), "iterations": d["iterations"], "solver": d["solver"],
+                     "gmres_iterations": d["gmres_iterations"], "shift": d["shift"], "escalated": d["escalated"],
+                     "factor_ms": d["factor_ms"], "refine_ms": d["refine_ms"]}
+        del X
+
+    lu_fl, ch_fl = 2.0 * n ** 3 / 3.0, n ** 3 / 3.0
+    other = "bf16" if args.prec == "f16" else "f16"
+    rec("lu_%s_n%d" % (other, n), lambda: cf.gesv_mixed(A_lu, B_lu, prec=other, leaf_h=args.leaf_h), A_lu, B_lu,
+        lu_fl)
+    rec("chol_%s_n%d" % (other, n), lambda: cf.posv_mixed(A_ch, B_ch, prec=other), A_ch, B_ch, ch_fl)
+    rec("lu_bf16x3_n%d" % n, lambda: cf.gesv_mixed(A_lu, B_lu, prec="bf16x3", leaf_h=args.leaf_h), A_lu, B_lu,
+        lu_fl)
+    rec("chol_bf16x3_n%d" % n, lambda: cf.posv_mixed(A_ch, B_ch, prec="bf16x3"), A_ch, B_ch, ch_fl)
+    A0 = inputs.uniform_pm1_torch(n, seed=0, shift=0.0, device=dev)
+    for p in ("bf16x3", "bf16", "f16"):
+        rec("lu_s0_%s_n%d" % (p, n), lambda: cf.gesv_mixed(A0, B_lu, prec=p, leaf_h=args.leaf_h), A0, B_lu, lu_fl)
+    del A0
+    torch.cuda.empty_cache()
+    if n == 32768:
+        # the N = 65536 Cholesky configuration: A = G G^T / N + alpha I
+        n2 = 65536
+        A2 = inputs.spd_gram_torch(n2, seed=1, alpha=0.0, device=dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(5)
+        x = torch.randn(n2, 1, generator=g, device=dev, dtype=torch.float64)
+        lam = 0.0
+        for _ in range(30):
+            y = A2 @ x
+            lam = float(torch.linalg.vector_norm(y) / torch.linalg.vector_norm(x))
+            x = y / torch.linalg.vector_norm(y)
+        B2 = inputs.rhs_normal_torch(n2, 8, seed=4, device=dev)
+        alpha_prev = 0.0
+        for kappa in (1e2, 1e4):
+            alpha = lam / (kappa - 1.0)
+            A2.diagonal().add_(alpha - alpha_prev)
+            alpha_prev = alpha
+            rec("chol_fp8_n%d_kappa%.0e" % (n2, kappa), lambda: cf.posv_mixed(A2, B2, prec="fp8"), A2, B2,
+                n2 ** 3 / 3.0)
+            out["chol_fp8_n%d_kappa%.0e" % (n2, kappa)]["alpha"] = alpha
+        out["lambda_max_est_n%d" % n2] = lam
+        del A2, B2
+        torch.cuda.empty_cache()
+    return out
 
 
 def _eta(A, X, B):
@@ -372,6 +450,15 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                 "note": "factorization only (FP64 path; its solve adds O(N^2))"}
         torch.cuda.empty_cache()
 
+    # ---- once-run legs of the other configurations (not part of value),
+    # after the timed legs so that their allocations cannot disturb them
+    variants = None
+    if not args.no_variants:
+        A_lu, B_lu, A_ch, B_ch, _ = _gen_inputs(n, dev)
+        variants = _run_variants(args, n, dev, A_lu, B_lu, A_ch, B_ch)
+        del A_lu, A_ch
+        torch.cuda.empty_cache()
+
     if rank != 0:
         return
     cpu = None
@@ -394,7 +481,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "parts": parts, "kernels": kernels,
         "clocks": clk.summary(),
         "e2e": e2e, "gpu_launches": launches,
-        "roofline": roof, "cpu_baseline": cpu, "fp64_path": fp64,
+        "roofline": roof, "cpu_baseline": cpu, "fp64_path": fp64, "variants": variants,
         "speedup_vs_fp64": (value / fp64["tflops"]) if (fp64 and ok) else None,
     }
     print(json.dumps(line), flush=True)

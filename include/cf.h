@@ -49,7 +49,11 @@ typedef enum {
     CF_F32 = 1,
     CF_BF16 = 2,
     CF_F16 = 3,
-    CF_FP8E4M3 = 4
+    CF_FP8E4M3 = 4,
+    CF_BF16X3 = 5      /* mixed solvers: each update operand as a BF16 pair
+                          hi + lo, three products (hi.hi + hi.lo + lo.hi)
+                          accumulated in FP32: 16 significant bits at three
+                          times the tensor work */
 } cf_prec;
 
 /* Tunables.  Pass NULL for the defaults (in brackets).  The pivot sequence
@@ -89,6 +93,8 @@ typedef struct {
     int residual_launches;  /* FP64 products with A (residuals and GMRES steps) */
     int update_launches;
     int gmres_iterations;   /* inner GMRES steps over all GMRES-IR corrections */
+    int escalated;          /* 1 if the solve refactored with CF_BF16X3 updates
+                               after the requested precision stalled */
 } cf_refine_stats;
 
 const char *cf_status_string(int status);
@@ -302,7 +308,8 @@ int cf_solve_batched_mixed(int batch, const int *kind, int default_kind,
  * LU + refinement as related work, Sec. 11).  A and B are never modified.
  * cf_posv_mixed factors the lower triangle but forms residuals with all of
  * A, which must hold both triangles.
- *   factor_prec  CF_BF16 or CF_F16 (CF_FP8E4M3 for cf_posv_mixed)
+ *   factor_prec  CF_BF16, CF_F16 or CF_BF16X3 (also CF_FP8E4M3 for
+ *                cf_posv_mixed)
  *   X            n x nrhs FP64 solution, ldx
  *   info         device int[1], info of the low-precision factorization
  *   stats        host cf_refine_stats (may be NULL)
@@ -310,8 +317,12 @@ int cf_solve_batched_mixed(int batch, const int *kind, int default_kind,
  * step cuts eta by at least 0.3x; after the first step that does not, GMRES-IR
  * (left-preconditioned GMRES with M, restart opt->gmres_restart, products
  * with A in FP64) for every remaining step.
- * Returns CF_ERR_NOT_CONVERGED when max_iter steps, or two GMRES-IR steps in
- * a row that fail to halve eta, leave eta > tol (X then holds the best
+ * If refinement stalls (max_iter steps, a GMRES-IR step that fails to halve
+ * eta, or a breakdown of the low-precision factorization), the
+ * matrix is refactored once with CF_BF16X3 updates and refinement continues
+ * from the best iterate with a fresh step budget (stats->escalated = 1).
+ * Returns CF_ERR_NOT_CONVERGED if that also stalls (max_iter more steps, or
+ * two GMRES-IR steps in a row that fail to halve eta; X then holds the best
  * iterate and stats->eta its backward error).
  * ------------------------------------------------------------------------ */
 size_t cf_gesv_mixed_workspace_size(int n, int nrhs, cf_prec factor_prec,

@@ -31,9 +31,9 @@ CF_ERR_WORKSPACE = -101
 CF_ERR_NOT_CONVERGED = -102
 CF_ERR_TIMEOUT = -103
 CF_ERR_UNSUPPORTED = -104
-CF_F64, CF_F32, CF_BF16, CF_F16, CF_FP8E4M3 = range(5)
+CF_F64, CF_F32, CF_BF16, CF_F16, CF_FP8E4M3, CF_BF16X3 = range(6)
 PREC = {"f64": CF_F64, "f32": CF_F32, "bf16": CF_BF16, "f16": CF_F16,
-        "fp8": CF_FP8E4M3, "fp8e4m3": CF_FP8E4M3}
+        "fp8": CF_FP8E4M3, "fp8e4m3": CF_FP8E4M3, "bf16x3": CF_BF16X3}
 
 
 class Options(ctypes.Structure):
@@ -49,7 +49,7 @@ class RefineStats(ctypes.Structure):
                 ("refine_ms", ctypes.c_double), ("residual_ms", ctypes.c_double),
                 ("update_ms", ctypes.c_double), ("update_flops", ctypes.c_double),
                 ("residual_launches", ctypes.c_int), ("update_launches", ctypes.c_int),
-                ("gmres_iterations", ctypes.c_int)]
+                ("gmres_iterations", ctypes.c_int), ("escalated", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

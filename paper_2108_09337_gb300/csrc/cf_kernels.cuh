@@ -93,6 +93,9 @@ int launch_ltrsm32(float *X, int ldx, int w, int cols, const float *L00, int ldl
 size_t trsv_ws_bytes(int n);
 size_t diag_inverse_floats(int n);
 int launch_diag_inverse(int mode, int n, const float *T, int ldt, float *Dinv, cudaStream_t st);
+int launch_diag_inverse64(int mode, int n, const float *T, int ldt, double *Dinv, cudaStream_t st);
+int launch_trsv_f64x(int mode, int n, int nrhs, const float *T, int ldt, const double *Dinv, double *X, int ldx,
+                     int *sync_ws, cudaStream_t st);
 int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
                     int *sync_ws, cudaStream_t st);
 int trsv_take_status(cudaStream_t st, int *status);

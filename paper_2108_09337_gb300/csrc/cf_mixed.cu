@@ -72,6 +72,50 @@ __global__ void k_cvt_cols_kmajor(int k, int cols, int kpad, const float *__rest
     }
 }
 
+// Split BF16 operands: x = hi + lo with hi = bf16(x), lo = bf16(x - hi)
+// (together 16 significant bits).  Three segments of K values, segment s at
+// dst + s * seg: PATTERN 0 (left operand) hi, hi, lo; PATTERN 1 (right
+// operand) hi, lo, hi -- so one contraction over the three segments sums
+// hi.hi + hi.lo + lo.hi, the split product without its lo.lo term.
+template <int PATTERN>
+__device__ __forceinline__ void put_split(__nv_bfloat16 *d, size_t seg, float x) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+    d[0] = hi;
+    d[seg] = PATTERN == 0 ? hi : lo;
+    d[2 * seg] = PATTERN == 0 ? lo : hi;
+}
+
+// Split form of k_cvt_rows_kmajor.
+template <int PATTERN>
+__global__ void __launch_bounds__(256)
+k_cvt_rows_split(int rows, int k, int kpad, const float *__restrict__ src, int lds, __nv_bfloat16 *__restrict__ dst,
+                 int ldk, int seg) {
+    __shared__ float t[32][33];
+    const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int q = ty; q < 32; q += 8) {
+        const int kk = k0 + q, r = r0 + tx;
+        t[q][tx] = (r < rows && kk < k) ? src[(size_t)r + (size_t)kk * lds] : 0.f;
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+        const int r = r0 + q, kk = k0 + tx;
+        if (r < rows && kk < kpad) put_split<PATTERN>(dst + (size_t)r * ldk + kk, (size_t)seg, t[tx][q]);
+    }
+}
+
+// Split form of k_cvt_cols_kmajor.
+template <int PATTERN>
+__global__ void k_cvt_cols_split(int k, int cols, int kpad, const float *__restrict__ src, int lds,
+                                 __nv_bfloat16 *__restrict__ dst, int ldk, int seg) {
+    const size_t tot = (size_t)cols * kpad;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int kk = (int)(e % kpad), j = (int)(e / kpad);
+        put_split<PATTERN>(dst + (size_t)j * ldk + kk, (size_t)seg, kk < k ? src[(size_t)kk + (size_t)j * lds] : 0.f);
+    }
+}
+
 __global__ void k_iota(int n, int *p) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
 }
@@ -207,29 +251,6 @@ __global__ void k_normalize(int n, int nrhs, const double *sq, double *nrm, cons
     }
 }
 
-// Rf[i, c] = (float)(Y[perm[i], c] / s_c), s_c = max_i |Y[i, c]| (1 if 0),
-// with s_c read from the bit patterns k_col_absmax leaves.
-__global__ void k_gather_scale_bits(int n, int nrhs, const int *perm, const double *Y, const unsigned long long *sbits,
-                                    float *Rf) {
-    const size_t tot = (size_t)n * nrhs;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % n), c = (int)(e / n);
-        const double sc = __longlong_as_double((long long)sbits[c]);
-        const int src = perm ? perm[i] : i;
-        Rf[e] = (float)(Y[(size_t)src + (size_t)c * n] / (sc > 0.0 ? sc : 1.0));
-    }
-}
-
-// Z[:, c] = s_c * Df[:, c]
-__global__ void k_scale_out_bits(int n, int nrhs, const float *Df, const unsigned long long *sbits, double *Z) {
-    const size_t tot = (size_t)n * nrhs;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e / n);
-        const double sc = __longlong_as_double((long long)sbits[c]);
-        Z[e] = (sc > 0.0 ? sc : 1.0) * (double)Df[e];
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Workspace
 // ---------------------------------------------------------------------------
@@ -243,6 +264,7 @@ struct MixedWS {
     double *R = nullptr, *scale = nullptr, *rowsum = nullptr;
     float *Rf = nullptr;
     float *DinvL = nullptr, *DinvU = nullptr;   // inverses of the 64 x 64 diagonal blocks
+    double *DinvL64 = nullptr, *DinvU64 = nullptr;   // the same in FP64 (GMRES-IR preconditioner)
     int *trsv_sync = nullptr;
     unsigned long long *norms = nullptr;   // [0..nrhs) |R|, [nrhs..2nrhs) |X|, [2nrhs..3nrhs) |B|, [3nrhs] ||A||
     // GMRES-IR
@@ -253,7 +275,6 @@ struct MixedWS {
     double *hcol = nullptr;                // (m + 2) x nrhs: one Hessenberg column per right-hand side
     double *coef = nullptr;                // (m + 1) x nrhs
     double *sq = nullptr;                  // nrhs squared norms
-    unsigned long long *sbits = nullptr;   // preconditioner input scales
     float *sc8 = nullptr;                  // FP8 tile scales: slab (rows/128 x V/128), then one step
     double *Xbest = nullptr;               // best iterate so far
     size_t bytes = 0;
@@ -270,12 +291,14 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     Carver cv(work);
     w->ldw = (n + 31) / 32 * 32;
     w->W = cv.take<float>((size_t)w->ldw * (n > 0 ? n : 1), 1024);
-    // Ab: the K-major left operand of one step (rows x kMaxV), also the
-    // pivot rows' slab operand (kMaxV x Vp) of the left-looking update
-    w->Ab = cv.take<uint16_t>((size_t)((n > Vp ? n : Vp) + 1) * kMaxV, 1024);
-    w->Bb = cv.take<uint16_t>((size_t)(n + 1) * kMaxV, 1024);
-    w->Lb = cv.take<uint16_t>((size_t)(n + 1) * Vp, 1024);
-    w->Ub = lu ? cv.take<uint16_t>((size_t)(n + 1) * Vp, 1024) : nullptr;
+    // Low-precision operands, sized for the split-BF16 form (three K
+    // segments): Ab the left operand of one step (rows x 3 kMaxV), also the
+    // pivot rows' slab operand (kMaxV x 3 Vp) of the left-looking update;
+    // Bb the right operand of one step; Lb / Ub the slab's operands.
+    w->Ab = cv.take<uint16_t>((size_t)((n > Vp ? n : Vp) + 1) * 3 * kMaxV, 1024);
+    w->Bb = cv.take<uint16_t>((size_t)(n + 1) * 3 * kMaxV, 1024);
+    w->Lb = cv.take<uint16_t>((size_t)(n + 1) * 3 * Vp, 1024);
+    w->Ub = cv.take<uint16_t>((size_t)(n + 1) * 3 * Vp, 1024);
     w->perm = cv.take<int>(n + 1);
     w->ipiv = cv.take<int>(n + 1);
     if (lu) {
@@ -296,6 +319,8 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->Rf = cv.take<float>((size_t)n * nrhs + 1);
     w->DinvL = cv.take<float>(diag_inverse_floats(n));
     w->DinvU = lu ? cv.take<float>(diag_inverse_floats(n)) : nullptr;
+    w->DinvL64 = cv.take<double>(diag_inverse_floats(n));
+    w->DinvU64 = lu ? cv.take<double>(diag_inverse_floats(n)) : nullptr;
     w->trsv_sync = cv.take<int>(trsv_ws_bytes(n) / sizeof(int) + 1);
     w->norms = cv.take<unsigned long long>(3 * nrhs + 2);
     w->m = o.gmres_restart;
@@ -307,7 +332,6 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->hcol = cv.take<double>((size_t)(w->m + 2) * nrhs);
     w->coef = cv.take<double>((size_t)(w->m + 1) * nrhs);
     w->sq = cv.take<double>(nrhs + 1);
-    w->sbits = cv.take<unsigned long long>(nrhs + 1);
     w->Xbest = cv.take<double>(blk + 1);
     w->sc8 = cv.take<float>((size_t)(ceil_div(n > 0 ? n : 1, 128) + 1) * (Vp / 128 + 2));
     w->bytes = cv.size();
@@ -370,15 +394,41 @@ static int cvt_cols(int k, int cols, int kpad, const float *src, int lds, void *
     return CF_OK;
 }
 
+static int cvt_rows_split(int rows, int k, int kpad, const float *src, int lds, void *dst, int ldk, int seg,
+                          int pattern, cudaStream_t st) {
+    if (rows <= 0) return CF_OK;
+    dim3 grid(ceil_div(rows, 32), ceil_div(kpad, 32));
+    if (pattern == 0)
+        k_cvt_rows_split<0><<<grid, 256, 0, st>>>(rows, k, kpad, src, lds, (__nv_bfloat16 *)dst, ldk, seg);
+    else
+        k_cvt_rows_split<1><<<grid, 256, 0, st>>>(rows, k, kpad, src, lds, (__nv_bfloat16 *)dst, ldk, seg);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+static int cvt_cols_split(int k, int cols, int kpad, const float *src, int lds, void *dst, int ldk, int seg,
+                          int pattern, cudaStream_t st) {
+    if (cols <= 0) return CF_OK;
+    if (pattern == 0)
+        k_cvt_cols_split<0><<<grid_for((size_t)cols * kpad), 256, 0, st>>>(k, cols, kpad, src, lds,
+                                                                           (__nv_bfloat16 *)dst, ldk, seg);
+    else
+        k_cvt_cols_split<1><<<grid_for((size_t)cols * kpad), 256, 0, st>>>(k, cols, kpad, src, lds,
+                                                                           (__nv_bfloat16 *)dst, ldk, seg);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Mixed LU of W (in place): tournament pivoting with FP32 panels, tensor-core
 // Schur updates.
 // ---------------------------------------------------------------------------
 template <typename LP>
-static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu) {
+static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu, bool split) {
     const bool bf16 = std::is_same<LP, __nv_bfloat16>::value;
     const int v = o.v, V = pick_V(n, o);
-    const int Vpad = (V + 63) / 64 * 64;        // K stride of the slab's U operand
+    const int Vpad = (V + 63) / 64 * 64;        // K stride (per segment) of the slab's U operand
+    const int S = split ? 3 : 1;                 // K segments per operand
     const size_t ld = (size_t)w.ldw;
     float *W = w.W;
     int rc;
@@ -405,39 +455,67 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             // U[J0:k0, JE:] (left-looking, K = off).
             if (off > 0 && nout > 0) {
                 const int Kp = (off + 63) / 64 * 64;
-                if ((rc = cvt_rows<LP>(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Ab, Kp, st))) return rc;
-                if ((rc = launch_schur_tc(wd, nout, Kp, w.Ab, Kp, w.Ub, Vpad, W + k0 + JE * ld, w.ldw, bf16, false,
-                                          st, 0)))
-                    return rc;
+                float *Cp = W + k0 + JE * ld;
+                if (!split) {
+                    if ((rc = cvt_rows<LP>(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Ab, Kp, st))) return rc;
+                    if ((rc = launch_schur_tc(wd, nout, Kp, w.Ab, Kp, w.Ub, Vpad, Cp, w.ldw, bf16, false, st, 0)))
+                        return rc;
+                } else {
+                    // segments (hi, hi, lo) x (hi, lo, hi): three K = off products
+                    if ((rc = cvt_rows_split(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Ab, 3 * Kp, Kp, 0, st)))
+                        return rc;
+                    for (int sg = 0; sg < 3; ++sg)
+                        if ((rc = launch_schur_tc(wd, nout, Kp, (const __nv_bfloat16 *)w.Ab + (size_t)sg * Kp, 3 * Kp,
+                                                  (const __nv_bfloat16 *)w.Ub + (size_t)sg * Vpad, 3 * Vpad, Cp,
+                                                  w.ldw, true, false, st, 0)))
+                            return rc;
+                }
             }
             // LU-3 / LU-4; they also write the K-major low-precision operands
-            // of the updates inside the slab.
-            if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, false, (LP *)w.Ab, kMaxV, kMaxV,
-                                         nullptr, st)))
+            // of the updates inside the slab (split form: converted after).
+            if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, false,
+                                         split ? nullptr : (LP *)w.Ab, kMaxV, kMaxV, nullptr, st)))
                 return rc;
-            if ((rc = launch_ltrsm32<LP>(A00 + wd * ld, w.ldw, wd, right, A00, w.ldw, (LP *)w.Bb, kMaxV, kMaxV, st)))
+            if ((rc = launch_ltrsm32<LP>(A00 + wd * ld, w.ldw, wd, right, A00, w.ldw, split ? nullptr : (LP *)w.Bb,
+                                         kMaxV, kMaxV, st)))
                 return rc;
+            if (split) {
+                if ((rc = cvt_rows_split(below, wd, kMaxV, A00 + wd, w.ldw, w.Ab, 3 * kMaxV, kMaxV, 0, st))) return rc;
+                if ((rc = cvt_cols_split(wd, right, kMaxV, A00 + wd * ld, w.ldw, w.Bb, 3 * kMaxV, kMaxV, 1, st)))
+                    return rc;
+            }
             // U rows of this step right of the slab -> K-major operand of the
             // slab's deferred update (K rows off .. off + wd, zeros up to the
             // next multiple of 64)
             if (nout > 0) {
                 const int kp = (off + wd + 63) / 64 * 64 - off;
-                if ((rc = cvt_cols<LP>(wd, nout, kp, W + k0 + JE * ld, w.ldw, (LP *)w.Ub + off, Vpad, st))) return rc;
+                if (!split) {
+                    if ((rc = cvt_cols<LP>(wd, nout, kp, W + k0 + JE * ld, w.ldw, (LP *)w.Ub + off, Vpad, st)))
+                        return rc;
+                } else if ((rc = cvt_cols_split(wd, nout, kp, W + k0 + JE * ld, w.ldw,
+                                                (__nv_bfloat16 *)w.Ub + off, 3 * Vpad, Vpad, 1, st))) {
+                    return rc;
+                }
             }
             if (below <= 0 || right <= 0) continue;
             // A11 restricted to the slab's remaining columns (every row below)
             const int nslab = JE - (k0 + wd);
             float *C = A00 + wd + wd * ld;
-            if (nslab > 0 &&
-                (rc = launch_schur_tc(below, nslab, kMaxV, w.Ab, kMaxV, w.Bb, kMaxV, C, w.ldw, bf16, false, st, 0)))
+            if (nslab > 0 && (rc = launch_schur_tc(below, nslab, S * kMaxV, w.Ab, S * kMaxV, w.Bb, S * kMaxV, C,
+                                                   w.ldw, bf16, false, st, 0)))
                 return rc;
         }
         if (JE < n) {
             // deferred update of everything right of and below the slab
             const int Vs = JE - J0, Vp = (Vs + 63) / 64 * 64, mr = n - JE;
-            if ((rc = cvt_rows<LP>(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Lb, Vp, st))) return rc;
+            if (!split) {
+                if ((rc = cvt_rows<LP>(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Lb, Vp, st))) return rc;
+            } else if ((rc = cvt_rows_split(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Lb, 3 * Vp, Vp, 0, st))) {
+                return rc;
+            }
             if (tu && (rc = tu->begin(st))) return rc;
-            if ((rc = launch_schur_tc(mr, mr, Vp, w.Lb, Vp, w.Ub, Vpad, W + JE + JE * ld, w.ldw, bf16, false, st, 0)))
+            if ((rc = launch_schur_tc(mr, mr, S * Vp, w.Lb, S * Vp, w.Ub, S * Vpad, W + JE + JE * ld, w.ldw, bf16,
+                                      false, st, 0)))
                 return rc;
             if (tu && (rc = tu->end(st, 2.0 * mr * (double)mr * Vs))) return rc;
         }
@@ -500,9 +578,10 @@ static int mixed_potrf_fp8(int n, MixedWS &w, int *info, const Opts &o, cudaStre
 // Mixed Cholesky of W (lower, in place).
 // ---------------------------------------------------------------------------
 template <typename LP>
-static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu) {
+static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu, bool split) {
     const bool bf16 = std::is_same<LP, __nv_bfloat16>::value;
     const int v = o.v, V = pick_V(n, o);
+    const int S = split ? 3 : 1;
     const size_t ld = (size_t)w.ldw;
     float *W = w.W;
     int rc;
@@ -516,20 +595,34 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             const int below = m - wd;
             if (below <= 0) continue;
             // CH-2: L10 = A10 L00^{-T}, with its K-major low-precision copy
-            if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, true, (LP *)w.Ab, kMaxV, kMaxV, info,
-                                         st)))
+            if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, true, split ? nullptr : (LP *)w.Ab,
+                                         kMaxV, kMaxV, info, st)))
                 return rc;
             const int nslab = JE - (k0 + wd);
             if (nslab <= 0) continue;
-            if ((rc = launch_schur_tc(below, nslab, kMaxV, w.Ab, kMaxV, w.Ab, kMaxV, A00 + wd + wd * ld, w.ldw, bf16,
-                                      true, st, 0)))
+            const void *Bop = w.Ab;
+            if (split) {   // left (hi, hi, lo) and right (hi, lo, hi) forms of L10
+                if ((rc = cvt_rows_split(below, wd, kMaxV, A00 + wd, w.ldw, w.Ab, 3 * kMaxV, kMaxV, 0, st))) return rc;
+                if ((rc = cvt_rows_split(below, wd, kMaxV, A00 + wd, w.ldw, w.Bb, 3 * kMaxV, kMaxV, 1, st))) return rc;
+                Bop = w.Bb;
+            }
+            if ((rc = launch_schur_tc(below, nslab, S * kMaxV, w.Ab, S * kMaxV, Bop, S * kMaxV, A00 + wd + wd * ld,
+                                      w.ldw, bf16, true, st, 0)))
                 return rc;
         }
         if (JE < n) {
             const int Vs = JE - J0, Vp = (Vs + 63) / 64 * 64, mr = n - JE;
-            if ((rc = cvt_rows<LP>(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Lb, Vp, st))) return rc;
+            const void *Bop = w.Lb;
+            if (!split) {
+                if ((rc = cvt_rows<LP>(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Lb, Vp, st))) return rc;
+            } else {
+                if ((rc = cvt_rows_split(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Lb, 3 * Vp, Vp, 0, st))) return rc;
+                if ((rc = cvt_rows_split(mr, Vs, Vp, W + JE + J0 * ld, w.ldw, w.Ub, 3 * Vp, Vp, 1, st))) return rc;
+                Bop = w.Ub;
+            }
             if (tu && (rc = tu->begin(st))) return rc;
-            if ((rc = launch_schur_tc(mr, mr, Vp, w.Lb, Vp, w.Lb, Vp, W + JE + JE * ld, w.ldw, bf16, true, st, 0)))
+            if ((rc = launch_schur_tc(mr, mr, S * Vp, w.Lb, S * Vp, Bop, S * Vp, W + JE + JE * ld, w.ldw, bf16, true,
+                                      st, 0)))
                 return rc;
             // algorithmic flops of the triangular update: m (m + 1) K
             if (tu && (rc = tu->end(st, (double)mr * (mr + 1.0) * Vs))) return rc;
@@ -556,19 +649,26 @@ static int solve_f32(int n, int nrhs, const MixedWS &w, bool lu, cudaStream_t st
 // the host; then X += d.  All right-hand sides advance together (one FP64
 // product A [v_1 .. v_nrhs] per step).
 // ---------------------------------------------------------------------------
-// Z = M^{-1} Y through the FP32 factors, Y scaled per column into FP32.
+// Z[i, c] = Y[perm[i], c] (perm == nullptr: copy)
+__global__ void k_gather_rows(int n, int nrhs, const int *perm, const double *Y, double *Z) {
+    const size_t tot = (size_t)n * nrhs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), c = (int)(e / n);
+        Z[e] = Y[(size_t)(perm ? perm[i] : i) + (size_t)c * n];
+    }
+}
+
+// Z = M^{-1} Y with the FP32-stored factors applied in FP64 arithmetic (with
+// the preconditioner applied in FP32, the Krylov relations are polluted at
+// the FP32 level times the factors' condition and GMRES stalls on the hard
+// cases).
 static int apply_precond(int n, int nrhs, const double *Yin, double *Z, MixedWS &w, bool lu, cudaStream_t st) {
     const size_t blk = (size_t)n * nrhs;
-    CF_CUDA_TRY(cudaMemsetAsync(w.sbits, 0, sizeof(unsigned long long) * nrhs, st));
-    k_col_absmax<<<dim3(grid_for(n), nrhs), 256, 0, st>>>(n, nrhs, Yin, n, w.sbits);
+    k_gather_rows<<<grid_for(blk), 256, 0, st>>>(n, nrhs, lu ? w.perm : nullptr, Yin, Z);
     CF_LAUNCH_CHECK();
-    k_gather_scale_bits<<<grid_for(blk), 256, 0, st>>>(n, nrhs, lu ? w.perm : nullptr, Yin, w.sbits, w.Rf);
-    CF_LAUNCH_CHECK();
-    int rc = solve_f32(n, nrhs, w, lu, st);
-    if (rc) return rc;
-    k_scale_out_bits<<<grid_for(blk), 256, 0, st>>>(n, nrhs, w.Rf, w.sbits, Z);
-    CF_LAUNCH_CHECK();
-    return CF_OK;
+    int rc;
+    if ((rc = launch_trsv_f64x(lu ? 0 : 2, n, nrhs, w.W, w.ldw, w.DinvL64, Z, n, w.trsv_sync, st))) return rc;
+    return launch_trsv_f64x(lu ? 1 : 3, n, nrhs, w.W, w.ldw, lu ? w.DinvU64 : w.DinvL64, Z, n, w.trsv_sync, st);
 }
 
 // out[i * nrhs + c] (+)= <V_i[:, c], W[:, c]> for i < nv, fixed summation order.
@@ -684,7 +784,7 @@ static int gmres_correct(int n, int nrhs, const double *A, int lda, double *X, i
 template <typename LP>
 static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *B, int ldb, double *X, int ldx,
                        int *info, cf_refine_stats *stats, void *work, size_t lwork, const Opts &o, bool lu,
-                       cudaStream_t st) {
+                       bool split0, cudaStream_t st) {
     MixedWS w;
     int rc = carve_mixed(nullptr, n, nrhs, o, lu, &w);
     if (rc) return rc;
@@ -700,46 +800,60 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
 
     // ---- factorization (Cholesky retries with a diagonal shift on breakdown)
+    Timer tupd, tres;
     double shift = 0.0;
     int hinfo = 0;
-    Timer tupd, tres;
-    const double u_lp = std::is_same<LP, __nv_bfloat16>::value ? 0x1p-8
-                        : std::is_same<LP, fp8_e4m3>::value   ? 0x1p-4
-                                                              : 0x1p-11;
-    for (int attempt = 0; attempt < 4; ++attempt) {
-        // W = fl32(A) (+ shift on the diagonal)
-        if ((rc = launch_split_f64(n, n, A, lda, nullptr, nullptr, w.ldw, w.W, w.ldw, shift, st))) return rc;
-        CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
-        if constexpr (std::is_same<LP, fp8_e4m3>::value)
-            rc = lu ? CF_ERR_UNSUPPORTED : mixed_potrf_fp8(n, w, info, o, st, &tupd);
-        else
-            rc = lu ? mixed_getrf<LP>(n, w, info, o, st, &tupd) : mixed_potrf<LP>(n, w, info, o, st, &tupd);
-        if (rc) return rc;
+    // one factorization of fl32(A) into w.W: split = BF16 hi + lo operands
+    auto factorize = [&](bool split) -> int {
+        const double u_lp = split                                  ? 0x1p-16
+                            : std::is_same<LP, __nv_bfloat16>::value ? 0x1p-8
+                            : std::is_same<LP, fp8_e4m3>::value    ? 0x1p-4
+                                                                   : 0x1p-11;
+        shift = 0.0;
+        int rc2 = CF_OK;
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            // W = fl32(A) (+ shift on the diagonal)
+            rc2 = launch_split_f64(n, n, A, lda, nullptr, nullptr, w.ldw, w.W, w.ldw, shift, st);
+            if (rc2) return rc2;
+            CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
+            if (split)
+                rc2 = lu ? mixed_getrf<__nv_bfloat16>(n, w, info, o, st, &tupd, true)
+                         : mixed_potrf<__nv_bfloat16>(n, w, info, o, st, &tupd, true);
+            else if constexpr (std::is_same<LP, fp8_e4m3>::value)
+                rc2 = lu ? CF_ERR_UNSUPPORTED : mixed_potrf_fp8(n, w, info, o, st, &tupd);
+            else
+                rc2 = lu ? mixed_getrf<LP>(n, w, info, o, st, &tupd, false)
+                         : mixed_potrf<LP>(n, w, info, o, st, &tupd, false);
+            if (rc2) return rc2;
+            CF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (hinfo == 0 || lu) break;
+            // Cholesky broke down in low precision: refactor A + s I with
+            // s = c u_lp max_i |a_ii|, c = 1, 4, 16 (diagonal shift of Higham and
+            // Pranesh, SISC 2021); refinement with the unshifted A removes it.
+            CF_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(unsigned long long), st));
+            k_diag_absmax<<<grid_for(n), 256, 0, st>>>(n, A, lda, w.norms);
+            CF_LAUNCH_CHECK();
+            unsigned long long dbits = 0;
+            CF_CUDA_TRY(cudaMemcpyAsync(&dbits, w.norms, sizeof(dbits), cudaMemcpyDeviceToHost, st));
+            CF_CUDA_TRY(cudaStreamSynchronize(st));
+            double dm;
+            memcpy(&dm, &dbits, sizeof(dm));
+            shift = u_lp * dm * (double)(1 << (2 * attempt));
+            hinfo = 0;
+        }
         CF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CF_CUDA_TRY(cudaStreamSynchronize(st));
-        if (hinfo == 0 || lu) break;
-        // Cholesky broke down in low precision: refactor A + s I with
-        // s = c u_lp max_i |a_ii|, c = 1, 4, 16 (diagonal shift of Higham and
-        // Pranesh, SISC 2021); refinement with the unshifted A removes it.
-        CF_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(unsigned long long), st));
-        k_diag_absmax<<<grid_for(n), 256, 0, st>>>(n, A, lda, w.norms);
-        CF_LAUNCH_CHECK();
-        unsigned long long dbits = 0;
-        CF_CUDA_TRY(cudaMemcpyAsync(&dbits, w.norms, sizeof(dbits), cudaMemcpyDeviceToHost, st));
-        CF_CUDA_TRY(cudaStreamSynchronize(st));
-        double dm;
-        memcpy(&dm, &dbits, sizeof(dm));
-        shift = u_lp * dm * (double)(1 << (2 * attempt));
-        hinfo = 0;
-    }
+        int tstat = 0;
+        if ((rc2 = tc_take_status(st, &tstat))) return rc2;
+        if (tstat != 0) return CF_ERR_TIMEOUT;
+        if ((rc2 = fp8_take_status(st, &tstat))) return rc2;
+        if (tstat != 0) return CF_ERR_TIMEOUT;
+        return CF_OK;
+    };
+    bool split = split0;
+    if ((rc = factorize(split))) return rc;
     S.shift = shift;
-    CF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
     CF_CUDA_TRY(cudaEventRecord(e1, st));
-    int tstat = 0;
-    if ((rc = tc_take_status(st, &tstat))) return rc;
-    if (tstat != 0) return CF_ERR_TIMEOUT;
-    if ((rc = fp8_take_status(st, &tstat))) return rc;
-    if (tstat != 0) return CF_ERR_TIMEOUT;
     S.info = hinfo;
 
     // ---- refinement
@@ -762,16 +876,18 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     k_copy_cols<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, B, ldb, w.R, ldr);
     CF_LAUNCH_CHECK();
 
-    if (S.info == 0) {
-        if ((rc = launch_diag_inverse(lu ? 0 : 2, n, w.W, w.ldw, w.DinvL, st))) return rc;
-        if (lu && (rc = launch_diag_inverse(1, n, w.W, w.ldw, w.DinvU, st))) return rc;
-    }
+    auto diag_inverses = [&]() -> int {
+        int rc2 = launch_diag_inverse(lu ? 0 : 2, n, w.W, w.ldw, w.DinvL, st);
+        if (rc2 == CF_OK && lu) rc2 = launch_diag_inverse(1, n, w.W, w.ldw, w.DinvU, st);
+        return rc2;
+    };
+    if (S.info == 0 && (rc = diag_inverses())) return rc;
 
     std::vector<unsigned long long> hn(3 * nrhs + 2);
     std::vector<double> hscale(nrhs);
     double eta_prev = HUGE_VAL, eta = HUGE_VAL, eta_best = HUGE_VAL;
-    int it = 0, stall = 0, solver = 0;
-    bool converged = false;
+    int it = 0, stall = 0, solver = 0, it_limit = o.max_iter;
+    bool converged = false, escalated = false;
     for (;; ++it) {
         if (it > 0) {
             if ((rc = tres.begin(st))) return rc;
@@ -806,17 +922,44 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             k_copy_cols<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, X, ldx, w.Xbest, n);
             CF_LAUNCH_CHECK();
         }
-        if (it >= o.max_iter || S.info != 0) break;
         // Classical refinement that fails to cut eta by kSwitchRate in one
         // step hands over to GMRES-IR (at that rate the remaining classical
         // steps would each cost as much as an inner GMRES step and converge
-        // slower); GMRES-IR that fails to halve eta twice in a row stops.
-        if (solver == 0 && it >= 1 && !(eta <= kSwitchRate * eta_prev)) {
+        // slower); GMRES-IR that fails to halve eta twice in a row, the step
+        // budget, or a breakdown of the low-precision factorization ends the
+        // attempt.
+        bool give_up = it >= it_limit || S.info != 0;
+        if (!give_up && solver == 0 && it >= 1 && !(eta <= kSwitchRate * eta_prev)) {
             solver = 1;
-        } else if (solver == 1 && !(eta <= 0.5 * eta_prev)) {
-            if (++stall >= 2) break;
+            if ((rc = launch_diag_inverse64(lu ? 0 : 2, n, w.W, w.ldw, w.DinvL64, st))) return rc;
+            if (lu && (rc = launch_diag_inverse64(1, n, w.W, w.ldw, w.DinvU64, st))) return rc;
+        } else if (!give_up && solver == 1 && !(eta <= 0.5 * eta_prev)) {
+            // before escalating one failed GMRES-IR step is enough (refactoring
+            // costs about one step); after it, two in a row
+            give_up = ++stall >= (split ? 2 : 1);
         } else {
             stall = 0;
+        }
+        if (give_up) {
+            if (split) break;
+            // Escalate once: refactor with split BF16 updates (hi + lo
+            // operands, 16 significant bits) and refine on from the best
+            // iterate with a fresh step budget.
+            split = escalated = true;
+            if ((rc = factorize(true))) return rc;
+            S.info = hinfo;
+            S.shift = shift;
+            if (S.info != 0) break;
+            if ((rc = diag_inverses())) return rc;
+            if (eta_best < eta) {
+                k_copy_cols<<<grid_for((size_t)n * nrhs), 256, 0, st>>>(n, nrhs, w.Xbest, n, X, ldx);
+                CF_LAUNCH_CHECK();
+            }
+            solver = 0;
+            stall = 0;
+            eta_prev = HUGE_VAL;
+            it_limit = it + o.max_iter;
+            continue;
         }
         eta_prev = eta;
         if (solver == 0) {
@@ -840,6 +983,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     }
     CF_CUDA_TRY(cudaEventRecord(e2, st));
     CF_CUDA_TRY(cudaEventSynchronize(e2));
+    int tstat = 0;
     if ((rc = trsv_take_status(st, &tstat))) return rc;
     if (tstat != 0) return CF_ERR_TIMEOUT;
     float f_ms = 0, r_ms = 0;
@@ -850,6 +994,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     cudaEventDestroy(e2);
     S.iterations = it;
     S.solver = solver;
+    S.escalated = escalated ? 1 : 0;
     S.converged = converged ? 1 : 0;
     S.eta = eta;
     S.factor_ms = f_ms;
@@ -873,7 +1018,7 @@ static int check_mixed_args(int n, int nrhs, const double *A, int lda, const dou
     if (ldb < (n > 1 ? n : 1)) return -6;
     if (n > 0 && nrhs > 0 && X == nullptr) return -7;
     if (ldx < (n > 1 ? n : 1)) return -8;
-    if (prec != CF_BF16 && prec != CF_F16 && prec != CF_FP8E4M3) return -9;
+    if (prec != CF_BF16 && prec != CF_F16 && prec != CF_FP8E4M3 && prec != CF_BF16X3) return -9;
     if (info == nullptr) return -10;
     return CF_OK;
 }
@@ -902,14 +1047,15 @@ static int mixed_entry(int n, int nrhs, const double *A, int lda, const double *
         if (stats) { memset(stats, 0, sizeof(*stats)); stats->converged = 1; }
         return CF_OK;
     }
-    if (prec == CF_BF16)
-        return mixed_solve<__nv_bfloat16>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, st);
+    if (prec == CF_BF16 || prec == CF_BF16X3)
+        return mixed_solve<__nv_bfloat16>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu,
+                                          prec == CF_BF16X3, st);
     if (prec == CF_FP8E4M3) {
         if (lu) return -9;                     // FP8 updates: Cholesky only
         if (pick_V(n, o) % 128 != 0) return CF_ERR_UNSUPPORTED;
-        return mixed_solve<fp8_e4m3>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, st);
+        return mixed_solve<fp8_e4m3>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, false, st);
     }
-    return mixed_solve<__half>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, st);
+    return mixed_solve<__half>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, false, st);
 }
 
 extern "C" size_t cf_gesv_mixed_workspace_size(int n, int nrhs, cf_prec prec, const cf_options *opt) {

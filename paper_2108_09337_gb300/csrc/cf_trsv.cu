@@ -29,21 +29,24 @@ __device__ __forceinline__ float m_elem(const float *T, int ldt, int i, int k) {
 }
 
 // Inverse of each 64 x 64 diagonal block of M, stored block after block,
-// column-major (Dinv[b*64*64 + i + 64*j]).
-template <int MODE>
-__global__ void __launch_bounds__(256) k_diag_inverse(int n, const float *__restrict__ T, int ldt, float *Dinv) {
-    __shared__ float Ms[kSB][kSB + 1];   // Ms[i][k] = M(b0+i, b0+k)
-    __shared__ float Xs[kSB][kSB + 1];   // Xs[i][j] = inverse
+// column-major (Dinv[b*64*64 + i + 64*j]), computed in VT (float, or double
+// for the FP64-arithmetic solves with the same FP32 factor).  Dynamic shared
+// memory: 2 * 64 * 65 VT.
+template <int MODE, typename VT>
+__global__ void __launch_bounds__(256) k_diag_inverse(int n, const float *__restrict__ T, int ldt, VT *Dinv) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    VT (*Ms)[kSB + 1] = reinterpret_cast<VT (*)[kSB + 1]>(dsm);                               // Ms[i][k] = M(b0+i, b0+k)
+    VT (*Xs)[kSB + 1] = reinterpret_cast<VT (*)[kSB + 1]>(dsm + sizeof(VT) * kSB * (kSB + 1));  // inverse
     const int b = blockIdx.x, b0 = b * kSB, nbk = min(kSB, n - b0);
     const int tid = threadIdx.x;
     for (int e = tid; e < kSB * kSB; e += 256) {
         const int i = e % kSB, k = e / kSB;
-        float v = 0.f;
-        if (i < nbk && k < nbk) v = m_elem<MODE>(T, ldt, b0 + i, b0 + k);
-        if (i >= nbk || k >= nbk) v = (i == k) ? 1.f : 0.f;
-        if (MODE == 0 && i == k) v = 1.f;
+        VT v = VT(0);
+        if (i < nbk && k < nbk) v = (VT)m_elem<MODE>(T, ldt, b0 + i, b0 + k);
+        if (i >= nbk || k >= nbk) v = (i == k) ? VT(1) : VT(0);
+        if (MODE == 0 && i == k) v = VT(1);
         Ms[i][k] = v;
-        Xs[i][k] = (i == k) ? 1.f : 0.f;
+        Xs[i][k] = (i == k) ? VT(1) : VT(0);
     }
     __syncthreads();
     const bool lower = (MODE != 1);
@@ -54,13 +57,13 @@ __global__ void __launch_bounds__(256) k_diag_inverse(int n, const float *__rest
         const int k = lower ? s : kSB - 1 - s;
         if (MODE != 0 && i0 == 0) Xs[k][j] = Xs[k][j] / Ms[k][k];
         __syncthreads();
-        const float xk = Xs[k][j];
+        const VT xk = Xs[k][j];
         for (int i = i0; i < kSB; i += 4) {
-            if ((lower && i > k) || (!lower && i < k)) Xs[i][j] = fmaf(-Ms[i][k], xk, Xs[i][j]);
+            if ((lower && i > k) || (!lower && i < k)) Xs[i][j] = fma(-Ms[i][k], xk, Xs[i][j]);
         }
         __syncthreads();
     }
-    float *D = Dinv + (size_t)b * kSB * kSB;
+    VT *D = Dinv + (size_t)b * kSB * kSB;
     for (int e = tid; e < kSB * kSB; e += 256) D[e] = Xs[e % kSB][e / kSB];
 }
 
@@ -94,15 +97,17 @@ __device__ __forceinline__ void stage_tile(float *St, const float *T, int ldt, i
     }
 }
 
-template <int MODE, int NR>
+// VT: arithmetic and right-hand-side type (float, or double for FP64
+// solves with the FP32 factor); the factor tiles stay FP32 in shared memory.
+template <int MODE, int NR, typename VT>
 __global__ void __launch_bounds__(256)
-k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const float *__restrict__ Dinv, float *X,
+k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *__restrict__ Dinv, VT *X,
                int ldx, int *flags, int *ticket) {
     extern __shared__ __align__(16) float sm[];
     float *St0 = sm;                               // two tile buffers
     float *St1 = sm + kSB * kTLD;
-    float *Ds = sm + 2 * kSB * kTLD;               // inverse of the diagonal block
-    float *Ys = sm + 3 * kSB * kTLD;               // [kSB][NR + 1]
+    VT *Ds = reinterpret_cast<VT *>(sm + 2 * kSB * kTLD);   // inverse of the diagonal block
+    VT *Ys = Ds + kSB * kTLD;                               // [kSB][NR + 1]
     __shared__ int s_ticket;
     constexpr bool fwd = (MODE == 0 || MODE == 2);
     constexpr int CPT = (NR + 3) / 4;              // right-hand sides per thread
@@ -119,18 +124,18 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const floa
     const bool aligned = ((ldt & 3) == 0) && ((((uintptr_t)T) & 15) == 0);
     // the diagonal block's inverse does not depend on anyone: fetch it now
     {
-        const float *D = Dinv + (size_t)b * kSB * kSB;
+        const VT *D = Dinv + (size_t)b * kSB * kSB;
         for (int e = tid; e < kSB * kSB; e += 256) {
             const int ii = e % kSB, kk = e / kSB;
             // MODE 3 uses (L_bb^{-1})^T
             Ds[kk * kTLD + ii] = (MODE == 3) ? D[kk + kSB * ii] : D[ii + kSB * kk];
         }
     }
-    float acc[CPT];
+    VT acc[CPT];
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
         const int c = q + 4 * t;
-        acc[t] = (i < rb && c < nrhs) ? X[(size_t)(r0 + i) + (size_t)c * ldx] : 0.f;
+        acc[t] = (i < rb && c < nrhs) ? X[(size_t)(r0 + i) + (size_t)c * ldx] : VT(0);
     }
     // Stored tile that holds M(block b, block cb): for MODE 3 it is L(cb, b).
     auto tile_origin = [&](int cb, int &ti, int &tj) {
@@ -167,15 +172,15 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const floa
         __syncthreads();
         for (int e = tid; e < kSB * NR; e += 256) {
             const int kk = e % kSB, c = e / kSB;
-            Ys[kk * YLD + c] = (kk < cbk && c < nrhs) ? __ldcg(X + (size_t)(c0 + kk) + (size_t)c * ldx) : 0.f;
+            Ys[kk * YLD + c] = (kk < cbk && c < nrhs) ? __ldcg(X + (size_t)(c0 + kk) + (size_t)c * ldx) : VT(0);
         }
         cp_async_wait<1>();                        // this step's tile has landed
         __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < kSB; ++kk) {
-            const float m = (MODE == 3) ? St[i * kTLD + kk] : St[kk * kTLD + i];
+            const VT m = (VT)((MODE == 3) ? St[i * kTLD + kk] : St[kk * kTLD + i]);
 #pragma unroll
-            for (int t = 0; t < CPT; ++t) acc[t] = fmaf(-m, Ys[kk * YLD + q + 4 * t], acc[t]);
+            for (int t = 0; t < CPT; ++t) acc[t] = fma(-m, Ys[kk * YLD + q + 4 * t], acc[t]);
         }
         __syncthreads();
     }
@@ -185,14 +190,14 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const floa
     for (int t = 0; t < CPT; ++t)
         if (q + 4 * t < NR) Ys[i * YLD + q + 4 * t] = acc[t];
     __syncthreads();
-    float y[CPT];
+    VT y[CPT];
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) y[t] = 0.f;
+    for (int t = 0; t < CPT; ++t) y[t] = VT(0);
 #pragma unroll 8
     for (int kk = 0; kk < kSB; ++kk) {
-        const float d = Ds[kk * kTLD + i];
+        const VT d = Ds[kk * kTLD + i];
 #pragma unroll
-        for (int t = 0; t < CPT; ++t) y[t] = fmaf(d, Ys[kk * YLD + q + 4 * t], y[t]);
+        for (int t = 0; t < CPT; ++t) y[t] = fma(d, Ys[kk * YLD + q + 4 * t], y[t]);
     }
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
@@ -215,52 +220,84 @@ size_t diag_inverse_floats(int n) {
 }
 
 // mode: 0 unit lower, 1 upper, 2 lower, 3 lower transposed (see m_elem).
-int launch_diag_inverse(int mode, int n, const float *T, int ldt, float *Dinv, cudaStream_t st) {
+template <typename VT>
+static int launch_diag_inverse_t(int mode, int n, const float *T, int ldt, VT *Dinv, cudaStream_t st) {
     if (n <= 0) return CF_OK;
     const int nb = (n + kSB - 1) / kSB;
+    const size_t smem = 2 * sizeof(VT) * kSB * (kSB + 1);
     switch (mode) {
-        case 0: k_diag_inverse<0><<<nb, 256, 0, st>>>(n, T, ldt, Dinv); break;
-        case 1: k_diag_inverse<1><<<nb, 256, 0, st>>>(n, T, ldt, Dinv); break;
-        case 2: k_diag_inverse<2><<<nb, 256, 0, st>>>(n, T, ldt, Dinv); break;
+        case 0:
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_diag_inverse<0, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_diag_inverse<0, VT><<<nb, 256, smem, st>>>(n, T, ldt, Dinv);
+            break;
+        case 1:
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_diag_inverse<1, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_diag_inverse<1, VT><<<nb, 256, smem, st>>>(n, T, ldt, Dinv);
+            break;
+        case 2:
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_diag_inverse<2, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_diag_inverse<2, VT><<<nb, 256, smem, st>>>(n, T, ldt, Dinv);
+            break;
         default: return CF_ERR_UNSUPPORTED;
     }
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
 
-template <int MODE>
-static int launch_trsv_mode(int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
-                            int *sync_ws, cudaStream_t st) {
+int launch_diag_inverse(int mode, int n, const float *T, int ldt, float *Dinv, cudaStream_t st) {
+    return launch_diag_inverse_t<float>(mode, n, T, ldt, Dinv, st);
+}
+int launch_diag_inverse64(int mode, int n, const float *T, int ldt, double *Dinv, cudaStream_t st) {
+    return launch_diag_inverse_t<double>(mode, n, T, ldt, Dinv, st);
+}
+
+template <int MODE, int NR, typename VT>
+static int launch_trsv_nr(int n, int nrhs, const float *T, int ldt, const VT *Dinv, VT *X, int ldx, int *flags,
+                          int *ticket, cudaStream_t st) {
+    const int nb = (n + kSB - 1) / kSB;
+    const size_t smem = sizeof(float) * 2 * (size_t)kSB * kTLD + sizeof(VT) * ((size_t)kSB * kTLD + (size_t)kSB * 17);
+    CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<MODE, NR, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    k_trsv_blocked<MODE, NR, VT><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+template <int MODE, typename VT>
+static int launch_trsv_mode(int n, int nrhs, const float *T, int ldt, const VT *Dinv, VT *X, int ldx, int *sync_ws,
+                            cudaStream_t st) {
     const int nb = (n + kSB - 1) / kSB;
     CF_CUDA_TRY(cudaMemsetAsync(sync_ws, 0, sizeof(int) * (size_t)(nb + 1), st));
     int *flags = sync_ws, *ticket = sync_ws + nb;
-    const size_t smem = sizeof(float) * (3 * (size_t)kSB * kTLD + (size_t)kSB * 17);
-    if (nrhs <= 4) {
-        CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<MODE, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_trsv_blocked<MODE, 4><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
-    } else if (nrhs <= 8) {
-        CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<MODE, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_trsv_blocked<MODE, 8><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
-    } else {
-        CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<MODE, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_trsv_blocked<MODE, 16><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    if (nrhs <= 4) return launch_trsv_nr<MODE, 4, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
+    if (nrhs <= 8) return launch_trsv_nr<MODE, 8, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
+    return launch_trsv_nr<MODE, 16, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
+}
+
+template <typename VT>
+static int launch_trsv_t(int mode, int n, int nrhs, const float *T, int ldt, const VT *Dinv, VT *X, int ldx,
+                         int *sync_ws, cudaStream_t st) {
+    if (n <= 0 || nrhs <= 0) return CF_OK;
+    if (nrhs > 16) return CF_ERR_UNSUPPORTED;
+    switch (mode) {
+        case 0: return launch_trsv_mode<0, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 1: return launch_trsv_mode<1, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 2: return launch_trsv_mode<2, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 3: return launch_trsv_mode<3, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        default: return CF_ERR_UNSUPPORTED;
     }
-    CF_LAUNCH_CHECK();
-    return CF_OK;
 }
 
 // X <- M^{-1} X for nrhs <= 16 columns; sync_ws holds trsv_ws_bytes(n).
 int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
                     int *sync_ws, cudaStream_t st) {
-    if (n <= 0 || nrhs <= 0) return CF_OK;
-    if (nrhs > 16) return CF_ERR_UNSUPPORTED;
-    switch (mode) {
-        case 0: return launch_trsv_mode<0>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        case 1: return launch_trsv_mode<1>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        case 2: return launch_trsv_mode<2>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        case 3: return launch_trsv_mode<3>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        default: return CF_ERR_UNSUPPORTED;
-    }
+    return launch_trsv_t<float>(mode, n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+}
+// The same with FP64 right-hand sides and arithmetic (FP64 Dinv from
+// launch_diag_inverse64); the FP32 factor is read as stored.
+int launch_trsv_f64x(int mode, int n, int nrhs, const float *T, int ldt, const double *Dinv, double *X, int ldx,
+                     int *sync_ws, cudaStream_t st) {
+    return launch_trsv_t<double>(mode, n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
 }
 
 int trsv_take_status(cudaStream_t st, int *status) {

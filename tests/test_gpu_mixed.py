@@ -159,6 +159,37 @@ def test_posv_mixed_fp8_conditioned(cf, kappa):
     _check_solution(S, B, X.cpu().numpy())
 
 
+@pytest.mark.parametrize("which", ["gesv_shifted", "gesv_s0", "posv"])
+def test_mixed_split_bf16(cf, which):
+    """CF_BF16X3 (split BF16 updates, hi.hi + hi.lo + lo.hi): converges on the
+    well-conditioned and the unshifted (s = 0) LU matrices and on the SPD one."""
+    n = 1500
+    if which == "posv":
+        A = inputs.spd_gram(n, seed=1)
+    else:
+        A = inputs.uniform_pm1(n, seed=0, shift=(2 * np.sqrt(n) if which == "gesv_shifted" else 0.0))
+    B = inputs.rhs_normal(n, 3, seed=3)
+    fn = cf.posv_mixed if which == "posv" else cf.gesv_mixed
+    X, info, stats, st = fn(_dev(A), _dev(B), prec="bf16x3")
+    assert st == cf.CF_OK, stats.as_dict()
+    assert stats.escalated == 0
+    _check_solution(A, B, X.cpu().numpy())
+
+
+def test_gesv_mixed_escalates_to_split(cf):
+    """s = 0 at n = 8192 with BF16 factors: GMRES-IR stalls (kappa(M^-1 A)
+    too large), the solver refactors with split BF16 updates and converges."""
+    n = 8192
+    A = inputs.uniform_pm1(n, seed=0)
+    B = inputs.rhs_normal(n, 4, seed=3)
+    X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec="bf16")
+    d = stats.as_dict()
+    assert st == cf.CF_OK, d
+    assert d["escalated"] == 1, d
+    eta = oracle.backward_error(A, X.cpu().numpy(), B).max()
+    assert eta <= 1e-14, (eta, d)
+
+
 def test_gesv_mixed_fp8_refused(cf):
     A = _dev(inputs.uniform_pm1(64, seed=1, shift=16.0))
     B = _dev(inputs.rhs_normal(64, 1))
