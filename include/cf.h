@@ -65,7 +65,10 @@ typedef struct {
                           tournament takes arity 2 only) */
     int arity;         /* children per playoff node, 2..4 [2]; the mixed paths use 2 */
     int outer_V;       /* mixed LU/Cholesky: depth of the deferred update, multiple of v [0 = auto] */
-    int lookahead;     /* mixed paths: overlap panel t+1 with update t [1] */
+    int lookahead;     /* cf_getrf: 1 = LU-6 look-ahead (TournPivot of step
+                          t+1 on a high-priority stream while the wide update
+                          of step t runs on a low-priority one), 0 = one
+                          stream [1]; the other routines ignore it */
     double tol;        /* refinement stop: max backward error [1e-14] */
     int max_iter;      /* refinement iterations [30] */
     int gmres_restart; /* GMRES-IR Krylov dimension per correction, 1..256 [30] */

@@ -187,14 +187,15 @@ def tourn_select(panel: torch.Tensor, leaf_h: int = 128, arity: int = 2) -> torc
     return win[:min(m, w)]
 
 
-def getrf(A: torch.Tensor, v=None, leaf_h=None, arity=None, work=None):
+def getrf(A: torch.Tensor, v=None, leaf_h=None, arity=None, work=None, lookahead=None):
     """In-place LU with tournament pivoting.  Returns (ipiv, info) device
-    int32 tensors (ipiv 1-based)."""
+    int32 tensors (ipiv 1-based).  lookahead: 1 (default) overlaps step
+    t+1's TournPivot with step t's trailing update, 0 keeps one stream."""
     assert A.dtype == torch.float64
     n = A.shape[0]
     assert A.shape == (n, n)
     lda = _ld(A, "A")
-    opt = options(v=v, leaf_h=leaf_h, arity=arity)
+    opt = options(v=v, leaf_h=leaf_h, arity=arity, lookahead=lookahead)
     ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
     info = torch.zeros(1, dtype=torch.int32, device=A.device)
     need = _lib.cf_getrf_workspace_size(n, ctypes.byref(opt))
@@ -221,11 +222,13 @@ def getrf_noalloc(A: torch.Tensor, v=None, leaf_h=None, arity=None, ipiv=None, i
     return ipiv[:n], info
 
 
-def potrf(A: torch.Tensor, v=None):
+def potrf(A: torch.Tensor, v=None, lookahead=None):
+    """In-place lower Cholesky.  Returns info (device int32).  lookahead as
+    in getrf."""
     assert A.dtype == torch.float64
     n = A.shape[0]
     lda = _ld(A, "A")
-    opt = options(v=v)
+    opt = options(v=v, lookahead=lookahead)
     info = torch.zeros(1, dtype=torch.int32, device=A.device)
     ws = _workspace(_lib.cf_potrf_workspace_size(n, ctypes.byref(opt)), A.device)
     _check("cf_potrf", _lib.cf_potrf(n, _ptr(A), lda, _ptr(info), _ptr(ws), ws.numel(),

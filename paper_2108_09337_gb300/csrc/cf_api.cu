@@ -112,6 +112,133 @@ extern "C" size_t cf_getrf_workspace_size(int n, const cf_options *opt) {
     return tourn_ws_bytes(n > 0 ? n : 1, o.leaf_h, o.arity);
 }
 
+// LU-6 look-ahead (FP64 path).  Step t runs its panel chain (TournPivot,
+// swaps, A00, both panel solves) and the update of only the next panel's
+// columns on a high-priority stream, and the update of the remaining columns
+// on a low-priority stream.  TournPivot of step t+1 reads only the next
+// panel's columns, so it runs while the wide update of step t is still in
+// flight (latency-bound selection next to an FP64-ALU-bound GEMM); the swaps
+// of step t+1 wait for that update.  Both streams fork from and join back to
+// the caller's stream, so the call stays stream-ordered (and capturable).
+namespace cf {
+// The two streams of a look-ahead factorization, forked from and joined back
+// to the caller's stream.
+struct LookaheadStreams {
+    cudaStream_t sp = nullptr, su = nullptr;   // panel chain (high priority), wide updates (low)
+    cudaEvent_t ev[5] = {};                    // fork, panel ready, rest done, join panel, join update
+    int open(cudaStream_t st) {
+        int lo = 0, hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&sp, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&su, cudaStreamNonBlocking, lo) != cudaSuccess)
+            return CF_ERR_CUDA;
+        for (auto &e : ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return CF_ERR_CUDA;
+        if (cudaEventRecord(ev[0], st) != cudaSuccess || cudaStreamWaitEvent(sp, ev[0], 0) != cudaSuccess ||
+            cudaStreamWaitEvent(su, ev[0], 0) != cudaSuccess)
+            return CF_ERR_CUDA;
+        return CF_OK;
+    }
+    int panel_to_update() {      // the wide update may start once the panel is ready
+        return (cudaEventRecord(ev[1], sp) == cudaSuccess && cudaStreamWaitEvent(su, ev[1], 0) == cudaSuccess)
+                   ? CF_OK : CF_ERR_CUDA;
+    }
+    int update_done() { return cudaEventRecord(ev[2], su) == cudaSuccess ? CF_OK : CF_ERR_CUDA; }
+    int wait_update() { return cudaStreamWaitEvent(sp, ev[2], 0) == cudaSuccess ? CF_OK : CF_ERR_CUDA; }
+    int join(cudaStream_t st) {
+        return (cudaEventRecord(ev[3], sp) == cudaSuccess && cudaEventRecord(ev[4], su) == cudaSuccess &&
+                cudaStreamWaitEvent(st, ev[3], 0) == cudaSuccess && cudaStreamWaitEvent(st, ev[4], 0) == cudaSuccess)
+                   ? CF_OK : CF_ERR_CUDA;
+    }
+    ~LookaheadStreams() {        // safe with work in flight: released on completion
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        if (sp) cudaStreamDestroy(sp);
+        if (su) cudaStreamDestroy(su);
+    }
+};
+
+static int getrf_lookahead(int n, double *A, int lda, int *ipiv, int *info, const Opts &o, TournWS &ws,
+                           TournEpilogue &ep, cudaStream_t st) {
+    LookaheadStreams L;
+    int rc = L.open(st);
+    if (rc) return rc;
+    cudaStream_t sp = L.sp, su = L.su;
+    auto fail = [](int r) { return r; };
+    const size_t ld = (size_t)lda;
+    bool rest_pending = false;
+    for (int k0 = 0; k0 < n; k0 += o.v) {
+        const int w = o.v < n - k0 ? o.v : n - k0;
+        const int m = n - k0;
+        double *A00 = A + k0 + k0 * ld;
+        ep.ipiv = ipiv;
+        ep.k0 = k0;
+        if ((rc = launch_tourn<double>(A00, lda, m, w, o.leaf_h, o.arity, ws, ep, sp))) return fail(rc);
+        if (rest_pending && (rc = L.wait_update())) return fail(rc);
+        if ((rc = launch_apply_swaps<double>(A, lda, n, k0, ep, nullptr, sp))) return fail(rc);
+        if ((rc = launch_getf2_nopiv<double>(A00, lda, w, k0, info, sp))) return fail(rc);
+        if ((rc = launch_trsm_right_upper<double>(A00 + w, lda, m - w, w, A00, lda, false, nullptr, sp)))
+            return fail(rc);
+        if ((rc = launch_trsm_left_lower_unit<double>(A00 + w * ld, lda, w, n - k0 - w, A00, lda, sp)))
+            return fail(rc);
+        rest_pending = false;
+        const int right = n - k0 - w;
+        if (m - w <= 0 || right <= 0) continue;
+        const int w1 = o.v < right ? o.v : right;       // the next panel's columns
+        if ((rc = launch_gemm_f64_sub(m - w, w1, w, A00 + w, lda, A00 + w * ld, lda, false, A00 + w + w * ld, lda,
+                                      false, nullptr, sp)))
+            return fail(rc);
+        if (right > w1) {
+            if ((rc = L.panel_to_update())) return fail(rc);
+            if ((rc = launch_gemm_f64_sub(m - w, right - w1, w, A00 + w, lda, A00 + (w + w1) * ld, lda, false,
+                                          A00 + w + (w + w1) * ld, lda, false, nullptr, su)))
+                return fail(rc);
+            if ((rc = L.update_done())) return fail(rc);
+            rest_pending = true;
+        }
+    }
+    return L.join(st);
+}
+
+// The same for Cholesky: step t's diagonal factorization and panel solve,
+// then the update of the next panel's columns (every row below) on the
+// high-priority stream; the lower update of the rest on the low-priority
+// one.  Step t+1's panel work overlaps that rest; its own update of the next
+// columns waits for it (same columns).
+static int potrf_lookahead(int n, double *A, int lda, int *info, const Opts &o, cudaStream_t st) {
+    LookaheadStreams L;
+    int rc = L.open(st);
+    if (rc) return rc;
+    cudaStream_t sp = L.sp, su = L.su;
+    const size_t ld = (size_t)lda;
+    bool rest_pending = false;
+    for (int k0 = 0; k0 < n; k0 += o.v) {
+        const int w = o.v < n - k0 ? o.v : n - k0;
+        const int m = n - k0;
+        double *A00 = A + k0 + k0 * ld;
+        if ((rc = launch_potf2<double>(A00, lda, w, k0, info, sp))) return rc;
+        if ((rc = launch_trsm_right_upper<double>(A00 + w, lda, m - w, w, A00, lda, true, info, sp))) return rc;
+        const int rest = m - w;
+        if (rest <= 0) continue;
+        if (rest_pending && (rc = L.wait_update())) return rc;
+        rest_pending = false;
+        const int w1 = o.v < rest ? o.v : rest;
+        if ((rc = launch_gemm_f64_sub(rest, w1, w, A00 + w, lda, A00 + w, lda, true, A00 + w + w * ld, lda, true,
+                                      info, sp)))
+            return rc;
+        if (rest > w1) {
+            if ((rc = L.panel_to_update())) return rc;
+            if ((rc = launch_gemm_f64_sub(rest - w1, rest - w1, w, A00 + w + w1, lda, A00 + w + w1, lda, true,
+                                          A00 + (w + w1) + (w + w1) * ld, lda, true, info, su)))
+                return rc;
+            if ((rc = L.update_done())) return rc;
+            rest_pending = true;
+        }
+    }
+    return L.join(st);
+}
+}  // namespace cf
+
 extern "C" int cf_getrf(int n, double *A, int lda, int *ipiv, int *info, void *work, size_t lwork,
                         const cf_options *opt, cudaStream_t st) {
     if (n < 0) return -1;
@@ -130,6 +257,7 @@ extern "C" int cf_getrf(int n, double *A, int lda, int *ipiv, int *info, void *w
     rc = tourn_ws_carve(work, n, o.leaf_h, o.arity, &ws, &ep);
     if (rc != CF_OK) return rc;
     CF_CUDA_TRY(cudaMemsetAsync(ws.counter, 0, ws.counter_bytes, st));
+    if (o.lookahead) return getrf_lookahead(n, A, lda, ipiv, info, o, ws, ep, st);
     const size_t ld = (size_t)lda;
     for (int k0 = 0; k0 < n; k0 += o.v) {
         const int w = o.v < n - k0 ? o.v : n - k0;
@@ -174,6 +302,7 @@ extern "C" int cf_potrf(int n, double *A, int lda, int *info, void *work, size_t
     int rc = resolve_options(opt, &o);
     if (rc != CF_OK) return rc;
     CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
+    if (o.lookahead && n > 0) return potrf_lookahead(n, A, lda, info, o, st);
     const size_t ld = (size_t)lda;
     for (int k0 = 0; k0 < n; k0 += o.v) {
         const int w = o.v < n - k0 ? o.v : n - k0;

@@ -275,6 +275,7 @@ struct MixedWS {
     double *hcol = nullptr;                // (m + 2) x nrhs: one Hessenberg column per right-hand side
     double *coef = nullptr;                // (m + 1) x nrhs
     double *sq = nullptr;                  // nrhs squared norms
+    unsigned long long *sbits = nullptr;   // per-column scales of the FP32 preconditioner input
     float *sc8 = nullptr;                  // FP8 tile scales: slab (rows/128 x V/128), then one step
     double *Xbest = nullptr;               // best iterate so far
     size_t bytes = 0;
@@ -332,6 +333,7 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->hcol = cv.take<double>((size_t)(w->m + 2) * nrhs);
     w->coef = cv.take<double>((size_t)(w->m + 1) * nrhs);
     w->sq = cv.take<double>(nrhs + 1);
+    w->sbits = cv.take<unsigned long long>(nrhs + 1);
     w->Xbest = cv.take<double>(blk + 1);
     w->sc8 = cv.take<float>((size_t)(ceil_div(n > 0 ? n : 1, 128) + 1) * (Vp / 128 + 2));
     w->bytes = cv.size();
@@ -658,15 +660,46 @@ __global__ void k_gather_rows(int n, int nrhs, const int *perm, const double *Y,
     }
 }
 
-// Z = M^{-1} Y with the FP32-stored factors applied in FP64 arithmetic (with
-// the preconditioner applied in FP32, the Krylov relations are polluted at
-// the FP32 level times the factors' condition and GMRES stalls on the hard
-// cases).
-static int apply_precond(int n, int nrhs, const double *Yin, double *Z, MixedWS &w, bool lu, cudaStream_t st) {
+// Rf[:, c] = (float)(Z[:, c] / s_c), s_c = max_i |Z[i, c]| read from the bit
+// patterns k_col_absmax leaves (1 if 0); and back, Z[:, c] = s_c Rf[:, c].
+__global__ void k_to_f32_scaled(int n, int nrhs, const double *Z, const unsigned long long *sbits, float *Rf) {
+    const size_t tot = (size_t)n * nrhs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const double sc = __longlong_as_double((long long)sbits[e / n]);
+        Rf[e] = (float)(Z[e] / (sc > 0.0 ? sc : 1.0));
+    }
+}
+__global__ void k_from_f32_scaled(int n, int nrhs, const float *Rf, const unsigned long long *sbits, double *Z) {
+    const size_t tot = (size_t)n * nrhs;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const double sc = __longlong_as_double((long long)sbits[e / n]);
+        Z[e] = (sc > 0.0 ? sc : 1.0) * (double)Rf[e];
+    }
+}
+
+// Z = M^{-1} Y with the FP32-stored factors.  Applied in FP64 arithmetic by
+// default: in FP32 the Krylov relations are polluted at the FP32 level times
+// the factors' condition, and GMRES stalls on the hard cases (e.g. unshifted
+// uniform LU at N = 32768).  With FP8 factors (unit roundoff 2^-4) the
+// factorization error dominates that level, and the FP32 solves (memory-
+// bound, a fraction of the FP64 ones' time) are used.
+static int apply_precond(int n, int nrhs, const double *Yin, double *Z, MixedWS &w, bool lu, bool f32,
+                         cudaStream_t st) {
     const size_t blk = (size_t)n * nrhs;
     k_gather_rows<<<grid_for(blk), 256, 0, st>>>(n, nrhs, lu ? w.perm : nullptr, Yin, Z);
     CF_LAUNCH_CHECK();
     int rc;
+    if (f32) {
+        CF_CUDA_TRY(cudaMemsetAsync(w.sbits, 0, sizeof(unsigned long long) * nrhs, st));
+        k_col_absmax<<<dim3(grid_for(n), nrhs), 256, 0, st>>>(n, nrhs, Z, n, w.sbits);
+        CF_LAUNCH_CHECK();
+        k_to_f32_scaled<<<grid_for(blk), 256, 0, st>>>(n, nrhs, Z, w.sbits, w.Rf);
+        CF_LAUNCH_CHECK();
+        if ((rc = solve_f32(n, nrhs, w, lu, st))) return rc;
+        k_from_f32_scaled<<<grid_for(blk), 256, 0, st>>>(n, nrhs, w.Rf, w.sbits, Z);
+        CF_LAUNCH_CHECK();
+        return CF_OK;
+    }
     if ((rc = launch_trsv_f64x(lu ? 0 : 2, n, nrhs, w.W, w.ldw, w.DinvL64, Z, n, w.trsv_sync, st))) return rc;
     return launch_trsv_f64x(lu ? 1 : 3, n, nrhs, w.W, w.ldw, lu ? w.DinvU64 : w.DinvL64, Z, n, w.trsv_sync, st);
 }
@@ -684,13 +717,13 @@ static int block_dots(int n, int nrhs, const double *V, int nv, const double *W,
 }
 
 static int gmres_correct(int n, int nrhs, const double *A, int lda, double *X, int ldx, MixedWS &w, bool lu,
-                         double tau, cudaStream_t st, Timer &tres, int *inner) {
+                         bool prec_f32, double tau, cudaStream_t st, Timer &tres, int *inner) {
     const size_t blk = (size_t)n * nrhs;
     const int m = w.m;
     int rc;
     *inner = 0;
     // z0 = M^{-1} r, beta = ||z0||_2, v_0 = z0 / beta
-    if ((rc = apply_precond(n, nrhs, w.R, w.Wv, w, lu, st))) return rc;
+    if ((rc = apply_precond(n, nrhs, w.R, w.Wv, w, lu, prec_f32, st))) return rc;
     if ((rc = block_dots(n, nrhs, w.Wv, 1, w.Wv, w.sq, 0, w, st))) return rc;
     k_normalize<<<grid_for(blk), 256, 0, st>>>(n, nrhs, w.sq, w.hcol, w.Wv, w.V);
     CF_LAUNCH_CHECK();
@@ -719,7 +752,7 @@ static int gmres_correct(int n, int nrhs, const double *A, int lda, double *X, i
         if ((rc = tres.begin(st))) return rc;
         if ((rc = launch_residual_f64(n, n, nrhs, A, lda, Vk, n, nullptr, 0, w.Y, n, st))) return rc;   // Y = A v_k
         if ((rc = tres.end(st, 2.0 * n * (double)n * nrhs))) return rc;
-        if ((rc = apply_precond(n, nrhs, w.Y, w.Wv, w, lu, st))) return rc;                          // w = M^{-1} Y
+        if ((rc = apply_precond(n, nrhs, w.Y, w.Wv, w, lu, prec_f32, st))) return rc;                // w = M^{-1} Y
         if ((rc = block_dots(n, nrhs, w.V, k + 1, w.Wv, w.hcol, 0, w, st))) return rc;               // CGS pass 1
         k_block_axpy<<<grid_for(blk), 256, 0, st>>>(n, nrhs, k + 1, w.V, w.hcol, w.Wv, n);
         CF_LAUNCH_CHECK();
@@ -972,7 +1005,8 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             CF_LAUNCH_CHECK();
         } else {
             int inner = 0;
-            if ((rc = gmres_correct(n, nrhs, A, lda, X, ldx, w, lu, kGmresTol, st, tres, &inner))) return rc;
+            const bool prec_f32 = std::is_same<LP, fp8_e4m3>::value && !split;
+            if ((rc = gmres_correct(n, nrhs, A, lda, X, ldx, w, lu, prec_f32, kGmresTol, st, tres, &inner))) return rc;
             S.gmres_iterations += inner;
         }
     }

@@ -311,3 +311,22 @@ def test_residual_pair_accuracy(cf):
         Rp = _host(cf.residual_pair(_dev(A), _dev(X), _dev(B)))
         den = np.abs(A).sum(1).max() * np.abs(X).max(0) + np.abs(B).max(0)
         assert (np.abs(Rp - Ro).max(0) / den).max() <= 2e-14
+
+
+@pytest.mark.parametrize("n", [1000, 2500])
+def test_lookahead_bit_identical(cf, n):
+    """LU-6 look-ahead (two streams) computes exactly what the one-stream loop
+    computes: the split of each step's update into the next panel's columns
+    and the rest does not change any element's sequence of operations."""
+    A = inputs.uniform_pm1(n, seed=n)
+    S = inputs.spd_gram(n, seed=n + 1)
+    out = {}
+    for la in (0, 1):
+        dA, dS = _dev(A), _dev(S)
+        ipiv, info = cf.getrf(dA, lookahead=la)
+        info2 = cf.potrf(dS, lookahead=la)
+        torch.cuda.synchronize()
+        assert int(info.item()) == 0 and int(info2.item()) == 0
+        out[la] = (dA.cpu().numpy(), ipiv.cpu().numpy(), np.tril(dS.cpu().numpy()))
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
