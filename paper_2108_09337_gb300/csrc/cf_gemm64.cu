@@ -126,25 +126,29 @@ int launch_gemm_f64_sub(int m, int n, int k, const double *A, int lda, const dou
 }
 
 // ---------------------------------------------------------------------------
-// R = B - A X (B null: R = A X), X thin (NR >= nrhs columns).  CTA: 64 rows; 16 row groups of 4
-// rows x 16 lanes along k; the 16 k-partial sums are combined in shared
-// memory at the end.  Reads A once, coalesced along the columns.
+// R = B - A X (B null: R = A X), X thin (NR >= nrhs columns).  CTA: 4 RG rows;
+// RG row groups of 4 rows x (256 / RG) lanes along k; the k-partial sums are
+// combined in shared memory at the end in a fixed order.  Reads A once,
+// coalesced along the columns.  RG = 16 (64 rows) or 8 (32 rows): the
+// launcher picks the one whose grid fills the last wave of CTAs better (the
+// kernel runs one CTA per SM, so a short last wave idles most SMs).
 // ---------------------------------------------------------------------------
-template <int NR>
+template <int NR, int RG>
 __global__ void __launch_bounds__(256)
 k_residual_f64(int m, int n, int nrhs, const double *__restrict__ A, int lda, const double *__restrict__ X, int ldx,
                const double *B, int ldb, double *R, int ldr) {
+    constexpr int KL = 256 / RG, ROWS = 4 * RG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *red = reinterpret_cast<double *>(smem_raw);     // [16][64][NR]
+    double *red = reinterpret_cast<double *>(smem_raw);     // [KL][ROWS][NR]
     const int tid = threadIdx.x;
-    const int rg = tid & 15, kl = tid >> 4;
-    const int row0 = blockIdx.x * 64 + rg * 4;
+    const int rg = tid % RG, kl = tid / RG;
+    const int row0 = blockIdx.x * ROWS + rg * 4;
     double acc[4][NR];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int c = 0; c < NR; ++c) acc[i][c] = 0.0;
-    for (int p = kl; p < n; p += 16) {
+    for (int p = kl; p < n; p += KL) {
         double a[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) a[i] = (row0 + i < m) ? A[(size_t)(row0 + i) + (size_t)p * lda] : 0.0;
@@ -159,27 +163,53 @@ k_residual_f64(int m, int n, int nrhs, const double *__restrict__ A, int lda, co
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int c = 0; c < NR; ++c) red[((size_t)kl * 64 + rg * 4 + i) * NR + c] = acc[i][c];
+        for (int c = 0; c < NR; ++c) red[((size_t)kl * ROWS + rg * 4 + i) * NR + c] = acc[i][c];
     __syncthreads();
-    for (int o = tid; o < 64 * NR; o += 256) {
+    for (int o = tid; o < ROWS * NR; o += 256) {
         const int rl = o / NR, c = o % NR;
-        const int row = blockIdx.x * 64 + rl;
+        const int row = blockIdx.x * ROWS + rl;
         if (row >= m || c >= nrhs) continue;
-        double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) s += red[((size_t)q * 64 + rl) * NR + c];
-        R[(size_t)row + (size_t)c * ldr] = B ? B[(size_t)row + (size_t)c * ldb] - s : s;   // B null: R = A X
+        double sum = 0.0;
+#pragma unroll 8
+        for (int q = 0; q < KL; ++q) sum += red[((size_t)q * ROWS + rl) * NR + c];
+        R[(size_t)row + (size_t)c * ldr] = B ? B[(size_t)row + (size_t)c * ldb] - sum : sum;   // B null: R = A X
     }
+}
+
+static int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+template <int NR, int RG>
+static int launch_residual_rg(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
+                              const double *B, int ldb, double *R, int ldr, cudaStream_t st) {
+    const size_t smem = sizeof(double) * 256 * 4 * NR;     // KL x ROWS x NR = 1024 NR
+    CF_CUDA_TRY(cudaFuncSetAttribute(k_residual_f64<NR, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_residual_f64<NR, RG><<<ceil_div(m, 4 * RG), 256, smem, st>>>(m, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+// Fraction of the SM-slots of the last wave that a grid of c one-per-SM CTAs fills.
+static double wave_fill(long long c, int sms) {
+    const long long waves = (c + sms - 1) / sms;
+    return waves > 0 ? (double)c / (double)(waves * sms) : 1.0;
 }
 
 template <int NR>
 static int launch_residual_nr(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
                               const double *B, int ldb, double *R, int ldr, cudaStream_t st) {
-    const size_t smem = sizeof(double) * 16 * 64 * NR;
-    CF_CUDA_TRY(cudaFuncSetAttribute(k_residual_f64<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_residual_f64<NR><<<ceil_div(m, 64), 256, smem, st>>>(m, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr);
-    CF_LAUNCH_CHECK();
-    return CF_OK;
+    const int sms = sm_count();
+    const bool small_rows = wave_fill(ceil_div(m, 32), sms) > wave_fill(ceil_div(m, 64), sms) + 0.02;
+    if (small_rows) return launch_residual_rg<NR, 8>(m, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, st);
+    return launch_residual_rg<NR, 16>(m, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, st);
 }
 
 int launch_residual_f64(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,

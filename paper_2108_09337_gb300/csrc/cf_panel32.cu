@@ -8,11 +8,13 @@
 //   k_ltrsm32       LU-4  A01 <- L00^{-1} A01
 //
 // Each thread holds one row (or, for LU-4, one column) of its tile in
-// registers and shifts it left while it eliminates, so the current column
-// is always element 0; the v x v triangle is read from shared memory as
-// float4 rows.  A00 kernels need one barrier per column; the panel solves
-// need none.  The solve kernels also write the BF16/FP16 K-major copies
-// that the tensor-core update reads.
+// registers, indexed relative to the current block of 8 columns so that all
+// register indices are compile-time constants; the v x v triangle is read
+// from shared memory as float4 rows.  A00 kernels need one barrier per
+// column; the panel solves need none, hold the row as float2 pairs updated
+// with packed FMAs and write their results straight from registers (no
+// staging), so three of their CTAs fit on an SM.  The solve kernels also
+// write the BF16/FP16 K-major copies that the tensor-core update reads.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -114,118 +116,179 @@ __global__ void __launch_bounds__(kMaxV, 1) k_a00_chol32(float *A00, int lda, in
     for_blocks(a, w, body);
 }
 
-struct RtrsmStep {
-    float (&a)[kMaxV];
+// Packs 8 consecutive values as low-precision and stores them as one 16-byte
+// chunk (dst 16-byte aligned).
+template <typename LP>
+__device__ __forceinline__ void store8_lp(LP *dst, const float (&v)[8]) {
+    union { uint4 u; LP h[8]; } pk;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) pk.h[i] = lp_from<LP>(v[i]);
+    *reinterpret_cast<uint4 *>(dst) = pk.u;
+}
+
+// Solve steps on a pair row (cf_regrow.cuh): x_k = a_k / M(k, k) (unit: a_k),
+// then a_t -= x_k M(k, t) for t > k; x_k is kept in xb for the block's
+// output.  RT: right solve (thread = row of X, M row k at Ms + k*kMaxV,
+// 1/M(k,k) in rinv), writes x_k to its FP32 column at once (coalesced over
+// the CTA's rows); LT: left solve with unit L (thread = column of X, L column
+// k at Ls + k*kMaxV).
+struct RtrsmPairStep {
+    float2 (&a)[kPairs];
+    float (&xb)[8];
     const float *Ms;
-    float *xs;
-    int w;
+    const float *rinv;
+    float *xcol;        // X + row, stride ldx (null: not a live row)
+    int ldx, w;
     template <int U>
     __device__ __forceinline__ void step(int j0) {
         const int k = j0 + U;
-        const float d = Ms[k * kMaxV + k];
-        const float xk = (d != 0.f) ? a[U] / d : a[U];
-        xs[k] = xk;
-        rank1_from<U>(a, xk, reinterpret_cast<const float4 *>(Ms + k * kMaxV + j0), w - j0);
+        const float xk = pair_elem<U>(a) * rinv[k];
+        xb[U] = xk;
+        if (xcol) xcol[(size_t)k * ldx] = xk;
+        rank1_pairs<U>(a, xk, reinterpret_cast<const float4 *>(Ms + k * kMaxV + j0), w - j0);
     }
 };
 
-struct LtrsmStep {
-    float (&a)[kMaxV];
+struct LtrsmPairStep {
+    float2 (&a)[kPairs];
+    float (&xb)[8];
     const float *Ls;
-    float *xs;
     int w;
     template <int U>
     __device__ __forceinline__ void step(int j0) {
         const int k = j0 + U;
-        const float xk = a[U];                       // unit diagonal
-        xs[k] = xk;
-        rank1_from<U>(a, xk, reinterpret_cast<const float4 *>(Ls + k * kMaxV + j0), w - j0);
+        const float xk = pair_elem<U>(a);            // unit diagonal
+        xb[U] = xk;
+        rank1_pairs<U>(a, xk, reinterpret_cast<const float4 *>(Ls + k * kMaxV + j0), w - j0);
     }
 };
+
+template <typename Body>
+__device__ __forceinline__ void run_block(Body &body, int j0, int w) {
+    body.template step<0>(j0);
+    if (j0 + 1 < w) body.template step<1>(j0);
+    if (j0 + 2 < w) body.template step<2>(j0);
+    if (j0 + 3 < w) body.template step<3>(j0);
+    if (j0 + 4 < w) body.template step<4>(j0);
+    if (j0 + 5 < w) body.template step<5>(j0);
+    if (j0 + 6 < w) body.template step<6>(j0);
+    if (j0 + 7 < w) body.template step<7>(j0);
+}
 
 // ---------------------------------------------------------------------------
 // Right solve of a panel: X (rows x w, column-major ldx) <- X M^{-1} with
 // M = U00 (upper, non-unit; trans_lower = false) or M = L00^T (trans_lower).
-// Thread = row; M staged row by row as Ms[k][t] = M(k, k+t).  Writes FP32
-// back and lp[r*ldk + j] (j < kpad; zero for j >= w).
+// Thread = row, held as a pair row; M staged row by row (Ms[k][c] = M(k, c),
+// zero below the diagonal) with the reciprocals of its diagonal (a zero
+// diagonal entry divides by one, as the FP64 path skips the division).  The
+// FP32 result goes back column by column as it is produced; lp[r*ldk + j]
+// (j < kpad, zero for j >= w) is written in 16-byte chunks of 8.
 // ---------------------------------------------------------------------------
 template <typename LP>
-__global__ void __launch_bounds__(kMaxV, 1)
+__global__ void __launch_bounds__(kMaxV)
 k_rtrsm32(float *X, int ldx, int rows, int w, const float *__restrict__ M00, int ldm, int trans_lower, LP *lp,
           int ldk, int kpad, const int *skip) {
     if (skip != nullptr && *skip != 0) return;
     extern __shared__ __align__(16) float smem[];
-    float *Ms = smem;                                // [kMaxV][kMaxV]
-    float *Xs = smem + kMaxV * kMaxV;                // [kMaxV][kMaxV + 4] outputs, row-major
-    constexpr int XLD = kMaxV + 4;
+    // [kMaxV + 1][kMaxV]: a step reads row k from column j0 in whole 32-column
+    // chunks, up to 31 floats past the row's end; the last row's overrun
+    // lands in the zeroed padding row
+    float *Ms = smem;
+    __shared__ float rinv[kMaxV];
     const int tid = threadIdx.x;
-    // Ms[k][c] = M(k, c) at absolute columns, read along the stored matrix's columns
+    Ms[kMaxV * kMaxV + tid] = 0.f;
     for (int e = tid; e < kMaxV * kMaxV; e += kMaxV) {
         const int i = e % kMaxV, c = e / kMaxV;          // stored element (i, c)
-        if (i < w && c < w) {
-            const float v = M00[(size_t)i + (size_t)c * ldm];
-            if (!trans_lower && i <= c) Ms[i * kMaxV + c] = v;          // U(i, c)
-            if (trans_lower && i >= c) Ms[c * kMaxV + i] = v;           // M(c, i) = L(i, c)
-        }
+        float v = 0.f;
+        if (i < w && c < w) v = M00[(size_t)i + (size_t)c * ldm];
+        if (!trans_lower) Ms[i * kMaxV + c] = (i <= c) ? v : 0.f;              // U(i, c)
+        else Ms[c * kMaxV + i] = (i >= c) ? v : 0.f;                            // M(c, i) = L(i, c)
+    }
+    __syncthreads();
+    if (tid < w) {
+        const float d = Ms[tid * kMaxV + tid];
+        rinv[tid] = d != 0.f ? 1.0f / d : 1.0f;
     }
     const int r0 = blockIdx.x * kMaxV;
     const int nr = min(kMaxV, rows - r0);
-    float a[kMaxV];
+    const bool live = tid < nr;
+    float2 a[kPairs];
     // coalesced load: for each column k, the CTA's rows are contiguous
 #pragma unroll
-    for (int k = 0; k < kMaxV; ++k) a[k] = (tid < nr && k < w) ? X[(size_t)(r0 + tid) + (size_t)k * ldx] : 0.f;
-    __syncthreads();
-    RtrsmStep body{a, Ms, Xs + tid * XLD, w};
-    for_blocks(a, w, body);
-    __syncthreads();
-    // write back: FP32 column-major (coalesced over rows) ...
-    for (int e = tid; e < kMaxV * w; e += kMaxV) {
-        const int rr = e % kMaxV, k = e / kMaxV;
-        if (rr < nr) X[(size_t)(r0 + rr) + (size_t)k * ldx] = Xs[rr * XLD + k];
+    for (int k = 0; k < kPairs; ++k) {
+        const float x0 = (live && 2 * k < w) ? X[(size_t)(r0 + tid) + (size_t)(2 * k) * ldx] : 0.f;
+        const float x1 = (live && 2 * k + 1 < w) ? X[(size_t)(r0 + tid) + (size_t)(2 * k + 1) * ldx] : 0.f;
+        a[k] = make_float2(x0, x1);
     }
-    // ... and the K-major low-precision rows (coalesced along k)
-    if (lp != nullptr) {
-        for (int e = tid; e < kMaxV * kpad; e += kMaxV) {
-            const int k = e % kpad, rr = e / kpad;
-            if (rr < nr) lp[(size_t)(r0 + rr) * ldk + k] = lp_from<LP>(k < w ? Xs[rr * XLD + k] : 0.f);
-        }
+    __syncthreads();
+    float xb[8];
+    RtrsmPairStep body{a, xb, Ms, rinv, live ? X + r0 + tid : nullptr, ldx, w};
+    LP *lrow = (lp != nullptr && live) ? lp + (size_t)(r0 + tid) * ldk : nullptr;
+    for (int j0 = 0; j0 < w; j0 += kBlk) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) xb[i] = 0.f;
+        run_block(body, j0, w);
+        shift_pairs(a, w - j0 - kBlk);
+        if (lrow) store8_lp<LP>(lrow + j0, xb);
+    }
+    if (lrow) {
+        float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int j0 = (w + 7) / 8 * 8; j0 < kpad; j0 += 8) store8_lp<LP>(lrow + j0, z);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Left solve of a row block: X (w x cols, column-major ldx) <- L00^{-1} X, L00
-// unit lower.  Thread = column; L staged column by column as Ls[k][t] =
-// L(k+t, k).  Writes FP32 back and lp[c*ldk + i] (i < kpad; zero for i >= w).
+// unit lower.  Thread = column, held as a pair row; L staged column by
+// column (Ls[k][i] = L(i, k), zero on and above the diagonal).  Results are
+// written per block of 8 rows (two 16-byte stores, scalar for a ragged last
+// block) and as 16-byte low-precision chunks at lp[c*ldk + i] (i < kpad,
+// zero for i >= w).
 // ---------------------------------------------------------------------------
 template <typename LP>
-__global__ void __launch_bounds__(kMaxV, 1)
+__global__ void __launch_bounds__(kMaxV)
 k_ltrsm32(float *X, int ldx, int w, int cols, const float *__restrict__ L00, int ldl, LP *lp, int ldk, int kpad) {
     extern __shared__ __align__(16) float smem[];
-    float *Ls = smem;                                // [kMaxV][kMaxV]: Ls[k][t] = L(k+t, k)
-    float *Xs = smem + kMaxV * kMaxV;                // [kMaxV][kMaxV + 4]: outputs by column
-    constexpr int XLD = kMaxV + 4;
+    float *Ls = smem;                                // [kMaxV + 1][kMaxV]: Ls[k][i] = L(i, k), zero padding row
     const int tid = threadIdx.x;
+    Ls[kMaxV * kMaxV + tid] = 0.f;
     for (int e = tid; e < kMaxV * kMaxV; e += kMaxV) {
-        const int k = e / kMaxV, i = e % kMaxV;          // Ls[k][i] = L(i, k), absolute rows
-        if (k < w && i > k && i < w) Ls[e] = L00[(size_t)i + (size_t)k * ldl];
+        const int k = e / kMaxV, i = e % kMaxV;
+        Ls[e] = (k < w && i > k && i < w) ? L00[(size_t)i + (size_t)k * ldl] : 0.f;
     }
     const int c0 = blockIdx.x * kMaxV;
     const int nc = min(kMaxV, cols - c0);
     const bool live = tid < nc;
-    float a[kMaxV];
-    const float *xc = X + (size_t)(c0 + (live ? tid : 0)) * ldx;
+    float *xc = X + (size_t)(c0 + (live ? tid : 0)) * ldx;
+    float2 a[kPairs];
 #pragma unroll
-    for (int i = 0; i < kMaxV; ++i) a[i] = (live && i < w) ? xc[i] : 0.f;
+    for (int i = 0; i < kPairs; ++i)
+        a[i] = make_float2((live && 2 * i < w) ? xc[2 * i] : 0.f, (live && 2 * i + 1 < w) ? xc[2 * i + 1] : 0.f);
     __syncthreads();
-    LtrsmStep body{a, Ls, Xs + tid * XLD, w};
-    for_blocks(a, w, body);
-    __syncthreads();
-    for (int e = tid; e < kMaxV * kMaxV; e += kMaxV) {
-        const int i = e % kMaxV, c = e / kMaxV;
-        if (c < nc) {
-            if (i < w) X[(size_t)i + (size_t)(c0 + c) * ldx] = Xs[c * XLD + i];
-            if (lp != nullptr && i < kpad) lp[(size_t)(c0 + c) * ldk + i] = lp_from<LP>(i < w ? Xs[c * XLD + i] : 0.f);
+    const bool vec = ((((uintptr_t)xc) & 15) == 0);
+    float xb[8];
+    LtrsmPairStep body{a, xb, Ls, w};
+    LP *lcol = (lp != nullptr && live) ? lp + (size_t)(c0 + tid) * ldk : nullptr;
+    for (int j0 = 0; j0 < w; j0 += kBlk) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) xb[i] = 0.f;
+        run_block(body, j0, w);
+        shift_pairs(a, w - j0 - kBlk);
+        if (live) {
+            if (vec && j0 + 8 <= w) {
+                reinterpret_cast<float4 *>(xc + j0)[0] = make_float4(xb[0], xb[1], xb[2], xb[3]);
+                reinterpret_cast<float4 *>(xc + j0)[1] = make_float4(xb[4], xb[5], xb[6], xb[7]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (j0 + i < w) xc[j0 + i] = xb[i];
+            }
         }
+        if (lcol) store8_lp<LP>(lcol + j0, xb);
+    }
+    if (lcol) {
+        float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int j0 = (w + 7) / 8 * 8; j0 < kpad; j0 += 8) store8_lp<LP>(lcol + j0, z);
     }
 }
 
@@ -248,7 +311,8 @@ template <typename LP>
 int launch_rtrsm32(float *X, int ldx, int rows, int w, const float *M00, int ldm, bool trans_lower, LP *lp, int ldk,
                    int kpad, const int *skip, cudaStream_t st) {
     if (rows <= 0 || w <= 0) return CF_OK;
-    const size_t smem = sizeof(float) * ((size_t)kMaxV * kMaxV + (size_t)kMaxV * (kMaxV + 4));
+    if (lp != nullptr && ((ldk % 8) != 0 || (kpad % 8) != 0 || (((uintptr_t)lp) & 15) != 0)) return CF_ERR_UNSUPPORTED;
+    const size_t smem = sizeof(float) * (size_t)(kMaxV + 1) * kMaxV;   // + padding row
     CF_CUDA_TRY(cudaFuncSetAttribute(k_rtrsm32<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_rtrsm32<LP><<<ceil_div(rows, kMaxV), kMaxV, smem, st>>>(X, ldx, rows, w, M00, ldm, trans_lower ? 1 : 0, lp, ldk,
                                                               kpad, skip);
@@ -260,7 +324,8 @@ template <typename LP>
 int launch_ltrsm32(float *X, int ldx, int w, int cols, const float *L00, int ldl, LP *lp, int ldk, int kpad,
                    cudaStream_t st) {
     if (cols <= 0 || w <= 0) return CF_OK;
-    const size_t smem = sizeof(float) * ((size_t)kMaxV * kMaxV + (size_t)kMaxV * (kMaxV + 4));
+    if (lp != nullptr && ((ldk % 8) != 0 || (kpad % 8) != 0 || (((uintptr_t)lp) & 15) != 0)) return CF_ERR_UNSUPPORTED;
+    const size_t smem = sizeof(float) * (size_t)(kMaxV + 1) * kMaxV;   // + padding row
     CF_CUDA_TRY(cudaFuncSetAttribute(k_ltrsm32<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_ltrsm32<LP><<<ceil_div(cols, kMaxV), kMaxV, smem, st>>>(X, ldx, w, cols, L00, ldl, lp, ldk, kpad);
     CF_LAUNCH_CHECK();
