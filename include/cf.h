@@ -72,6 +72,9 @@ typedef struct {
     double tol;        /* refinement stop: max backward error [1e-14] */
     int max_iter;      /* refinement iterations [30] */
     int gmres_restart; /* GMRES-IR Krylov dimension per correction, 1..256 [30] */
+    int batch_cps;     /* batched calls: resident CTAs per SM, 1..3 (LU /
+                          Cholesky) or 1..2 (mixed), 0 = as many as fit [0];
+                          cf_batched_autotune picks it with v */
 } cf_options;
 
 void cf_default_options(cf_options *opt /* host */);
@@ -267,19 +270,21 @@ int cf_device_status(cudaStream_t stream);
  * info[i].  kind[i] = 0 for LU (tournament rule with one leaf per panel, i.e.
  * partial pivoting, block size min(v, 32)), 1 for Cholesky (lower); kind ==
  * NULL means every matrix has default_kind.  One CTA factors one matrix at a
- * time; matrices are taken longest-first (decreasing n).  info[i] = -1 for
- * n[i] > 512.  Capturable in a CUDA graph (no host synchronisation).
+ * time (opt->batch_cps CTAs per SM; cf_batched_autotune picks it and v);
+ * matrices are taken longest-first (decreasing n).  info[i] = -1 for
+ * n[i] > 512.  Capturable in a CUDA graph (no host synchronisation, no
+ * allocation); the workspace size depends on opt.
  * ------------------------------------------------------------------------ */
-size_t cf_factor_batched_workspace_size(int batch);
+size_t cf_factor_batched_workspace_size(int batch, const cf_options *opt);
 int cf_factor_batched(int batch, const int *kind, int default_kind,
                       const int *n, double *const *A, const int *lda,
                       int *const *ipiv, int *info, void *work, size_t lwork,
                       const cf_options *opt, cudaStream_t stream);
-size_t cf_getrf_batched_workspace_size(int batch);
+size_t cf_getrf_batched_workspace_size(int batch, const cf_options *opt);
 int cf_getrf_batched(int batch, const int *n, double *const *A,
                      const int *lda, int *const *ipiv, int *info, void *work,
                      size_t lwork, const cf_options *opt, cudaStream_t stream);
-size_t cf_potrf_batched_workspace_size(int batch);
+size_t cf_potrf_batched_workspace_size(int batch, const cf_options *opt);
 int cf_potrf_batched(int batch, const int *n, double *const *A,
                      const int *lda, int *info, void *work, size_t lwork,
                      const cf_options *opt, cudaStream_t stream);
@@ -298,13 +303,31 @@ int cf_potrf_batched(int batch, const int *n, double *const *A,
  * factorization met a zero (LU) or non-positive (Cholesky) pivot at step k,
  * -1 if n[i] > 512.  solver (device, may be NULL): 32 or 64, the precision
  * of the factors that produced x_i. */
-size_t cf_solve_batched_mixed_workspace_size(int batch);
+size_t cf_solve_batched_mixed_workspace_size(int batch, const cf_options *opt);
 int cf_solve_batched_mixed(int batch, const int *kind, int default_kind,
                            const int *n, const double *const *A,
                            const int *lda, const double *const *B,
                            double *const *X, int *info, int *iters,
                            double *eta, int *solver, void *work, size_t lwork,
                            const cf_options *opt, cudaStream_t stream);
+
+/* BAT-1 autotuner (spec: tile and schedule chosen by the project's
+ * tuner; no counterpart in the paper).  Times every candidate block size
+ * v in {8, 16, 32} with every resident-CTA count the hardware allows on up to
+ * 512 synthetic matrices whose sizes are an evenly spaced sample of
+ * n_host[0..batch) (host array; kind_host may be NULL: default_kind), for
+ * the FP64 factorization (mixed = 0) or the mixed solve (mixed = 1), and
+ * writes the fastest into opt->v and opt->batch_cps (opt is in/out, host;
+ * its other fields are used as given).  best_ms (host, may be NULL) gets the
+ * sample's time.  Synchronises `stream`.  The batch's own matrices are not
+ * touched. */
+size_t cf_batched_autotune_workspace_size(int batch, const int *n_host,
+                                          const int *kind_host,
+                                          int default_kind, int mixed);
+int cf_batched_autotune(int batch, const int *n_host, const int *kind_host,
+                        int default_kind, int mixed, void *work,
+                        size_t lwork, cf_options *opt, float *best_ms,
+                        cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * Mixed-precision refined solves (north star; the paper cites GPU mixed

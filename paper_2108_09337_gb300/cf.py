@@ -39,7 +39,7 @@ PREC = {"f64": CF_F64, "f32": CF_F32, "bf16": CF_BF16, "f16": CF_F16,
 class Options(ctypes.Structure):
     _fields_ = [("v", ctypes.c_int), ("leaf_h", ctypes.c_int), ("arity", ctypes.c_int),
                 ("outer_V", ctypes.c_int), ("lookahead", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("batch_cps", ctypes.c_int)]
 
 
 class RefineStats(ctypes.Structure):
@@ -78,13 +78,15 @@ _SIG = {
     "cf_residual_pair": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _S, _P]),
     "cf_schur_update_lp": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
     "cf_device_status": (_I, [_P]),
-    "cf_factor_batched_workspace_size": (_S, [_I]),
+    "cf_factor_batched_workspace_size": (_S, [_I, _OPT]),
     "cf_factor_batched": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P, _S, _OPT, _P]),
-    "cf_getrf_batched_workspace_size": (_S, [_I]),
+    "cf_getrf_batched_workspace_size": (_S, [_I, _OPT]),
     "cf_getrf_batched": (_I, [_I, _P, _P, _P, _P, _P, _P, _S, _OPT, _P]),
-    "cf_potrf_batched_workspace_size": (_S, [_I]),
+    "cf_potrf_batched_workspace_size": (_S, [_I, _OPT]),
     "cf_potrf_batched": (_I, [_I, _P, _P, _P, _P, _P, _S, _OPT, _P]),
-    "cf_solve_batched_mixed_workspace_size": (_S, [_I]),
+    "cf_solve_batched_mixed_workspace_size": (_S, [_I, _OPT]),
+    "cf_batched_autotune_workspace_size": (_S, [_I, _P, _P, _I, _I]),
+    "cf_batched_autotune": (_I, [_I, _P, _P, _I, _I, _P, _S, _OPT, ctypes.POINTER(ctypes.c_float), _P]),
     "cf_solve_batched_mixed": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _S, _OPT, _P]),
     "cf_quantize_e4m3": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P]),
     "cf_schur_update_fp8": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _I, _I, _P]),
@@ -390,23 +392,26 @@ class Batch:
                             device=buf.device)
 
 
-def factor_batched(batch: "Batch", default_kind=0, v=None, work=None):
+def factor_batched(batch: "Batch", default_kind=0, v=None, work=None, batch_cps=None, opt=None):
     """In-place FP64 LU / Cholesky of every matrix (cf_factor_batched).
     Returns (ipiv buffer, ipiv pointer array, info)."""
     nb = len(batch.sizes)
     ipiv = torch.zeros(batch.vec_total, dtype=torch.int32, device=batch.data.device)
     iptr = batch.vec_ptrs(ipiv)
     info = torch.zeros(max(nb, 1), dtype=torch.int32, device=batch.data.device)
-    opt = options(v=v)
-    ws = work if work is not None else _workspace(_lib.cf_factor_batched_workspace_size(nb), batch.data.device)
+    opt = opt if opt is not None else options(v=v, batch_cps=batch_cps)
+    ws = work if work is not None else _workspace(_lib.cf_factor_batched_workspace_size(nb, ctypes.byref(opt)),
+                                                  batch.data.device)
     kind = _ptr(batch.kind) if batch.kind is not None else ctypes.c_void_p(0)
     _check("cf_factor_batched", _lib.cf_factor_batched(nb, kind, default_kind, _ptr(batch.n), _ptr(batch.ptrs),
                                                        _ptr(batch.lda), _ptr(iptr), _ptr(info), _ptr(ws),
                                                        ws.numel(), ctypes.byref(opt), _stream()))
+    torch.cuda.current_stream().synchronize()     # iptr is freed on return
     return ipiv, iptr, info
 
 
-def solve_batched_mixed(batch: "Batch", B: torch.Tensor, default_kind=0, tol=None, max_iter=None, work=None):
+def solve_batched_mixed(batch: "Batch", B: torch.Tensor, default_kind=0, tol=None, max_iter=None, work=None,
+                        v=None, batch_cps=None, opt=None):
     """FP32 factors + FP64 refinement for every A_i x_i = b_i
     (cf_solve_batched_mixed); B packed like batch.vec_offsets.  Returns
     (X, info, iters, eta, solver), solver[i] = 32 or 64 (the precision of
@@ -418,8 +423,9 @@ def solve_batched_mixed(batch: "Batch", B: torch.Tensor, default_kind=0, tol=Non
     iters = torch.zeros(max(nb, 1), dtype=torch.int32, device=dev)
     eta = torch.zeros(max(nb, 1), dtype=torch.float64, device=dev)
     solver = torch.zeros(max(nb, 1), dtype=torch.int32, device=dev)
-    opt = options(tol=tol, max_iter=max_iter)
-    ws = work if work is not None else _workspace(_lib.cf_solve_batched_mixed_workspace_size(nb), dev)
+    opt = opt if opt is not None else options(tol=tol, max_iter=max_iter, v=v, batch_cps=batch_cps)
+    ws = work if work is not None else _workspace(_lib.cf_solve_batched_mixed_workspace_size(nb, ctypes.byref(opt)),
+                                                  dev)
     kind = _ptr(batch.kind) if batch.kind is not None else ctypes.c_void_p(0)
     bptr = batch.vec_ptrs(B)      # keep the pointer arrays alive across the call
     xptr = batch.vec_ptrs(X)
@@ -429,6 +435,86 @@ def solve_batched_mixed(batch: "Batch", B: torch.Tensor, default_kind=0, tol=Non
                                        _ptr(ws), ws.numel(), ctypes.byref(opt), _stream()))
     torch.cuda.current_stream().synchronize()
     return X, info, iters, eta, solver
+
+
+def batched_autotune(batch: "Batch", mixed=False, default_kind=0, **opt_kw):
+    """cf_batched_autotune: times the candidate (v, batch_cps) pairs on a
+    synthetic sample with the batch's sizes and kinds; returns (Options with
+    the fastest, sample milliseconds)."""
+    nb = len(batch.sizes)
+    hn = (ctypes.c_int * nb)(*batch.sizes)
+    hk = None
+    if batch.kind is not None:
+        hk = (ctypes.c_int * nb)(*[int(x) for x in batch.kind.cpu().tolist()])
+    kptr = ctypes.cast(hk, ctypes.c_void_p) if hk is not None else ctypes.c_void_p(0)
+    nptr = ctypes.cast(hn, ctypes.c_void_p)
+    need = _lib.cf_batched_autotune_workspace_size(nb, nptr, kptr, default_kind, int(mixed))
+    ws = _workspace(need, batch.data.device)
+    opt = options(**opt_kw)
+    ms = ctypes.c_float(0.0)
+    _check("cf_batched_autotune", _lib.cf_batched_autotune(nb, nptr, kptr, default_kind, int(mixed), _ptr(ws),
+                                                           ws.numel(), ctypes.byref(opt), ctypes.byref(ms),
+                                                           _stream()))
+    return opt, ms.value
+
+
+class BatchedPlan:
+    """Everything a batched call needs, allocated once, so that the call
+    itself only enqueues work: run() on the current stream, or capture() into
+    a CUDA graph and replay() it (BAT-1 "one persistent launch captured in a
+    CUDA graph").  kind: "factor" (in-place FP64 LU / Cholesky) or "mixed"
+    (FP32 factors + FP64 refinement; set the right-hand sides in .B)."""
+
+    def __init__(self, batch: "Batch", kind="factor", default_kind=0, opt=None):
+        self.batch, self.kind_name, self.default_kind = batch, kind, default_kind
+        self.opt = opt if opt is not None else options()
+        dev = batch.data.device
+        nb = len(batch.sizes)
+        self.nb = nb
+        self.info = torch.zeros(max(nb, 1), dtype=torch.int32, device=dev)
+        if kind == "factor":
+            self.ipiv = torch.zeros(batch.vec_total, dtype=torch.int32, device=dev)
+            self.iptr = batch.vec_ptrs(self.ipiv)
+            need = _lib.cf_factor_batched_workspace_size(nb, ctypes.byref(self.opt))
+        else:
+            self.B = torch.zeros(batch.vec_total, dtype=torch.float64, device=dev)
+            self.X = torch.zeros(batch.vec_total, dtype=torch.float64, device=dev)
+            self.bptr, self.xptr = batch.vec_ptrs(self.B), batch.vec_ptrs(self.X)
+            self.iters = torch.zeros(max(nb, 1), dtype=torch.int32, device=dev)
+            self.eta = torch.zeros(max(nb, 1), dtype=torch.float64, device=dev)
+            self.solver = torch.zeros(max(nb, 1), dtype=torch.int32, device=dev)
+            need = _lib.cf_solve_batched_mixed_workspace_size(nb, ctypes.byref(self.opt))
+        self.ws = _workspace(need, dev)
+        self.graph = None
+        torch.cuda.synchronize()
+
+    def run(self):
+        b = self.batch
+        kind = _ptr(b.kind) if b.kind is not None else ctypes.c_void_p(0)
+        if self.kind_name == "factor":
+            _check("cf_factor_batched", _lib.cf_factor_batched(
+                self.nb, kind, self.default_kind, _ptr(b.n), _ptr(b.ptrs), _ptr(b.lda), _ptr(self.iptr),
+                _ptr(self.info), _ptr(self.ws), self.ws.numel(), ctypes.byref(self.opt), _stream()))
+        else:
+            _check("cf_solve_batched_mixed", _lib.cf_solve_batched_mixed(
+                self.nb, kind, self.default_kind, _ptr(b.n), _ptr(b.ptrs), _ptr(b.lda), _ptr(self.bptr),
+                _ptr(self.xptr), _ptr(self.info), _ptr(self.iters), _ptr(self.eta), _ptr(self.solver),
+                _ptr(self.ws), self.ws.numel(), ctypes.byref(self.opt), _stream()))
+
+    def capture(self):
+        """Capture one run() into a CUDA graph (on a side stream, as torch
+        requires); replay() then launches it."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(self.graph, stream=s):
+                self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
 
 
 def kernel_launches() -> int:

@@ -37,11 +37,13 @@ int resolve_options(const cf_options *in, Opts *o) {
     if (in->tol > 0) o->tol = in->tol;
     if (in->max_iter > 0) o->max_iter = in->max_iter;
     if (in->gmres_restart > 0) o->gmres_restart = in->gmres_restart;
+    o->batch_cps = in->batch_cps;
     if (o->v < 1 || o->v > kMaxV) return CF_ERR_UNSUPPORTED;
     if (o->leaf_h < 1 || o->leaf_h > 2 * kMaxV) return CF_ERR_UNSUPPORTED;   // FP64 tournament: <= kMaxV
     if (o->arity < 2 || o->arity > 4) return CF_ERR_UNSUPPORTED;
     if (o->outer_V < 0 || (o->outer_V % o->v) != 0) return CF_ERR_UNSUPPORTED;
     if (o->gmres_restart < 1 || o->gmres_restart > 256) return CF_ERR_UNSUPPORTED;
+    if (o->batch_cps < 0 || o->batch_cps > 8) return CF_ERR_UNSUPPORTED;
     return CF_OK;
 }
 
@@ -87,6 +89,7 @@ extern "C" void cf_default_options(cf_options *opt) {
     opt->tol = o.tol;
     opt->max_iter = o.max_iter;
     opt->gmres_restart = o.gmres_restart;
+    opt->batch_cps = o.batch_cps;
 }
 
 extern "C" const char *cf_status_string(int s) {

@@ -19,6 +19,7 @@
 // so the whole batch can be captured in a CUDA graph.
 #include <climits>
 #include <cmath>
+#include <vector>
 
 #include "cf_common.cuh"
 #include "cf_kernels.cuh"
@@ -29,9 +30,11 @@ constexpr int kBT = 256;                // threads per CTA
 constexpr int kBMaxN = 512;             // largest matrix
 constexpr int kBMaxV = 32;              // largest block size
 
+// Per-CTA shared memory: this header, then the panel copy P (kBMaxN x vb
+// elements of T; its size follows the block size, which sets how many CTAs
+// fit on an SM).
 template <typename T>
 struct BSmem {
-    T P[kBMaxN * kBMaxV];               // panel copy (pivot search) / L10 block
     T D[kBMaxV * (kBMaxV + 1)];         // diagonal block
     T redv[kBT / 32];
     int redi[kBT / 32];
@@ -41,6 +44,19 @@ struct BSmem {
     int where_[kBMaxN];
     int fail;
 };
+
+template <typename T>
+__host__ __device__ constexpr size_t bsmem_header_bytes() {
+    return (sizeof(BSmem<T>) + 15) / 16 * 16;
+}
+template <typename T>
+__host__ __device__ constexpr size_t bsmem_bytes(int vb) {
+    return bsmem_header_bytes<T>() + sizeof(T) * (size_t)kBMaxN * vb;
+}
+template <typename T>
+__device__ __forceinline__ T *bsmem_panel(BSmem<T> &s) {
+    return reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(&s) + bsmem_header_bytes<T>());
+}
 
 template <typename T>
 __device__ __forceinline__ T bkey(T a) {
@@ -127,13 +143,14 @@ __device__ void cta_gemm_sub(int mm, int nn, int kk, const T *A, int lda, const 
 template <typename T>
 __device__ void cta_getrf(BSmem<T> &s, T *A, int n, int lda, int *ipiv, int *info, int vb) {
     const int tid = threadIdx.x;
+    T *P = bsmem_panel(s);
     for (int k0 = 0; k0 < n; k0 += vb) {
         const int w = min(vb, n - k0), m = n - k0;
         T *A00 = A + k0 + (size_t)k0 * lda;
         // ---- LU-1: partial-pivoting selection on a copy of the panel
         for (int e = tid; e < m * w; e += kBT) {
             const int r = e % m, c = e / m;
-            s.P[c * m + r] = A00[r + (size_t)c * lda];
+            P[c * m + r] = A00[r + (size_t)c * lda];
         }
         for (int r = tid; r < m; r += kBT) s.used[r] = 0;
         __syncthreads();
@@ -141,16 +158,16 @@ __device__ void cta_getrf(BSmem<T> &s, T *A, int n, int lda, int *ipiv, int *inf
             T bv = T(-1);
             int bi = INT_MAX;
             for (int r = tid; r < m; r += kBT)
-                if (!s.used[r]) bbetter(bv, bi, bkey(s.P[j * m + r]), r);
+                if (!s.used[r]) bbetter(bv, bi, bkey(P[j * m + r]), r);
             cta_argmax(s, bv, bi);
             if (tid == 0) { s.order[j] = bi; s.used[bi] = 1; }
             __syncthreads();
-            const T piv = s.P[j * m + bi];
+            const T piv = P[j * m + bi];
             if (piv != T(0)) {
                 for (int r = tid; r < m; r += kBT) {
                     if (s.used[r]) continue;
-                    const T l = s.P[j * m + r] / piv;
-                    for (int c = j + 1; c < w; ++c) s.P[c * m + r] = s.P[c * m + r] - l * s.P[c * m + bi];
+                    const T l = P[j * m + r] / piv;
+                    for (int c = j + 1; c < w; ++c) P[c * m + r] = P[c * m + r] - l * P[c * m + bi];
                 }
             }
             __syncthreads();
@@ -358,7 +375,8 @@ struct BatchArgs {
 // ---------------------------------------------------------------------------
 // FP64 factorizations in place.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBT, 1) k_factor_batched(BatchArgs a) {
+template <int MINB>
+__global__ void __launch_bounds__(kBT, MINB) k_factor_batched(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BSmem<double> &s = *reinterpret_cast<BSmem<double> *>(smem_raw);
     __shared__ int s_idx;
@@ -500,7 +518,8 @@ __device__ int cta_refine(int kind, int n, const double *A, int lda, const doubl
     }
 }
 
-__global__ void __launch_bounds__(kBT, 1) k_solve_batched_mixed(BatchArgs a) {
+template <int MINB>
+__global__ void __launch_bounds__(kBT, MINB) k_solve_batched_mixed(BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_idx;
     __shared__ int s_info;
@@ -603,22 +622,74 @@ struct BatchWS {
     size_t bytes;
 };
 
-static int batch_grid(int vb) {
-    (void)vb;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;    // one CTA per SM (the panel copy needs most of the shared memory)
+static int sm_count_b() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 148;
+    }
+    return sms;
 }
 
+// Launch configuration: block size vb and resident CTAs per SM (cps).  The
+// kernel variant compiled for cps resident CTAs is used; cps = 0 asks for
+// the largest count the occupancy calculator grants at this vb.
+struct BatchCfg {
+    int vb, cps, grid;
+};
 
-static int carve_batch(void *work, int batch, bool mixed, BatchWS *w) {
+template <int MINB>
+static int occ_factor(size_t smem) {
+    int b = 0;
+    if (cudaFuncSetAttribute(k_factor_batched<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_factor_batched<MINB>, kBT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return b;
+}
+template <int MINB>
+static int occ_mixed(size_t smem) {
+    int b = 0;
+    if (cudaFuncSetAttribute(k_solve_batched_mixed<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_solve_batched_mixed<MINB>, kBT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return b;
+}
+
+constexpr int kMaxCpsFactor = 3, kMaxCpsMixed = 2;
+
+static BatchCfg resolve_cfg(const Opts &o, bool mixed) {
+    BatchCfg c{};
+    c.vb = o.v < kBMaxV ? o.v : kBMaxV;
+    const size_t smem = bsmem_bytes<double>(c.vb);
+    const int maxc = mixed ? kMaxCpsMixed : kMaxCpsFactor;
+    int want = o.batch_cps > 0 ? (o.batch_cps < maxc ? o.batch_cps : maxc) : maxc;
+    // largest cps <= want whose variant the hardware can hold that many times
+    int cps = 1;
+    for (int k = want; k >= 1; --k) {
+        int occ = 0;
+        if (mixed) occ = k == 2 ? occ_mixed<2>(smem) : occ_mixed<1>(smem);
+        else occ = k == 3 ? occ_factor<3>(smem) : k == 2 ? occ_factor<2>(smem) : occ_factor<1>(smem);
+        if (occ >= k) { cps = k; break; }
+    }
+    c.cps = cps;
+    c.grid = sm_count_b() * cps;
+    return c;
+}
+
+static int carve_batch(void *work, int batch, bool mixed, int grid, BatchWS *w) {
     Carver cv(work);
     w->order = cv.take<int>(batch > 0 ? batch : 1);
     w->queue = cv.take<int>(1);
     w->hist = cv.take<int>(kBMaxN + 1);
     w->cursor = cv.take<int>(kBMaxN + 1);
-    w->scratch = mixed ? cv.take<double>(batched_scratch_bytes_per_cta() / sizeof(double) * batch_grid(32), 1024)
+    w->scratch = mixed ? cv.take<double>(batched_scratch_bytes_per_cta() / sizeof(double) * (size_t)grid, 1024)
                        : nullptr;
     w->bytes = cv.size();
     return CF_OK;
@@ -637,14 +708,89 @@ static int enqueue_order(int batch, const int *n, BatchWS &w, cudaStream_t st) {
     return CF_OK;
 }
 
+static int launch_factor_cfg(const BatchArgs &a, const BatchCfg &c, cudaStream_t st) {
+    const size_t smem = bsmem_bytes<double>(c.vb);
+    switch (c.cps) {
+        case 3:
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_factor_batched<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_factor_batched<3><<<c.grid, kBT, smem, st>>>(a);
+            break;
+        case 2:
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_factor_batched<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_factor_batched<2><<<c.grid, kBT, smem, st>>>(a);
+            break;
+        default:
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_factor_batched<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_factor_batched<1><<<c.grid, kBT, smem, st>>>(a);
+    }
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+static int launch_mixed_cfg(const BatchArgs &a, const BatchCfg &c, cudaStream_t st) {
+    const size_t smem = bsmem_bytes<double>(c.vb);   // holds the FP32 layout too
+    if (c.cps == 2) {
+        CF_CUDA_TRY(cudaFuncSetAttribute(k_solve_batched_mixed<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_solve_batched_mixed<2><<<c.grid, kBT, smem, st>>>(a);
+    } else {
+        CF_CUDA_TRY(cudaFuncSetAttribute(k_solve_batched_mixed<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_solve_batched_mixed<1><<<c.grid, kBT, smem, st>>>(a);
+    }
+    CF_LAUNCH_CHECK();
+    return CF_OK;
+}
+
+static size_t factor_ws_bytes(int batch, const Opts &o) {
+    BatchWS w{};
+    carve_batch(nullptr, batch, false, resolve_cfg(o, false).grid, &w);
+    return w.bytes;
+}
+static size_t mixed_ws_bytes(int batch, const Opts &o) {
+    BatchWS w{};
+    carve_batch(nullptr, batch, true, resolve_cfg(o, true).grid, &w);
+    return w.bytes;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner input: synthetic matrices of the sampled sizes, diagonally
+// dominant (u[-1,1] entries from a counter-based hash, n on the diagonal),
+// symmetric for Cholesky entries, so every candidate factors the same bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double hash_u11(unsigned long long key) {
+    // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) finaliser -> [-1, 1)
+    key += 0x9E3779B97F4A7C15ull;
+    key = (key ^ (key >> 30)) * 0xBF58476D1CE4E5B9ull;
+    key = (key ^ (key >> 27)) * 0x94D049BB133111EBull;
+    key ^= key >> 31;
+    return (double)(key >> 11) * 0x1p-52 - 1.0;
+}
+
+__global__ void k_tune_fill(int cnt, const int *n, const long long *off, const long long *voff, const int *kind,
+                            double *pool, double *vpool) {
+    const int j = blockIdx.y;
+    if (j >= cnt) return;
+    const int nj = n[j];
+    double *A = pool + off[j];
+    const long long tot = (long long)nj * nj;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % nj), c = (int)(e / nj);
+        const int lo = (kind[j] == 1 && c < r) ? c : r, hi = (kind[j] == 1 && c < r) ? r : c;
+        const unsigned long long key = ((unsigned long long)j << 40) ^ ((unsigned long long)lo << 20) ^ (unsigned long long)hi;
+        A[e] = hash_u11(key) + (r == c ? (double)nj : 0.0);
+    }
+    if (vpool != nullptr && blockIdx.x == 0)
+        for (int r = threadIdx.x; r < nj; r += blockDim.x)
+            vpool[voff[j] + r] = hash_u11(0xB000000000000000ull ^ ((unsigned long long)j << 20) ^ (unsigned long long)r);
+}
+
 }  // namespace cf
 
 using namespace cf;
 
-extern "C" size_t cf_factor_batched_workspace_size(int batch) {
-    BatchWS w{};
-    carve_batch(nullptr, batch, false, &w);
-    return w.bytes;
+extern "C" size_t cf_factor_batched_workspace_size(int batch, const cf_options *opt) {
+    Opts o;
+    if (resolve_options(opt, &o) != CF_OK) return 0;
+    return factor_ws_bytes(batch, o);
 }
 
 extern "C" int cf_factor_batched(int batch, const int *kind, int default_kind, const int *n, double *const *A,
@@ -657,23 +803,25 @@ extern "C" int cf_factor_batched(int batch, const int *kind, int default_kind, c
     int rc = resolve_options(opt, &o);
     if (rc) return rc;
     if (batch == 0) return CF_OK;
-    if (work == nullptr || lwork < cf_factor_batched_workspace_size(batch)) return CF_ERR_WORKSPACE;
+    const BatchCfg c = resolve_cfg(o, false);
     BatchWS w{};
-    carve_batch(work, batch, false, &w);
+    carve_batch(nullptr, batch, false, c.grid, &w);
+    if (work == nullptr || lwork < w.bytes) return CF_ERR_WORKSPACE;
+    carve_batch(work, batch, false, c.grid, &w);
     if ((rc = enqueue_order(batch, n, w, st))) return rc;
     BatchArgs a{};
     a.batch = batch; a.kind = kind; a.default_kind = default_kind; a.n = n; a.lda = lda; a.A = A;
     a.ipiv = ipiv; a.info = info; a.order = w.order; a.queue = w.queue;
-    a.vb = o.v < kBMaxV ? o.v : kBMaxV;
-    const size_t smem = sizeof(BSmem<double>);
-    CF_CUDA_TRY(cudaFuncSetAttribute(k_factor_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_factor_batched<<<batch_grid(a.vb), kBT, smem, st>>>(a);
-    CF_LAUNCH_CHECK();
-    return CF_OK;
+    a.vb = c.vb;
+    return launch_factor_cfg(a, c, st);
 }
 
-extern "C" size_t cf_getrf_batched_workspace_size(int batch) { return cf_factor_batched_workspace_size(batch); }
-extern "C" size_t cf_potrf_batched_workspace_size(int batch) { return cf_factor_batched_workspace_size(batch); }
+extern "C" size_t cf_getrf_batched_workspace_size(int batch, const cf_options *opt) {
+    return cf_factor_batched_workspace_size(batch, opt);
+}
+extern "C" size_t cf_potrf_batched_workspace_size(int batch, const cf_options *opt) {
+    return cf_factor_batched_workspace_size(batch, opt);
+}
 
 extern "C" int cf_getrf_batched(int batch, const int *n, double *const *A, const int *lda, int *const *ipiv,
                                 int *info, void *work, size_t lwork, const cf_options *opt, cudaStream_t st) {
@@ -686,10 +834,10 @@ extern "C" int cf_potrf_batched(int batch, const int *n, double *const *A, const
     return cf_factor_batched(batch, nullptr, 1, n, A, lda, nullptr, info, work, lwork, opt, st);
 }
 
-extern "C" size_t cf_solve_batched_mixed_workspace_size(int batch) {
-    BatchWS w{};
-    carve_batch(nullptr, batch, true, &w);
-    return w.bytes;
+extern "C" size_t cf_solve_batched_mixed_workspace_size(int batch, const cf_options *opt) {
+    Opts o;
+    if (resolve_options(opt, &o) != CF_OK) return 0;
+    return mixed_ws_bytes(batch, o);
 }
 
 extern "C" int cf_solve_batched_mixed(int batch, const int *kind, int default_kind, const int *n,
@@ -705,20 +853,175 @@ extern "C" int cf_solve_batched_mixed(int batch, const int *kind, int default_ki
     int rc = resolve_options(opt, &o);
     if (rc) return rc;
     if (batch == 0) return CF_OK;
-    if (work == nullptr || lwork < cf_solve_batched_mixed_workspace_size(batch)) return CF_ERR_WORKSPACE;
+    const BatchCfg c = resolve_cfg(o, true);
     BatchWS w{};
-    carve_batch(work, batch, true, &w);
+    carve_batch(nullptr, batch, true, c.grid, &w);
+    if (work == nullptr || lwork < w.bytes) return CF_ERR_WORKSPACE;
+    carve_batch(work, batch, true, c.grid, &w);
     if ((rc = enqueue_order(batch, n, w, st))) return rc;
     BatchArgs a{};
     a.batch = batch; a.kind = kind; a.default_kind = default_kind; a.n = n; a.lda = lda;
     a.A = const_cast<double *const *>(A);
     a.info = info; a.order = w.order; a.queue = w.queue;
-    a.vb = o.v < kBMaxV ? o.v : kBMaxV;
+    a.vb = c.vb;
     a.B = B; a.X = X; a.iters = iters; a.eta = eta; a.solver = solver; a.scratch = w.scratch;
     a.tol = o.tol; a.max_iter = o.max_iter;
-    const size_t smem = sizeof(BSmem<double>);      // holds BSmem<float> too
-    CF_CUDA_TRY(cudaFuncSetAttribute(k_solve_batched_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_solve_batched_mixed<<<batch_grid(a.vb), kBT, smem, st>>>(a);
-    CF_LAUNCH_CHECK();
+    return launch_mixed_cfg(a, c, st);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner (BAT-1): times every (block size, resident CTAs per SM) candidate
+// on up to kTuneSample synthetic matrices whose sizes are an evenly spaced
+// sample of the batch's, and returns the fastest in opt->v and
+// opt->batch_cps.  Only the sizes and kinds of the batch are used.
+// ---------------------------------------------------------------------------
+namespace cf {
+constexpr int kTuneSample = 512;
+
+struct TuneLayout {
+    int cnt;
+    std::vector<int> n, kind, lda;
+    std::vector<long long> off, voff;
+    long long pool, vpool;
+};
+
+static TuneLayout tune_layout(int batch, const int *n_host, const int *kind_host, int default_kind) {
+    TuneLayout L{};
+    L.cnt = batch < kTuneSample ? batch : kTuneSample;
+    long long acc = 0, vacc = 0;
+    for (int j = 0; j < L.cnt; ++j) {
+        const int i = (int)((long long)j * batch / L.cnt);
+        int nj = n_host[i];
+        nj = nj < 1 ? 1 : (nj > kBMaxN ? kBMaxN : nj);
+        L.n.push_back(nj);
+        L.kind.push_back(kind_host ? kind_host[i] : default_kind);
+        L.lda.push_back(nj);
+        L.off.push_back(acc);
+        L.voff.push_back(vacc);
+        acc += (long long)nj * nj;
+        vacc += nj;
+    }
+    L.pool = acc;
+    L.vpool = vacc;
+    return L;
+}
+
+static size_t tune_ws_bytes(const TuneLayout &L, bool mixed) {
+    Carver cv(nullptr);
+    cv.take<double>((size_t)L.pool + 1, 256);                      // matrices
+    cv.take<double>((size_t)L.vpool + 1, 256);                     // B
+    cv.take<double>((size_t)L.vpool + 1, 256);                     // X
+    cv.take<int>((size_t)L.vpool + 1);                             // ipiv
+    cv.take<int>(4 * (size_t)L.cnt + 4);                           // n, lda, kind, info
+    cv.take<int>(2 * (size_t)L.cnt + 2);                           // iters, solver
+    cv.take<double>((size_t)L.cnt + 1);                            // eta
+    cv.take<long long>(2 * (size_t)L.cnt + 2);                     // off, voff
+    cv.take<double *>(3 * (size_t)L.cnt + 3);                      // A, B, X pointers
+    cv.take<int *>((size_t)L.cnt + 1);                             // ipiv pointers
+    // the batched call's own workspace at the largest candidate grid
+    BatchWS w{};
+    carve_batch(nullptr, L.cnt, mixed, sm_count_b() * (mixed ? kMaxCpsMixed : kMaxCpsFactor), &w);
+    cv.take<unsigned char>(w.bytes, 1024);
+    return cv.size();
+}
+}  // namespace cf
+
+extern "C" size_t cf_batched_autotune_workspace_size(int batch, const int *n_host, const int *kind_host,
+                                                     int default_kind, int mixed) {
+    if (batch <= 0 || n_host == nullptr) return 0;
+    return tune_ws_bytes(tune_layout(batch, n_host, kind_host, default_kind), mixed != 0);
+}
+
+extern "C" int cf_batched_autotune(int batch, const int *n_host, const int *kind_host, int default_kind, int mixed,
+                                   void *work, size_t lwork, cf_options *opt, float *best_ms, cudaStream_t st) {
+    if (batch <= 0) return -1;
+    if (n_host == nullptr) return -2;
+    if (default_kind != 0 && default_kind != 1) return -4;
+    if (opt == nullptr) return -8;
+    Opts o;
+    int rc = resolve_options(opt, &o);
+    if (rc) return rc;
+    const TuneLayout L = tune_layout(batch, n_host, kind_host, default_kind);
+    if (work == nullptr || lwork < tune_ws_bytes(L, mixed != 0)) return CF_ERR_WORKSPACE;
+    Carver cv(work);
+    double *pool = cv.take<double>((size_t)L.pool + 1, 256);
+    double *vB = cv.take<double>((size_t)L.vpool + 1, 256);
+    double *vX = cv.take<double>((size_t)L.vpool + 1, 256);
+    int *piv = cv.take<int>((size_t)L.vpool + 1);
+    int *d_n = cv.take<int>(4 * (size_t)L.cnt + 4);
+    int *d_lda = d_n + L.cnt + 1, *d_kind = d_lda + L.cnt + 1, *d_info = d_kind + L.cnt + 1;
+    int *d_it = cv.take<int>(2 * (size_t)L.cnt + 2);
+    int *d_solver = d_it + L.cnt + 1;
+    double *d_eta = cv.take<double>((size_t)L.cnt + 1);
+    long long *d_off = cv.take<long long>(2 * (size_t)L.cnt + 2);
+    long long *d_voff = d_off + L.cnt + 1;
+    double **d_A = cv.take<double *>(3 * (size_t)L.cnt + 3);
+    double **d_B = d_A + L.cnt + 1, **d_X = d_B + L.cnt + 1;
+    int **d_piv = cv.take<int *>((size_t)L.cnt + 1);
+    BatchWS wmax{};
+    carve_batch(nullptr, L.cnt, mixed != 0, sm_count_b() * (mixed ? kMaxCpsMixed : kMaxCpsFactor), &wmax);
+    unsigned char *bws = cv.take<unsigned char>(wmax.bytes, 1024);
+
+    std::vector<double *> hA(L.cnt), hB(L.cnt), hX(L.cnt);
+    std::vector<int *> hP(L.cnt);
+    for (int j = 0; j < L.cnt; ++j) {
+        hA[j] = pool + L.off[j];
+        hB[j] = vB + L.voff[j];
+        hX[j] = vX + L.voff[j];
+        hP[j] = piv + L.voff[j];
+    }
+    CF_CUDA_TRY(cudaMemcpyAsync(d_n, L.n.data(), sizeof(int) * L.cnt, cudaMemcpyHostToDevice, st));
+    CF_CUDA_TRY(cudaMemcpyAsync(d_lda, L.lda.data(), sizeof(int) * L.cnt, cudaMemcpyHostToDevice, st));
+    CF_CUDA_TRY(cudaMemcpyAsync(d_kind, L.kind.data(), sizeof(int) * L.cnt, cudaMemcpyHostToDevice, st));
+    CF_CUDA_TRY(cudaMemcpyAsync(d_off, L.off.data(), sizeof(long long) * L.cnt, cudaMemcpyHostToDevice, st));
+    CF_CUDA_TRY(cudaMemcpyAsync(d_voff, L.voff.data(), sizeof(long long) * L.cnt, cudaMemcpyHostToDevice, st));
+    CF_CUDA_TRY(cudaMemcpyAsync(d_A, hA.data(), sizeof(double *) * L.cnt, cudaMemcpyHostToDevice, st));
+    CF_CUDA_TRY(cudaMemcpyAsync(d_B, hB.data(), sizeof(double *) * L.cnt, cudaMemcpyHostToDevice, st));
+    CF_CUDA_TRY(cudaMemcpyAsync(d_X, hX.data(), sizeof(double *) * L.cnt, cudaMemcpyHostToDevice, st));
+    CF_CUDA_TRY(cudaMemcpyAsync(d_piv, hP.data(), sizeof(int *) * L.cnt, cudaMemcpyHostToDevice, st));
+    CF_CUDA_TRY(cudaStreamSynchronize(st));                      // host vectors go out of scope below
+
+    cudaEvent_t e0, e1;
+    CF_CUDA_TRY(cudaEventCreate(&e0));
+    CF_CUDA_TRY(cudaEventCreate(&e1));
+    const int vbs[3] = {8, 16, 32};
+    const int maxc = mixed ? kMaxCpsMixed : kMaxCpsFactor;
+    float best = -1.f;
+    int best_vb = o.v < kBMaxV ? o.v : kBMaxV, best_cps = 1;
+    for (int pass = 0; pass < 2; ++pass) {                        // pass 0 warms up, pass 1 times
+        for (int vi = 0; vi < 3; ++vi) {
+            for (int cps = 1; cps <= maxc; ++cps) {
+                Opts oc = o;
+                oc.v = vbs[vi];
+                oc.batch_cps = cps;
+                const BatchCfg c = resolve_cfg(oc, mixed != 0);
+                if (c.cps != cps) continue;                     // this many CTAs do not fit
+                k_tune_fill<<<dim3(16, L.cnt), 256, 0, st>>>(L.cnt, d_n, d_off, d_voff, d_kind, pool,
+                                                             mixed ? vB : nullptr);
+                CF_LAUNCH_CHECK();
+                BatchWS w{};
+                carve_batch(bws, L.cnt, mixed != 0, c.grid, &w);
+                if ((rc = enqueue_order(L.cnt, d_n, w, st))) return rc;
+                BatchArgs a{};
+                a.batch = L.cnt; a.kind = d_kind; a.default_kind = default_kind; a.n = d_n; a.lda = d_lda;
+                a.A = d_A; a.ipiv = d_piv; a.info = d_info; a.order = w.order; a.queue = w.queue; a.vb = c.vb;
+                a.B = d_B; a.X = d_X; a.iters = d_it; a.eta = d_eta; a.solver = d_solver; a.scratch = w.scratch;
+                a.tol = o.tol; a.max_iter = o.max_iter;
+                CF_CUDA_TRY(cudaEventRecord(e0, st));
+                rc = mixed ? launch_mixed_cfg(a, c, st) : launch_factor_cfg(a, c, st);
+                if (rc) return rc;
+                CF_CUDA_TRY(cudaEventRecord(e1, st));
+                CF_CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if (pass == 1 && (best < 0.f || ms < best)) { best = ms; best_vb = c.vb; best_cps = c.cps; }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    opt->v = best_vb;
+    opt->batch_cps = best_cps;
+    if (best_ms) *best_ms = best;
     return CF_OK;
 }

@@ -57,6 +57,7 @@ struct Opts {
     int v = 128, leaf_h = 128, arity = 2, outer_V = 0, lookahead = 1;
     double tol = 1e-14;
     int max_iter = 30, gmres_restart = 30;
+    int batch_cps = 0;           // batched calls: resident CTAs per SM (0 = as many as fit)
 };
 // Returns 0 or a negative status for an out-of-range field.
 int resolve_options(const cf_options *in, Opts *out);

@@ -196,3 +196,76 @@ def test_batched_mixed_fp64_fallback(cf):
         x = X[b.vec_offsets[i]:b.vec_offsets[i] + n]
         e = oracle.backward_error(mats[i], x.reshape(n, 1), rhs[i].reshape(n, 1)).max()
         assert eta[i] <= 1e-14 and e <= 1e-14, (i, eta[i], e, iters[i])
+
+
+@pytest.mark.parametrize("v,cps", [(8, 1), (16, 2), (32, 1), (16, 3)])
+def test_batched_block_size_and_residency(cf, v, cps):
+    """Every (block size, CTAs per SM) the autotuner can pick gives LU and
+    Cholesky factors with oracle-level backward error."""
+    rng = np.random.default_rng(11)
+    sizes = [int(x) for x in rng.integers(1, 513, 40)]
+    kinds = [i % 2 for i in range(len(sizes))]
+    mats = _gen(sizes, kinds, seed0=300)
+    b = cf.Batch(sizes, kinds=kinds)
+    _fill(b, mats)
+    ipiv, iptr, info = cf.factor_batched(b, v=v, batch_cps=cps)
+    assert (info.cpu().numpy() == 0).all()
+    ipv = ipiv.cpu().numpy()
+    for i, (n, k) in enumerate(zip(sizes, kinds)):
+        out = b.matrix(i).cpu().numpy()
+        if k == 0:
+            assert oracle.lu_residual(mats[i], out, ipv[b.vec_offsets[i]:b.vec_offsets[i] + n]) <= 20, (i, n)
+        else:
+            assert oracle.chol_residual(mats[i], np.tril(out)) <= 20, (i, n)
+
+
+def test_batched_graph_capture_replay(cf):
+    """The batched factorization and the batched mixed solve captured in CUDA
+    graphs: replays reproduce the direct calls bit for bit."""
+    rng = np.random.default_rng(12)
+    sizes = [int(x) for x in rng.integers(16, 300, 64)]
+    kinds = [i % 2 for i in range(len(sizes))]
+    mats = _gen(sizes, kinds, seed0=400)
+    b = cf.Batch(sizes, kinds=kinds)
+    _fill(b, mats)
+    A0 = b.data.clone()
+    ipiv_ref, _, info_ref = cf.factor_batched(b)
+    F_ref = b.data.clone()
+    plan = cf.BatchedPlan(b, "factor")
+    b.data.copy_(A0)
+    plan.capture()                         # capture only records; nothing runs
+    for _ in range(2):
+        b.data.copy_(A0)
+        plan.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(b.data, F_ref)
+        assert torch.equal(plan.ipiv, ipiv_ref) and torch.equal(plan.info, info_ref)
+    # mixed solve
+    b.data.copy_(A0)
+    Bv = torch.randn(b.vec_total, dtype=torch.float64, device="cuda")
+    X_ref, info2, iters, eta, solver = cf.solve_batched_mixed(b, Bv)
+    mp = cf.BatchedPlan(b, "mixed")
+    mp.B.copy_(Bv)
+    mp.capture()
+    mp.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(mp.X, X_ref) and torch.equal(mp.eta, eta)
+    assert (mp.eta.cpu().numpy() <= 1e-14).all()
+
+
+def test_batched_autotune(cf):
+    """The autotuner returns a candidate configuration that runs and
+    factors correctly; the sample's time is positive."""
+    sizes = np.random.default_rng(7).integers(16, 513, 3000).tolist()
+    kinds = [0 if i % 2 else 1 for i in range(len(sizes))]
+    b = cf.Batch(sizes, kinds=kinds)
+    for mixed in (False, True):
+        opt, ms = cf.batched_autotune(b, mixed=mixed)
+        assert opt.v in (8, 16, 32) and 1 <= opt.batch_cps <= (2 if mixed else 3) and ms > 0
+    opt, ms = cf.batched_autotune(b, mixed=False)
+    sub = [16, 100, 257, 512]
+    mats = _gen(sub, [0, 1, 0, 1], seed0=500)
+    bs = cf.Batch(sub, kinds=[0, 1, 0, 1])
+    _fill(bs, mats)
+    ipiv, iptr, info = cf.factor_batched(bs, opt=opt)
+    assert (info.cpu().numpy() == 0).all()
