@@ -91,7 +91,8 @@ int launch_ltrsm32(float *X, int ldx, int w, int cols, const float *L00, int ldl
 // ---- thin triangular solves with FP32 factors (cf_trsv.cu)
 // mode: 0 unit lower (L of LU), 1 upper (U), 2 lower (Cholesky L), 3 L^T.
 size_t trsv_ws_bytes(int n);
-size_t diag_inverse_floats(int n);
+size_t diag_inverse_floats(int n);      // FP32 inverses (128-row blocks)
+size_t diag_inverse64_elems(int n);     // FP64 inverses (64-row blocks)
 int launch_diag_inverse(int mode, int n, const float *T, int ldt, float *Dinv, cudaStream_t st);
 int launch_diag_inverse64(int mode, int n, const float *T, int ldt, double *Dinv, cudaStream_t st);
 int launch_trsv_f64x(int mode, int n, int nrhs, const float *T, int ldt, const double *Dinv, double *X, int ldx,

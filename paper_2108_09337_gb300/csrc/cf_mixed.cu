@@ -320,8 +320,8 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->Rf = cv.take<float>((size_t)n * nrhs + 1);
     w->DinvL = cv.take<float>(diag_inverse_floats(n));
     w->DinvU = lu ? cv.take<float>(diag_inverse_floats(n)) : nullptr;
-    w->DinvL64 = cv.take<double>(diag_inverse_floats(n));
-    w->DinvU64 = lu ? cv.take<double>(diag_inverse_floats(n)) : nullptr;
+    w->DinvL64 = cv.take<double>(diag_inverse64_elems(n));
+    w->DinvU64 = lu ? cv.take<double>(diag_inverse64_elems(n)) : nullptr;
     w->trsv_sync = cv.take<int>(trsv_ws_bytes(n) / sizeof(int) + 1);
     w->norms = cv.take<unsigned long long>(3 * nrhs + 2);
     w->m = o.gmres_restart;

@@ -1,13 +1,14 @@
 // cf_trsv.cu -- S-1 for the refinement loop: triangular solves with the FP32
 // factors and a thin right-hand side (nrhs <= 16), one launch per solve.
 //
-// Block rows of 64 are processed by CTAs that take a ticket in launch order
+// Block rows (128 for FP32, 64 for FP64 arithmetic) are processed by CTAs
+// that take a ticket in launch order
 // (atomic counter), so every block a CTA depends on belongs to a CTA that
 // started earlier and never waits on a later one.  A CTA subtracts the
 // contributions of the finished blocks as their flags appear, applies the
 // precomputed inverse of its diagonal block, publishes its block of the
 // solution and raises its flag.  The factor is read exactly once; the chain
-// of dependent work is one 64 x 64 tile product per block.  Waits on flags
+// of dependent work is one tile product per block.  Waits on flags
 // are bounded: after the limit the kernel records CF_ERR_TIMEOUT and goes
 // on (results are then wrong, never hung).
 #include "cf_common.cuh"
@@ -17,7 +18,11 @@ namespace cf {
 
 __device__ int g_trsv_status = 0;
 
-constexpr int kSB = 64;                // block size
+// Block sizes: the FP32 solves use 128-row blocks (half the chain of
+// dependent blocks of 64-row ones; their shared memory fits one CTA per SM);
+// the FP64-arithmetic solves keep 64-row blocks (FP64 tiles of 128 would not
+// fit).
+constexpr int kSB32 = 128, kSB64 = 64;
 constexpr long long kFlagSpin = 1ll << 22;
 
 // Effective matrix M (n x n) seen by a solve:
@@ -28,19 +33,20 @@ __device__ __forceinline__ float m_elem(const float *T, int ldt, int i, int k) {
     return (MODE == 3) ? T[(size_t)k + (size_t)i * ldt] : T[(size_t)i + (size_t)k * ldt];
 }
 
-// Inverse of each 64 x 64 diagonal block of M, stored block after block,
-// column-major (Dinv[b*64*64 + i + 64*j]), computed in VT (float, or double
+// Inverse of each SB x SB diagonal block of M, stored block after block,
+// column-major (Dinv[b*SB*SB + i + SB*j]), computed in VT (float, or double
 // for the FP64-arithmetic solves with the same FP32 factor).  Dynamic shared
-// memory: 2 * 64 * 65 VT.
-template <int MODE, typename VT>
+// memory: 2 * SB * (SB + 1) VT.
+template <int SB, int MODE, typename VT>
 __global__ void __launch_bounds__(256) k_diag_inverse(int n, const float *__restrict__ T, int ldt, VT *Dinv) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    VT (*Ms)[kSB + 1] = reinterpret_cast<VT (*)[kSB + 1]>(dsm);                               // Ms[i][k] = M(b0+i, b0+k)
-    VT (*Xs)[kSB + 1] = reinterpret_cast<VT (*)[kSB + 1]>(dsm + sizeof(VT) * kSB * (kSB + 1));  // inverse
-    const int b = blockIdx.x, b0 = b * kSB, nbk = min(kSB, n - b0);
+    VT (*Ms)[SB + 1] = reinterpret_cast<VT (*)[SB + 1]>(dsm);                             // Ms[i][k] = M(b0+i, b0+k)
+    VT (*Xs)[SB + 1] = reinterpret_cast<VT (*)[SB + 1]>(dsm + sizeof(VT) * SB * (SB + 1));  // inverse
+    constexpr int G = 256 / SB;                      // row groups of the column-parallel solve
+    const int b = blockIdx.x, b0 = b * SB, nbk = min(SB, n - b0);
     const int tid = threadIdx.x;
-    for (int e = tid; e < kSB * kSB; e += 256) {
-        const int i = e % kSB, k = e / kSB;
+    for (int e = tid; e < SB * SB; e += 256) {
+        const int i = e % SB, k = e / SB;
         VT v = VT(0);
         if (i < nbk && k < nbk) v = (VT)m_elem<MODE>(T, ldt, b0 + i, b0 + k);
         if (i >= nbk || k >= nbk) v = (i == k) ? VT(1) : VT(0);
@@ -50,21 +56,21 @@ __global__ void __launch_bounds__(256) k_diag_inverse(int n, const float *__rest
     }
     __syncthreads();
     const bool lower = (MODE != 1);
-    // Solve M X = I column-parallel: thread owns column j = tid % 64 and rows
-    // i = tid / 64 + 4 t.
-    const int j = tid % kSB, i0 = tid / kSB;
-    for (int s = 0; s < kSB; ++s) {
-        const int k = lower ? s : kSB - 1 - s;
+    // Solve M X = I column-parallel: thread owns column j = tid % SB and rows
+    // i = tid / SB + G t.
+    const int j = tid % SB, i0 = tid / SB;
+    for (int s = 0; s < SB; ++s) {
+        const int k = lower ? s : SB - 1 - s;
         if (MODE != 0 && i0 == 0) Xs[k][j] = Xs[k][j] / Ms[k][k];
         __syncthreads();
         const VT xk = Xs[k][j];
-        for (int i = i0; i < kSB; i += 4) {
+        for (int i = i0; i < SB; i += G) {
             if ((lower && i > k) || (!lower && i < k)) Xs[i][j] = fma(-Ms[i][k], xk, Xs[i][j]);
         }
         __syncthreads();
     }
-    VT *D = Dinv + (size_t)b * kSB * kSB;
-    for (int e = tid; e < kSB * kSB; e += 256) D[e] = Xs[e % kSB][e / kSB];
+    VT *D = Dinv + (size_t)b * SB * SB;
+    for (int e = tid; e < SB * SB; e += 256) D[e] = Xs[e % SB][e / SB];
 }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -76,76 +82,164 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-constexpr int kTLD = kSB + 4;          // smem leading dimension (16-byte rows)
-
-// Stages the STORED 64 x 64 tile whose top-left element is (i0, j0) of T
-// (column-major, ld ldt) into St[col * kTLD + row] with 16-byte async copies
-// when the whole tile is inside the matrix and aligned; element by element
-// otherwise (zero outside).
+// Stages the STORED SB x SB tile whose top-left element is (i0, j0) of T
+// (column-major, ld ldt) into St[col * (SB + 4) + row] with 16-byte async
+// copies when the whole tile is inside the matrix and aligned; element by
+// element otherwise (zero outside).
+template <int SB>
 __device__ __forceinline__ void stage_tile(float *St, const float *T, int ldt, int n, int i0, int j0, bool fast) {
+    constexpr int TLD = SB + 4;
     const int tid = threadIdx.x;
     if (fast) {
-        for (int e = tid; e < kSB * kSB / 4; e += 256) {
-            const int r4 = e % (kSB / 4), c = e / (kSB / 4);
-            cp_async16(St + c * kTLD + 4 * r4, T + (size_t)(i0 + 4 * r4) + (size_t)(j0 + c) * ldt);
+        for (int e = tid; e < SB * SB / 4; e += 256) {
+            const int r4 = e % (SB / 4), c = e / (SB / 4);
+            cp_async16(St + c * TLD + 4 * r4, T + (size_t)(i0 + 4 * r4) + (size_t)(j0 + c) * ldt);
         }
     } else {
-        for (int e = tid; e < kSB * kSB; e += 256) {
-            const int r = e % kSB, c = e / kSB;
-            St[c * kTLD + r] = (i0 + r < n && j0 + c < n) ? T[(size_t)(i0 + r) + (size_t)(j0 + c) * ldt] : 0.f;
+        for (int e = tid; e < SB * SB; e += 256) {
+            const int r = e % SB, c = e / SB;
+            St[c * TLD + r] = (i0 + r < n && j0 + c < n) ? T[(size_t)(i0 + r) + (size_t)(j0 + c) * ldt] : 0.f;
+        }
+    }
+}
+
+// Row length of the staged right-hand sides: every thread reads columns
+// cg + CG t for t < CPT, which may pass NR (those are never written back).
+template <int SB, int NR>
+__host__ __device__ constexpr int trsv_yld() {
+    return (256 / (SB / 4)) * ((NR + (256 / (SB / 4)) - 1) / (256 / (SB / 4))) + 1;
+}
+
+template <int SB, typename VT, int NR>
+__host__ __device__ constexpr size_t trsv_smem_bytes() {
+    return sizeof(float) * 2 * (size_t)SB * (SB + 4) +
+           sizeof(VT) * ((size_t)SB * (SB + 4) + (size_t)SB * trsv_yld<SB, NR>());
+}
+
+// Four consecutive 16-byte-aligned shared-memory values as VT.
+template <typename VT>
+__device__ __forceinline__ void load4(VT (&m)[4], const float *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    m[0] = (VT)v.x; m[1] = (VT)v.y; m[2] = (VT)v.z; m[3] = (VT)v.w;
+}
+__device__ __forceinline__ void load4(double (&m)[4], const double *p) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    m[0] = a.x; m[1] = a.y; m[2] = b.x; m[3] = b.y;
+}
+__device__ __forceinline__ void load4(float (&m)[4], const float *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    m[0] = v.x; m[1] = v.y; m[2] = v.z; m[3] = v.w;
+}
+
+// Row r (0..3) of a thread's four: 4 rg + r (consecutive), or rg + RG r
+// (STRIDED, used by the transposed solve so that the lanes of a warp read
+// consecutive rows of a row-major tile without bank conflicts).
+template <bool STRIDED, int RG>
+__device__ __forceinline__ int trow(int rg, int r) { return STRIDED ? rg + RG * r : 4 * rg + r; }
+
+// acc[r][t] += sign * sum_kk Mt(row(r), kk) * Ys[kk][cg + CG t] for one staged
+// tile; Mt(i, kk) = Tt[kk * LD + i] (COLMAJ) or Tt[i * LD + kk].  Column-major
+// tiles with consecutive rows are read as one 16-byte vector per kk;
+// row-major ones (strided rows) as one vector per four kk; the right-hand
+// sides are broadcast within a warp.
+template <int SB, int NR, int CPT, int CG, bool COLMAJ, bool STRIDED, typename MT, typename VT>
+__device__ __forceinline__ void tile_update(VT (&acc)[4][CPT], const MT *Tt, int LD, const VT *Ys, int YLD, int rg,
+                                            int cg, VT sign) {
+    constexpr int RG = SB / 4;
+    if (COLMAJ) {
+#pragma unroll 4
+        for (int kk = 0; kk < SB; ++kk) {
+            VT m[4];
+            if (!STRIDED) {
+                load4(m, Tt + kk * LD + 4 * rg);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) m[r] = (VT)Tt[kk * LD + trow<true, RG>(rg, r)];
+            }
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) {
+                const VT y = Ys[kk * YLD + cg + CG * t];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r][t] = fma(sign * m[r], y, acc[r][t]);
+            }
+        }
+    } else {
+#pragma unroll 2
+        for (int k4 = 0; k4 < SB; k4 += 4) {
+            VT m[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) load4(m[r], Tt + trow<STRIDED, RG>(rg, r) * LD + k4);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int t = 0; t < CPT; ++t) {
+                    const VT y = Ys[(k4 + u) * YLD + cg + CG * t];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[r][t] = fma(sign * m[r][u], y, acc[r][t]);
+                }
         }
     }
 }
 
 // VT: arithmetic and right-hand-side type (float, or double for FP64
 // solves with the FP32 factor); the factor tiles stay FP32 in shared memory.
-template <int MODE, int NR, typename VT>
+// Thread = (row group rg = tid % (SB / 4): rows 4 rg .. 4 rg + 3, or
+// rg + (SB / 4) r for the transposed solve; right-hand-side group
+// cg = tid / (SB / 4): columns cg + CG t).
+template <int SB, int MODE, int NR, typename VT>
 __global__ void __launch_bounds__(256)
 k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *__restrict__ Dinv, VT *X,
                int ldx, int *flags, int *ticket) {
+    constexpr int TLD = SB + 4;
+    constexpr int RG = SB / 4;                     // row groups of 4
+    constexpr int CG = 256 / RG;                   // right-hand-side groups
+    constexpr int CPT = (NR + CG - 1) / CG;        // right-hand sides per thread
+    constexpr int YLD = trsv_yld<SB, NR>();
+    static_assert(YLD >= CG * CPT + 1, "staged right-hand-side rows too short");
+    constexpr bool STR = (MODE == 3);              // strided rows (see trow)
     extern __shared__ __align__(16) float sm[];
     float *St0 = sm;                               // two tile buffers
-    float *St1 = sm + kSB * kTLD;
-    VT *Ds = reinterpret_cast<VT *>(sm + 2 * kSB * kTLD);   // inverse of the diagonal block
-    VT *Ys = Ds + kSB * kTLD;                               // [kSB][NR + 1]
+    float *St1 = sm + SB * TLD;
+    VT *Ds = reinterpret_cast<VT *>(sm + 2 * SB * TLD);     // inverse of the diagonal block
+    VT *Ys = Ds + SB * TLD;                                 // [SB][YLD]
     __shared__ int s_ticket;
     constexpr bool fwd = (MODE == 0 || MODE == 2);
-    constexpr int CPT = (NR + 3) / 4;              // right-hand sides per thread
-    constexpr int YLD = NR + 1;
-    const int nb = (n + kSB - 1) / kSB;
+    const int nb = (n + SB - 1) / SB;
     const int tid = threadIdx.x;
     if (tid == 0) s_ticket = atomicAdd(ticket, 1);
     __syncthreads();
     const int s = s_ticket;
     if (s >= nb) return;
     const int b = fwd ? s : nb - 1 - s;
-    const int r0 = b * kSB, rb = min(kSB, n - r0);
-    const int i = tid % kSB, q = tid / kSB;        // row, rhs group
+    const int r0 = b * SB, rb = min(SB, n - r0);
+    const int rg = tid % RG, cg = tid / RG;
     const bool aligned = ((ldt & 3) == 0) && ((((uintptr_t)T) & 15) == 0);
     // the diagonal block's inverse does not depend on anyone: fetch it now
+    // (Ds[kk * TLD + ii] = (Dinv_b)(ii, kk); MODE 3 uses (L_bb^{-1})^T)
     {
-        const VT *D = Dinv + (size_t)b * kSB * kSB;
-        for (int e = tid; e < kSB * kSB; e += 256) {
-            const int ii = e % kSB, kk = e / kSB;
-            // MODE 3 uses (L_bb^{-1})^T
-            Ds[kk * kTLD + ii] = (MODE == 3) ? D[kk + kSB * ii] : D[ii + kSB * kk];
+        const VT *D = Dinv + (size_t)b * SB * SB;
+        for (int e = tid; e < SB * SB; e += 256) {
+            const int ii = e % SB, kk = e / SB;
+            Ds[kk * TLD + ii] = (MODE == 3) ? D[kk + SB * ii] : D[ii + SB * kk];
         }
     }
-    VT acc[CPT];
+    VT acc[4][CPT];
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) {
-        const int c = q + 4 * t;
-        acc[t] = (i < rb && c < nrhs) ? X[(size_t)(r0 + i) + (size_t)c * ldx] : VT(0);
-    }
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) {
+            const int i = trow<STR, RG>(rg, r), c = cg + CG * t;
+            acc[r][t] = (i < rb && c < nrhs) ? X[(size_t)(r0 + i) + (size_t)c * ldx] : VT(0);
+        }
     // Stored tile that holds M(block b, block cb): for MODE 3 it is L(cb, b).
     auto tile_origin = [&](int cb, int &ti, int &tj) {
-        if (MODE == 3) { ti = cb * kSB; tj = r0; } else { ti = r0; tj = cb * kSB; }
+        if (MODE == 3) { ti = cb * SB; tj = r0; } else { ti = r0; tj = cb * SB; }
     };
     if (s > 0) {
         const int cb = fwd ? 0 : nb - 1;
         int ti, tj;
         tile_origin(cb, ti, tj);
-        stage_tile(St0, T, ldt, n, ti, tj, aligned && ti + kSB <= n && tj + kSB <= n);
+        stage_tile<SB>(St0, T, ldt, n, ti, tj, aligned && ti + SB <= n && tj + SB <= n);
         cp_async_commit();
     }
     for (int step = 0; step < s; ++step) {
@@ -154,11 +248,11 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
             const int cb = fwd ? step + 1 : nb - 2 - step;
             int ti, tj;
             tile_origin(cb, ti, tj);
-            stage_tile((step & 1) ? St0 : St1, T, ldt, n, ti, tj, aligned && ti + kSB <= n && tj + kSB <= n);
+            stage_tile<SB>((step & 1) ? St0 : St1, T, ldt, n, ti, tj, aligned && ti + SB <= n && tj + SB <= n);
         }
         cp_async_commit();
         const int cb = fwd ? step : nb - 1 - step;
-        const int c0 = cb * kSB, cbk = min(kSB, n - c0);
+        const int c0 = cb * SB, cbk = min(SB, n - c0);
         if (tid == 0) {
             volatile int *f = flags + cb;
             long long it = 0;
@@ -170,120 +264,121 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
             __threadfence();
         }
         __syncthreads();
-        for (int e = tid; e < kSB * NR; e += 256) {
-            const int kk = e % kSB, c = e / kSB;
+        for (int e = tid; e < SB * NR; e += 256) {
+            const int kk = e % SB, c = e / SB;
             Ys[kk * YLD + c] = (kk < cbk && c < nrhs) ? __ldcg(X + (size_t)(c0 + kk) + (size_t)c * ldx) : VT(0);
         }
         cp_async_wait<1>();                        // this step's tile has landed
         __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < kSB; ++kk) {
-            const VT m = (VT)((MODE == 3) ? St[i * kTLD + kk] : St[kk * kTLD + i]);
-#pragma unroll
-            for (int t = 0; t < CPT; ++t) acc[t] = fma(-m, Ys[kk * YLD + q + 4 * t], acc[t]);
-        }
+        // M(i, kk) = St[kk * TLD + i], or St[i * TLD + kk] for MODE 3
+        tile_update<SB, NR, CPT, CG, MODE != 3, STR>(acc, St, TLD, Ys, YLD, rg, cg, VT(-1));
         __syncthreads();
     }
     cp_async_wait<0>();
     // y_b = Dinv_b acc
 #pragma unroll
-    for (int t = 0; t < CPT; ++t)
-        if (q + 4 * t < NR) Ys[i * YLD + q + 4 * t] = acc[t];
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int t = 0; t < CPT; ++t)
+            if (cg + CG * t < NR) Ys[trow<STR, RG>(rg, r) * YLD + cg + CG * t] = acc[r][t];
     __syncthreads();
-    VT y[CPT];
+    VT y[4][CPT];
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) y[t] = VT(0);
-#pragma unroll 8
-    for (int kk = 0; kk < kSB; ++kk) {
-        const VT d = Ds[kk * kTLD + i];
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int t = 0; t < CPT; ++t) y[t] = fma(d, Ys[kk * YLD + q + 4 * t], y[t]);
-    }
+        for (int t = 0; t < CPT; ++t) y[r][t] = VT(0);
+    tile_update<SB, NR, CPT, CG, true, STR>(y, Ds, TLD, Ys, YLD, rg, cg, VT(1));
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) {
-        const int c = q + 4 * t;
-        if (i < rb && c < nrhs) X[(size_t)(r0 + i) + (size_t)c * ldx] = y[t];
-    }
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) {
+            const int i = trow<STR, RG>(rg, r), c = cg + CG * t;
+            if (i < rb && c < nrhs) X[(size_t)(r0 + i) + (size_t)c * ldx] = y[r][t];
+        }
     __threadfence();
     __syncthreads();
     if (tid == 0) atomicExch(flags + b, 1);
 }
 
+// Flags for the smaller block size (the larger needs fewer).
 size_t trsv_ws_bytes(int n) {
-    const int nb = (n + kSB - 1) / kSB;
+    const int nb = (n + kSB64 - 1) / kSB64;
     return sizeof(int) * (size_t)(nb + 1);
 }
 
+// Elements of the FP32 (128-row blocks) and FP64 (64-row blocks) inverse sets.
 size_t diag_inverse_floats(int n) {
-    const int nb = (n + kSB - 1) / kSB;
-    return (size_t)nb * kSB * kSB;
+    const int nb = (n + kSB32 - 1) / kSB32;
+    return (size_t)nb * kSB32 * kSB32;
+}
+size_t diag_inverse64_elems(int n) {
+    const int nb = (n + kSB64 - 1) / kSB64;
+    return (size_t)nb * kSB64 * kSB64;
+}
+
+template <int SB, int MODE, typename VT>
+static int launch_diag_inverse_m(int n, const float *T, int ldt, VT *Dinv, cudaStream_t st) {
+    const int nb = (n + SB - 1) / SB;
+    const size_t smem = 2 * sizeof(VT) * SB * (SB + 1);
+    CF_CUDA_TRY(cudaFuncSetAttribute(k_diag_inverse<SB, MODE, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    k_diag_inverse<SB, MODE, VT><<<nb, 256, smem, st>>>(n, T, ldt, Dinv);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
 }
 
 // mode: 0 unit lower, 1 upper, 2 lower, 3 lower transposed (see m_elem).
-template <typename VT>
+template <int SB, typename VT>
 static int launch_diag_inverse_t(int mode, int n, const float *T, int ldt, VT *Dinv, cudaStream_t st) {
     if (n <= 0) return CF_OK;
-    const int nb = (n + kSB - 1) / kSB;
-    const size_t smem = 2 * sizeof(VT) * kSB * (kSB + 1);
     switch (mode) {
-        case 0:
-            CF_CUDA_TRY(cudaFuncSetAttribute(k_diag_inverse<0, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_diag_inverse<0, VT><<<nb, 256, smem, st>>>(n, T, ldt, Dinv);
-            break;
-        case 1:
-            CF_CUDA_TRY(cudaFuncSetAttribute(k_diag_inverse<1, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_diag_inverse<1, VT><<<nb, 256, smem, st>>>(n, T, ldt, Dinv);
-            break;
-        case 2:
-            CF_CUDA_TRY(cudaFuncSetAttribute(k_diag_inverse<2, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_diag_inverse<2, VT><<<nb, 256, smem, st>>>(n, T, ldt, Dinv);
-            break;
+        case 0: return launch_diag_inverse_m<SB, 0, VT>(n, T, ldt, Dinv, st);
+        case 1: return launch_diag_inverse_m<SB, 1, VT>(n, T, ldt, Dinv, st);
+        case 2: return launch_diag_inverse_m<SB, 2, VT>(n, T, ldt, Dinv, st);
         default: return CF_ERR_UNSUPPORTED;
     }
-    CF_LAUNCH_CHECK();
-    return CF_OK;
 }
 
 int launch_diag_inverse(int mode, int n, const float *T, int ldt, float *Dinv, cudaStream_t st) {
-    return launch_diag_inverse_t<float>(mode, n, T, ldt, Dinv, st);
+    return launch_diag_inverse_t<kSB32, float>(mode, n, T, ldt, Dinv, st);
 }
 int launch_diag_inverse64(int mode, int n, const float *T, int ldt, double *Dinv, cudaStream_t st) {
-    return launch_diag_inverse_t<double>(mode, n, T, ldt, Dinv, st);
+    return launch_diag_inverse_t<kSB64, double>(mode, n, T, ldt, Dinv, st);
 }
 
-template <int MODE, int NR, typename VT>
+template <int SB, int MODE, int NR, typename VT>
 static int launch_trsv_nr(int n, int nrhs, const float *T, int ldt, const VT *Dinv, VT *X, int ldx, int *flags,
                           int *ticket, cudaStream_t st) {
-    const int nb = (n + kSB - 1) / kSB;
-    const size_t smem = sizeof(float) * 2 * (size_t)kSB * kTLD + sizeof(VT) * ((size_t)kSB * kTLD + (size_t)kSB * 17);
-    CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<MODE, NR, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const int nb = (n + SB - 1) / SB;
+    const size_t smem = trsv_smem_bytes<SB, VT, NR>();
+    CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<SB, MODE, NR, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    k_trsv_blocked<MODE, NR, VT><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    k_trsv_blocked<SB, MODE, NR, VT><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
 
-template <int MODE, typename VT>
+template <int SB, int MODE, typename VT>
 static int launch_trsv_mode(int n, int nrhs, const float *T, int ldt, const VT *Dinv, VT *X, int ldx, int *sync_ws,
                             cudaStream_t st) {
-    const int nb = (n + kSB - 1) / kSB;
+    const int nb = (n + SB - 1) / SB;
     CF_CUDA_TRY(cudaMemsetAsync(sync_ws, 0, sizeof(int) * (size_t)(nb + 1), st));
     int *flags = sync_ws, *ticket = sync_ws + nb;
-    if (nrhs <= 4) return launch_trsv_nr<MODE, 4, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
-    if (nrhs <= 8) return launch_trsv_nr<MODE, 8, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
-    return launch_trsv_nr<MODE, 16, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
+    if (nrhs <= 4) return launch_trsv_nr<SB, MODE, 4, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
+    if (nrhs <= 8) return launch_trsv_nr<SB, MODE, 8, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
+    return launch_trsv_nr<SB, MODE, 16, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
 }
 
-template <typename VT>
+template <int SB, typename VT>
 static int launch_trsv_t(int mode, int n, int nrhs, const float *T, int ldt, const VT *Dinv, VT *X, int ldx,
                          int *sync_ws, cudaStream_t st) {
     if (n <= 0 || nrhs <= 0) return CF_OK;
     if (nrhs > 16) return CF_ERR_UNSUPPORTED;
     switch (mode) {
-        case 0: return launch_trsv_mode<0, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        case 1: return launch_trsv_mode<1, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        case 2: return launch_trsv_mode<2, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        case 3: return launch_trsv_mode<3, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 0: return launch_trsv_mode<SB, 0, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 1: return launch_trsv_mode<SB, 1, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 2: return launch_trsv_mode<SB, 2, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 3: return launch_trsv_mode<SB, 3, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
         default: return CF_ERR_UNSUPPORTED;
     }
 }
@@ -291,13 +386,13 @@ static int launch_trsv_t(int mode, int n, int nrhs, const float *T, int ldt, con
 // X <- M^{-1} X for nrhs <= 16 columns; sync_ws holds trsv_ws_bytes(n).
 int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
                     int *sync_ws, cudaStream_t st) {
-    return launch_trsv_t<float>(mode, n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+    return launch_trsv_t<kSB32, float>(mode, n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
 }
 // The same with FP64 right-hand sides and arithmetic (FP64 Dinv from
 // launch_diag_inverse64); the FP32 factor is read as stored.
 int launch_trsv_f64x(int mode, int n, int nrhs, const float *T, int ldt, const double *Dinv, double *X, int ldx,
                      int *sync_ws, cudaStream_t st) {
-    return launch_trsv_t<double>(mode, n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+    return launch_trsv_t<kSB64, double>(mode, n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
 }
 
 int trsv_take_status(cudaStream_t st, int *status) {
