@@ -75,6 +75,9 @@ typedef struct {
     int batch_cps;     /* batched calls: resident CTAs per SM, 1..3 (LU /
                           Cholesky) or 1..2 (mixed), 0 = as many as fit [0];
                           cf_batched_autotune picks it with v */
+    int fp64_residual; /* mixed solvers: 1 = every residual and GMRES product
+                          in FP64 arithmetic; 0 = pair arithmetic (see
+                          cf_residual_pair) where the backward error allows [0] */
 } cf_options;
 
 void cf_default_options(cf_options *opt /* host */);
@@ -101,6 +104,8 @@ typedef struct {
     int gmres_iterations;   /* inner GMRES steps over all GMRES-IR corrections */
     int escalated;          /* 1 if the solve refactored with CF_BF16X3 updates
                                after the requested precision stalled */
+    double pair_ms;         /* device time inside the pair-arithmetic products */
+    int pair_launches;      /* pair-arithmetic products with A */
 } cf_refine_stats;
 
 const char *cf_status_string(int status);
@@ -196,16 +201,25 @@ int cf_residual(int m, int n, int nrhs, const double *A, int lda,
                 const double *X, int ldx, const double *B, int ldb, double *R,
                 int ldr, cudaStream_t stream);
 
-/* R-1 on the FP32 pipes (an alternative to cf_residual, not used by the
- * mixed solvers): R = B - A X with A and X split into pairs of FP32 arrays
- * (hi = fl32(v), lo = fl32(v - hi)); products are formed exactly as FP32
- * pairs and summed with error-free transformations, restarting from zero
- * every 32 terms into an FP64 accumulator.  Accuracy: the pair carries 48
- * bits relative to its running value, so the error is about 2^-48 times the
- * largest partial sums of a row (measured 4e-15 to 8e-15 of
- * ||A||_inf ||x||_inf + ||b||_inf on diagonally dominant matrices, against
- * 1e-16 for cf_residual); about 1.8x the throughput of FP64 on this part.
- * work: cf_residual_pair_workspace_size(m, n, nrhs) bytes. */
+/* R-1 on the FP32 pipes: R = B - A X (A m x n FP64, lda; X n x nrhs FP64,
+ * ldx; B, R m x nrhs FP64, column-major; R may alias B) in pair ("double-
+ * float") arithmetic.  Each A element is split on the fly into two FP32
+ * numbers after scaling by a power of two above max |a_ij| (computed here in
+ * one extra pass over A), X once per call after scaling each column by a
+ * power of two; every product is formed exactly as an FP32 pair and summed
+ * with error-free transformations (Knuth's TwoSum), restarting into an FP64
+ * accumulator every 64 terms.  Elements below 2^-74 max |a_ij| are dropped.
+ * Accuracy: about 2^-48 sqrt(64) of the largest partial sums of 64 terms of
+ * a row (1e-16 to a few 1e-14 of ||A||_inf ||x||_inf + ||b||_inf, the latter
+ * on rows dominated by one term; ~1e-16 for cf_residual).  The mixed solvers
+ * use this kernel for the residuals of refinement steps whose backward error
+ * is above 1e-12 and for
+ * the matrix-vector products of GMRES-IR, and cf_residual for the residual
+ * that decides convergence.
+ * work: cf_residual_pair_workspace_size(m, n, nrhs) bytes (device memory,
+ * owned by the caller).  Errors: -k for the k-th argument out of range,
+ * CF_ERR_WORKSPACE if work is null or too small.  Inf / NaN in A or X give
+ * NaN in the affected rows. */
 size_t cf_residual_pair_workspace_size(int m, int n, int nrhs);
 int cf_residual_pair(int m, int n, int nrhs, const double *A, int lda,
                      const double *X, int ldx, const double *B, int ldb,
@@ -341,8 +355,13 @@ int cf_batched_autotune(int batch, const int *n_host, const int *kind_host,
  *   stats        host cf_refine_stats (may be NULL)
  * Refinement: classical (x += M^{-1} r with the FP32 factors M) while each
  * step cuts eta by at least 0.3x; after the first step that does not, GMRES-IR
- * (left-preconditioned GMRES with M, restart opt->gmres_restart, products
- * with A in FP64) for every remaining step.
+ * (left-preconditioned GMRES with M, restart opt->gmres_restart) for every
+ * remaining step.  Residuals: in pair arithmetic (cf_residual_pair) while
+ * the backward error predicted from the last two steps is at least 1e-12,
+ * else in FP64; a pair-arithmetic eta below 1e-12 is recomputed in FP64
+ * before it is used, so convergence to tol < 1e-12 is always decided on an
+ * FP64 residual.  GMRES products with A: pair arithmetic.
+ * opt->fp64_residual = 1 takes every product in FP64.
  * If refinement stalls (max_iter steps, a GMRES-IR step that fails to halve
  * eta, or a breakdown of the low-precision factorization), the
  * matrix is refactored once with CF_BF16X3 updates and refinement continues

@@ -39,7 +39,8 @@ PREC = {"f64": CF_F64, "f32": CF_F32, "bf16": CF_BF16, "f16": CF_F16,
 class Options(ctypes.Structure):
     _fields_ = [("v", ctypes.c_int), ("leaf_h", ctypes.c_int), ("arity", ctypes.c_int),
                 ("outer_V", ctypes.c_int), ("lookahead", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("batch_cps", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("batch_cps", ctypes.c_int),
+                ("fp64_residual", ctypes.c_int)]
 
 
 class RefineStats(ctypes.Structure):
@@ -49,7 +50,8 @@ class RefineStats(ctypes.Structure):
                 ("refine_ms", ctypes.c_double), ("residual_ms", ctypes.c_double),
                 ("update_ms", ctypes.c_double), ("update_flops", ctypes.c_double),
                 ("residual_launches", ctypes.c_int), ("update_launches", ctypes.c_int),
-                ("gmres_iterations", ctypes.c_int), ("escalated", ctypes.c_int)]
+                ("gmres_iterations", ctypes.c_int), ("escalated", ctypes.c_int),
+                ("pair_ms", ctypes.c_double), ("pair_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

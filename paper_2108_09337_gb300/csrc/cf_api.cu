@@ -38,6 +38,8 @@ int resolve_options(const cf_options *in, Opts *o) {
     if (in->max_iter > 0) o->max_iter = in->max_iter;
     if (in->gmres_restart > 0) o->gmres_restart = in->gmres_restart;
     o->batch_cps = in->batch_cps;
+    o->fp64_residual = in->fp64_residual;
+    if (o->fp64_residual < 0 || o->fp64_residual > 1) return CF_ERR_UNSUPPORTED;
     if (o->v < 1 || o->v > kMaxV) return CF_ERR_UNSUPPORTED;
     if (o->leaf_h < 1 || o->leaf_h > 2 * kMaxV) return CF_ERR_UNSUPPORTED;   // FP64 tournament: <= kMaxV
     if (o->arity < 2 || o->arity > 4) return CF_ERR_UNSUPPORTED;
@@ -90,6 +92,7 @@ extern "C" void cf_default_options(cf_options *opt) {
     opt->max_iter = o.max_iter;
     opt->gmres_restart = o.gmres_restart;
     opt->batch_cps = o.batch_cps;
+    opt->fp64_residual = o.fp64_residual;
 }
 
 extern "C" const char *cf_status_string(int s) {
@@ -424,13 +427,8 @@ extern "C" int cf_residual(int m, int n, int nrhs, const double *A, int lda, con
 }
 
 extern "C" size_t cf_residual_pair_workspace_size(int m, int n, int nrhs) {
-    Carver cv(nullptr);
-    const size_t mm = m > 0 ? m : 1, nn = n > 0 ? n : 1, rr = nrhs > 0 ? nrhs : 1;
-    cv.take<float>(mm * nn);
-    cv.take<float>(mm * nn);
-    cv.take<float>(nn * rr);
-    cv.take<float>(nn * rr);
-    return cv.size();
+    (void)nrhs;
+    return pair_residual_ws_bytes(m, n);
 }
 
 extern "C" int cf_residual_pair(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
@@ -448,12 +446,6 @@ extern "C" int cf_residual_pair(int m, int n, int nrhs, const double *A, int lda
     if (m > 0 && nrhs > 0 && R == nullptr) return -10;
     if (ldr < (m > 1 ? m : 1)) return -11;
     if (m == 0 || nrhs == 0) return CF_OK;
-    if (work == nullptr || lwork < cf_residual_pair_workspace_size(m, n, nrhs)) return CF_ERR_WORKSPACE;
-    Carver cv(work);
-    float *Ahi = cv.take<float>((size_t)m * n), *Alo = cv.take<float>((size_t)m * n);
-    float *Xhi = cv.take<float>((size_t)n * nrhs), *Xlo = cv.take<float>((size_t)n * nrhs);
-    int rc;
-    if ((rc = launch_split_f64(m, n, A, lda, Ahi, Alo, m, nullptr, 0, 0.0, st))) return rc;
-    if ((rc = launch_split_f64(n, nrhs, X, ldx, Xhi, Xlo, n, nullptr, 0, 0.0, st))) return rc;
-    return launch_residual_df(m, n, nrhs, Ahi, Alo, m, Xhi, Xlo, n, B, ldb, R, ldr, st);
+    if (work == nullptr || lwork < pair_residual_ws_bytes(m, n)) return CF_ERR_WORKSPACE;
+    return launch_residual_pair_auto(m, n, nrhs, A, lda, X, ldx, B, ldb, R, ldr, work, st);
 }

@@ -58,6 +58,7 @@ struct Opts {
     double tol = 1e-14;
     int max_iter = 30, gmres_restart = 30;
     int batch_cps = 0;           // batched calls: resident CTAs per SM (0 = as many as fit)
+    int fp64_residual = 0;       // mixed solvers: 1 = no pair-arithmetic residuals
 };
 // Returns 0 or a negative status for an out-of-range field.
 int resolve_options(const cf_options *in, Opts *out);

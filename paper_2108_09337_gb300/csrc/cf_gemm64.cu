@@ -235,96 +235,6 @@ int launch_residual_f64(int m, int n, int nrhs, const double *A, int lda, const 
 
 namespace cf {
 
-// ---------------------------------------------------------------------------
-// R-1 on the FP32 pipes: R = B - A X with A = Ahi + Alo and X = Xhi + Xlo
-// split into pairs of FP32 numbers (each pair holds its FP64 value to within
-// 2^-48 relative).  Per term: the exact product Ahi*Xhi as a pair (product +
-// FMA-recovered error), the two cross products into a low accumulator, and a
-// TwoSum (Knuth) that keeps the running sum as a pair; the eight k-lane
-// partial pairs are combined in FP64 at the end.  The residual is then
-// accurate to a few units of 2^-48 per term with errors that average out over
-// a row, far below the 1e-14 backward error the refinement is asked for, at
-// roughly 4-5x the throughput of FP64 arithmetic on this part.
-// CTA: 64 rows; 32 row groups of 2 rows x 8 lanes along k.
-// ---------------------------------------------------------------------------
-// Explicitly rounded operations: the error-free transformations must not be
-// contracted into fused multiply-adds by the compiler.
-__device__ __forceinline__ void acc_df(float &hi, float &lo, float ah, float al, float xh, float xl) {
-    const float p = __fmul_rn(ah, xh);
-    const float e = fmaf(ah, xh, -p);               // ah*xh = p + e exactly
-    lo = fmaf(ah, xl, lo);
-    lo = fmaf(al, xh, lo);
-    lo = __fadd_rn(lo, e);
-    const float s = __fadd_rn(hi, p);               // TwoSum(hi, p)
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    hi = s;
-    lo = __fadd_rn(lo, err);
-}
-
-template <int NR>
-__global__ void __launch_bounds__(256)
-k_residual_df(int m, int n, int nrhs, const float *__restrict__ Ahi, const float *__restrict__ Alo, int lds,
-              const float *__restrict__ Xhi, const float *__restrict__ Xlo, int ldxs, const double *B, int ldb,
-              double *R, int ldr) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *red = reinterpret_cast<double *>(smem_raw);     // [8][64][NR]
-    const int tid = threadIdx.x;
-    const int rg = tid & 31, kl = tid >> 5;
-    const int row0 = blockIdx.x * 64 + rg * 2;
-    const bool ok0 = row0 < m, ok1 = row0 + 1 < m;
-    float hi[2][NR], lo[2][NR];
-    double acc[2][NR];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int c = 0; c < NR; ++c) { hi[i][c] = 0.f; lo[i][c] = 0.f; acc[i][c] = 0.0; }
-    int cnt = 0;
-    for (int p = kl; p < n; p += 8) {
-        const size_t off = (size_t)row0 + (size_t)p * lds;
-        const float ah0 = ok0 ? Ahi[off] : 0.f, ah1 = ok1 ? Ahi[off + 1] : 0.f;
-        const float al0 = ok0 ? Alo[off] : 0.f, al1 = ok1 ? Alo[off + 1] : 0.f;
-#pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            const float xh = (c < nrhs) ? __ldg(Xhi + (size_t)p + (size_t)c * ldxs) : 0.f;
-            const float xl = (c < nrhs) ? __ldg(Xlo + (size_t)p + (size_t)c * ldxs) : 0.f;
-            acc_df(hi[0][c], lo[0][c], ah0, al0, xh, xl);
-            acc_df(hi[1][c], lo[1][c], ah1, al1, xh, xl);
-        }
-        // Every 32 terms the pair is added into an FP64 accumulator and
-        // restarted from zero.  A pair carries 48 bits relative to its own
-        // size; restarting keeps that size at the size of a chunk of terms
-        // rather than the size of the running sum (which a large diagonal
-        // term would otherwise set for the rest of the row).
-        if (++cnt == 32) {
-            cnt = 0;
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int c = 0; c < NR; ++c) {
-                    acc[i][c] += (double)hi[i][c] + (double)lo[i][c];
-                    hi[i][c] = 0.f;
-                    lo[i][c] = 0.f;
-                }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int c = 0; c < NR; ++c)
-            red[((size_t)kl * 64 + rg * 2 + i) * NR + c] = acc[i][c] + ((double)hi[i][c] + (double)lo[i][c]);
-    __syncthreads();
-    for (int o = tid; o < 64 * NR; o += 256) {
-        const int rl = o / NR, c = o % NR;
-        const int row = blockIdx.x * 64 + rl;
-        if (row >= m || c >= nrhs) continue;
-        double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) s += red[((size_t)q * 64 + rl) * NR + c];
-        R[(size_t)row + (size_t)c * ldr] = B ? B[(size_t)row + (size_t)c * ldb] - s : s;   // B null: R = A X
-    }
-}
-
 // hi = fl32(v), lo = fl32(v - hi) for an m x n FP64 block (optional W copy of
 // hi: the mixed path's working matrix starts as fl32(A)).
 __global__ void k_split_f64(int m, int n, const double *__restrict__ A, int lda, float *__restrict__ hi,
@@ -349,35 +259,6 @@ int launch_split_f64(int m, int n, const double *A, int lda, float *hi, float *l
     if (g > 8192) g = 8192;
     k_split_f64<<<(int)g, 256, 0, st>>>(m, n, A, lda, hi, lo, lds, W, ldw, shift);
     CF_LAUNCH_CHECK();
-    return CF_OK;
-}
-
-template <int NR>
-static int launch_residual_df_nr(int m, int n, int nrhs, const float *Ahi, const float *Alo, int lds,
-                                 const float *Xhi, const float *Xlo, int ldxs, const double *B, int ldb, double *R,
-                                 int ldr, cudaStream_t st) {
-    const size_t smem = sizeof(double) * 8 * 64 * NR;
-    CF_CUDA_TRY(cudaFuncSetAttribute(k_residual_df<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_residual_df<NR><<<ceil_div(m, 64), 256, smem, st>>>(m, n, nrhs, Ahi, Alo, lds, Xhi, Xlo, ldxs, B, ldb, R, ldr);
-    CF_LAUNCH_CHECK();
-    return CF_OK;
-}
-
-// R = B - A X with A given as an FP32 pair (Ahi, Alo) and X as a pair.
-int launch_residual_df(int m, int n, int nrhs, const float *Ahi, const float *Alo, int lds, const float *Xhi,
-                       const float *Xlo, int ldxs, const double *B, int ldb, double *R, int ldr, cudaStream_t st) {
-    if (m <= 0 || nrhs <= 0) return CF_OK;
-    for (int c0 = 0; c0 < nrhs; c0 += 16) {
-        const int nc = nrhs - c0 < 16 ? nrhs - c0 : 16;
-        const float *xh = Xhi + (size_t)c0 * ldxs, *xl = Xlo + (size_t)c0 * ldxs;
-        const double *Bc = B + (size_t)c0 * ldb;
-        double *Rc = R + (size_t)c0 * ldr;
-        int rc;
-        if (nc <= 4) rc = launch_residual_df_nr<4>(m, n, nc, Ahi, Alo, lds, xh, xl, ldxs, Bc, ldb, Rc, ldr, st);
-        else if (nc <= 8) rc = launch_residual_df_nr<8>(m, n, nc, Ahi, Alo, lds, xh, xl, ldxs, Bc, ldb, Rc, ldr, st);
-        else rc = launch_residual_df_nr<16>(m, n, nc, Ahi, Alo, lds, xh, xl, ldxs, Bc, ldb, Rc, ldr, st);
-        if (rc) return rc;
-    }
     return CF_OK;
 }
 

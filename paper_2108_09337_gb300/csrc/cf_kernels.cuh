@@ -101,11 +101,19 @@ int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const fl
                     int *sync_ws, cudaStream_t st);
 int trsv_take_status(cudaStream_t st, int *status);
 // FP64 -> FP32 pair split (and optional FP32 working copy with a diagonal
-// shift), and the FP32-pipe residual on the split operands.
+// shift).
 int launch_split_f64(int m, int n, const double *A, int lda, float *hi, float *lo, int lds, float *W, int ldw,
                      double shift, cudaStream_t st);
-int launch_residual_df(int m, int n, int nrhs, const float *Ahi, const float *Alo, int lds, const float *Xhi,
-                       const float *Xlo, int ldxs, const double *B, int ldb, double *R, int ldr, cudaStream_t st);
+// R = B - A X (B null: R = A X) in FP32-pair arithmetic (cf_pair.cu).  amax:
+// device pointer to the FP64 bits of a bound >= max |a_ij| (e.g. ||A||_inf);
+// ws: pair_residual_ws_bytes(m, n) bytes.  The _auto form computes max |a_ij|
+// itself into the workspace.
+size_t pair_residual_ws_bytes(int m, int n);
+int launch_residual_pair(int m, int n, int nrhs, const double *A, int lda, const unsigned long long *amax,
+                         const double *X, int ldx, const double *B, int ldb, double *R, int ldr, void *ws,
+                         cudaStream_t st);
+int launch_residual_pair_auto(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
+                              const double *B, int ldb, double *R, int ldr, void *ws, cudaStream_t st);
 // R = B - A X for a thin X (nrhs columns).
 int launch_residual_f64(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
                         int ldb, double *R, int ldr, cudaStream_t st);

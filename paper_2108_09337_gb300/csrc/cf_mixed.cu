@@ -195,6 +195,11 @@ __global__ void k_copy_cols(int n, int nrhs, const double *S, int lds, double *D
 constexpr int kDotRows = 2048;         // rows per partial-dot block
 constexpr double kGmresTol = 1e-8;     // inner GMRES: stop at ||g_k|| <= tol ||M^{-1} r||
 constexpr double kSwitchRate = 0.3;    // classical refinement must cut eta at least this much per step
+// Pair-arithmetic residuals (cf_pair.cu) are accurate to between ~1e-16 and a
+// few 1e-14 of ||A|| ||x|| (worst on rows dominated by one term): a step whose
+// backward error is predicted at or above kPairFloor takes one, and an eta
+// below kPairFloor from one is recomputed in FP64.
+constexpr double kPairFloor = 1e-12;
 
 // part[(chunk * nv + i) * nrhs + c] = sum over the chunk's rows of V_i[r, c] * W[r, c]
 __global__ void __launch_bounds__(256) k_dots_partial(int n, int nrhs, const double *__restrict__ V,
@@ -278,6 +283,8 @@ struct MixedWS {
     unsigned long long *sbits = nullptr;   // per-column scales of the FP32 preconditioner input
     float *sc8 = nullptr;                  // FP8 tile scales: slab (rows/128 x V/128), then one step
     double *Xbest = nullptr;               // best iterate so far
+    void *pairws = nullptr;                // pair-arithmetic residual workspace
+    const unsigned long long *anorm = nullptr;   // bits of ||A||_inf (bound for the pair residual's scaling)
     size_t bytes = 0;
 };
 
@@ -335,6 +342,7 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->sq = cv.take<double>(nrhs + 1);
     w->sbits = cv.take<unsigned long long>(nrhs + 1);
     w->Xbest = cv.take<double>(blk + 1);
+    w->pairws = cv.take<char>(pair_residual_ws_bytes(n, n));
     w->sc8 = cv.take<float>((size_t)(ceil_div(n > 0 ? n : 1, 128) + 1) * (Vp / 128 + 2));
     w->bytes = cv.size();
     return CF_OK;
@@ -717,7 +725,7 @@ static int block_dots(int n, int nrhs, const double *V, int nv, const double *W,
 }
 
 static int gmres_correct(int n, int nrhs, const double *A, int lda, double *X, int ldx, MixedWS &w, bool lu,
-                         bool prec_f32, double tau, cudaStream_t st, Timer &tres, int *inner) {
+                         bool prec_f32, bool pair, double tau, cudaStream_t st, Timer &tres, int *inner) {
     const size_t blk = (size_t)n * nrhs;
     const int m = w.m;
     int rc;
@@ -750,7 +758,9 @@ static int gmres_correct(int n, int nrhs, const double *A, int lda, double *X, i
         if (all) break;
         const double *Vk = w.V + (size_t)k * blk;
         if ((rc = tres.begin(st))) return rc;
-        if ((rc = launch_residual_f64(n, n, nrhs, A, lda, Vk, n, nullptr, 0, w.Y, n, st))) return rc;   // Y = A v_k
+        rc = pair ? launch_residual_pair(n, n, nrhs, A, lda, w.anorm, Vk, n, nullptr, 0, w.Y, n, w.pairws, st)
+                  : launch_residual_f64(n, n, nrhs, A, lda, Vk, n, nullptr, 0, w.Y, n, st);   // Y = A v_k
+        if (rc) return rc;
         if ((rc = tres.end(st, 2.0 * n * (double)n * nrhs))) return rc;
         if ((rc = apply_precond(n, nrhs, w.Y, w.Wv, w, lu, prec_f32, st))) return rc;                // w = M^{-1} Y
         if ((rc = block_dots(n, nrhs, w.V, k + 1, w.Wv, w.hcol, 0, w, st))) return rc;               // CGS pass 1
@@ -833,7 +843,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
 
     // ---- factorization (Cholesky retries with a diagonal shift on breakdown)
-    Timer tupd, tres;
+    Timer tupd, tres, tpair;
     double shift = 0.0;
     int hinfo = 0;
     // one factorization of fl32(A) into w.W: split = BF16 hi + lo operands
@@ -902,6 +912,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     CF_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(unsigned long long) * (3 * nrhs + 2), st));
     k_max_reduce<<<grid_for(n), 256, 0, st>>>(n, w.rowsum, nA);
     CF_LAUNCH_CHECK();
+    w.anorm = nA;
     k_col_absmax<<<dim3(grid_for(n), nrhs), 256, 0, st>>>(n, nrhs, B, ldb, nB);
     CF_LAUNCH_CHECK();
     // x = 0, r = b
@@ -918,15 +929,22 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
 
     std::vector<unsigned long long> hn(3 * nrhs + 2);
     std::vector<double> hscale(nrhs);
-    double eta_prev = HUGE_VAL, eta = HUGE_VAL, eta_best = HUGE_VAL;
+    double eta_prev = HUGE_VAL, eta_pp = HUGE_VAL, eta = HUGE_VAL, eta_best = HUGE_VAL;
     int it = 0, stall = 0, solver = 0, it_limit = o.max_iter;
     bool converged = false, escalated = false;
-    for (;; ++it) {
-        if (it > 0) {
-            if ((rc = tres.begin(st))) return rc;
-            if ((rc = launch_residual_f64(n, n, nrhs, A, lda, X, ldx, B, ldb, w.R, ldr, st))) return rc;
-            if ((rc = tres.end(st, 2.0 * n * (double)n * nrhs))) return rc;
-        }
+    // R = B - A X in pair arithmetic or in FP64
+    auto residual = [&](bool pair) -> int {
+        Timer &t = pair ? tpair : tres;
+        int rc2 = t.begin(st);
+        if (rc2) return rc2;
+        rc2 = pair ? launch_residual_pair(n, n, nrhs, A, lda, w.anorm, X, ldx, B, ldb, w.R, ldr, w.pairws, st)
+                   : launch_residual_f64(n, n, nrhs, A, lda, X, ldx, B, ldb, w.R, ldr, st);
+        if (rc2) return rc2;
+        return t.end(st, 2.0 * n * (double)n * nrhs);
+    };
+    // eta = max_c ||r_c|| / (||A|| ||x_c|| + ||b_c||) and the per-column
+    // scales of the next correction's right-hand side (one synchronisation)
+    auto measure = [&]() -> int {
         CF_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(unsigned long long) * 2 * nrhs, st));
         k_col_absmax<<<dim3(grid_for(n), nrhs), 256, 0, st>>>(n, nrhs, w.R, ldr, nR);
         CF_LAUNCH_CHECK();
@@ -947,6 +965,24 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             const double e = den > 0 ? r / den : (r > 0 ? HUGE_VAL : 0.0);
             eta = (e > eta || e != e) ? e : eta;
             hscale[c] = r > 0 ? r : 1.0;
+        }
+        return CF_OK;
+    };
+    for (;; ++it) {
+        bool pair = false;
+        if (it > 0) {
+            // backward error this residual should show: the last one times
+            // the last step's contraction (unknown: above the floor)
+            const double pred = (eta_prev < HUGE_VAL && eta_pp < HUGE_VAL && eta_pp > 0.0)
+                                    ? eta_prev * std::fmin(1.0, eta_prev / eta_pp)
+                                    : HUGE_VAL;
+            pair = !o.fp64_residual && !(pred < kPairFloor);
+            if ((rc = residual(pair))) return rc;
+        }
+        if ((rc = measure())) return rc;
+        if (pair && eta < kPairFloor) {   // too close to the pair residual's accuracy: redo in FP64
+            if ((rc = residual(false))) return rc;
+            if ((rc = measure())) return rc;
         }
         if (it == 1) S.eta0 = eta;
         if (eta <= o.tol) { converged = true; break; }
@@ -990,10 +1026,11 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             }
             solver = 0;
             stall = 0;
-            eta_prev = HUGE_VAL;
+            eta_prev = eta_pp = HUGE_VAL;
             it_limit = it + o.max_iter;
             continue;
         }
+        eta_pp = eta_prev;
         eta_prev = eta;
         if (solver == 0) {
             CF_CUDA_TRY(cudaMemcpyAsync(w.scale, hscale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
@@ -1006,7 +1043,10 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
         } else {
             int inner = 0;
             const bool prec_f32 = std::is_same<LP, fp8_e4m3>::value && !split;
-            if ((rc = gmres_correct(n, nrhs, A, lda, X, ldx, w, lu, prec_f32, kGmresTol, st, tres, &inner))) return rc;
+            const bool gpair = !o.fp64_residual;
+            if ((rc = gmres_correct(n, nrhs, A, lda, X, ldx, w, lu, prec_f32, gpair, kGmresTol, st,
+                                    gpair ? tpair : tres, &inner)))
+                return rc;
             S.gmres_iterations += inner;
         }
     }
@@ -1035,6 +1075,8 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     S.refine_ms = r_ms;
     S.residual_ms = tres.ms();
     S.residual_launches = tres.launches;
+    S.pair_ms = tpair.ms();
+    S.pair_launches = tpair.launches;
     S.update_ms = tupd.ms();
     S.update_flops = tupd.flops;
     S.update_launches = tupd.launches;

@@ -298,19 +298,74 @@ def test_config_n2048_lu_and_cholesky(cf):
     assert oracle.chol_residual(S, L) <= 20.0
 
 
-def test_residual_pair_accuracy(cf):
-    """cf_residual_pair (FP32-pipe residual) against the compensated oracle
-    residual: error below 2e-14 of ||A|| ||x|| + ||b|| (its documented floor is
-    ~2^-48 times a row's largest partial sums)."""
-    for n, nrhs in ((129, 3), (1000, 8), (2000, 17)):
-        A = inputs.uniform_pm1(n, seed=n, shift=2 * np.sqrt(n))
-        rng = np.random.default_rng(n)
-        X = np.asfortranarray(rng.standard_normal((n, nrhs)) * 0.1)
-        B = np.asfortranarray(A @ X + 1e-12 * rng.standard_normal((n, nrhs)))
-        Ro = oracle.residual(A, X, B)
-        Rp = _host(cf.residual_pair(_dev(A), _dev(X), _dev(B)))
-        den = np.abs(A).sum(1).max() * np.abs(X).max(0) + np.abs(B).max(0)
-        assert (np.abs(Rp - Ro).max(0) / den).max() <= 2e-14
+def _pair_err(A, X, B, Rp):
+    """max over columns of |Rp - R| / (||A||_inf ||x||_inf + ||b||_inf), R the
+    oracle's compensated residual."""
+    Ro = oracle.residual(A, X, B)
+    den = np.abs(A).sum(1).max() * np.abs(X).max(0) + np.abs(B).max(0)
+    return (np.abs(Rp - Ro).max(0) / den).max()
+
+
+@pytest.mark.parametrize("m,n,nrhs,ld", [(129, 129, 3, None), (1000, 1000, 8, None), (2000, 2000, 17, None),
+                                         (777, 1500, 1, 781), (9728, 600, 16, None), (3000, 257, 5, 3001)])
+def test_residual_pair_accuracy(cf, m, n, nrhs, ld):
+    """cf_residual_pair (FP32-pipe pair arithmetic) against the compensated
+    oracle residual: error below 5e-14 of ||A|| ||x|| + ||b|| on a
+    diagonally dominant system whose residual cancels to 1e-12 (the pair's
+    floor is ~2^-48 sqrt(chunk) of a chunk's largest partial sums, here set
+    by the diagonal term, ~1/12 of the row's norm at n = 2000).  Shapes cover the
+    k-split with partial sums (small m), the direct grid (m = 304 row blocks),
+    groups of 16 right-hand sides (17), odd leading dimensions and m != n."""
+    rng = np.random.default_rng(m + n)
+    A = rng.uniform(-1.0, 1.0, (m, n))
+    k = min(m, n)
+    A[np.arange(k), np.arange(k)] += 2 * np.sqrt(n)
+    X = rng.standard_normal((n, nrhs)) * 0.1
+    B = A @ X + 1e-12 * rng.standard_normal((m, nrhs))
+    Rp = _host(cf.residual_pair(_dev(A, ld), _dev(X), _dev(B)))
+    assert _pair_err(A, X, B, Rp) <= 5e-14
+
+
+def test_residual_pair_scale_invariance(cf):
+    """Power-of-two scaling of A and X by 2^-700 and 2^600 (far outside FP32
+    range) gives the same error relative to ||A|| ||x||: the kernel scales by
+    powers of two before splitting.  Exact zeros and entries far below
+    max |a_ij| (dropped below 2^-74 of it) stay within the same bound."""
+    n, nrhs = 700, 4
+    rng = np.random.default_rng(7)
+    A = rng.uniform(-1.0, 1.0, (n, n)) + 2 * np.sqrt(n) * np.eye(n)
+    A[:, 5] = 0.0
+    A[3, :] *= 1e-30
+    X = rng.standard_normal((n, nrhs))
+    B = A @ X
+    for sa, sx in ((0, 0), (-700, 600), (300, -900)):
+        As, Xs, Bs = np.ldexp(A, sa), np.ldexp(X, sx), np.ldexp(B, sa + sx)
+        Rp = _host(cf.residual_pair(_dev(As), _dev(Xs), _dev(Bs)))
+        assert np.isfinite(Rp).all()
+        assert _pair_err(As, Xs, Bs, Rp) <= 5e-14
+
+
+def test_residual_pair_nonfinite_and_alias(cf):
+    """A NaN or inf in A gives NaN in its row only; R may alias B; a zero X
+    column gives R = B exactly."""
+    n, nrhs = 300, 3
+    rng = np.random.default_rng(11)
+    A = rng.uniform(-1.0, 1.0, (n, n)) + 20 * np.eye(n)
+    A[17, 40] = np.nan
+    A[99, 3] = np.inf
+    X = rng.standard_normal((n, nrhs))
+    X[:, 2] = 0.0
+    B = rng.standard_normal((n, nrhs))
+    dB = _dev(B)
+    cf.residual_pair(_dev(A), _dev(X), dB, R=dB)
+    R = _host(dB)
+    assert np.isnan(R[17, :2]).all() and np.isnan(R[99, :2]).all()
+    ok = np.ones(n, bool)
+    ok[[17, 99]] = False
+    Ac = A.copy()
+    Ac[~ok] = 0.0
+    assert _pair_err(Ac[ok], X, B[ok], R[ok]) <= 5e-14
+    np.testing.assert_array_equal(R[ok, 2], B[ok, 2])
 
 
 @pytest.mark.parametrize("n", [1000, 2500])
