@@ -32,51 +32,61 @@ template <>
 __device__ __forceinline__ __half lp_from<__half>(float x) { return __float2half_rn(x); }
 
 // ---------------------------------------------------------------------------
-// A00 = L00 U00, no pivoting, in place (w <= 128).  Thread r owns row r.  The
-// pivot row of step k is published in shared memory (double-buffered).
+// A00 = L00 U00, no pivoting, in place (w <= 128).  Thread r owns row r as a
+// pair row (cf_regrow.cuh, packed FMAs).  The live part of the pivot row of
+// step k is published in shared memory (double-buffered).
 // ---------------------------------------------------------------------------
 struct LuStep {
     float4 (&pr)[2][kMaxV / 4];
-    float (&a)[kMaxV];
+    float2 (&a)[kPairs];
     float *A00;
     int lda, w, r, kglob;
     int *info;
     template <int U>
     __device__ __forceinline__ void step(int j0) {
         const int k = j0 + U, par = k & 1;
-        if (r == k) store_row4(pr[par], a);              // row k, relative to j0
+        if (r == k) store_live_pairs<U>(pr[par], a, w - j0);   // row k from column k on, relative to j0
         __syncthreads();
         const float *pf = reinterpret_cast<const float *>(pr[par]);
         if (r < w - k) A00[(size_t)k + (size_t)(k + r) * lda] = pf[U + r];        // U(k, k+r)
         const float piv = pf[U];
         if (r > k && r < w) {
-            const float l = (piv != 0.f) ? a[U] / piv : a[U];
+            const float au = pair_elem<U>(a);
+            const float l = (piv != 0.f) ? au / piv : au;
             A00[(size_t)r + (size_t)k * lda] = l;                                   // L(r, k)
-            rank1_from<U>(a, l, pr[par], w - j0);
+            rank1_pairs<U>(a, l, pr[par], w - j0);
         }
         if (r == 0 && piv == 0.f) atomicCAS(info, 0, kglob + k + 1);
     }
 };
 
+__device__ __forceinline__ void load_pair_row(float2 (&a)[kPairs], const float *A00, int lda, int r, int w) {
+#pragma unroll
+    for (int k = 0; k < kPairs; ++k) {
+        const float x = (r < w && 2 * k < w) ? A00[(size_t)r + (size_t)(2 * k) * lda] : 0.f;
+        const float y = (r < w && 2 * k + 1 < w) ? A00[(size_t)r + (size_t)(2 * k + 1) * lda] : 0.f;
+        a[k] = make_float2(x, y);
+    }
+}
+
 __global__ void __launch_bounds__(kMaxV, 1) k_a00_lu32(float *A00, int lda, int w, int kglob, int *info) {
     __shared__ __align__(16) float4 pr[2][kMaxV / 4];
     const int r = threadIdx.x;
-    float a[kMaxV];
-#pragma unroll
-    for (int k = 0; k < kMaxV; ++k) a[k] = (r < w && k < w) ? A00[(size_t)r + (size_t)k * lda] : 0.f;
+    float2 a[kPairs];
+    load_pair_row(a, A00, lda, r, w);
     LuStep body{pr, a, A00, lda, w, r, kglob, info};
-    for_blocks(a, w, body);
+    for_blocks_pairs(a, w, w, body);
 }
 
 // ---------------------------------------------------------------------------
-// A00 = L00 L00^T (lower), in place.  Thread r owns row r; before each
-// barrier every live row publishes its current column entry, so after it
-// each thread has the whole column k of the Schur complement: one barrier
+// A00 = L00 L00^T (lower), in place.  Thread r owns row r (pair row); before
+// each barrier every live row publishes its current column entry, so after
+// it each thread has the whole column k of the Schur complement: one barrier
 // per column.  Stops at the first pivot that is not positive (info).
 // ---------------------------------------------------------------------------
 struct CholStep {
     float4 (&col)[2][kMaxV / 4 + 1];
-    float (&a)[kMaxV];
+    float2 (&a)[kPairs];
     float *A00;
     int lda, w, r, kglob;
     int *info;
@@ -86,7 +96,8 @@ struct CholStep {
         if (failed) return;                          // uniform
         const int k = j0 + U, par = k & 1;
         float *cf = reinterpret_cast<float *>(col[par]);
-        if (r >= k && r < w) cf[r - j0] = a[U];      // column k by relative row
+        const float au = pair_elem<U>(a);
+        if (r >= k && r < w) cf[r - j0] = au;        // column k by relative row
         __syncthreads();
         const float d = cf[U];
         if (!(d > 0.f)) {
@@ -97,10 +108,10 @@ struct CholStep {
         const float lkk = sqrtf(d);
         if (r == k) A00[(size_t)k + (size_t)k * lda] = lkk;
         if (r > k && r < w) {
-            const float l = a[U] / lkk;
+            const float l = au / lkk;
             A00[(size_t)r + (size_t)k * lda] = l;                               // L(r, k)
             // a(r, j0+t) -= L(r,k) L(j0+t,k) = (l / lkk) col[t], for j0+t <= r
-            rank1_from<U>(a, l / lkk, col[par], r - j0 + 1);
+            rank1_pairs<U>(a, l / lkk, col[par], r - j0 + 1);
         }
     }
 };
@@ -109,11 +120,10 @@ __global__ void __launch_bounds__(kMaxV, 1) k_a00_chol32(float *A00, int lda, in
     if (*info != 0) return;
     __shared__ __align__(16) float4 col[2][kMaxV / 4 + 1];
     const int r = threadIdx.x;
-    float a[kMaxV];
-#pragma unroll
-    for (int k = 0; k < kMaxV; ++k) a[k] = (r < w && k < w) ? A00[(size_t)r + (size_t)k * lda] : 0.f;
+    float2 a[kPairs];
+    load_pair_row(a, A00, lda, r, w);
     CholStep body{col, a, A00, lda, w, r, kglob, info, false};
-    for_blocks(a, w, body);
+    for_blocks_pairs(a, w, w, body);
 }
 
 // Packs 8 consecutive values as low-precision and stores them as one 16-byte

@@ -9,9 +9,8 @@
 //     relative to the current block of 8 columns (cf_regrow.cuh), so all
 //     register indices are compile-time constants;
 //   * per column: a warp maximum of integer keys (one redux.sync and a
-//     ballot), eight packed 64-bit warp keys in shared memory, and only the
-//     winning row is written to shared memory (its live part), so the
-//     shared-memory traffic per column is one row, not one per warp;
+//     ballot); each warp's candidate publishes its row before the column's
+//     only barrier, so the winner's row is readable right after it;
 //   * the CTA that finishes a node second climbs to the parent (atomic
 //     counter), so no CTA waits for another.
 // FP32 with FMA: the mixed path's pivots are reported, not held to bit
@@ -28,9 +27,16 @@ constexpr int kT2 = 256;                 // rows per unit = threads per CTA
 constexpr int kT2Warps = kT2 / 32;
 
 struct T2Smem {
-    float4 prow[kMaxV / 4];               // the current pivot row (relative to the block start)
-    unsigned wkey[kT2Warps];              // each warp's largest key
-    float rinv;                           // 1 / pivot
+    // Column U of the current block of 8: each warp's candidate (its in-block
+    // values, key and 1 / its value).
+    float4 slot[kBlk][kT2Warps][2];
+    unsigned wkey[kBlk][kT2Warps];
+    float wrinv[kBlk][kT2Warps];
+    // Block end: pivot U's row at the block start (relative to the block,
+    // columns 8 on; stride padded against bank conflicts) and its
+    // multipliers with respect to pivots 0..U-1 of the block.
+    float4 prow[kBlk][kMaxV / 4 + 1];
+    float lmat[kBlk][kBlk];
     int order[kMaxV];
     int rows[kT2];
     int nrows;
@@ -49,18 +55,28 @@ __device__ __forceinline__ unsigned key32u(float a, bool used) {
 
 // Masked partial-pivoting selection on the rows held by this CTA's threads
 // (thread r holds stacked row r if r < s.nrows).  s.order[0..npiv) = stacked
-// indices of the pivots.  Per column:
-//   warp maximum of the keys (redux.sync) and its smallest lane (ballot);
-//   barrier; every warp takes the maximum of the eight warp keys the same
-//   way (lane q reads warp q's key), so ties go to the smallest warp, then
-//   the smallest lane: the smallest stacked row;
-//   the winner publishes the live part of its row and 1 / pivot; barrier;
-//   every remaining row applies the rank-1 update with l = a * (1 / pivot)
-//   (FP32 selection only: the factors are recomputed from the original rows).
-struct TournStep {
+// indices of the pivots.  Blocked by 8 columns (a right-looking blocked GEPP
+// whose trailing update is deferred to the block end):
+//   column U of the block: warp maximum of the keys (redux.sync) and its
+//   smallest lane (ballot); that lane publishes its 8 in-block values, key
+//   and 1 / value in its warp's slot; barrier; every warp takes the maximum
+//   of the eight warp keys the same way (lane q reads warp q's key), so ties
+//   go to the smallest warp, then the smallest lane: the smallest stacked
+//   row; every remaining row takes l_U = a * (1 / pivot) and updates only its
+//   in-block columns.  One barrier and 32 bytes per candidate per column.
+//   block end (if pivots remain): the eight pivots publish the rest of their
+//   rows as they were at the block start, â_U, and their multipliers L with
+//   respect to the block's earlier pivots; barrier; every remaining row
+//   applies a -= sum_U c_U â_U with c^T (I + L) = l^T, which equals the
+//   eight rank-1 updates of unblocked elimination (the pivot rows' own
+//   updates u_U = â_U - sum_{U' < U} L(U, U') u_U' folded into c).
+// Pivot rows are not updated once chosen: only the selection is used (the
+// factors are recomputed from the original rows).
+struct TournBlockStep {
     T2Smem &s;
     float2 (&a)[kPairs];
-    int w, r, lane, warp;
+    float (&lb)[kBlk];
+    int w, r, lane, warp, pidx;
     bool used;
     template <int U>
     __device__ __forceinline__ void step(int j0) {
@@ -69,29 +85,104 @@ struct TournStep {
         const unsigned k = key32u(aj, used);
         const unsigned m = __reduce_max_sync(0xffffffffu, k);
         const int wl = __ffs(__ballot_sync(0xffffffffu, k == m)) - 1;
-        if (lane == 0) s.wkey[warp] = m;
+        if (lane == wl) {
+            s.slot[U][warp][0] = make_float4(a[0].x, a[0].y, a[1].x, a[1].y);
+            s.slot[U][warp][1] = make_float4(a[2].x, a[2].y, a[3].x, a[3].y);
+            s.wkey[U][warp] = m;
+            s.wrinv[U][warp] = aj != 0.f ? __frcp_rn(aj) : 0.f;   // zero pivot: no elimination
+        }
         __syncthreads();
-        const unsigned kk = s.wkey[lane & (kT2Warps - 1)];
+        const unsigned kk = s.wkey[U][lane & (kT2Warps - 1)];
         const unsigned gm = __reduce_max_sync(0xffffffffu, kk);
         const int wb = __ffs(__ballot_sync(0xffffffffu, kk == gm)) - 1;
         if (warp == wb && lane == wl) {
-            store_live_pairs<U>(s.prow, a, w - j0);
-            s.rinv = aj != 0.f ? 1.0f / aj : 0.f;      // zero pivot: no elimination
             s.order[j] = r;
             used = true;
+            pidx = U;
+#pragma unroll
+            for (int t = 0; t < U; ++t) s.lmat[U][t] = lb[t];
+        }
+        if (!used) {
+            const float ri = s.wrinv[U][wb];
+            const float l = ri != 0.f ? aj * ri : 0.f;
+            lb[U] = l;
+            if (ri != 0.f) {
+                const float2 nl = make_float2(-l, -l);
+                const float4 u0 = s.slot[U][wb][0], u1 = s.slot[U][wb][1];
+                if (1 > U) a[0] = __ffma2_rn(nl, make_float2(u0.x, u0.y), a[0]);
+                if (3 > U) a[1] = __ffma2_rn(nl, make_float2(u0.z, u0.w), a[1]);
+                if (5 > U) a[2] = __ffma2_rn(nl, make_float2(u1.x, u1.y), a[2]);
+                if (7 > U) a[3] = __ffma2_rn(nl, make_float2(u1.z, u1.w), a[3]);
+            }
+        }
+    }
+    // Deferred update of the columns past the block (relative 8 .. w - j0).
+    __device__ __forceinline__ void block_end(int j0) {
+        const int lim = w - j0;
+        if (pidx >= 0) {
+            float4 *dst = s.prow[pidx];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c * 32 < lim) {
+#pragma unroll
+                    for (int q = c * 8; q < c * 8 + 8; ++q)
+                        if (q >= 2) dst[q] = make_float4(a[2 * q].x, a[2 * q].y, a[2 * q + 1].x, a[2 * q + 1].y);
+                }
         }
         __syncthreads();
         if (!used) {
-            const float ri = s.rinv;
-            if (ri != 0.f) rank1_pairs<U>(a, aj * ri, s.prow, w - j0);
+            float c[kBlk];
+#pragma unroll
+            for (int u = kBlk - 1; u >= 0; --u) {
+                float t = lb[u];
+#pragma unroll
+                for (int u2 = u + 1; u2 < kBlk; ++u2) t = fmaf(-c[u2], s.lmat[u2][u], t);
+                c[u] = t;
+            }
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch)
+                if (ch * 32 < lim) {
+#pragma unroll
+                    for (int q = ch * 8; q < ch * 8 + 8; ++q) {
+                        if (q < 2) continue;
+                        float2 x0 = a[2 * q], x1 = a[2 * q + 1];
+#pragma unroll
+                        for (int u = 0; u < kBlk; ++u) {
+                            const float4 p = s.prow[u][q];
+                            const float2 nc = make_float2(-c[u], -c[u]);
+                            x0 = __ffma2_rn(nc, make_float2(p.x, p.y), x0);
+                            x1 = __ffma2_rn(nc, make_float2(p.z, p.w), x1);
+                        }
+                        a[2 * q] = x0;
+                        a[2 * q + 1] = x1;
+                    }
+                }
         }
+#pragma unroll
+        for (int u = 0; u < kBlk; ++u) lb[u] = 0.f;
+        pidx = -1;
     }
 };
 
 __device__ void gepp_select_t2(T2Smem &s, float2 (&a)[kPairs], int w, int npiv) {
     const int r = threadIdx.x;
-    TournStep body{s, a, w, r, r & 31, r >> 5, !(r < s.nrows)};
-    for_blocks_pairs(a, npiv, w, body);
+    float lb[kBlk];
+#pragma unroll
+    for (int u = 0; u < kBlk; ++u) lb[u] = 0.f;
+    TournBlockStep body{s, a, lb, w, r, r & 31, r >> 5, -1, !(r < s.nrows)};
+    for (int j0 = 0; j0 < npiv; j0 += kBlk) {
+        body.template step<0>(j0);
+        if (j0 + 1 < npiv) body.template step<1>(j0);
+        if (j0 + 2 < npiv) body.template step<2>(j0);
+        if (j0 + 3 < npiv) body.template step<3>(j0);
+        if (j0 + 4 < npiv) body.template step<4>(j0);
+        if (j0 + 5 < npiv) body.template step<5>(j0);
+        if (j0 + 6 < npiv) body.template step<6>(j0);
+        if (j0 + 7 < npiv) body.template step<7>(j0);
+        if (j0 + kBlk >= npiv) break;              // no selection left: skip the update
+        body.block_end(j0);
+        shift_pairs(a, w - j0 - kBlk);
+    }
     __syncthreads();
 }
 
