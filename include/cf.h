@@ -208,8 +208,8 @@ int cf_residual(int m, int n, int nrhs, const double *A, int lda,
  * one extra pass over A), X once per call after scaling each column by a
  * power of two; every product is formed exactly as an FP32 pair and summed
  * with error-free transformations (Knuth's TwoSum), restarting into an FP64
- * accumulator every 64 terms.  Elements below 2^-74 max |a_ij| are dropped.
- * Accuracy: about 2^-48 sqrt(64) of the largest partial sums of 64 terms of
+ * accumulator every 16 terms.  Elements below 2^-74 max |a_ij| are dropped.
+ * Accuracy: about 2^-48 sqrt(16) of the largest partial sums of 16 terms of
  * a row (1e-16 to a few 1e-14 of ||A||_inf ||x||_inf + ||b||_inf, the latter
  * on rows dominated by one term; ~1e-16 for cf_residual).  The mixed solvers
  * use this kernel for the residuals of refinement steps whose backward error

@@ -200,6 +200,7 @@ constexpr double kSwitchRate = 0.3;    // classical refinement must cut eta at l
 // backward error is predicted at or above kPairFloor takes one, and an eta
 // below kPairFloor from one is recomputed in FP64.
 constexpr double kPairFloor = 1e-12;
+constexpr double kAssumedRate = 1e-2;
 
 // part[(chunk * nv + i) * nrhs + c] = sum over the chunk's rows of V_i[r, c] * W[r, c]
 __global__ void __launch_bounds__(256) k_dots_partial(int n, int nrhs, const double *__restrict__ V,
@@ -433,6 +434,27 @@ static int cvt_cols_split(int k, int cols, int kpad, const float *src, int lds, 
 // Mixed LU of W (in place): tournament pivoting with FP32 panels, tensor-core
 // Schur updates.
 // ---------------------------------------------------------------------------
+// A second stream for the parts of a panel step that do not depend on each
+// other (released when its work completes).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t swapped = nullptr, a00_done = nullptr, side_done = nullptr;
+    int open() {
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&swapped, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a00_done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&side_done, cudaEventDisableTiming) != cudaSuccess)
+            return CF_ERR_CUDA;
+        return CF_OK;
+    }
+    ~SideStream() {
+        if (swapped) cudaEventDestroy(swapped);
+        if (a00_done) cudaEventDestroy(a00_done);
+        if (side_done) cudaEventDestroy(side_done);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
 template <typename LP>
 static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu, bool split) {
     const bool bf16 = std::is_same<LP, __nv_bfloat16>::value;
@@ -442,6 +464,8 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
     const size_t ld = (size_t)w.ldw;
     float *W = w.W;
     int rc;
+    SideStream ss;
+    if ((rc = ss.open())) return rc;
     k_iota<<<grid_for(n), 256, 0, st>>>(n, w.perm);
     CF_LAUNCH_CHECK();
     CF_CUDA_TRY(cudaMemsetAsync(w.tws.counter, 0, w.tws.counter_bytes, st));
@@ -455,58 +479,70 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             w.tep.k0 = k0;
             if ((rc = launch_tourn32(A00, w.ldw, m, wd, o.leaf_h, o.arity, w.tws, w.tep, st))) return rc;
             if ((rc = launch_apply_swaps<float>(W, w.ldw, n, k0, w.tep, w.perm, st))) return rc;
+            // Fork: the side stream takes the pivot rows' left-looking update
+            // (concurrent with the A00 LU) and LU-4 with its operand copies
+            // (concurrent with LU-3); the main stream joins before the slab
+            // update, which reads both solves' operands.
+            CF_CUDA_TRY(cudaEventRecord(ss.swapped, st));
+            CF_CUDA_TRY(cudaStreamWaitEvent(ss.s, ss.swapped, 0));
             if ((rc = launch_a00_lu32(A00, w.ldw, wd, k0, info, st))) return rc;
+            CF_CUDA_TRY(cudaEventRecord(ss.a00_done, st));
             const int below = m - wd, right = n - k0 - wd;
             const int off = k0 - J0, nout = n - JE;
             // The part of the new pivot rows right of the slab has not yet
             // received this slab's earlier steps (they are deferred for every
             // row still below, and a pivot row may have come from anywhere
             // below): apply them now, A[k0:k0+wd, JE:] -= L[k0:k0+wd, J0:k0]
-            // U[J0:k0, JE:] (left-looking, K = off).
+            // U[J0:k0, JE:] (left-looking, K = off; operand in Lb, which is
+            // free until the slab's deferred update).
             if (off > 0 && nout > 0) {
                 const int Kp = (off + 63) / 64 * 64;
                 float *Cp = W + k0 + JE * ld;
                 if (!split) {
-                    if ((rc = cvt_rows<LP>(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Ab, Kp, st))) return rc;
-                    if ((rc = launch_schur_tc(wd, nout, Kp, w.Ab, Kp, w.Ub, Vpad, Cp, w.ldw, bf16, false, st, 0)))
+                    if ((rc = cvt_rows<LP>(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Lb, Kp, ss.s))) return rc;
+                    if ((rc = launch_schur_tc(wd, nout, Kp, w.Lb, Kp, w.Ub, Vpad, Cp, w.ldw, bf16, false, ss.s, 0)))
                         return rc;
                 } else {
                     // segments (hi, hi, lo) x (hi, lo, hi): three K = off products
-                    if ((rc = cvt_rows_split(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Ab, 3 * Kp, Kp, 0, st)))
+                    if ((rc = cvt_rows_split(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Lb, 3 * Kp, Kp, 0, ss.s)))
                         return rc;
                     for (int sg = 0; sg < 3; ++sg)
-                        if ((rc = launch_schur_tc(wd, nout, Kp, (const __nv_bfloat16 *)w.Ab + (size_t)sg * Kp, 3 * Kp,
+                        if ((rc = launch_schur_tc(wd, nout, Kp, (const __nv_bfloat16 *)w.Lb + (size_t)sg * Kp, 3 * Kp,
                                                   (const __nv_bfloat16 *)w.Ub + (size_t)sg * Vpad, 3 * Vpad, Cp,
-                                                  w.ldw, true, false, st, 0)))
+                                                  w.ldw, true, false, ss.s, 0)))
                             return rc;
                 }
             }
-            // LU-3 / LU-4; they also write the K-major low-precision operands
-            // of the updates inside the slab (split form: converted after).
-            if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, false,
-                                         split ? nullptr : (LP *)w.Ab, kMaxV, kMaxV, nullptr, st)))
-                return rc;
+            // LU-4 (side) after the A00 LU; it also writes the K-major
+            // low-precision operand of the updates inside the slab (split
+            // form: converted after), and the U rows of this step right of
+            // the slab go to the K-major operand of the slab's deferred update
+            // (K rows off .. off + wd, zeros up to the next multiple of 64).
+            CF_CUDA_TRY(cudaStreamWaitEvent(ss.s, ss.a00_done, 0));
             if ((rc = launch_ltrsm32<LP>(A00 + wd * ld, w.ldw, wd, right, A00, w.ldw, split ? nullptr : (LP *)w.Bb,
-                                         kMaxV, kMaxV, st)))
+                                         kMaxV, kMaxV, ss.s)))
                 return rc;
-            if (split) {
-                if ((rc = cvt_rows_split(below, wd, kMaxV, A00 + wd, w.ldw, w.Ab, 3 * kMaxV, kMaxV, 0, st))) return rc;
-                if ((rc = cvt_cols_split(wd, right, kMaxV, A00 + wd * ld, w.ldw, w.Bb, 3 * kMaxV, kMaxV, 1, st)))
-                    return rc;
-            }
-            // U rows of this step right of the slab -> K-major operand of the
-            // slab's deferred update (K rows off .. off + wd, zeros up to the
-            // next multiple of 64)
+            if (split && (rc = cvt_cols_split(wd, right, kMaxV, A00 + wd * ld, w.ldw, w.Bb, 3 * kMaxV, kMaxV, 1,
+                                              ss.s)))
+                return rc;
             if (nout > 0) {
                 const int kp = (off + wd + 63) / 64 * 64 - off;
                 if (!split) {
-                    if ((rc = cvt_cols<LP>(wd, nout, kp, W + k0 + JE * ld, w.ldw, (LP *)w.Ub + off, Vpad, st)))
+                    if ((rc = cvt_cols<LP>(wd, nout, kp, W + k0 + JE * ld, w.ldw, (LP *)w.Ub + off, Vpad, ss.s)))
                         return rc;
                 } else if ((rc = cvt_cols_split(wd, nout, kp, W + k0 + JE * ld, w.ldw,
-                                                (__nv_bfloat16 *)w.Ub + off, 3 * Vpad, Vpad, 1, st))) {
+                                                (__nv_bfloat16 *)w.Ub + off, 3 * Vpad, Vpad, 1, ss.s))) {
                     return rc;
                 }
             }
+            CF_CUDA_TRY(cudaEventRecord(ss.side_done, ss.s));
+            // LU-3 (main)
+            if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, false,
+                                         split ? nullptr : (LP *)w.Ab, kMaxV, kMaxV, nullptr, st)))
+                return rc;
+            if (split && (rc = cvt_rows_split(below, wd, kMaxV, A00 + wd, w.ldw, w.Ab, 3 * kMaxV, kMaxV, 0, st)))
+                return rc;
+            CF_CUDA_TRY(cudaStreamWaitEvent(st, ss.side_done, 0));
             if (below <= 0 || right <= 0) continue;
             // A11 restricted to the slab's remaining columns (every row below)
             const int nslab = JE - (k0 + wd);
@@ -972,10 +1008,13 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
         bool pair = false;
         if (it > 0) {
             // backward error this residual should show: the last one times
-            // the last step's contraction (unknown: above the floor)
-            const double pred = (eta_prev < HUGE_VAL && eta_pp < HUGE_VAL && eta_pp > 0.0)
-                                    ? eta_prev * std::fmin(1.0, eta_prev / eta_pp)
-                                    : HUGE_VAL;
+            // the last step's contraction; before two refinement residuals
+            // exist (the first eta is that of x = 0) a contraction of
+            // kAssumedRate is assumed: erring high costs at most a pair
+            // residual that is then redone in FP64
+            const double rate = (it >= 3 && eta_pp < HUGE_VAL && eta_pp > 0.0) ? std::fmin(1.0, eta_prev / eta_pp)
+                                                                              : kAssumedRate;
+            const double pred = eta_prev < HUGE_VAL ? eta_prev * rate : HUGE_VAL;
             pair = !o.fp64_residual && !(pred < kPairFloor);
             if ((rc = residual(pair))) return rc;
         }

@@ -18,11 +18,11 @@
 //     ah xl + al xh, and Knuth's TwoSum of p into the running pair (hi, lo):
 //     twelve FP32 operations, issued as packed f32x2 instructions over two
 //     right-hand sides.
-//   * Every kChunk terms the pair is added into an FP64 accumulator and
-//     restarted, so the pair's 48 bits are relative to the partial sum of one
-//     chunk, not of the whole row.
+//   * Every kPairChunk (16) terms the pair is added into an FP64 accumulator
+//     and restarted, so the pair's 48 bits are relative to the partial sum of
+//     one chunk, not of the whole row.
 //
-// Accuracy: about 2^-48 sqrt(kChunk) of the largest partial sums of a chunk
+// Accuracy: about 2^-48 sqrt(kPairChunk) of the largest partial sums of a chunk
 // (the running pair's low word collects the rounding errors of the chunk and
 // itself rounds at 2^-24 of its size): from ~1e-16 of ||A||_inf ||x||_inf
 // on dense rows to a few 1e-14 on rows dominated by one term (the FP64 kernel
@@ -37,7 +37,7 @@ namespace cf {
 namespace {
 constexpr int kPairThreads = 256;  // rows per CTA (one per thread)
 constexpr int kTile = 32;          // terms per shared-memory X tile
-constexpr int kPairChunk = 64;     // terms per thread between FP64 restarts (a multiple of kTile)
+constexpr int kPairChunk = 16;     // terms per thread between FP64 restarts (divides kTile)
 constexpr int kPairMaxSplit = 8;   // split of the k range over CTAs (partial sums in the workspace)
 constexpr int kPairGroup = 16;     // right-hand sides per pass
 }  // namespace
@@ -185,6 +185,19 @@ k_residual_pair(int m, int n, int kspan, const double *__restrict__ A, int lda, 
     for (int q = 0; q < NQ; ++q) hi[q] = lo[q] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < NR; ++c) acc[c] = 0.0;
+    // Restart: both words of the running pairs go into the FP64
+    // accumulators.  (An FP32 accumulator for the low words would round at
+    // 2^-24 of the largest chunk's low word on every later add, which on
+    // rows with one dominant term is as large as the error the restarts
+    // avoid.)
+    auto flush = [&]() {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            acc[2 * q] += pair_f2d(hi[q].x) + pair_f2d(lo[q].x);
+            acc[2 * q + 1] += pair_f2d(hi[q].y) + pair_f2d(lo[q].y);
+            hi[q] = lo[q] = make_float2(0.f, 0.f);
+        }
+    };
     double ring[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) ring[g] = (okr && k0 + g < k1) ? __ldg(Ar + (size_t)(k0 + g) * lda) : 0.0;
@@ -195,6 +208,7 @@ k_residual_pair(int m, int n, int kspan, const double *__restrict__ A, int lda, 
         const float4 *xt = xs[t & 1];
         const int base = k0 + t * kTile;
         for (int j = 0; j < kTile; j += G) {
+            if (j > 0 && j % kPairChunk == 0) flush();
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 // terms past k1 have a = 0 and zero-filled x: they add nothing
@@ -212,14 +226,7 @@ k_residual_pair(int m, int n, int kspan, const double *__restrict__ A, int lda, 
                 }
             }
         }
-        if ((t + 1) % (kPairChunk / kTile) == 0) {
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                acc[2 * q] += pair_f2d(hi[q].x) + pair_f2d(lo[q].x);
-                acc[2 * q + 1] += pair_f2d(hi[q].y) + pair_f2d(lo[q].y);
-                hi[q] = lo[q] = make_float2(0.f, 0.f);
-            }
-        }
+        flush();
         __syncthreads();                                    // everyone is done with buffer t & 1
         if (t + 2 < ntile) issue(t + 2);
         pair_cp_commit();
@@ -328,7 +335,7 @@ int launch_group(int m, int n, int nc, const double *A, int lda, const unsigned 
     CF_LAUNCH_CHECK();
     const int rb = ceil_div(m, kPairThreads);
     const int ks = pick_split(rb, n, sm_count_pair() * resident_ctas<NR>());
-    const int kspan = ceil_div(ceil_div(n, ks), kPairChunk) * kPairChunk;
+    const int kspan = ceil_div(ceil_div(n, ks), kTile) * kTile;
     dim3 grid(rb, ks);
     k_residual_pair<NR><<<grid, kPairThreads, 0, st>>>(m, n, kspan, A, lda, amax,
                                                           reinterpret_cast<const float4 *>(Xs), sx, B, ldb, R, ldr,

@@ -30,8 +30,8 @@ struct T2Smem {
     // Column U of the current block of 8: each warp's candidate (its in-block
     // values, key and 1 / its value).
     float4 slot[kBlk][kT2Warps][2];
-    unsigned wkey[kBlk][kT2Warps];
-    float wrinv[kBlk][kT2Warps];
+    alignas(16) unsigned wkey[kBlk][kT2Warps];
+    alignas(16) float wrinv[kBlk][kT2Warps];
     // Block end: pivot U's row at the block start (relative to the block,
     // columns 8 on; stride padded against bank conflicts) and its
     // multipliers with respect to pivots 0..U-1 of the block.
@@ -53,17 +53,48 @@ __device__ __forceinline__ unsigned key32u(float a, bool used) {
     return used ? 0u : ((x != x) ? 1u : __float_as_uint(x) + 2u);
 }
 
+// Fast reciprocal (MUFU, relative error ~2^-23): the multipliers only steer
+// the selection, whose factors are recomputed from the original rows.
+__device__ __forceinline__ float rcp_fast(float x) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The largest of eight warp keys (smallest index on ties) and the reciprocal
+// published with it, from four broadcast loads and a three-level comparison
+// tree in registers.
+__device__ __forceinline__ int warp_argmax8(const unsigned (&wk)[kT2Warps], const float (&wr)[kT2Warps], float &rinv) {
+    const uint4 k0 = *reinterpret_cast<const uint4 *>(&wk[0]);
+    const uint4 k1 = *reinterpret_cast<const uint4 *>(&wk[4]);
+    const float4 r0 = *reinterpret_cast<const float4 *>(&wr[0]);
+    const float4 r1 = *reinterpret_cast<const float4 *>(&wr[4]);
+    const bool c01 = k0.y > k0.x, c23 = k0.w > k0.z, c45 = k1.y > k1.x, c67 = k1.w > k1.z;
+    const unsigned a01 = c01 ? k0.y : k0.x, a23 = c23 ? k0.w : k0.z;
+    const unsigned a45 = c45 ? k1.y : k1.x, a67 = c67 ? k1.w : k1.z;
+    const float f01 = c01 ? r0.y : r0.x, f23 = c23 ? r0.w : r0.z, f45 = c45 ? r1.y : r1.x, f67 = c67 ? r1.w : r1.z;
+    const int i01 = c01 ? 1 : 0, i23 = c23 ? 3 : 2, i45 = c45 ? 5 : 4, i67 = c67 ? 7 : 6;
+    const bool d0 = a23 > a01, d1 = a67 > a45;
+    const unsigned b0 = d0 ? a23 : a01, b1 = d1 ? a67 : a45;
+    const float g0 = d0 ? f23 : f01, g1 = d1 ? f67 : f45;
+    const int j0 = d0 ? i23 : i01, j1 = d1 ? i67 : i45;
+    const bool e = b1 > b0;
+    rinv = e ? g1 : g0;
+    return e ? j1 : j0;
+}
+
 // Masked partial-pivoting selection on the rows held by this CTA's threads
 // (thread r holds stacked row r if r < s.nrows).  s.order[0..npiv) = stacked
 // indices of the pivots.  Blocked by 8 columns (a right-looking blocked GEPP
 // whose trailing update is deferred to the block end):
 //   column U of the block: warp maximum of the keys (redux.sync) and its
 //   smallest lane (ballot); that lane publishes its 8 in-block values, key
-//   and 1 / value in its warp's slot; barrier; every warp takes the maximum
-//   of the eight warp keys the same way (lane q reads warp q's key), so ties
-//   go to the smallest warp, then the smallest lane: the smallest stacked
-//   row; every remaining row takes l_U = a * (1 / pivot) and updates only its
-//   in-block columns.  One barrier and 32 bytes per candidate per column.
+//   and 1 / value in its warp's slot; barrier; every thread takes the
+//   largest of the eight warp keys (smallest warp on ties; within the warp
+//   the smallest lane won), so ties go to the smallest stacked row; every remaining row takes l_U = a * (1 / pivot) and updates only its
+//   in-block columns.  One barrier and 32 bytes per candidate per column;
+//   1 / value is the MUFU approximation (the multipliers only steer the
+//   selection).
 //   block end (if pivots remain): the eight pivots publish the rest of their
 //   rows as they were at the block start, â_U, and their multipliers L with
 //   respect to the block's earlier pivots; barrier; every remaining row
@@ -89,21 +120,17 @@ struct TournBlockStep {
             s.slot[U][warp][0] = make_float4(a[0].x, a[0].y, a[1].x, a[1].y);
             s.slot[U][warp][1] = make_float4(a[2].x, a[2].y, a[3].x, a[3].y);
             s.wkey[U][warp] = m;
-            s.wrinv[U][warp] = aj != 0.f ? __frcp_rn(aj) : 0.f;   // zero pivot: no elimination
+            s.wrinv[U][warp] = aj != 0.f ? rcp_fast(aj) : 0.f;   // zero pivot: no elimination
         }
         __syncthreads();
-        const unsigned kk = s.wkey[U][lane & (kT2Warps - 1)];
-        const unsigned gm = __reduce_max_sync(0xffffffffu, kk);
-        const int wb = __ffs(__ballot_sync(0xffffffffu, kk == gm)) - 1;
+        float ri;
+        const int wb = warp_argmax8(s.wkey[U], s.wrinv[U], ri);
         if (warp == wb && lane == wl) {
             s.order[j] = r;
             used = true;
             pidx = U;
-#pragma unroll
-            for (int t = 0; t < U; ++t) s.lmat[U][t] = lb[t];
         }
         if (!used) {
-            const float ri = s.wrinv[U][wb];
             const float l = ri != 0.f ? aj * ri : 0.f;
             lb[U] = l;
             if (ri != 0.f) {
@@ -120,6 +147,9 @@ struct TournBlockStep {
     __device__ __forceinline__ void block_end(int j0) {
         const int lim = w - j0;
         if (pidx >= 0) {
+#pragma unroll
+            for (int t = 0; t < kBlk - 1; ++t)
+                if (t < pidx) s.lmat[pidx][t] = lb[t];
             float4 *dst = s.prow[pidx];
 #pragma unroll
             for (int c = 0; c < 4; ++c)
@@ -139,24 +169,22 @@ struct TournBlockStep {
                 for (int u2 = u + 1; u2 < kBlk; ++u2) t = fmaf(-c[u2], s.lmat[u2][u], t);
                 c[u] = t;
             }
+            // pivot by pivot, so consecutive FMAs on one element are a row apart
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch)
-                if (ch * 32 < lim) {
+            for (int u = 0; u < kBlk; ++u) {
+                const float2 nc = make_float2(-c[u], -c[u]);
 #pragma unroll
-                    for (int q = ch * 8; q < ch * 8 + 8; ++q) {
-                        if (q < 2) continue;
-                        float2 x0 = a[2 * q], x1 = a[2 * q + 1];
+                for (int ch = 0; ch < 4; ++ch)
+                    if (ch * 32 < lim) {
 #pragma unroll
-                        for (int u = 0; u < kBlk; ++u) {
+                        for (int q = ch * 8; q < ch * 8 + 8; ++q) {
+                            if (q < 2) continue;
                             const float4 p = s.prow[u][q];
-                            const float2 nc = make_float2(-c[u], -c[u]);
-                            x0 = __ffma2_rn(nc, make_float2(p.x, p.y), x0);
-                            x1 = __ffma2_rn(nc, make_float2(p.z, p.w), x1);
+                            a[2 * q] = __ffma2_rn(nc, make_float2(p.x, p.y), a[2 * q]);
+                            a[2 * q + 1] = __ffma2_rn(nc, make_float2(p.z, p.w), a[2 * q + 1]);
                         }
-                        a[2 * q] = x0;
-                        a[2 * q + 1] = x1;
                     }
-                }
+            }
         }
 #pragma unroll
         for (int u = 0; u < kBlk; ++u) lb[u] = 0.f;
