@@ -378,44 +378,60 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     eta_ch = _eta(A_ch, X2, B_ch)
     ok = (eta_lu <= TOL) and (eta_ch <= TOL) and st1 == cf.CF_OK and st2 == cf.CF_OK
 
-    # ---- dominant kernel and its roofline (device time measured inside the steps)
-    res_ms = sum(s["residual_ms"] for s in stats_lu + stats_ch)
-    res_n = sum(s["residual_launches"] for s in stats_lu + stats_ch)
-    res_fl = sum(2.0 * n * n * k * s["residual_launches"] for s, k in
-                 [(s, 16) for s in stats_lu] + [(s, 8) for s in stats_ch])
-    upd_ms = sum(s["update_ms"] for s in stats_lu + stats_ch)
-    upd_n = sum(s["update_launches"] for s in stats_lu + stats_ch)
-    upd_fl = sum(s["update_flops"] for s in stats_lu + stats_ch)
+    # ---- per-kernel device time inside the timed steps (CUDA events on the
+    # solver's stream around every launch of these kernels), and the roofline
+    # of the one that takes the most time
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    if res_ms >= upd_ms and res_n > 0:
-        ach = (res_fl / res_n) / (res_ms / res_n * 1e-3) / 1e12
-        # DRAM bytes per launch from one ncu capture at N = 8192, 16 RHS
-        # (profiles/k_residual_f64_n8192.md: 539.1 MB read + 3.2 MB written),
-        # scaled to this N by the N^2 elements of A each launch streams once
-        traffic = RESID_TRAFFIC_8192 * (n / 8192.0) ** 2
-        roof = {"kernel": "k_residual_f64 (R-1, FP64 r = b - A x)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": traffic, "traffic_note": "bytes per launch, ncu capture at N=8192 scaled by N^2",
-                "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (~2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
-                "launches": res_n, "avg_ms": res_ms / res_n}
-    else:
-        pk = peaks.get("bf16_tflops_sustained") or 1700.0
-        ach = (upd_fl / max(upd_n, 1)) / (upd_ms / max(upd_n, 1) * 1e-3) / 1e12 if upd_n else 0.0
-        roof = {"kernel": "k_schur_tc (LU-5/CH-3, K=V tcgen05 update)", "bound": "tensor", "achieved": ach,
-                "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks
-                else "fallback 1.7 PFLOP/s sustained",
-                "launches": upd_n, "avg_ms": upd_ms / max(upd_n, 1)}
-    kernels = {
-        "residual_f64": {"ms_per_step": res_ms / args.steps, "launches_per_step": res_n / args.steps,
-                         "tflops": (res_fl / (res_ms * 1e-3) / 1e12) if res_ms else None},
-        "schur_tc_KV": {"ms_per_step": upd_ms / args.steps, "launches_per_step": upd_n / args.steps,
-                        "tflops": (upd_fl / (upd_ms * 1e-3) / 1e12) if upd_ms else None},
+    sm_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = 2.0 * 128 * n_sm * sm_mhz * 1e6 / 1e12          # FFMA: 128 lanes/clk/SM
+    allst = [(s, 16) for s in stats_lu] + [(s, 8) for s in stats_ch]
+
+    def kern(ms_key, n_key, flops):
+        ms = sum(s[ms_key] for s, _ in allst)
+        cnt = sum(s[n_key] for s, _ in allst)
+        return ms, cnt, flops
+    res = kern("residual_ms", "residual_launches",
+               sum(2.0 * n * n * k * s["residual_launches"] for s, k in allst))
+    pair = kern("pair_ms", "pair_launches", sum(2.0 * n * n * k * s["pair_launches"] for s, k in allst))
+    upd = kern("update_ms", "update_launches", sum(s["update_flops"] for s, _ in allst))
+    tourn = kern("tourn_ms", "tourn_launches", sum(s["tourn_flops"] for s, _ in allst))
+    bf16_pk = peaks.get("bf16_tflops_sustained") or 1700.0
+    cand = {
+        "tourn32": (tourn, "k_tourn32 (LU-1, FP32 tournament pivoting; latency-bound: one barrier per column "
+                           "per tree level)", "alu", fp32_peak,
+                    "FP32 FMA nominal: 128 lanes/clk/SM x %d SMs x %.0f MHz x 2 flops" % (n_sm, sm_mhz),
+                    # ncu at N = 8192 (profiles/k_tourn32_n8192.md): DRAM read = the panel's bytes
+                    sum(4.0 * 128 * (n - 128 * i) for i in range(n // 128)) / (n // 128)),
+        "residual_f64": (res, "k_residual_f64 (R-1, FP64 r = b - A x)", "alu", FP64_PEAK_TFLOPS,
+                         "GB300 FP64 nominal 1.25 TFLOP/s (~2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
+                         RESID_TRAFFIC_8192 * (n / 8192.0) ** 2),
+        "residual_pair": (pair, "k_residual_pair (R-1 in FP32 pair arithmetic)", "alu", fp32_peak / 12.0,
+                          "FP32 nominal / 12 (12 FP32 operations per term and right-hand side, 2 flops)",
+                          None),
+        "schur_tc_KV": (upd, "k_schur_tc (LU-5/CH-3, K=V tcgen05 update)", "tensor", bf16_pk,
+                        "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks
+                        else "fallback 1.7 PFLOP/s sustained", None),
     }
+    kernels = {}
+    for name, ((ms, cnt, fl), _, _, pk, _, _) in cand.items():
+        t = (fl / (ms * 1e-3) / 1e12) if ms else None
+        kernels[name] = {"ms_per_step": ms / args.steps, "launches_per_step": cnt / args.steps, "tflops": t,
+                         "frac_of_peak": (t / pk) if t else None}
+    top = max(cand, key=lambda k: cand[k][0][0])
+    (ms, cnt, fl), label, bound, pk, src, traffic = cand[top]
+    ach = (fl / max(cnt, 1)) / (ms / max(cnt, 1) * 1e-3) / 1e12 if cnt else 0.0
+    roof = {"kernel": label, "bound": bound, "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "traffic": traffic, "peak_source": src, "launches": cnt, "avg_ms": ms / max(cnt, 1)}
+    if top == "residual_f64":
+        roof["traffic_note"] = "bytes per launch, ncu capture at N=8192 scaled by N^2"
+    elif top == "tourn32":
+        roof["traffic_note"] = ("bytes per launch: the panel (m x 128 FP32) averaged over the LU's panels; an ncu "
+                                "capture at N=8192 read exactly the panel")
     parts = {
         "lu": {"factor_ms": statistics.median(s["factor_ms"] for s in stats_lu),
                "refine_ms": statistics.median(s["refine_ms"] for s in stats_lu),

@@ -106,6 +106,10 @@ typedef struct {
                                after the requested precision stalled */
     double pair_ms;         /* device time inside the pair-arithmetic products */
     int pair_launches;      /* pair-arithmetic products with A */
+    double tourn_ms;        /* device time inside the FP32 tournaments (LU) */
+    int tourn_launches;
+    double tourn_flops;     /* their elimination flops: per GEPP on r rows x w
+                               columns, sum_j (r-j-1)(2(w-j-1) + 1) */
 } cf_refine_stats;
 
 const char *cf_status_string(int status);

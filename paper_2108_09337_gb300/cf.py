@@ -51,7 +51,8 @@ class RefineStats(ctypes.Structure):
                 ("update_ms", ctypes.c_double), ("update_flops", ctypes.c_double),
                 ("residual_launches", ctypes.c_int), ("update_launches", ctypes.c_int),
                 ("gmres_iterations", ctypes.c_int), ("escalated", ctypes.c_int),
-                ("pair_ms", ctypes.c_double), ("pair_launches", ctypes.c_int)]
+                ("pair_ms", ctypes.c_double), ("pair_launches", ctypes.c_int),
+                ("tourn_ms", ctypes.c_double), ("tourn_launches", ctypes.c_int), ("tourn_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

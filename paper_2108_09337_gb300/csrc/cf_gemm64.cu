@@ -232,34 +232,3 @@ int launch_residual_f64(int m, int n, int nrhs, const double *A, int lda, const 
 }
 
 }  // namespace cf
-
-namespace cf {
-
-// hi = fl32(v), lo = fl32(v - hi) for an m x n FP64 block (optional W copy of
-// hi: the mixed path's working matrix starts as fl32(A)).
-__global__ void k_split_f64(int m, int n, const double *__restrict__ A, int lda, float *__restrict__ hi,
-                            float *__restrict__ lo, int lds, float *__restrict__ W, int ldw, double shift) {
-    const size_t tot = (size_t)m * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % m), j = (int)(e / m);
-        const double a = A[(size_t)i + (size_t)j * lda];
-        const float h = (float)a;
-        if (hi) {
-            hi[(size_t)i + (size_t)j * lds] = h;
-            lo[(size_t)i + (size_t)j * lds] = (float)(a - (double)h);
-        }
-        if (W) W[(size_t)i + (size_t)j * ldw] = (i == j && shift != 0.0) ? (float)(a + shift) : h;
-    }
-}
-
-int launch_split_f64(int m, int n, const double *A, int lda, float *hi, float *lo, int lds, float *W, int ldw,
-                     double shift, cudaStream_t st) {
-    if (m <= 0 || n <= 0) return CF_OK;
-    size_t g = ((size_t)m * n + 255) / 256;
-    if (g > 8192) g = 8192;
-    k_split_f64<<<(int)g, 256, 0, st>>>(m, n, A, lda, hi, lo, lds, W, ldw, shift);
-    CF_LAUNCH_CHECK();
-    return CF_OK;
-}
-
-}  // namespace cf

@@ -100,15 +100,13 @@ int launch_trsv_f64x(int mode, int n, int nrhs, const float *T, int ldt, const d
 int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
                     int *sync_ws, cudaStream_t st);
 int trsv_take_status(cudaStream_t st, int *status);
-// FP64 -> FP32 pair split (and optional FP32 working copy with a diagonal
-// shift).
-int launch_split_f64(int m, int n, const double *A, int lda, float *hi, float *lo, int lds, float *W, int ldw,
-                     double shift, cudaStream_t st);
 // R = B - A X (B null: R = A X) in FP32-pair arithmetic (cf_pair.cu).  amax:
 // device pointer to the FP64 bits of a bound >= max |a_ij| (e.g. ||A||_inf);
 // ws: pair_residual_ws_bytes(m, n) bytes.  The _auto form computes max |a_ij|
 // itself into the workspace.
 size_t pair_residual_ws_bytes(int m, int n);
+// Elimination flops of one FP32 tournament (cf_tourn32.cu).
+double tourn32_flops(int m, int w, int h);
 int launch_residual_pair(int m, int n, int nrhs, const double *A, int lda, const unsigned long long *amax,
                          const double *X, int ldx, const double *B, int ldb, double *R, int ldr, void *ws,
                          cudaStream_t st);

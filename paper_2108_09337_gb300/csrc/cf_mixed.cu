@@ -120,16 +120,54 @@ __global__ void k_iota(int n, int *p) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
 }
 
-// Row sums of |A| (atomically accumulated over column chunks).
-__global__ void __launch_bounds__(256) k_row_abssum(int n, const double *__restrict__ A, int lda, int cols_per_block,
-                                                    double *rowsum) {
-    const int i = blockIdx.x * 256 + threadIdx.x;
-    const int j0 = blockIdx.y * cols_per_block, j1 = min(n, j0 + cols_per_block);
+// One pass over A: W = fl32(A) (+ shift on the diagonal) and, if rowsum is
+// set, rowsum[i] += sum_j |a_ij| over this CTA's columns (atomic over column
+// chunks).  CTA: 512 rows, two per thread (16-byte loads when vec: lda even
+// and A 16-byte aligned; W stores as float2, ldw even) x kCvtCols columns.
+constexpr int kCvtCols = 1024;
+__global__ void __launch_bounds__(256) k_to_f32_rowsum(int n, const double *__restrict__ A, int lda,
+                                                       float *__restrict__ W, int ldw, double shift, double *rowsum,
+                                                       int vec) {
+    const int i = (blockIdx.x * 256 + threadIdx.x) * 2;
     if (i >= n) return;
-    double s = 0.0;
-#pragma unroll 8
-    for (int j = j0; j < j1; ++j) s += fabs(A[(size_t)i + (size_t)j * lda]);
-    atomicAdd(rowsum + i, s);
+    const int j0 = blockIdx.y * kCvtCols, j1 = min(n, j0 + kCvtCols);
+    const bool two = i + 1 < n;
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const double *src = A + (size_t)i + (size_t)j * lda;
+        double a0, a1 = 0.0;
+        if (vec && two) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(src));
+            a0 = v.x;
+            a1 = v.y;
+        } else {
+            a0 = src[0];
+            if (two) a1 = src[1];
+        }
+        s0 += fabs(a0);
+        s1 += fabs(a1);
+        const float w0 = (i == j && shift != 0.0) ? (float)(a0 + shift) : (float)a0;
+        const float w1 = (i + 1 == j && shift != 0.0) ? (float)(a1 + shift) : (float)a1;
+        float *dst = W + (size_t)i + (size_t)j * ldw;
+        if (two) *reinterpret_cast<float2 *>(dst) = make_float2(w0, w1);
+        else dst[0] = w0;
+    }
+    if (rowsum) {
+        atomicAdd(rowsum + i, s0);
+        if (two) atomicAdd(rowsum + i + 1, s1);
+    }
+}
+
+static int launch_to_f32_rowsum(int n, const double *A, int lda, float *W, int ldw, double shift, double *rowsum,
+                                cudaStream_t st) {
+    if (n <= 0) return CF_OK;
+    if (ldw % 2 != 0 || ((uintptr_t)W & 7)) return CF_ERR_UNSUPPORTED;
+    const int vec = (lda % 2 == 0 && ((uintptr_t)A & 15) == 0) ? 1 : 0;
+    dim3 g(ceil_div(n, 512), ceil_div(n, kCvtCols));
+    k_to_f32_rowsum<<<g, 256, 0, st>>>(n, A, lda, W, ldw, shift, rowsum, vec);
+    CF_LAUNCH_CHECK();
+    return CF_OK;
 }
 
 // out[c] = max(out[c], max_i |X[i, c]|); out must start at 0.  Non-negative
@@ -456,7 +494,8 @@ struct SideStream {
 };
 
 template <typename LP>
-static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu, bool split) {
+static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu, bool split,
+                       Timer *tt = nullptr) {
     const bool bf16 = std::is_same<LP, __nv_bfloat16>::value;
     const int v = o.v, V = pick_V(n, o);
     const int Vpad = (V + 63) / 64 * 64;        // K stride (per segment) of the slab's U operand
@@ -477,7 +516,9 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             float *A00 = W + k0 + k0 * ld;
             w.tep.ipiv = w.ipiv;
             w.tep.k0 = k0;
+            if (tt && (rc = tt->begin(st))) return rc;
             if ((rc = launch_tourn32(A00, w.ldw, m, wd, o.leaf_h, o.arity, w.tws, w.tep, st))) return rc;
+            if (tt && (rc = tt->end(st, tourn32_flops(m, wd, o.leaf_h)))) return rc;
             if ((rc = launch_apply_swaps<float>(W, w.ldw, n, k0, w.tep, w.perm, st))) return rc;
             // Fork: the side stream takes the pivot rows' left-looking update
             // (concurrent with the A00 LU) and LU-4 with its operand copies
@@ -879,9 +920,10 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
 
     // ---- factorization (Cholesky retries with a diagonal shift on breakdown)
-    Timer tupd, tres, tpair;
+    Timer tupd, tres, tpair, ttourn;
     double shift = 0.0;
     int hinfo = 0;
+    bool need_rowsum = true;     // row sums of |A| come with the first W = fl32(A)
     // one factorization of fl32(A) into w.W: split = BF16 hi + lo operands
     auto factorize = [&](bool split) -> int {
         const double u_lp = split                                  ? 0x1p-16
@@ -892,16 +934,18 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
         int rc2 = CF_OK;
         for (int attempt = 0; attempt < 4; ++attempt) {
             // W = fl32(A) (+ shift on the diagonal)
-            rc2 = launch_split_f64(n, n, A, lda, nullptr, nullptr, w.ldw, w.W, w.ldw, shift, st);
+            if (need_rowsum) CF_CUDA_TRY(cudaMemsetAsync(w.rowsum, 0, sizeof(double) * (n > 0 ? n : 1), st));
+            rc2 = launch_to_f32_rowsum(n, A, lda, w.W, w.ldw, shift, need_rowsum ? w.rowsum : nullptr, st);
             if (rc2) return rc2;
+            need_rowsum = false;
             CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
             if (split)
-                rc2 = lu ? mixed_getrf<__nv_bfloat16>(n, w, info, o, st, &tupd, true)
+                rc2 = lu ? mixed_getrf<__nv_bfloat16>(n, w, info, o, st, &tupd, true, &ttourn)
                          : mixed_potrf<__nv_bfloat16>(n, w, info, o, st, &tupd, true);
             else if constexpr (std::is_same<LP, fp8_e4m3>::value)
                 rc2 = lu ? CF_ERR_UNSUPPORTED : mixed_potrf_fp8(n, w, info, o, st, &tupd);
             else
-                rc2 = lu ? mixed_getrf<LP>(n, w, info, o, st, &tupd, false)
+                rc2 = lu ? mixed_getrf<LP>(n, w, info, o, st, &tupd, false, &ttourn)
                          : mixed_potrf<LP>(n, w, info, o, st, &tupd, false);
             if (rc2) return rc2;
             CF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -937,13 +981,6 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
 
     // ---- refinement
     const int ldr = n;
-    CF_CUDA_TRY(cudaMemsetAsync(w.rowsum, 0, sizeof(double) * n, st));
-    {
-        const int cpb = 1024;
-        dim3 g(ceil_div(n, 256), ceil_div(n, cpb));
-        k_row_abssum<<<g, 256, 0, st>>>(n, A, lda, cpb, w.rowsum);
-        CF_LAUNCH_CHECK();
-    }
     unsigned long long *nR = w.norms, *nX = w.norms + nrhs, *nB = w.norms + 2 * nrhs, *nA = w.norms + 3 * nrhs;
     CF_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(unsigned long long) * (3 * nrhs + 2), st));
     k_max_reduce<<<grid_for(n), 256, 0, st>>>(n, w.rowsum, nA);
@@ -1116,6 +1153,9 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     S.residual_launches = tres.launches;
     S.pair_ms = tpair.ms();
     S.pair_launches = tpair.launches;
+    S.tourn_ms = ttourn.ms();
+    S.tourn_launches = ttourn.launches;
+    S.tourn_flops = ttourn.flops;
     S.update_ms = tupd.ms();
     S.update_flops = tupd.flops;
     S.update_launches = tupd.launches;

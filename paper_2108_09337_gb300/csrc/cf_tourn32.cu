@@ -16,6 +16,7 @@
 // FP32 with FMA: the mixed path's pivots are reported, not held to bit
 // equality with the FP64 oracle.
 #include <climits>
+#include <vector>
 
 #include "cf_common.cuh"
 #include "cf_kernels.cuh"
@@ -331,6 +332,37 @@ k_tourn32(const float *__restrict__ P, int ldp, TournPlan plan, TournWS ws, Tour
             return;
         }
     }
+}
+
+// Elimination flops of one FP32 tournament (m x w panel, leaves of h rows,
+// binary tree): per GEPP on r rows x w columns, sum_j (r-j-1)(2(w-j-1) + 1)
+// for j < min(r, w); nodes with one child pass their winners through.
+double tourn32_flops(int m, int w, int h) {
+    auto gepp = [w](int r) {
+        double f = 0.0;
+        const int p = r < w ? r : w;
+        for (int j = 0; j < p; ++j) f += (double)(r - j - 1) * (2.0 * (w - j - 1) + 1.0);
+        return f;
+    };
+    if (m <= 0 || w <= 0 || h <= 0) return 0.0;
+    std::vector<int> cnt;
+    double f = 0.0;
+    for (int r0 = 0; r0 < m; r0 += h) {
+        const int r = m - r0 < h ? m - r0 : h;
+        f += gepp(r);
+        cnt.push_back(r < w ? r : w);
+    }
+    while (cnt.size() > 1) {
+        std::vector<int> up;
+        for (size_t i = 0; i < cnt.size(); i += 2) {
+            if (i + 1 == cnt.size()) { up.push_back(cnt[i]); continue; }
+            const int r = cnt[i] + cnt[i + 1];
+            f += gepp(r);
+            up.push_back(r < w ? r : w);
+        }
+        cnt.swap(up);
+    }
+    return f;
 }
 
 int launch_tourn32(const float *P, int ldp, int m, int w, int h, int arity, const TournWS &ws, const TournEpilogue &ep,
