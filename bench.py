@@ -5,13 +5,17 @@ path and the CPU oracle.
 
 One step = cf_gesv_mixed (LU with tournament pivoting, FP16 tensor-core
 Schur updates with FP32 accumulation, FP64 refinement; A = U[-1,1] +
-2 sqrt(N) I, 16 right-hand sides) + cf_posv_mixed (Cholesky, FP16 updates,
-FP64 refinement; A = G G^T / N + alpha I with kappa ~ 1e2, 8 right-hand
-sides).  value = (2N^3/3 + N^3/3) / step time.  A step counts only if every
+2 sqrt(N) I, 16 right-hand sides) + cf_posv_mixed (Cholesky, split-BF16
+updates: BF16 hi + lo operands, three products accumulated in FP32; FP64
+refinement; A = G G^T / N + alpha I with kappa ~ 1e2, 8 right-hand sides).
+Each system takes the update precision with which it is solved fastest
+(measured: FP16 for this LU, split BF16 for this Cholesky, whose 16
+significant bits save two refinement steps; the others run as variants).
+value = (2N^3/3 + N^3/3) / step time.  A step counts only if every
 right-hand side reaches eta <= 1e-14 (checked here with an FP64 residual).
---prec bf16 times the same step with BF16 updates; by default the BF16 and
-split-BF16 solves, the unshifted LU (s = 0) and the N = 65536 Cholesky with
-FP8 updates run once after the timed step ("variants").
+--prec / --chol-prec choose the precisions; by default the other BF16, FP16
+and split-BF16 solves, the unshifted LU (s = 0) and the N = 65536 Cholesky
+with FP8 updates run once after the timed step ("variants").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cf|reference]
 
@@ -48,6 +52,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cf", "reference"], default="cf")
     ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--chol-prec", default="bf16x3", choices=["bf16", "f16", "bf16x3"],
+                    help="update precision of the timed Cholesky solve")
     ap.add_argument("--prec", default="f16", choices=["bf16", "f16", "bf16x3"],
                     help="update precision of the timed step (the other 16-bit one runs once as a variant)")
     ap.add_argument("--leaf-h", type=int, default=256, help="tournament leaf height of the mixed LU")
@@ -208,13 +214,12 @@ def _run_variants(args, n, dev, A_lu, B_lu, A_ch, B_ch):
         del X
 
     lu_fl, ch_fl = 2.0 * n ** 3 / 3.0, n ** 3 / 3.0
-    other = "bf16" if args.prec == "f16" else "f16"
-    rec("lu_%s_n%d" % (other, n), lambda: cf.gesv_mixed(A_lu, B_lu, prec=other, leaf_h=args.leaf_h), A_lu, B_lu,
-        lu_fl)
-    rec("chol_%s_n%d" % (other, n), lambda: cf.posv_mixed(A_ch, B_ch, prec=other), A_ch, B_ch, ch_fl)
-    rec("lu_bf16x3_n%d" % n, lambda: cf.gesv_mixed(A_lu, B_lu, prec="bf16x3", leaf_h=args.leaf_h), A_lu, B_lu,
-        lu_fl)
-    rec("chol_bf16x3_n%d" % n, lambda: cf.posv_mixed(A_ch, B_ch, prec="bf16x3"), A_ch, B_ch, ch_fl)
+    for p in ("bf16", "f16", "bf16x3"):
+        if p != args.prec:
+            rec("lu_%s_n%d" % (p, n), lambda: cf.gesv_mixed(A_lu, B_lu, prec=p, leaf_h=args.leaf_h), A_lu, B_lu,
+                lu_fl)
+        if p != args.chol_prec:
+            rec("chol_%s_n%d" % (p, n), lambda: cf.posv_mixed(A_ch, B_ch, prec=p), A_ch, B_ch, ch_fl)
     A0 = inputs.uniform_pm1_torch(n, seed=0, shift=0.0, device=dev)
     for p in ("bf16x3", "bf16", "f16"):
         rec("lu_s0_%s_n%d" % (p, n), lambda: cf.gesv_mixed(A0, B_lu, prec=p, leaf_h=args.leaf_h), A0, B_lu, lu_fl)
@@ -326,12 +331,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
 
     A_lu, B_lu, A_ch, B_ch, gen_info = _gen_inputs(n, dev)
     ws_lu = torch.empty(cf.gesv_mixed_workspace_size(n, 16, prec, leaf_h=args.leaf_h), dtype=torch.uint8, device=dev)
-    ws_ch = torch.empty(cf.posv_mixed_workspace_size(n, 8, prec), dtype=torch.uint8, device=dev)
+    cprec = args.chol_prec
+    ws_ch = torch.empty(cf.posv_mixed_workspace_size(n, 8, cprec), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
     def step():
         X1, info1, st1, s1 = cf.gesv_mixed(A_lu, B_lu, prec=prec, work=ws_lu, leaf_h=args.leaf_h, tol=SOLVER_TOL)
-        X2, info2, st2, s2 = cf.posv_mixed(A_ch, B_ch, prec=prec, work=ws_ch, tol=SOLVER_TOL)
+        X2, info2, st2, s2 = cf.posv_mixed(A_ch, B_ch, prec=cprec, work=ws_ch, tol=SOLVER_TOL)
         return (X1, st1, s1), (X2, st2, s2)
 
     def barrier():
@@ -501,7 +507,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                 lu_free[slot].record(stream)
                 hX1.copy_(X1_, non_blocking=True)
                 stream.wait_event(ch_in)
-                X2_, _, _, _ = cf.posv_mixed(dA2, dB2, prec=prec, work=ws_ch, tol=SOLVER_TOL)
+                X2_, _, _, _ = cf.posv_mixed(dA2, dB2, prec=cprec, work=ws_ch, tol=SOLVER_TOL)
                 ch_free.record(stream)
                 hX2.copy_(X2_, non_blocking=True)
             stream.wait_stream(side)
@@ -574,11 +580,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     line = {
         "metric": METRIC, "value": value if ok else 0.0, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": prec, "data": "synthetic",
-        "config": {"workload": "mixed LU solve (N=32768, 16 RHS, A=U[-1,1]+2sqrt(N)I) + mixed Cholesky solve "
-                               "(N=32768, 8 RHS, A=GG^T/N+alpha I, kappa~1e2), %s tensor-core updates, FP64 "
-                               "refinement to 1e-14" % prec,
+        "vs_baseline": None, "dtype": prec if prec == cprec else "%s (LU) + %s (Cholesky)" % (prec, cprec),
+        "data": "synthetic",
+        "config": {"workload": "mixed LU solve (N=32768, 16 RHS, A=U[-1,1]+2sqrt(N)I, %s tensor-core updates) + "
+                               "mixed Cholesky solve (N=32768, 8 RHS, A=GG^T/N+alpha I, kappa~1e2, %s tensor-core "
+                               "updates), FP32 accumulation, FP64 refinement to 1e-14" % (prec, cprec),
                    "n": n, "v": 128, "leaf_h": args.leaf_h, "arity": 2, "outer_V": 1024, "factor_prec": prec,
+                   "chol_factor_prec": cprec,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (A is 8.6 GB per matrix)", "inputs": gen_info},
         "converged": ok, "eta": {"lu": eta_lu, "chol": eta_ch},
