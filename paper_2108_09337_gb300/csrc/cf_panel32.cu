@@ -33,30 +33,120 @@ __device__ __forceinline__ __half lp_from<__half>(float x) { return __float2half
 
 // ---------------------------------------------------------------------------
 // A00 = L00 U00, no pivoting, in place (w <= 128).  Thread r owns row r as a
-// pair row (cf_regrow.cuh, packed FMAs).  The live part of the pivot row of
-// step k is published in shared memory (double-buffered).
+// pair row (cf_regrow.cuh, packed FMAs), blocked by 8 columns:
+//   column k = j0 + U: row k publishes its 8 in-block values; barrier; row k
+//   of U inside the block is stored, every row r > k takes l = a / pivot,
+//   stores L(r, k) and updates its in-block columns only;
+//   block end: the 8 pivot rows publish the rest of their rows as they were
+//   at the block start, â_U, and their multipliers L(U, U') (U' < U); barrier;
+//   every row after the block's first applies a -= sum_U c_U â_U with
+//   c^T (I + L) = l^T (its multipliers, zero past its own position for a
+//   pivot row), which equals the 8 rank-1 updates; the pivot rows' finished
+//   U rows go out through shared memory as coalesced column segments.
+// A zero pivot is reported in info and its column is not divided (LAPACK
+// dgetf2); the elimination then proceeds with the undivided column.
 // ---------------------------------------------------------------------------
+struct A00LuSmem {
+    float4 slot[kBlk][2];                 // pivot k's in-block values (relative to the block)
+    float4 prow[kBlk][kMaxV / 4 + 1];     // block end: pivot rows at the block start (padded stride)
+    float4 ufin[kBlk][kMaxV / 4 + 1];     // block end: pivot rows' finished U values
+    float lmat[kBlk][kBlk];
+};
+
 struct LuStep {
-    float4 (&pr)[2][kMaxV / 4];
+    A00LuSmem &s;
     float2 (&a)[kPairs];
+    float (&lb)[kBlk];
     float *A00;
     int lda, w, r, kglob;
     int *info;
     template <int U>
     __device__ __forceinline__ void step(int j0) {
-        const int k = j0 + U, par = k & 1;
-        if (r == k) store_live_pairs<U>(pr[par], a, w - j0);   // row k from column k on, relative to j0
+        const int k = j0 + U;
+        if (r == k) {
+            s.slot[U][0] = make_float4(a[0].x, a[0].y, a[1].x, a[1].y);
+            s.slot[U][1] = make_float4(a[2].x, a[2].y, a[3].x, a[3].y);
+        }
         __syncthreads();
-        const float *pf = reinterpret_cast<const float *>(pr[par]);
-        if (r < w - k) A00[(size_t)k + (size_t)(k + r) * lda] = pf[U + r];        // U(k, k+r)
+        const float *pf = reinterpret_cast<const float *>(s.slot[U]);
+        if (r < kBlk - U && k + r < w) A00[(size_t)k + (size_t)(k + r) * lda] = pf[U + r];     // U(k, k + r)
         const float piv = pf[U];
         if (r > k && r < w) {
             const float au = pair_elem<U>(a);
             const float l = (piv != 0.f) ? au / piv : au;
-            A00[(size_t)r + (size_t)k * lda] = l;                                   // L(r, k)
-            rank1_pairs<U>(a, l, pr[par], w - j0);
+            A00[(size_t)r + (size_t)k * lda] = l;                                          // L(r, k)
+            lb[U] = l;
+            const float2 nl = make_float2(-l, -l);
+            const float4 u0 = s.slot[U][0], u1 = s.slot[U][1];
+            if (1 > U) a[0] = __ffma2_rn(nl, make_float2(u0.x, u0.y), a[0]);
+            if (3 > U) a[1] = __ffma2_rn(nl, make_float2(u0.z, u0.w), a[1]);
+            if (5 > U) a[2] = __ffma2_rn(nl, make_float2(u1.x, u1.y), a[2]);
+            if (7 > U) a[3] = __ffma2_rn(nl, make_float2(u1.z, u1.w), a[3]);
         }
         if (r == 0 && piv == 0.f) atomicCAS(info, 0, kglob + k + 1);
+    }
+    __device__ __forceinline__ void block_end(int j0) {
+        const int lim = w - j0;                // live columns relative to the block
+        const int P = r - j0;                  // position of a pivot row in the block
+        const bool pivot_row = P >= 0 && P < kBlk;
+        if (pivot_row) {
+#pragma unroll
+            for (int t = 0; t < kBlk - 1; ++t)
+                if (t < P) s.lmat[P][t] = lb[t];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c * 32 < lim) {
+#pragma unroll
+                    for (int q = c * 8; q < c * 8 + 8; ++q)
+                        if (q >= 2)
+                            s.prow[P][q] = make_float4(a[2 * q].x, a[2 * q].y, a[2 * q + 1].x, a[2 * q + 1].y);
+                }
+        }
+        __syncthreads();
+        if (P > 0 && r < w) {
+            float c[kBlk];
+#pragma unroll
+            for (int u = kBlk - 1; u >= 0; --u) {
+                float t = lb[u];
+#pragma unroll
+                for (int u2 = u + 1; u2 < kBlk; ++u2) t = fmaf(-c[u2], s.lmat[u2][u], t);
+                c[u] = t;
+            }
+#pragma unroll
+            for (int u = 0; u < kBlk; ++u) {
+                const float2 nc = make_float2(-c[u], -c[u]);
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch)
+                    if (ch * 32 < lim) {
+#pragma unroll
+                        for (int q = ch * 8; q < ch * 8 + 8; ++q) {
+                            if (q < 2) continue;
+                            const float4 p = s.prow[u][q];
+                            a[2 * q] = __ffma2_rn(nc, make_float2(p.x, p.y), a[2 * q]);
+                            a[2 * q + 1] = __ffma2_rn(nc, make_float2(p.z, p.w), a[2 * q + 1]);
+                        }
+                    }
+            }
+        }
+        if (pivot_row) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c * 32 < lim) {
+#pragma unroll
+                    for (int q = c * 8; q < c * 8 + 8; ++q)
+                        if (q >= 2)
+                            s.ufin[P][q] = make_float4(a[2 * q].x, a[2 * q].y, a[2 * q + 1].x, a[2 * q + 1].y);
+                }
+        }
+        __syncthreads();
+        const float *uf = reinterpret_cast<const float *>(&s.ufin[0][0]);
+        constexpr int UFS = 4 * (kMaxV / 4 + 1);
+        for (int e = threadIdx.x; e < kBlk * (lim - kBlk); e += blockDim.x) {
+            const int q = e % kBlk, t = kBlk + e / kBlk;          // U(j0 + q, j0 + t)
+            A00[(size_t)(j0 + q) + (size_t)(j0 + t) * lda] = uf[q * UFS + t];
+        }
+#pragma unroll
+        for (int u = 0; u < kBlk; ++u) lb[u] = 0.f;
     }
 };
 
@@ -70,23 +160,48 @@ __device__ __forceinline__ void load_pair_row(float2 (&a)[kPairs], const float *
 }
 
 __global__ void __launch_bounds__(kMaxV, 1) k_a00_lu32(float *A00, int lda, int w, int kglob, int *info) {
-    __shared__ __align__(16) float4 pr[2][kMaxV / 4];
+    __shared__ __align__(16) A00LuSmem s;
     const int r = threadIdx.x;
     float2 a[kPairs];
+    float lb[kBlk];
+#pragma unroll
+    for (int u = 0; u < kBlk; ++u) lb[u] = 0.f;
     load_pair_row(a, A00, lda, r, w);
-    LuStep body{pr, a, A00, lda, w, r, kglob, info};
-    for_blocks_pairs(a, w, w, body);
+    LuStep body{s, a, lb, A00, lda, w, r, kglob, info};
+    for (int j0 = 0; j0 < w; j0 += kBlk) {
+        body.template step<0>(j0);
+        if (j0 + 1 < w) body.template step<1>(j0);
+        if (j0 + 2 < w) body.template step<2>(j0);
+        if (j0 + 3 < w) body.template step<3>(j0);
+        if (j0 + 4 < w) body.template step<4>(j0);
+        if (j0 + 5 < w) body.template step<5>(j0);
+        if (j0 + 6 < w) body.template step<6>(j0);
+        if (j0 + 7 < w) body.template step<7>(j0);
+        if (j0 + kBlk >= w) break;
+        body.block_end(j0);
+        shift_pairs(a, w - j0 - kBlk);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// A00 = L00 L00^T (lower), in place.  Thread r owns row r (pair row); before
-// each barrier every live row publishes its current column entry, so after
-// it each thread has the whole column k of the Schur complement: one barrier
-// per column.  Stops at the first pivot that is not positive (info).
+// A00 = L00 L00^T (lower), in place.  Thread r owns row r (pair row), blocked
+// by 8 columns: for column k = j0 + U every live row r >= k publishes its
+// entry a(r, k) (the column k of the Schur complement, kept for the block);
+// barrier; L(k, k) = sqrt(a(k, k)), every row r > k stores L(r, k) and
+// updates its in-block columns; at the block end every row below the block
+// applies the rank-8 update a(r, t) -= sum_U L(r, U) L(t, U) for the columns
+// t past the block (L(t, U) = the published a(t, U) / L(U, U)), with no
+// barrier (the column buffers alternate between blocks).  Stops at the first
+// pivot that is not positive (info).
 // ---------------------------------------------------------------------------
+struct A00CholSmem {
+    float4 col[2][kBlk][kMaxV / 4 + 1];   // [block parity][U][relative row]
+};
+
 struct CholStep {
-    float4 (&col)[2][kMaxV / 4 + 1];
+    A00CholSmem &s;
     float2 (&a)[kPairs];
+    float (&lb)[kBlk];                    // L(r, U) / L(U, U)
     float *A00;
     int lda, w, r, kglob;
     int *info;
@@ -94,8 +209,8 @@ struct CholStep {
     template <int U>
     __device__ __forceinline__ void step(int j0) {
         if (failed) return;                          // uniform
-        const int k = j0 + U, par = k & 1;
-        float *cf = reinterpret_cast<float *>(col[par]);
+        const int k = j0 + U, bp = (j0 / kBlk) & 1;
+        float *cf = reinterpret_cast<float *>(s.col[bp][U]);
         const float au = pair_elem<U>(a);
         if (r >= k && r < w) cf[r - j0] = au;        // column k by relative row
         __syncthreads();
@@ -110,20 +225,66 @@ struct CholStep {
         if (r > k && r < w) {
             const float l = au / lkk;
             A00[(size_t)r + (size_t)k * lda] = l;                               // L(r, k)
-            // a(r, j0+t) -= L(r,k) L(j0+t,k) = (l / lkk) col[t], for j0+t <= r
-            rank1_pairs<U>(a, l / lkk, col[par], r - j0 + 1);
+            // a(r, j0+t) -= L(r,k) L(j0+t,k) = (l / lkk) col[t]
+            const float cl = l / lkk;
+            lb[U] = cl;
+            const float2 nl = make_float2(-cl, -cl);
+            const float4 u0 = s.col[bp][U][0], u1 = s.col[bp][U][1];
+            if (1 > U) a[0] = __ffma2_rn(nl, make_float2(u0.x, u0.y), a[0]);
+            if (3 > U) a[1] = __ffma2_rn(nl, make_float2(u0.z, u0.w), a[1]);
+            if (5 > U) a[2] = __ffma2_rn(nl, make_float2(u1.x, u1.y), a[2]);
+            if (7 > U) a[3] = __ffma2_rn(nl, make_float2(u1.z, u1.w), a[3]);
         }
+    }
+    __device__ __forceinline__ void block_end(int j0) {
+        if (failed) return;
+        const int bp = (j0 / kBlk) & 1;
+        const int lim = r - j0 + 1;                  // columns up to the diagonal
+        if (r >= j0 + kBlk && r < w) {
+#pragma unroll
+            for (int u = 0; u < kBlk; ++u) {
+                const float2 nc = make_float2(-lb[u], -lb[u]);
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch)
+                    if (ch * 32 < lim) {
+#pragma unroll
+                        for (int q = ch * 8; q < ch * 8 + 8; ++q) {
+                            if (q < 2) continue;
+                            const float4 p = s.col[bp][u][q];
+                            a[2 * q] = __ffma2_rn(nc, make_float2(p.x, p.y), a[2 * q]);
+                            a[2 * q + 1] = __ffma2_rn(nc, make_float2(p.z, p.w), a[2 * q + 1]);
+                        }
+                    }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBlk; ++u) lb[u] = 0.f;
     }
 };
 
 __global__ void __launch_bounds__(kMaxV, 1) k_a00_chol32(float *A00, int lda, int w, int kglob, int *info) {
     if (*info != 0) return;
-    __shared__ __align__(16) float4 col[2][kMaxV / 4 + 1];
+    __shared__ __align__(16) A00CholSmem s;
     const int r = threadIdx.x;
     float2 a[kPairs];
+    float lb[kBlk];
+#pragma unroll
+    for (int u = 0; u < kBlk; ++u) lb[u] = 0.f;
     load_pair_row(a, A00, lda, r, w);
-    CholStep body{col, a, A00, lda, w, r, kglob, info, false};
-    for_blocks_pairs(a, w, w, body);
+    CholStep body{s, a, lb, A00, lda, w, r, kglob, info, false};
+    for (int j0 = 0; j0 < w; j0 += kBlk) {
+        body.template step<0>(j0);
+        if (j0 + 1 < w) body.template step<1>(j0);
+        if (j0 + 2 < w) body.template step<2>(j0);
+        if (j0 + 3 < w) body.template step<3>(j0);
+        if (j0 + 4 < w) body.template step<4>(j0);
+        if (j0 + 5 < w) body.template step<5>(j0);
+        if (j0 + 6 < w) body.template step<6>(j0);
+        if (j0 + 7 < w) body.template step<7>(j0);
+        if (j0 + kBlk >= w) break;
+        body.block_end(j0);
+        shift_pairs(a, w - j0 - kBlk);
+    }
 }
 
 // Packs 8 consecutive values as low-precision and stores them as one 16-byte
