@@ -368,12 +368,33 @@ k_rtrsm32(float *X, int ldx, int rows, int w, const float *__restrict__ M00, int
     __shared__ float rinv[kMaxV];
     const int tid = threadIdx.x;
     Ms[kMaxV * kMaxV + tid] = 0.f;
-    for (int e = tid; e < kMaxV * kMaxV; e += kMaxV) {
-        const int i = e % kMaxV, c = e / kMaxV;          // stored element (i, c)
-        float v = 0.f;
-        if (i < w && c < w) v = M00[(size_t)i + (size_t)c * ldm];
-        if (!trans_lower) Ms[i * kMaxV + c] = (i <= c) ? v : 0.f;              // U(i, c)
-        else Ms[c * kMaxV + i] = (i >= c) ? v : 0.f;                            // M(c, i) = L(i, c)
+    // Staged 16 loads at a time (the triangle is L2-resident; one load per
+    // iteration left its latency exposed 128 times), with shared-memory stores
+    // along rows of Ms: for U00 a thread takes a column c (strided reads,
+    // conflict-free stores), for L00^T a row i of L (coalesced reads).
+    constexpr int kStage = 16;
+    if (!trans_lower) {
+        for (int i0 = 0; i0 < kMaxV; i0 += kStage) {
+            float v[kStage];
+#pragma unroll
+            for (int u = 0; u < kStage; ++u) {
+                const int i = i0 + u;
+                v[u] = (i < w && tid < w && i <= tid) ? M00[(size_t)i + (size_t)tid * ldm] : 0.f;   // U(i, c)
+            }
+#pragma unroll
+            for (int u = 0; u < kStage; ++u) Ms[(i0 + u) * kMaxV + tid] = v[u];
+        }
+    } else {
+        for (int c0 = 0; c0 < kMaxV; c0 += kStage) {
+            float v[kStage];
+#pragma unroll
+            for (int u = 0; u < kStage; ++u) {
+                const int c = c0 + u;
+                v[u] = (tid < w && c < w && tid >= c) ? M00[(size_t)tid + (size_t)c * ldm] : 0.f;   // L(i, c)
+            }
+#pragma unroll
+            for (int u = 0; u < kStage; ++u) Ms[(c0 + u) * kMaxV + tid] = v[u];                // M(c, i)
+        }
     }
     __syncthreads();
     if (tid < w) {
@@ -423,9 +444,15 @@ k_ltrsm32(float *X, int ldx, int w, int cols, const float *__restrict__ L00, int
     float *Ls = smem;                                // [kMaxV + 1][kMaxV]: Ls[k][i] = L(i, k), zero padding row
     const int tid = threadIdx.x;
     Ls[kMaxV * kMaxV + tid] = 0.f;
-    for (int e = tid; e < kMaxV * kMaxV; e += kMaxV) {
-        const int k = e / kMaxV, i = e % kMaxV;
-        Ls[e] = (k < w && i > k && i < w) ? L00[(size_t)i + (size_t)k * ldl] : 0.f;
+    for (int k0 = 0; k0 < kMaxV; k0 += 16) {         // 16 loads in flight per thread
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int k = k0 + u;
+            v[u] = (k < w && tid > k && tid < w) ? L00[(size_t)tid + (size_t)k * ldl] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) Ls[(k0 + u) * kMaxV + tid] = v[u];
     }
     const int c0 = blockIdx.x * kMaxV;
     const int nc = min(kMaxV, cols - c0);
