@@ -18,11 +18,11 @@
 //     ah xl + al xh, and Knuth's TwoSum of p into the running pair (hi, lo):
 //     twelve FP32 operations, issued as packed f32x2 instructions over two
 //     right-hand sides.
-//   * Every kPairChunk (16) terms the pair is added into an FP64 accumulator
+//   * Every kTile (16) terms the pair is added into an FP64 accumulator
 //     and restarted, so the pair's 48 bits are relative to the partial sum of
 //     one chunk, not of the whole row.
 //
-// Accuracy: about 2^-48 sqrt(kPairChunk) of the largest partial sums of a chunk
+// Accuracy: about 2^-48 sqrt(kTile) of the largest partial sums of a chunk
 // (the running pair's low word collects the rounding errors of the chunk and
 // itself rounds at 2^-24 of its size): from ~1e-16 of ||A||_inf ||x||_inf
 // on dense rows to a few 1e-14 on rows dominated by one term (the FP64 kernel
@@ -36,8 +36,8 @@ namespace cf {
 
 namespace {
 constexpr int kPairThreads = 256;  // rows per CTA (one per thread)
-constexpr int kTile = 32;          // terms per shared-memory X tile
-constexpr int kPairChunk = 16;     // terms per thread between FP64 restarts (divides kTile)
+constexpr int kTile = 16;          // terms per stage, and between FP64 restarts
+constexpr int kStages = 3;         // stages in shared memory
 constexpr int kPairMaxSplit = 8;   // split of the k range over CTAs (partial sums in the workspace)
 constexpr int kPairGroup = 16;     // right-hand sides per pass
 }  // namespace
@@ -143,11 +143,25 @@ __device__ __forceinline__ void pair_cp_commit() { asm volatile("cp.async.commit
 template <int N>
 __device__ __forceinline__ void pair_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+__device__ __forceinline__ void pair_cp_async8(void *dst, const void *src, unsigned src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+// Shared memory of k_residual_pair<NR>: kStages stages of kTile terms, the A
+// elements of the CTA's 256 rows and the split X values.
+template <int NR>
+constexpr size_t pair_smem_bytes() {
+    return (size_t)kStages * kTile * kPairThreads * sizeof(double) + (size_t)kStages * kTile * (NR / 2) * 16;
+}
+
 // Partial sums of A X over the k range of blockIdx.y for 256 rows (one per
-// thread) x NR right-hand sides.  All warps walk the same k sequence: the X
-// values of kTile terms are staged in shared memory (double-buffered,
-// cp.async) and read as broadcasts; each thread's A elements are loaded G
-// terms ahead (one coalesced 256-byte column segment per warp and term).
+// thread) x NR right-hand sides.  All warps walk the same k sequence in
+// stages of kTile terms: the stage's A elements (one 8-byte copy per thread
+// and term: coalesced 2 KB column segments) and split X values go to shared
+// memory by cp.async, kStages - 1 stages ahead of the one being summed, so
+// that ~100 KB per SM are in flight without holding registers.
 // P == nullptr: R = B - 2^(ea + sx) S directly (B null: R = A X); else the
 // unscaled partials go to P[ks][c][m].
 template <int NR>
@@ -156,28 +170,38 @@ k_residual_pair(int m, int n, int kspan, const double *__restrict__ A, int lda, 
                 const float4 *__restrict__ Xs, const int *__restrict__ sx, const double *B, int ldb, double *R,
                 int ldr, double *P) {
     constexpr int NQ = NR / 2;
-    constexpr int TILE = kTile * NQ;                        // float4 per X tile
-    constexpr int G = NR >= 16 ? 2 : 4;
-    __shared__ __align__(16) float4 xs[2][TILE];
+    constexpr int XT = kTile * NQ;                          // float4 per X stage
+    extern __shared__ __align__(16) unsigned char pair_smem[];
+    double *as = reinterpret_cast<double *>(pair_smem);     // [kStages][kTile][kPairThreads]
+    float4 *xs = reinterpret_cast<float4 *>(as + (size_t)kStages * kTile * kPairThreads);   // [kStages][XT]
     const int row = blockIdx.x * kPairThreads + threadIdx.x;
     const bool okr = row < m;
     const int k0 = blockIdx.y * kspan, k1 = min(n, k0 + kspan);
     const int ntile = k1 > k0 ? (k1 - k0 + kTile - 1) / kTile : 0;
     const int ea = pair_scale_exp(*amax);
-    const double *Ar = A + (okr ? row : 0);
 
+    // stage t -> buffer t % kStages; rows past m and terms past k1 are zero
+    // (zero-filled copies: a = 0 and x = 0 add nothing)
     auto issue = [&](int t) {
-        const int base = k0 + t * kTile;
-        float4 *dst = xs[t & 1];
-        for (int i = threadIdx.x; i < TILE; i += kPairThreads) {
-            if (base + i / NQ < k1) pair_cp_async16(dst + i, Xs + (size_t)base * NQ + i);
-            else dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int base = k0 + t * kTile, b = t % kStages;
+        double *ad = as + (size_t)b * kTile * kPairThreads + threadIdx.x;
+#pragma unroll
+        for (int tt = 0; tt < kTile; ++tt) {
+            const bool ok = okr && base + tt < k1;
+            const double *src = ok ? A + (size_t)row + (size_t)(base + tt) * lda : A;
+            pair_cp_async8(ad + tt * kPairThreads, src, ok ? 8u : 0u);
+        }
+        float4 *xd = xs + (size_t)b * XT;
+        for (int i = threadIdx.x; i < XT; i += kPairThreads) {
+            if (base + i / NQ < k1) pair_cp_async16(xd + i, Xs + (size_t)base * NQ + i);
+            else xd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
-    if (ntile > 0) issue(0);
-    pair_cp_commit();
-    if (ntile > 1) issue(1);
-    pair_cp_commit();
+#pragma unroll
+    for (int t = 0; t < kStages - 1; ++t) {
+        if (t < ntile) issue(t);
+        pair_cp_commit();
+    }
 
     float2 hi[NQ], lo[NQ];
     double acc[NR];
@@ -198,38 +222,27 @@ k_residual_pair(int m, int n, int kspan, const double *__restrict__ A, int lda, 
             hi[q] = lo[q] = make_float2(0.f, 0.f);
         }
     };
-    double ring[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) ring[g] = (okr && k0 + g < k1) ? __ldg(Ar + (size_t)(k0 + g) * lda) : 0.0;
 
     for (int t = 0; t < ntile; ++t) {
-        pair_cp_wait<1>();                                  // tile t has landed
-        __syncthreads();
-        const float4 *xt = xs[t & 1];
-        const int base = k0 + t * kTile;
-        for (int j = 0; j < kTile; j += G) {
-            if (j > 0 && j % kPairChunk == 0) flush();
+        pair_cp_wait<kStages - 2>();                        // stage t has landed
+        __syncthreads();                                    // ... for every thread; stage t - 1 is free
+        if (t + kStages - 1 < ntile) issue(t + kStages - 1);
+        pair_cp_commit();
+        const double *at = as + (size_t)(t % kStages) * kTile * kPairThreads + threadIdx.x;
+        const float4 *xt = xs + (size_t)(t % kStages) * XT;
+#pragma unroll 4
+        for (int tt = 0; tt < kTile; ++tt) {
+            float ah, al;
+            pair_split_a(at[tt * kPairThreads], ea, ah, al);
+            const float2 AH = make_float2(ah, ah), AL = make_float2(al, al), NAH = make_float2(-ah, -ah);
+            const float4 *xp = xt + tt * NQ;
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                // terms past k1 have a = 0 and zero-filled x: they add nothing
-                const double a = ring[g];
-                const int pn = base + j + g + G;
-                ring[g] = (okr && pn < k1) ? __ldg(Ar + (size_t)pn * lda) : 0.0;
-                float ah, al;
-                pair_split_a(a, ea, ah, al);
-                const float2 AH = make_float2(ah, ah), AL = make_float2(al, al), NAH = make_float2(-ah, -ah);
-                const float4 *xp = xt + (j + g) * NQ;
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    const float4 xv = xp[q];
-                    pair_term(hi[q], lo[q], AH, AL, NAH, make_float2(xv.x, xv.y), make_float2(xv.z, xv.w));
-                }
+            for (int q = 0; q < NQ; ++q) {
+                const float4 xv = xp[q];
+                pair_term(hi[q], lo[q], AH, AL, NAH, make_float2(xv.x, xv.y), make_float2(xv.z, xv.w));
             }
         }
-        flush();
-        __syncthreads();                                    // everyone is done with buffer t & 1
-        if (t + 2 < ntile) issue(t + 2);
-        pair_cp_commit();
+        flush();                                            // every kTile = 16 terms
     }
     pair_cp_wait<0>();
     if (!okr) return;
@@ -302,7 +315,8 @@ template <int NR>
 int resident_ctas() {
     static int occ = 0;
     if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual_pair<NR>, kPairThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual_pair<NR>, kPairThreads,
+                                                          pair_smem_bytes<NR>()) !=
                 cudaSuccess ||
             occ <= 0)
             occ = 1;
@@ -333,11 +347,17 @@ int launch_group(int m, int n, int nc, const double *A, int lda, const unsigned 
                  cudaStream_t st) {
     k_pair_split_x<NR><<<NR, 256, 0, st>>>(n, nc, X, ldx, Xs, sx);
     CF_LAUNCH_CHECK();
+    static bool attr_set = false;
+    if (!attr_set) {
+        CF_CUDA_TRY(cudaFuncSetAttribute(k_residual_pair<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pair_smem_bytes<NR>()));
+        attr_set = true;
+    }
     const int rb = ceil_div(m, kPairThreads);
     const int ks = pick_split(rb, n, sm_count_pair() * resident_ctas<NR>());
     const int kspan = ceil_div(ceil_div(n, ks), kTile) * kTile;
     dim3 grid(rb, ks);
-    k_residual_pair<NR><<<grid, kPairThreads, 0, st>>>(m, n, kspan, A, lda, amax,
+    k_residual_pair<NR><<<grid, kPairThreads, pair_smem_bytes<NR>(), st>>>(m, n, kspan, A, lda, amax,
                                                           reinterpret_cast<const float4 *>(Xs), sx, B, ldb, R, ldr,
                                                           ks > 1 ? P : nullptr);
     CF_LAUNCH_CHECK();
