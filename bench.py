@@ -585,7 +585,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "config": {"workload": "mixed LU solve (N=32768, 16 RHS, A=U[-1,1]+2sqrt(N)I, %s tensor-core updates) + "
                                "mixed Cholesky solve (N=32768, 8 RHS, A=GG^T/N+alpha I, kappa~1e2, %s tensor-core "
                                "updates), FP32 accumulation, FP64 refinement to 1e-14" % (prec, cprec),
-                   "n": n, "v": 128, "leaf_h": args.leaf_h, "arity": 2, "outer_V": 1024, "factor_prec": prec,
+                   "n": n, "v": 128, "leaf_h": args.leaf_h, "arity": 2, "outer_V": {"lu": 2048, "chol": 1024},
+                   "factor_prec": prec,
                    "chol_factor_prec": cprec,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (A is 8.6 GB per matrix)", "inputs": gen_info},

@@ -64,7 +64,9 @@ typedef struct {
                           routines, 1..256 for the mixed solvers (whose FP32
                           tournament takes arity 2 only) */
     int arity;         /* children per playoff node, 2..4 [2]; the mixed paths use 2 */
-    int outer_V;       /* mixed LU/Cholesky: depth of the deferred update, multiple of v [0 = auto] */
+    int outer_V;       /* mixed LU/Cholesky: depth of the deferred update,
+                          multiple of v [0 = auto: 2048 for LU at n >= 16384,
+                          1024 at n >= 8192, 512 below] */
     int lookahead;     /* cf_getrf: 1 = LU-6 look-ahead (TournPivot of step
                           t+1 on a high-priority stream while the wide update
                           of step t runs on a low-priority one), 0 = one

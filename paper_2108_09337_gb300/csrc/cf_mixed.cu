@@ -327,13 +327,20 @@ struct MixedWS {
     size_t bytes = 0;
 };
 
-static int pick_V(int n, const Opts &o) {
+// Depth V of the slab's deferred K = V update.  Deeper slabs raise the
+// update's arithmetic intensity (its FP32 C is read and written once per
+// slab) and cost more right-looking work inside the slab; measured at
+// N = 32768: V = 2048 runs the LU's update at 1.27 PFLOP/s against 0.76 with
+// V = 1024 (factorization 211 vs 217 ms), while the Cholesky factorization is
+// faster with V = 1024.
+static int pick_V(int n, const Opts &o, bool lu) {
     if (o.outer_V > 0) return o.outer_V;
+    if (lu && n >= 16384) return 2048;
     return n >= 8192 ? 1024 : 512;
 }
 
 static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, MixedWS *w) {
-    const int V = pick_V(n, o);
+    const int V = pick_V(n, o, lu);
     const int Vp = (V + 63) / 64 * 64;
     Carver cv(work);
     w->ldw = (n + 31) / 32 * 32;
@@ -497,7 +504,7 @@ template <typename LP>
 static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu, bool split,
                        Timer *tt = nullptr) {
     const bool bf16 = std::is_same<LP, __nv_bfloat16>::value;
-    const int v = o.v, V = pick_V(n, o);
+    const int v = o.v, V = pick_V(n, o, true);
     const int Vpad = (V + 63) / 64 * 64;        // K stride (per segment) of the slab's U operand
     const int S = split ? 3 : 1;                 // K segments per operand
     const size_t ld = (size_t)w.ldw;
@@ -618,7 +625,7 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
 // Requires V to be a multiple of 128.
 // ---------------------------------------------------------------------------
 static int mixed_potrf_fp8(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu) {
-    const int v = o.v, V = pick_V(n, o);
+    const int v = o.v, V = pick_V(n, o, false);
     if (V % 128 != 0) return CF_ERR_UNSUPPORTED;
     const size_t ld = (size_t)w.ldw;
     float *W = w.W;
@@ -667,7 +674,7 @@ static int mixed_potrf_fp8(int n, MixedWS &w, int *info, const Opts &o, cudaStre
 template <typename LP>
 static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu, bool split) {
     const bool bf16 = std::is_same<LP, __nv_bfloat16>::value;
-    const int v = o.v, V = pick_V(n, o);
+    const int v = o.v, V = pick_V(n, o, false);
     const int S = split ? 3 : 1;
     const size_t ld = (size_t)w.ldw;
     float *W = w.W;
@@ -1207,7 +1214,7 @@ static int mixed_entry(int n, int nrhs, const double *A, int lda, const double *
                                           prec == CF_BF16X3, st);
     if (prec == CF_FP8E4M3) {
         if (lu) return -9;                     // FP8 updates: Cholesky only
-        if (pick_V(n, o) % 128 != 0) return CF_ERR_UNSUPPORTED;
+        if (pick_V(n, o, false) % 128 != 0) return CF_ERR_UNSUPPORTED;
         return mixed_solve<fp8_e4m3>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, false, st);
     }
     return mixed_solve<__half>(n, nrhs, A, lda, B, ldb, X, ldx, info, stats, work, lwork, o, lu, false, st);

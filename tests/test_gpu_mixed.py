@@ -274,3 +274,17 @@ def test_pair_residual_policy(cf, solver):
     Xs = np.linalg.solve(A, B)
     kappa = np.linalg.cond(A, np.inf)
     assert np.abs(out[0] - out[1]).max() / np.abs(Xs).max() <= 8 * kappa * 1e-14
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16x3"])
+def test_gesv_mixed_deep_slab(cf, prec):
+    """Slabs of V = 2048 (the LU default from n = 16384 on) at a size the host
+    check affords: two slabs, the second ragged (4500 = 2048 + 2048 + 404),
+    left-looking pivot-row updates with K up to 1920, split-BF16 operands
+    with three K segments of 2048."""
+    n = 4500
+    A = inputs.uniform_pm1(n, seed=9, shift=2 * np.sqrt(n))
+    B = inputs.rhs_normal(n, 3, seed=10)
+    X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec=prec, outer_V=2048)
+    assert st == cf.CF_OK, stats.as_dict()
+    _check_solution(A, B, X.cpu().numpy())
