@@ -428,6 +428,15 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         t = (fl / (ms * 1e-3) / 1e12) if ms else None
         kernels[name] = {"ms_per_step": ms / args.steps, "launches_per_step": cnt / args.steps, "tflops": t,
                          "frac_of_peak": (t / pk) if t else None}
+    # the K = V updates of each solve: algorithmic rate, and the tensor-pipe
+    # rate (split BF16 runs three products per algorithmic flop)
+    for name, sts, pr in (("schur_tc_KV_lu", stats_lu, prec), ("schur_tc_KV_chol", stats_ch, cprec)):
+        ms = sum(x["update_ms"] for x in sts)
+        fl = sum(x["update_flops"] for x in sts)
+        t = (fl / (ms * 1e-3) / 1e12) if ms else None
+        tt = t * (3.0 if pr == "bf16x3" else 1.0) if t else None
+        kernels[name] = {"ms_per_step": ms / args.steps, "tflops": t, "tensor_tflops": tt,
+                         "tensor_frac_of_sustained_bf16": (tt / bf16_pk) if tt else None, "prec": pr}
     top = max(cand, key=lambda k: cand[k][0][0])
     (ms, cnt, fl), label, bound, pk, src, traffic = cand[top]
     ach = (fl / max(cnt, 1)) / (ms / max(cnt, 1) * 1e-3) / 1e12 if cnt else 0.0
