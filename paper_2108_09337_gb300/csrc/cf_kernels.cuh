@@ -97,7 +97,9 @@ int launch_diag_inverse(int mode, int n, const float *T, int ldt, float *Dinv, c
 int launch_diag_inverse64(int mode, int n, const float *T, int ldt, double *Dinv, cudaStream_t st);
 int launch_trsv_f64x(int mode, int n, int nrhs, const float *T, int ldt, const double *Dinv, double *X, int ldx,
                      int *sync_ws, cudaStream_t st);
-int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
+int launch_neighbor_premul(int mode, int n, const float *T, int ldt, const float *Dinv, float *Gout, cudaStream_t st);
+int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, const float *Gn, float *X,
+                    int ldx,
                     int *sync_ws, cudaStream_t st);
 int trsv_take_status(cudaStream_t st, int *status);
 // R = B - A X (B null: R = A X) in FP32-pair arithmetic (cf_pair.cu).  amax:

@@ -307,7 +307,8 @@ struct MixedWS {
     TournEpilogue tep{};
     double *R = nullptr, *scale = nullptr, *rowsum = nullptr;
     float *Rf = nullptr;
-    float *DinvL = nullptr, *DinvU = nullptr;   // inverses of the 64 x 64 diagonal blocks
+    float *DinvL = nullptr, *DinvU = nullptr;   // inverses of the 128 x 128 diagonal blocks
+    float *G0 = nullptr, *G1 = nullptr;         // neighbour tiles premultiplied by them (first, second solve)
     double *DinvL64 = nullptr, *DinvU64 = nullptr;   // the same in FP64 (GMRES-IR preconditioner)
     int *trsv_sync = nullptr;
     unsigned long long *norms = nullptr;   // [0..nrhs) |R|, [nrhs..2nrhs) |X|, [2nrhs..3nrhs) |B|, [3nrhs] ||A||
@@ -373,6 +374,8 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->Rf = cv.take<float>((size_t)n * nrhs + 1);
     w->DinvL = cv.take<float>(diag_inverse_floats(n));
     w->DinvU = lu ? cv.take<float>(diag_inverse_floats(n)) : nullptr;
+    w->G0 = cv.take<float>(diag_inverse_floats(n));
+    w->G1 = cv.take<float>(diag_inverse_floats(n));
     w->DinvL64 = cv.take<double>(diag_inverse64_elems(n));
     w->DinvU64 = lu ? cv.take<double>(diag_inverse64_elems(n)) : nullptr;
     w->trsv_sync = cv.take<int>(trsv_ws_bytes(n) / sizeof(int) + 1);
@@ -729,8 +732,8 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
 // blocked triangular solves.
 static int solve_f32(int n, int nrhs, const MixedWS &w, bool lu, cudaStream_t st) {
     int rc;
-    if ((rc = launch_trsv_f32(lu ? 0 : 2, n, nrhs, w.W, w.ldw, w.DinvL, w.Rf, n, w.trsv_sync, st))) return rc;
-    return launch_trsv_f32(lu ? 1 : 3, n, nrhs, w.W, w.ldw, lu ? w.DinvU : w.DinvL, w.Rf, n, w.trsv_sync, st);
+    if ((rc = launch_trsv_f32(lu ? 0 : 2, n, nrhs, w.W, w.ldw, w.DinvL, w.G0, w.Rf, n, w.trsv_sync, st))) return rc;
+    return launch_trsv_f32(lu ? 1 : 3, n, nrhs, w.W, w.ldw, lu ? w.DinvU : w.DinvL, w.G1, w.Rf, n, w.trsv_sync, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1003,6 +1006,8 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     auto diag_inverses = [&]() -> int {
         int rc2 = launch_diag_inverse(lu ? 0 : 2, n, w.W, w.ldw, w.DinvL, st);
         if (rc2 == CF_OK && lu) rc2 = launch_diag_inverse(1, n, w.W, w.ldw, w.DinvU, st);
+        if (rc2 == CF_OK) rc2 = launch_neighbor_premul(lu ? 0 : 2, n, w.W, w.ldw, w.DinvL, w.G0, st);
+        if (rc2 == CF_OK) rc2 = launch_neighbor_premul(lu ? 1 : 3, n, w.W, w.ldw, lu ? w.DinvU : w.DinvL, w.G1, st);
         return rc2;
     };
     if (S.info == 0 && (rc = diag_inverses())) return rc;

@@ -7,8 +7,9 @@
 // started earlier and never waits on a later one.  A CTA subtracts the
 // contributions of the finished blocks as their flags appear, applies the
 // precomputed inverse of its diagonal block, publishes its block of the
-// solution and raises its flag.  The factor is read exactly once; the chain
-// of dependent work is one tile product per block.  Waits on flags
+// solution and raises its flag.  The factor is read exactly once; with the
+// neighbour tiles premultiplied by the diagonal inverses (FP32 solves), the
+// chain of dependent work is one tile product per block.  Waits on flags
 // are bounded: after the limit the kernel records CF_ERR_TIMEOUT and goes
 // on (results are then wrong, never hung).
 #include "cf_common.cuh"
@@ -71,6 +72,47 @@ __global__ void __launch_bounds__(256) k_diag_inverse(int n, const float *__rest
     }
     VT *D = Dinv + (size_t)b * SB * SB;
     for (int e = tid; e < SB * SB; e += 256) D[e] = Xs[e % SB][e / SB];
+}
+
+// G_b = Dinv_b M(b, b - 1) (forward modes) or Dinv_b M(b, b + 1) (backward),
+// the neighbour block of M premultiplied by the inverse of the diagonal
+// block as the solve applies it (MODE 3: (L_bb^-1)^T), stored like Dinv
+// (column-major SB x SB per block); blocks without a neighbour are skipped.
+// Dynamic shared memory: 2 SB (SB + 1) floats.
+template <int SB, int MODE>
+__global__ void __launch_bounds__(256) k_neighbor_premul(int n, const float *__restrict__ T, int ldt,
+                                                         const float *__restrict__ Dinv, float *Gout) {
+    extern __shared__ __align__(16) float gsm[];
+    float (*Dm)[SB + 1] = reinterpret_cast<float (*)[SB + 1]>(gsm);                // Dm[i][k]
+    float (*Mm)[SB + 1] = reinterpret_cast<float (*)[SB + 1]>(gsm + SB * (SB + 1));  // Mm[k][j]
+    const int nb = (n + SB - 1) / SB, b = blockIdx.x;
+    constexpr bool fwd = (MODE == 0 || MODE == 2);
+    const int nbk = fwd ? b - 1 : b + 1;
+    if (nbk < 0 || nbk >= nb) return;
+    const int b0 = b * SB, c0 = nbk * SB, tid = threadIdx.x;
+    const float *D = Dinv + (size_t)b * SB * SB;
+    for (int e = tid; e < SB * SB; e += 256) {
+        const int i = e % SB, k = e / SB;
+        Dm[i][k] = (MODE == 3) ? D[k + SB * i] : D[i + SB * k];
+        // e as (row k, column j) of the neighbour tile
+        const int kr = e % SB, j = e / SB;
+        Mm[kr][j] = (b0 + kr < n && c0 + j < n) ? m_elem<MODE>(T, ldt, b0 + kr, c0 + j) : 0.f;
+    }
+    __syncthreads();
+    // thread: column j, rows i0, i0 + 2, ...
+    const int j = tid % SB, i0 = tid / SB;
+    constexpr int R = SB / 2;
+    float g[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) g[t] = 0.f;
+    for (int k = 0; k < SB; ++k) {
+        const float mk = Mm[k][j];
+#pragma unroll
+        for (int t = 0; t < R; ++t) g[t] = fmaf(Dm[i0 + 2 * t][k], mk, g[t]);
+    }
+    float *G = Gout + (size_t)b * SB * SB;
+#pragma unroll
+    for (int t = 0; t < R; ++t) G[(i0 + 2 * t) + SB * j] = g[t];
 }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -181,15 +223,30 @@ __device__ __forceinline__ void tile_update(VT (&acc)[4][CPT], const MT *Tt, int
     }
 }
 
+// Stages the tile of one step of block r0 / SB: the stored tile of M's block
+// (r0, column block of the step), or G_b for the last step when pre.
+template <int SB, int MODE>
+__device__ __forceinline__ void trsv_stage_step(float *dst, int step, int s, bool pre, const float *Gb,
+                                                const float *T, int ldt, int n, int nb, int r0, bool aligned) {
+    constexpr bool fwd = (MODE == 0 || MODE == 2);
+    if (pre && step == s - 1) {
+        stage_tile<SB>(dst, Gb, SB, SB, 0, 0, (((uintptr_t)Gb) & 15) == 0);
+        return;
+    }
+    const int cb = fwd ? step : nb - 1 - step;
+    const int ti = (MODE == 3) ? cb * SB : r0, tj = (MODE == 3) ? r0 : cb * SB;
+    stage_tile<SB>(dst, T, ldt, n, ti, tj, aligned && ti + SB <= n && tj + SB <= n);
+}
+
 // VT: arithmetic and right-hand-side type (float, or double for FP64
 // solves with the FP32 factor); the factor tiles stay FP32 in shared memory.
 // Thread = (row group rg = tid % (SB / 4): rows 4 rg .. 4 rg + 3, or
 // rg + (SB / 4) r for the transposed solve; right-hand-side group
 // cg = tid / (SB / 4): columns cg + CG t).
 template <int SB, int MODE, int NR, typename VT>
-__global__ void __launch_bounds__(256)
-k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *__restrict__ Dinv, VT *X,
-               int ldx, int *flags, int *ticket) {
+__global__ void __launch_bounds__(256, 1)        // one CTA per SM (shared memory)
+k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *__restrict__ Dinv,
+               const float *__restrict__ Gn, VT *X, int ldx, int *flags, int *ticket) {
     constexpr int TLD = SB + 4;
     constexpr int RG = SB / 4;                     // row groups of 4
     constexpr int CG = 256 / RG;                   // right-hand-side groups
@@ -231,28 +288,43 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
             const int i = trow<STR, RG>(rg, r), c = cg + CG * t;
             acc[r][t] = (i < rb && c < nrhs) ? X[(size_t)(r0 + i) + (size_t)c * ldx] : VT(0);
         }
-    // Stored tile that holds M(block b, block cb): for MODE 3 it is L(cb, b).
-    auto tile_origin = [&](int cb, int &ti, int &tj) {
-        if (MODE == 3) { ti = cb * SB; tj = r0; } else { ti = r0; tj = cb * SB; }
-    };
+    // With Gn (the neighbour block's tile premultiplied by this block's
+    // diagonal inverse, G_b = Dinv_b M(b, b -+ 1)), the last step, which waits
+    // for the neighbour, is one tile product: y = Dinv_b acc - G_b x_nb, with
+    // Dinv_b acc formed before the wait.
+    const bool pre = (Gn != nullptr) && s > 0;
+    const float *Gb = pre ? Gn + (size_t)b * SB * SB : nullptr;
     if (s > 0) {
-        const int cb = fwd ? 0 : nb - 1;
-        int ti, tj;
-        tile_origin(cb, ti, tj);
-        stage_tile<SB>(St0, T, ldt, n, ti, tj, aligned && ti + SB <= n && tj + SB <= n);
+        trsv_stage_step<SB, MODE>(St0, 0, s, pre, Gb, T, ldt, n, nb, r0, aligned);
         cp_async_commit();
     }
     for (int step = 0; step < s; ++step) {
         float *St = (step & 1) ? St1 : St0;
-        if (step + 1 < s) {                        // prefetch the next tile
-            const int cb = fwd ? step + 1 : nb - 2 - step;
-            int ti, tj;
-            tile_origin(cb, ti, tj);
-            stage_tile<SB>((step & 1) ? St0 : St1, T, ldt, n, ti, tj, aligned && ti + SB <= n && tj + SB <= n);
-        }
+        if (step + 1 < s)                          // prefetch the next tile
+            trsv_stage_step<SB, MODE>((step & 1) ? St0 : St1, step + 1, s, pre, Gb, T, ldt, n, nb, r0, aligned);
         cp_async_commit();
         const int cb = fwd ? step : nb - 1 - step;
         const int c0 = cb * SB, cbk = min(SB, n - c0);
+        const bool last_pre = pre && step == s - 1;
+        if (last_pre) {                            // acc <- Dinv_b acc before the neighbour's wait
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int t = 0; t < CPT; ++t)
+                    if (cg + CG * t < NR) Ys[trow<STR, RG>(rg, r) * YLD + cg + CG * t] = acc[r][t];
+            __syncthreads();
+            VT z[4][CPT];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int t = 0; t < CPT; ++t) z[r][t] = VT(0);
+            tile_update<SB, NR, CPT, CG, true, STR>(z, Ds, TLD, Ys, YLD, rg, cg, VT(1));
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int t = 0; t < CPT; ++t) acc[r][t] = z[r][t];
+            __syncthreads();
+        }
         if (tid == 0) {
             volatile int *f = flags + cb;
             long long it = 0;
@@ -270,11 +342,26 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
         }
         cp_async_wait<1>();                        // this step's tile has landed
         __syncthreads();
-        // M(i, kk) = St[kk * TLD + i], or St[i * TLD + kk] for MODE 3
-        tile_update<SB, NR, CPT, CG, MODE != 3, STR>(acc, St, TLD, Ys, YLD, rg, cg, VT(-1));
+        // M(i, kk) = St[kk * TLD + i], or St[i * TLD + kk] for MODE 3; G_b
+        // is staged column-major in every mode
+        if (last_pre) tile_update<SB, NR, CPT, CG, true, STR>(acc, St, TLD, Ys, YLD, rg, cg, VT(-1));
+        else tile_update<SB, NR, CPT, CG, MODE != 3, STR>(acc, St, TLD, Ys, YLD, rg, cg, VT(-1));
         __syncthreads();
     }
     cp_async_wait<0>();
+    if (pre) {                                     // acc already holds y_b
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) {
+                const int i = trow<STR, RG>(rg, r), c = cg + CG * t;
+                if (i < rb && c < nrhs) X[(size_t)(r0 + i) + (size_t)c * ldx] = acc[r][t];
+            }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicExch(flags + b, 1);
+        return;
+    }
     // y_b = Dinv_b acc
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -347,52 +434,80 @@ int launch_diag_inverse64(int mode, int n, const float *T, int ldt, double *Dinv
 }
 
 template <int SB, int MODE, int NR, typename VT>
-static int launch_trsv_nr(int n, int nrhs, const float *T, int ldt, const VT *Dinv, VT *X, int ldx, int *flags,
-                          int *ticket, cudaStream_t st) {
+static int launch_trsv_nr(int n, int nrhs, const float *T, int ldt, const VT *Dinv, const float *Gn, VT *X, int ldx,
+                          int *flags, int *ticket, cudaStream_t st) {
     const int nb = (n + SB - 1) / SB;
     const size_t smem = trsv_smem_bytes<SB, VT, NR>();
     CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<SB, MODE, NR, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    k_trsv_blocked<SB, MODE, NR, VT><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket);
+    k_trsv_blocked<SB, MODE, NR, VT><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
 
 template <int SB, int MODE, typename VT>
-static int launch_trsv_mode(int n, int nrhs, const float *T, int ldt, const VT *Dinv, VT *X, int ldx, int *sync_ws,
-                            cudaStream_t st) {
+static int launch_trsv_mode(int n, int nrhs, const float *T, int ldt, const VT *Dinv, const float *Gn, VT *X, int ldx,
+                            int *sync_ws, cudaStream_t st) {
     const int nb = (n + SB - 1) / SB;
     CF_CUDA_TRY(cudaMemsetAsync(sync_ws, 0, sizeof(int) * (size_t)(nb + 1), st));
     int *flags = sync_ws, *ticket = sync_ws + nb;
-    if (nrhs <= 4) return launch_trsv_nr<SB, MODE, 4, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
-    if (nrhs <= 8) return launch_trsv_nr<SB, MODE, 8, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
-    return launch_trsv_nr<SB, MODE, 16, VT>(n, nrhs, T, ldt, Dinv, X, ldx, flags, ticket, st);
+    if (nrhs <= 4) return launch_trsv_nr<SB, MODE, 4, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, st);
+    if (nrhs <= 8) return launch_trsv_nr<SB, MODE, 8, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, st);
+    return launch_trsv_nr<SB, MODE, 16, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, st);
 }
 
 template <int SB, typename VT>
-static int launch_trsv_t(int mode, int n, int nrhs, const float *T, int ldt, const VT *Dinv, VT *X, int ldx,
-                         int *sync_ws, cudaStream_t st) {
+static int launch_trsv_t(int mode, int n, int nrhs, const float *T, int ldt, const VT *Dinv, const float *Gn, VT *X,
+                         int ldx, int *sync_ws, cudaStream_t st) {
     if (n <= 0 || nrhs <= 0) return CF_OK;
     if (nrhs > 16) return CF_ERR_UNSUPPORTED;
     switch (mode) {
-        case 0: return launch_trsv_mode<SB, 0, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        case 1: return launch_trsv_mode<SB, 1, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        case 2: return launch_trsv_mode<SB, 2, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
-        case 3: return launch_trsv_mode<SB, 3, VT>(n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+        case 0: return launch_trsv_mode<SB, 0, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, st);
+        case 1: return launch_trsv_mode<SB, 1, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, st);
+        case 2: return launch_trsv_mode<SB, 2, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, st);
+        case 3: return launch_trsv_mode<SB, 3, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, st);
         default: return CF_ERR_UNSUPPORTED;
     }
 }
 
 // X <- M^{-1} X for nrhs <= 16 columns; sync_ws holds trsv_ws_bytes(n).
-int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, float *X, int ldx,
-                    int *sync_ws, cudaStream_t st) {
-    return launch_trsv_t<kSB32, float>(mode, n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+// Gn (may be null): the premultiplied neighbour tiles of launch_neighbor_premul
+// for the same mode and Dinv.
+int launch_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, const float *Dinv, const float *Gn, float *X,
+                    int ldx, int *sync_ws, cudaStream_t st) {
+    return launch_trsv_t<kSB32, float>(mode, n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, st);
 }
 // The same with FP64 right-hand sides and arithmetic (FP64 Dinv from
 // launch_diag_inverse64); the FP32 factor is read as stored.
 int launch_trsv_f64x(int mode, int n, int nrhs, const float *T, int ldt, const double *Dinv, double *X, int ldx,
                      int *sync_ws, cudaStream_t st) {
-    return launch_trsv_t<kSB64, double>(mode, n, nrhs, T, ldt, Dinv, X, ldx, sync_ws, st);
+    return launch_trsv_t<kSB64, double>(mode, n, nrhs, T, ldt, Dinv, nullptr, X, ldx, sync_ws, st);
+}
+
+// G_b for every block of an FP32 solve (k_neighbor_premul); Gout holds
+// diag_inverse_floats(n) floats.
+int launch_neighbor_premul(int mode, int n, const float *T, int ldt, const float *Dinv, float *Gout,
+                           cudaStream_t st) {
+    if (n <= 0) return CF_OK;
+    constexpr int SB = kSB32;
+    const int nb = (n + SB - 1) / SB;
+    const size_t smem = sizeof(float) * 2 * SB * (SB + 1);
+#define CF_PREMUL(M)                                                                                            \
+    case M:                                                                                                     \
+        CF_CUDA_TRY(cudaFuncSetAttribute(k_neighbor_premul<SB, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem));                                                           \
+        k_neighbor_premul<SB, M><<<nb, 256, smem, st>>>(n, T, ldt, Dinv, Gout);                                \
+        break;
+    switch (mode) {
+        CF_PREMUL(0)
+        CF_PREMUL(1)
+        CF_PREMUL(2)
+        CF_PREMUL(3)
+        default: return CF_ERR_UNSUPPORTED;
+    }
+#undef CF_PREMUL
+    CF_LAUNCH_CHECK();
+    return CF_OK;
 }
 
 int trsv_take_status(cudaStream_t st, int *status) {
