@@ -523,7 +523,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
 
         e2e_run(1)
         torch.cuda.synchronize()
-        k2 = max(1, min(args.steps, 3))
+        k2 = max(1, args.steps)
         barrier()
         e0.record(stream)
         e2e_run(k2)
