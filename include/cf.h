@@ -248,9 +248,9 @@ int cf_schur_update_lp(int m, int n, int k, const void *A_lp, int lda_k,
                        cf_prec prec, int lower, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
- * CH-3 / LU-5 with FP8 operands (spec: trailing SYRK/GEMM in FP8 e4m3
- * with per-128 x 128-tile FP32 scales, FP32 accumulation; the paper has no
- * low-precision update), exposed for testing.
+ * CH-3 / LU-5 with FP8 operands (trailing SYRK/GEMM in FP8 e4m3 with
+ * per-128 x 128-tile FP32 scales, FP32 accumulation; an addition of this
+ * project, the paper has no low-precision update), exposed for testing.
  *
  * cf_quantize_e4m3: src is a rows x k FP32 block, column-major (lds).  For
  * every tile of 128 rows x 128 columns (K-block), scale = amax / 448 (1 for
@@ -283,8 +283,8 @@ int cf_schur_update_fp8(int m, int n, int k, const void *qA, int ldqa,
 int cf_device_status(cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
- * BAT-1  Batched uneven factorizations in one persistent launch (north star;
- * the paper's small-N regime, Sec. 9).  All per-matrix arguments are DEVICE
+ * BAT-1  Batched uneven factorizations in one persistent launch (an addition
+ * of this project; the paper's small-N regime, Sec. 9).  All per-matrix arguments are DEVICE
  * arrays of length batch: n[i] (0 <= n[i] <= 512), lda[i], A[i] (device
  * pointer to an n x n column-major matrix), ipiv[i] (device int[n[i]]),
  * info[i].  kind[i] = 0 for LU (tournament rule with one leaf per panel, i.e.
@@ -331,8 +331,8 @@ int cf_solve_batched_mixed(int batch, const int *kind, int default_kind,
                            double *eta, int *solver, void *work, size_t lwork,
                            const cf_options *opt, cudaStream_t stream);
 
-/* BAT-1 autotuner (spec: tile and schedule chosen by the project's
- * tuner; no counterpart in the paper).  Times every candidate block size
+/* BAT-1 autotuner (block size and schedule chosen by measurement; no
+ * counterpart in the paper).  Times every candidate block size
  * v in {8, 16, 32} with every resident-CTA count the hardware allows on up to
  * 512 synthetic matrices whose sizes are an evenly spaced sample of
  * n_host[0..batch) (host array; kind_host may be NULL: default_kind), for
@@ -350,8 +350,8 @@ int cf_batched_autotune(int batch, const int *n_host, const int *kind_host,
                         cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
- * Mixed-precision refined solves (north star; the paper cites GPU mixed
- * LU + refinement as related work, Sec. 11).  A and B are never modified.
+ * Mixed-precision refined solves (an addition of this project; the paper
+ * cites GPU mixed LU + refinement as related work, Sec. 11).  A and B are never modified.
  * cf_posv_mixed factors the lower triangle but forms residuals with all of
  * A, which must hold both triangles.
  *   factor_prec  CF_BF16, CF_F16 or CF_BF16X3 (also CF_FP8E4M3 for

@@ -1,6 +1,6 @@
 // cf_batched.cu -- BAT-1: thousands of independent, uneven factorizations in
-// one persistent launch (north star; the paper's small-N motivation is its
-// Sec. 9.3 discussion of small matrices on many nodes).
+// one persistent launch (an addition of this project; the paper's small-N
+// motivation is its Sec. 9.3 discussion of small matrices on many nodes).
 //
 // One CTA factors one matrix at a time.  CTAs pull matrix indices from an
 // atomic queue ordered by decreasing n^3 (longest processing time first), so

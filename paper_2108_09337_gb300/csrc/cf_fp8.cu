@@ -2,8 +2,9 @@
 // FP32 scales on the 5th-generation tensor cores:
 //     C[m x n] -= sum_kb sA(i, kb) sB(j, kb) (qA qB^T)_kb      (FP32 C)
 // where kb runs over K-blocks of 128 and sA(i, kb) is the scale of the
-// 128 x 128 tile of A holding row i in K-block kb (spec: trailing
-// SYRK/GEMM in FP8 with tile scales; the paper's Table 2 gemmt / gemm).
+// 128 x 128 tile of A holding row i in K-block kb (the paper's Table 2
+// gemmt / gemm with FP8 operands and tile scales, an addition of this
+// project: the paper has no low-precision update).
 //
 // A tile scale changes from one K-block to the next, so the K sum cannot run
 // in one tensor-memory accumulator.  Per output tile (128 x 256) and K-block:

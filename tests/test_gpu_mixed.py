@@ -2,7 +2,7 @@
 (cf_gesv_mixed, cf_posv_mixed): BF16 / FP16 tensor-core Schur updates on FP32
 working storage, FP64 refinement.
 
-Bar (the benchmark spec): backward error eta = max_j ||b_j - A x_j||_inf /
+Bar: backward error eta = max_j ||b_j - A x_j||_inf /
 (||A||_inf ||x_j||_inf + ||b_j||_inf) <= 1e-14, computed here on the host by
 the oracle's compensated residual from the returned x; the forward error
 against the oracle's FP64 solution is bounded by kappa_inf(A) * eta * 4.
