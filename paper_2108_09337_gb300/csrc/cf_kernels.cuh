@@ -24,6 +24,9 @@ struct TournWS {
     int *counter;             // [total_nodes] arrivals; zero before and after
     int *root_win;            // [kMaxV] winners in pivot order
     size_t counter_bytes;
+    // FP32 tournament, optional: [m][kMaxV] row-major copy of the panel's
+    // original rows, written by the leaves, read by the playoff nodes
+    float *rows32 = nullptr;
 };
 
 // Root-node outputs used by the LU driver (ipiv == nullptr: none).

@@ -364,6 +364,7 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
         w->tws.counter = cv.take<int>(p.total_nodes);
         w->tws.root_win = cv.take<int>(kMaxV);
         w->tws.counter_bytes = sizeof(int) * (size_t)p.total_nodes;
+        w->tws.rows32 = cv.take<float>((size_t)(n > 0 ? n : 1) * kMaxV);
         w->tep.swap_cnt = cv.take<int>(1);
         w->tep.swap_dst = cv.take<int>(2 * kMaxV);
         w->tep.swap_src = cv.take<int>(2 * kMaxV);

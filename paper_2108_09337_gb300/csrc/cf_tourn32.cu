@@ -12,7 +12,11 @@
 //     ballot); each warp's candidate publishes its row before the column's
 //     only barrier, so the winner's row is readable right after it;
 //   * the CTA that finishes a node second climbs to the parent (atomic
-//     counter), so no CTA waits for another.
+//     counter), so no CTA waits for another;
+//   * with a rows32 workspace the leaves also write their rows' original
+//     values row-major, so a playoff node reads each candidate row as 32
+//     contiguous 16-byte loads instead of 128 loads from a scattered row of
+//     the column-major panel (an eighth of the L2 sectors).
 // FP32 with FMA: the mixed path's pivots are reported, not held to bit
 // equality with the FP64 oracle.
 #include <climits>
@@ -266,6 +270,12 @@ k_tourn32(const float *__restrict__ P, int ldp, TournPlan plan, TournWS ws, Tour
         if (tid == 0) s.nrows = nr;
         s.rows[tid] = row0 + tid;
         load_row32(a, P, ldp, row0 + tid, w, tid < nr);
+        if (ws.rows32 != nullptr && tid < nr && plan.nlevels > 1) {   // original rows for the playoff nodes
+            float4 *dst = reinterpret_cast<float4 *>(ws.rows32 + (size_t)(row0 + tid) * kMaxV);
+#pragma unroll
+            for (int q = 0; q < kMaxV / 4; ++q)
+                dst[q] = make_float4(a[2 * q].x, a[2 * q].y, a[2 * q + 1].x, a[2 * q + 1].y);
+        }
         __syncthreads();
         const int np = min(nr, w);
         gepp_select_t2(s, a, w, np);
@@ -318,7 +328,17 @@ k_tourn32(const float *__restrict__ P, int ldp, TournPlan plan, TournWS ws, Tour
             else if (tid < nr) s.rows[tid] = __ldcg(ws.node_win + (size_t)(s0 + 1) * kMaxV + (tid - c0));
             if (tid == 0) s.nrows = nr;
             __syncthreads();
-            load_row32(a, P, ldp, tid < nr ? s.rows[tid] : 0, w, tid < nr);
+            if (ws.rows32 != nullptr) {            // contiguous original rows (the leaves' copy)
+                const float4 *src = reinterpret_cast<const float4 *>(ws.rows32 + (size_t)s.rows[tid < nr ? tid : 0] * kMaxV);
+#pragma unroll
+                for (int q = 0; q < kMaxV / 4; ++q) {
+                    const float4 v = tid < nr ? __ldcg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    a[2 * q] = make_float2(v.x, v.y);
+                    a[2 * q + 1] = make_float2(v.z, v.w);
+                }
+            } else {
+                load_row32(a, P, ldp, tid < nr ? s.rows[tid] : 0, w, tid < nr);
+            }
             __syncthreads();
             gepp_select_t2(s, a, w, np);
             if (tid < np) dst[tid] = s.rows[s.order[tid]];
