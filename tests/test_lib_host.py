@@ -68,3 +68,27 @@ def test_argument_validation_returns_before_any_cuda_call(lib):
     assert L.cf_tourn_select(10, 4, ctypes.c_void_p(16), 10, 8, 7, null, null, 0, null) == -6
     assert L.cf_residual(-1, 1, 1, null, 1, null, 1, null, 1, null, 1, null) == -1
     assert L.cf_getrs(4, 1, ctypes.c_void_p(16), 2, null, null, 4, null, 0, null) == -4
+
+
+def test_mixed_options_and_workspace(lib):
+    """The refinement options and workspace queries of the mixed solvers:
+    fp64_residual takes 0 or 1 (anything else is refused by the size query,
+    which returns 0), the default is 0 (pair-arithmetic residuals where
+    allowed), deeper LU slabs from n = 16384 make the LU workspace grow
+    faster than the Cholesky one, and the pair-residual query is host-only
+    and linear in m + n."""
+    from paper_2108_09337_gb300 import cf
+    L = cf.lib()
+    o = cf.options()
+    assert o.fp64_residual == 0
+    ok = cf.gesv_mixed_workspace_size(4096, 4, "f16")
+    assert ok > 0
+    assert cf.gesv_mixed_workspace_size(4096, 4, "f16", fp64_residual=1) == ok
+    assert cf.gesv_mixed_workspace_size(4096, 4, "f16", fp64_residual=2) == 0
+    assert cf.posv_mixed_workspace_size(4096, 4, "f16", fp64_residual=-1) == 0
+    lu16, ch16 = cf.gesv_mixed_workspace_size(16384, 16, "f16"), cf.posv_mixed_workspace_size(16384, 16, "f16")
+    lu8, ch8 = cf.gesv_mixed_workspace_size(8192, 16, "f16"), cf.posv_mixed_workspace_size(8192, 16, "f16")
+    assert lu16 - ch16 > 2 * (lu8 - ch8)          # Lb / Ub sized for V = 2048 vs 1024
+    p1 = L.cf_residual_pair_workspace_size(1000, 1000, 16)
+    p2 = L.cf_residual_pair_workspace_size(2000, 2000, 16)
+    assert 0 < p1 < p2 <= 2 * p1 + 4096
