@@ -347,12 +347,8 @@ int launch_group(int m, int n, int nc, const double *A, int lda, const unsigned 
                  cudaStream_t st) {
     k_pair_split_x<NR><<<NR, 256, 0, st>>>(n, nc, X, ldx, Xs, sx);
     CF_LAUNCH_CHECK();
-    static bool attr_set = false;
-    if (!attr_set) {
-        CF_CUDA_TRY(cudaFuncSetAttribute(k_residual_pair<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pair_smem_bytes<NR>()));
-        attr_set = true;
-    }
+    CF_CUDA_TRY(cudaFuncSetAttribute(k_residual_pair<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pair_smem_bytes<NR>()));   // per device: set on every call
     const int rb = ceil_div(m, kPairThreads);
     const int ks = pick_split(rb, n, sm_count_pair() * resident_ctas<NR>());
     const int kspan = ceil_div(ceil_div(n, ks), kTile) * kTile;
