@@ -114,6 +114,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
+# ------------------------------------------------------------------ ranks
+def _reduce_over_ranks(x: float, world: int, device, op: str = "max") -> float:
+    """Max (or min) of a host scalar over the ranks of the default process
+    group (NCCL on GPUs, gloo on the CPU); x itself for a single rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.MIN)
+    return float(t.item())
+
+
+def _job_tflops(world: int, flops_per_rank: float, ms_per_step: float) -> float:
+    """Whole-job rate of `world` replicas, each doing flops_per_rank per step,
+    timed by the slowest rank's ms_per_step."""
+    return world * flops_per_rank / (ms_per_step * 1e-3) / 1e12
+
+
 # ------------------------------------------------------------------ oracle
 def _oracle_sample(n_sample: int):
     """The FP64 oracle as it stands on this host's cores: LU (v = h = 128)
@@ -371,18 +390,15 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize()
         barrier()
     launches = cf.kernel_launches() - launches0
-    total_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _reduce_over_ranks(e0.elapsed_time(e1), world, dev, "max")
     ms_step = total_ms / args.steps
-    value = world * (lu_fl + ch_fl) / (ms_step * 1e-3) / 1e12
+    value = _job_tflops(world, lu_fl + ch_fl, ms_step)
 
     # verify the last step's solutions independently (FP64 residual in torch)
     eta_lu = _eta(A_lu, X1, B_lu)
     eta_ch = _eta(A_ch, X2, B_ch)
     ok = (eta_lu <= TOL) and (eta_ch <= TOL) and st1 == cf.CF_OK and st2 == cf.CF_OK
+    ok = _reduce_over_ranks(1.0 if ok else 0.0, world, dev, "min") > 0.5   # every replica converged
 
     # ---- per-kernel device time inside the timed steps (CUDA events on the
     # solver's stream around every launch of these kernels), and the roofline
@@ -530,14 +546,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms2 = e0.elapsed_time(e1) / k2
-        if world > 1:
-            t = torch.tensor([ms2], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms2 = float(t.item())
+        ms2 = _reduce_over_ranks(e0.elapsed_time(e1) / k2, world, dev, "max")
         h2d = 2 * n * n * 8 + (16 + 8) * n * 8
         d2h = (16 + 8) * n * 8
-        e2e = {"value": world * (lu_fl + ch_fl) / (ms2 * 1e-3) / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": _job_tflops(world, lu_fl + ch_fl, ms2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms2}
         del hA_lu, hA_ch, dA1, dA2, dB1, dB2
         torch.cuda.empty_cache()

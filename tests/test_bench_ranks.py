@@ -1,0 +1,71 @@
+"""The benchmark's multi-rank bookkeeping on the CPU: two gloo ranks stand in
+for two GPUs running independent replicas.  The slowest rank's time sets the
+step time, the job rate counts every rank's flops, a replica that did not
+converge zeroes the line for all, and the oracle arm runs on rank 0 only."""
+import contextlib
+import io
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = [120.0, 150.0][rank]                      # rank 1 is the slow one
+        t = bench._reduce_over_ranks(ms, world, "cpu", "max")
+        ok = bench._reduce_over_ranks([1.0, 0.0][rank], world, "cpu", "min")
+        ok_all = bench._reduce_over_ranks(1.0, world, "cpu", "min")
+
+        class A:                                        # the reference arm's arguments
+            warmup, steps, gpus = 0, 0, world
+        buf = io.StringIO()
+        if rank != 0:
+            with contextlib.redirect_stdout(buf):
+                bench.run_reference(A, rank)
+        out[rank] = (t, ok, ok_all, buf.getvalue())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    for rank in (0, 1):
+        t, ok, ok_all, printed = out[rank]
+        assert t == 150.0                      # max over ranks on every rank
+        assert ok == 0.0 and ok_all == 1.0     # one failed replica fails the job
+    assert out[1][3] == ""                     # rank 1 prints nothing in the oracle arm
+
+
+def test_single_rank_is_identity():
+    assert bench._reduce_over_ranks(3.5, 1, "cpu", "max") == 3.5
+    assert bench._reduce_over_ranks(0.0, 1, "cpu", "min") == 0.0
+
+
+@pytest.mark.parametrize("world", [1, 2, 8])
+def test_job_rate_counts_every_replica(world):
+    # weak scaling: each replica does F flops per step; the job's rate is
+    # world * F over the slowest rank's step time
+    F = 2.0 * 32768 ** 3 / 3.0 + 32768 ** 3 / 3.0
+    r = bench._job_tflops(world, F, 400.0)
+    assert r == pytest.approx(world * F / 0.4 / 1e12, rel=1e-15)
