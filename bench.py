@@ -335,6 +335,11 @@ def _eta(A, X, B):
     return float((num / den).max())
 
 
+def _fwd_err(X, Xref):
+    """max_j ||x_j - xref_j||_inf / ||xref_j||_inf."""
+    return float(((X - Xref).abs().amax(dim=0) / Xref.abs().amax(dim=0)).max())
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import numpy as np  # noqa: F401
     import torch
@@ -566,7 +571,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         e1.record(stream)
         torch.cuda.synchronize()
         lu_ms = e0.elapsed_time(e1)
-        del A64, ipiv
+        # forward error of the timed step's mixed solutions against this
+        # FP64 path's solutions of the same systems (untimed)
+        fwd = {}
+        X64 = B_lu.t().clone().t()
+        cf.getrs(A64, ipiv, X64)
+        fwd["lu"] = _fwd_err(X1, X64)
+        del A64, ipiv, X64
         S64 = inputs.spd_gram_torch(n, seed=1, alpha=gen_info["alpha"], device=dev)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -574,10 +585,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         e1.record(stream)
         torch.cuda.synchronize()
         ch_ms = e0.elapsed_time(e1)
-        del S64
+        X64 = B_ch.t().clone().t()
+        cf.potrs(S64, X64)
+        fwd["chol"] = _fwd_err(X2, X64)
+        del S64, X64
         fp64 = {"lu_ms": lu_ms, "chol_ms": ch_ms, "lu_tflops": lu_fl / (lu_ms * 1e-3) / 1e12,
                 "chol_tflops": ch_fl / (ch_ms * 1e-3) / 1e12,
                 "tflops": (lu_fl + ch_fl) / ((lu_ms + ch_ms) * 1e-3) / 1e12,
+                "mixed_forward_error_vs_fp64": fwd,
                 "note": "factorization only (FP64 path; its solve adds O(N^2))"}
         torch.cuda.empty_cache()
 
