@@ -56,8 +56,11 @@ typedef enum {
                           times the tensor work */
 } cf_prec;
 
-/* Tunables.  Pass NULL for the defaults (in brackets).  The pivot sequence
- * is a function of (v, leaf_h, arity) only; the oracle takes the same three. */
+/* Tunables.  Pass NULL for the defaults (in brackets); a field left 0 in v,
+ * leaf_h, arity, tol, max_iter or gmres_restart also takes its default.  A
+ * value out of range makes the call return CF_ERR_UNSUPPORTED (the size
+ * queries return 0) before anything is enqueued.  The pivot sequence is a
+ * function of (v, leaf_h, arity) only; the oracle takes the same three. */
 typedef struct {
     int v;             /* block size of a step, 1..128 [128] (Sec. 7.2, "Block size v") */
     int leaf_h;        /* tournament leaf height [128]: 1..128 for the FP64
@@ -289,7 +292,10 @@ int cf_device_status(cudaStream_t stream);
  * pointer to an n x n column-major matrix), ipiv[i] (device int[n[i]]),
  * info[i].  kind[i] = 0 for LU (tournament rule with one leaf per panel, i.e.
  * partial pivoting, block size min(v, 32)), 1 for Cholesky (lower); kind ==
- * NULL means every matrix has default_kind.  One CTA factors one matrix at a
+ * NULL means every matrix has default_kind.  ipiv may be NULL only when every
+ * matrix is Cholesky by default (kind NULL, default_kind 1); otherwise it and
+ * each LU matrix's ipiv[i] must be valid.  A NULL array argument returns its
+ * own (negative) position.  One CTA factors one matrix at a
  * time (opt->batch_cps CTAs per SM; cf_batched_autotune picks it and v);
  * matrices are taken longest-first (decreasing n).  info[i] = -1 for
  * n[i] > 512.  Capturable in a CUDA graph (no host synchronisation, no

@@ -798,7 +798,13 @@ extern "C" int cf_factor_batched(int batch, const int *kind, int default_kind, c
                                  const cf_options *opt, cudaStream_t st) {
     if (batch < 0) return -1;
     if (default_kind != 0 && default_kind != 1) return -3;
-    if (batch > 0 && (n == nullptr || A == nullptr || lda == nullptr || info == nullptr)) return -4;
+    if (batch > 0) {
+        if (n == nullptr) return -4;
+        if (A == nullptr) return -5;
+        if (lda == nullptr) return -6;
+        if (ipiv == nullptr && (kind != nullptr || default_kind == 0)) return -7;   // some matrix may be LU
+        if (info == nullptr) return -8;
+    }
     Opts o;
     int rc = resolve_options(opt, &o);
     if (rc) return rc;
@@ -825,12 +831,26 @@ extern "C" size_t cf_potrf_batched_workspace_size(int batch, const cf_options *o
 
 extern "C" int cf_getrf_batched(int batch, const int *n, double *const *A, const int *lda, int *const *ipiv,
                                 int *info, void *work, size_t lwork, const cf_options *opt, cudaStream_t st) {
-    if (batch > 0 && ipiv == nullptr) return -5;
+    if (batch < 0) return -1;
+    if (batch > 0) {                 // this entry point's own argument numbers
+        if (n == nullptr) return -2;
+        if (A == nullptr) return -3;
+        if (lda == nullptr) return -4;
+        if (ipiv == nullptr) return -5;
+        if (info == nullptr) return -6;
+    }
     return cf_factor_batched(batch, nullptr, 0, n, A, lda, ipiv, info, work, lwork, opt, st);
 }
 
 extern "C" int cf_potrf_batched(int batch, const int *n, double *const *A, const int *lda, int *info, void *work,
                                 size_t lwork, const cf_options *opt, cudaStream_t st) {
+    if (batch < 0) return -1;
+    if (batch > 0) {
+        if (n == nullptr) return -2;
+        if (A == nullptr) return -3;
+        if (lda == nullptr) return -4;
+        if (info == nullptr) return -5;
+    }
     return cf_factor_batched(batch, nullptr, 1, n, A, lda, nullptr, info, work, lwork, opt, st);
 }
 
@@ -846,9 +866,16 @@ extern "C" int cf_solve_batched_mixed(int batch, const int *kind, int default_ki
                                       void *work, size_t lwork, const cf_options *opt, cudaStream_t st) {
     if (batch < 0) return -1;
     if (default_kind != 0 && default_kind != 1) return -3;
-    if (batch > 0 && (n == nullptr || A == nullptr || lda == nullptr || B == nullptr || X == nullptr ||
-                      info == nullptr || iters == nullptr || eta == nullptr))
-        return -4;
+    if (batch > 0) {
+        if (n == nullptr) return -4;
+        if (A == nullptr) return -5;
+        if (lda == nullptr) return -6;
+        if (B == nullptr) return -7;
+        if (X == nullptr) return -8;
+        if (info == nullptr) return -9;
+        if (iters == nullptr) return -10;
+        if (eta == nullptr) return -11;
+    }
     Opts o;
     int rc = resolve_options(opt, &o);
     if (rc) return rc;

@@ -388,11 +388,13 @@ extern "C" int cf_schur_update_fp8(int m, int n, int k, const void *qA, int ldqa
     if (m < 0) return -1;
     if (n < 0) return -2;
     if (k < 0 || k % 128 != 0) return -3;
-    if (m > 0 && k > 0 && (qA == nullptr || sA == nullptr)) return -4;
+    if (m > 0 && k > 0 && qA == nullptr) return -4;
     if (ldqa < k || ldqa % 16 != 0) return -5;
+    if (m > 0 && k > 0 && sA == nullptr) return -6;
     if (ldsa < k / 128) return -7;
-    if (n > 0 && k > 0 && (qB == nullptr || sB == nullptr)) return -8;
+    if (n > 0 && k > 0 && qB == nullptr) return -8;
     if (ldqb < k || ldqb % 16 != 0) return -9;
+    if (n > 0 && k > 0 && sB == nullptr) return -10;
     if (ldsb < k / 128) return -11;
     if (m > 0 && n > 0 && C == nullptr) return -12;
     if (ldc < (m > 1 ? m : 1)) return -13;
