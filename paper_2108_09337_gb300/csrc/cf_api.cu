@@ -114,7 +114,7 @@ extern "C" long long cf_kernel_launches(void) { return g_launches.load(); }
 // ------------------------------------------------------------------- getrf
 extern "C" size_t cf_getrf_workspace_size(int n, const cf_options *opt) {
     Opts o;
-    if (resolve_options(opt, &o) != CF_OK) return 0;
+    if (resolve_options(opt, &o) != CF_OK || o.leaf_h > kMaxV) return 0;   // FP64 leaves: <= kMaxV rows
     return tourn_ws_bytes(n > 0 ? n : 1, o.leaf_h, o.arity);
 }
 
@@ -255,6 +255,7 @@ extern "C" int cf_getrf(int n, double *A, int lda, int *ipiv, int *info, void *w
     Opts o;
     int rc = resolve_options(opt, &o);
     if (rc != CF_OK) return rc;
+    if (o.leaf_h > kMaxV) return CF_ERR_UNSUPPORTED;     // FP64 leaves: <= kMaxV rows
     CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
     if (n == 0) return CF_OK;
     if (work == nullptr || lwork < cf_getrf_workspace_size(n, opt)) return CF_ERR_WORKSPACE;

@@ -107,6 +107,15 @@ def test_bad_options_are_unsupported_before_any_cuda_call():
             cf.CF_ERR_UNSUPPORTED, kw
 
 
+def test_fp64_leaves_at_most_128_rows():
+    # the mixed solvers take leaves of up to 256 rows, the FP64 routines 128
+    assert L.cf_getrf(8, P, 8, P, P, P, BIG, _opt(leaf_h=200), None) == cf.CF_ERR_UNSUPPORTED
+    assert L.cf_getrf_noalloc(8, P, 8, P, P, _opt(leaf_h=129), None) == cf.CF_ERR_UNSUPPORTED
+    assert L.cf_getrf_workspace_size(1000, _opt(leaf_h=129)) == 0
+    assert L.cf_getrf_workspace_size(1000, _opt(leaf_h=128)) > 0
+    assert cf.gesv_mixed_workspace_size(1000, 1, "f16", leaf_h=256) > 0
+
+
 def test_zero_fields_select_defaults():
     z = cf.Options()                      # every field 0
     d = cf.options()
