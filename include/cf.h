@@ -117,6 +117,30 @@ typedef struct {
                                columns, sum_j (r-j-1)(2(w-j-1) + 1) */
 } cf_refine_stats;
 
+/* One workspace query for every call that takes (work, lwork): the bytes
+ * that call needs, equal to its own *_workspace_size query.  n is the order
+ * (rows of the panel for CF_OP_TOURN_SELECT, the batch size for the batched
+ * calls); nrhs is the right-hand sides (the panel width for
+ * CF_OP_TOURN_SELECT; ignored where the call has none); prec matters only for
+ * the mixed solvers; opt may be NULL (defaults).  Host only; returns 0 for an
+ * unknown op or an invalid configuration, and for calls that need no
+ * workspace (CF_OP_POTRF, CF_OP_POTRS). */
+typedef enum {
+    CF_OP_GETRF = 0,
+    CF_OP_POTRF = 1,
+    CF_OP_GETRS = 2,
+    CF_OP_POTRS = 3,
+    CF_OP_GESV_MIXED = 4,
+    CF_OP_POSV_MIXED = 5,
+    CF_OP_GETRF_BATCHED = 6,
+    CF_OP_POTRF_BATCHED = 7,
+    CF_OP_FACTOR_BATCHED = 8,
+    CF_OP_SOLVE_BATCHED_MIXED = 9,
+    CF_OP_RESIDUAL_PAIR = 10,
+    CF_OP_TOURN_SELECT = 11
+} cf_op;
+size_t cf_workspace_size(int op, int n, int nrhs, cf_prec prec, const cf_options *opt);
+
 const char *cf_status_string(int status);
 int cf_last_cuda_error(void);   /* last cudaError_t seen by the library */
 /* Number of kernel launches the library has enqueued in this process so far

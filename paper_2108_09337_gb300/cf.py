@@ -63,6 +63,7 @@ _OPT = ctypes.POINTER(Options)
 _SIG = {
     "cf_default_options": (None, [_OPT]),
     "cf_status_string": (ctypes.c_char_p, [_I]),
+    "cf_workspace_size": (_S, [_I, _I, _I, _I, _OPT]),
     "cf_last_cuda_error": (_I, []),
     "cf_kernel_launches": (ctypes.c_longlong, []),
     "cf_tourn_workspace_size": (_S, [_I, _I, _I, _I]),
@@ -171,6 +172,20 @@ def options(**kw) -> Options:
         if v is not None:
             setattr(o, k, v)
     return o
+
+
+OPS = {name: i for i, name in enumerate(
+    ["getrf", "potrf", "getrs", "potrs", "gesv_mixed", "posv_mixed", "getrf_batched", "potrf_batched",
+     "factor_batched", "solve_batched_mixed", "residual_pair", "tourn_select"])}
+
+
+def workspace_size(op: str, n: int, nrhs: int = 0, prec="f64", **opt_kw) -> int:
+    """cf_workspace_size: bytes of work the call `op` needs (n = order, or
+    batch size for the batched calls, or panel rows for tourn_select; nrhs =
+    right-hand sides, or the panel width for tourn_select)."""
+    opt = options(**opt_kw)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    return _lib.cf_workspace_size(OPS[op], n, nrhs, p, ctypes.byref(opt))
 
 
 def _workspace(nbytes: int, device) -> torch.Tensor:

@@ -112,6 +112,27 @@ extern "C" int cf_last_cuda_error(void) { return g_last_cuda_error.load(); }
 extern "C" long long cf_kernel_launches(void) { return g_launches.load(); }
 
 // ------------------------------------------------------------------- getrf
+extern "C" size_t cf_workspace_size(int op, int n, int nrhs, cf_prec prec, const cf_options *opt) {
+    if (n < 0 || nrhs < 0) return 0;
+    Opts o;
+    if (resolve_options(opt, &o) != CF_OK) return 0;
+    switch (op) {
+        case CF_OP_GETRF: return cf_getrf_workspace_size(n, opt);
+        case CF_OP_POTRF: return cf_potrf_workspace_size(n, opt);
+        case CF_OP_GETRS: return cf_getrs_workspace_size(n, nrhs);
+        case CF_OP_POTRS: return 0;
+        case CF_OP_GESV_MIXED: return cf_gesv_mixed_workspace_size(n, nrhs, prec, opt);
+        case CF_OP_POSV_MIXED: return cf_posv_mixed_workspace_size(n, nrhs, prec, opt);
+        case CF_OP_GETRF_BATCHED: return cf_getrf_batched_workspace_size(n, opt);
+        case CF_OP_POTRF_BATCHED: return cf_potrf_batched_workspace_size(n, opt);
+        case CF_OP_FACTOR_BATCHED: return cf_factor_batched_workspace_size(n, opt);
+        case CF_OP_SOLVE_BATCHED_MIXED: return cf_solve_batched_mixed_workspace_size(n, opt);
+        case CF_OP_RESIDUAL_PAIR: return cf_residual_pair_workspace_size(n, n, nrhs);
+        case CF_OP_TOURN_SELECT: return cf_tourn_workspace_size(n, nrhs, o.leaf_h, o.arity);
+        default: return 0;
+    }
+}
+
 extern "C" size_t cf_getrf_workspace_size(int n, const cf_options *opt) {
     Opts o;
     if (resolve_options(opt, &o) != CF_OK || o.leaf_h > kMaxV) return 0;   // FP64 leaves: <= kMaxV rows

@@ -92,3 +92,30 @@ def test_mixed_options_and_workspace(lib):
     p1 = L.cf_residual_pair_workspace_size(1000, 1000, 16)
     p2 = L.cf_residual_pair_workspace_size(2000, 2000, 16)
     assert 0 < p1 < p2 <= 2 * p1 + 4096
+
+
+def test_generic_workspace_query_matches_each_call(lib):
+    """cf_workspace_size(op, ...) equals the per-call queries."""
+    from paper_2108_09337_gb300 import cf
+    L = cf.lib()
+    o = cf.options()
+    ob = ctypes.byref(o)
+    W = cf.workspace_size
+    assert W("getrf", 4096) == L.cf_getrf_workspace_size(4096, ob) > 0
+    assert W("getrf", 4096, leaf_h=64) == L.cf_getrf_workspace_size(4096, ctypes.byref(cf.options(leaf_h=64)))
+    assert W("potrf", 4096) == L.cf_potrf_workspace_size(4096, ob)
+    assert W("getrs", 1000, 4) == L.cf_getrs_workspace_size(1000, 4) > 0
+    assert W("potrs", 1000, 4) == 0
+    for prec in ("bf16", "f16", "bf16x3"):
+        assert W("gesv_mixed", 4096, 16, prec) == cf.gesv_mixed_workspace_size(4096, 16, prec) > 0
+        assert W("posv_mixed", 4096, 8, prec) == cf.posv_mixed_workspace_size(4096, 8, prec) > 0
+    assert W("posv_mixed", 8192, 8, "fp8") == cf.posv_mixed_workspace_size(8192, 8, "fp8") > 0
+    assert W("getrf_batched", 2000) == L.cf_getrf_batched_workspace_size(2000, ob) > 0
+    assert W("potrf_batched", 2000) == L.cf_potrf_batched_workspace_size(2000, ob)
+    assert W("factor_batched", 2000) == L.cf_factor_batched_workspace_size(2000, ob)
+    assert W("solve_batched_mixed", 2000) == L.cf_solve_batched_mixed_workspace_size(2000, ob) > 0
+    assert W("residual_pair", 3000, 16) == L.cf_residual_pair_workspace_size(3000, 3000, 16) > 0
+    assert W("tourn_select", 5000, 128) == L.cf_tourn_workspace_size(5000, 128, 128, 2) > 0
+    assert L.cf_workspace_size(99, 100, 1, 0, None) == 0
+    assert L.cf_workspace_size(0, -1, 0, 0, None) == 0
+    assert W("getrf", 100, v=200) == 0
