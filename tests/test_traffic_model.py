@@ -61,3 +61,15 @@ def test_traffic_against_bound(name, parts, kind, loads_x, hbm_x):
     assert hbm < b
     if loads_x < 2:
         assert loads < 2 * b
+
+
+def test_hbm_against_the_l2_level_bound():
+    """The same bound with the whole GPU as one processor whose fast memory
+    is the 129 MB L2 (P = 1): the HBM side's sharper yardstick."""
+    ML2 = 129e6 / 4
+    for parts, f, x in ((tm.mixed_lu(N, 2048, S=1), oracle.io_lower_bound_lu, 5.77),
+                        (tm.mixed_chol(N, 1024, S=3), oracle.io_lower_bound_chol, 8.36),
+                        (tm.mixed_chol(N, 1024, S=1), oracle.io_lower_bound_chol, 6.97)):
+        b = 4.0 * f(float(N), 1.0, ML2)
+        _, hbm = tm.totals(parts)
+        assert hbm / b == pytest.approx(x, abs=0.01)
