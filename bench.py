@@ -127,6 +127,23 @@ def _reduce_over_ranks(x: float, world: int, device, op: str = "max") -> float:
     return float(t.item())
 
 
+# two-sided 95% Student t quantiles for 1..10 degrees of freedom (1.96 beyond)
+_T95 = (12.706, 4.303, 3.182, 2.776, 2.571, 2.447, 2.365, 2.306, 2.262, 2.228)
+
+
+def _step_stats(ms):
+    """Median, min, max and mean of the per-step times with the 95%
+    confidence half-width of the mean (Student t; None for one step)."""
+    k = len(ms)
+    mean = statistics.fmean(ms)
+    ci = None
+    if k > 1:
+        t = _T95[k - 2] if k - 1 <= len(_T95) else 1.96
+        ci = t * statistics.stdev(ms) / math.sqrt(k)
+    return {"median_ms": statistics.median(ms), "min_ms": min(ms), "max_ms": max(ms), "mean_ms": mean,
+            "ci95_mean_ms": ci, "steps": k}
+
+
 def _job_tflops(world: int, flops_per_rank: float, ms_per_step: float) -> float:
     """Whole-job rate of `world` replicas, each doing flops_per_rank per step,
     timed by the slowest rank's ms_per_step."""
@@ -395,6 +412,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize()
         barrier()
     launches = cf.kernel_launches() - launches0
+    step_stats = _step_stats([a.elapsed_time(b) for a, b in per_step])
     total_ms = _reduce_over_ranks(e0.elapsed_time(e1), world, dev, "max")
     ms_step = total_ms / args.steps
     value = _job_tflops(world, lu_fl + ch_fl, ms_step)
@@ -627,7 +645,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (A is 8.6 GB per matrix)", "inputs": gen_info},
         "converged": ok, "eta": {"lu": eta_lu, "chol": eta_ch},
-        "parts": parts, "kernels": kernels,
+        "step_stats": step_stats, "parts": parts, "kernels": kernels,
         "clocks": clk.summary(),
         "e2e": e2e, "gpu_launches": launches,
         "roofline": roof, "cpu_baseline": cpu, "fp64_path": fp64, "variants": variants,

@@ -69,3 +69,11 @@ def test_job_rate_counts_every_replica(world):
     F = 2.0 * 32768 ** 3 / 3.0 + 32768 ** 3 / 3.0
     r = bench._job_tflops(world, F, 400.0)
     assert r == pytest.approx(world * F / 0.4 / 1e12, rel=1e-15)
+
+
+def test_step_stats():
+    s = bench._step_stats([380.0, 381.0, 379.5, 382.0, 380.5])
+    assert (s["median_ms"], s["min_ms"], s["max_ms"], s["steps"]) == (380.5, 379.5, 382.0, 5)
+    # t(0.975, 4) * sd / sqrt(5), sd = 0.9618...
+    assert s["ci95_mean_ms"] == pytest.approx(2.776 * 0.96176920308356 / 5 ** 0.5, rel=1e-9)
+    assert bench._step_stats([1.0])["ci95_mean_ms"] is None
