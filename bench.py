@@ -144,6 +144,21 @@ def _step_stats(ms):
             "ci95_mean_ms": ci, "steps": k}
 
 
+def _lpt_shards(costs, world: int):
+    """Longest-processing-time partition of independent jobs over `world`
+    ranks: jobs in decreasing cost, each to the least-loaded rank (ties to the
+    lowest rank).  Returns one list of job indices per rank."""
+    import heapq
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    heap = [(0.0, r) for r in range(world)]
+    shards = [[] for _ in range(world)]
+    for i in order:
+        load, r = heapq.heappop(heap)
+        shards[r].append(i)
+        heapq.heappush(heap, (load + costs[i], r))
+    return shards
+
+
 def _job_tflops(world: int, flops_per_rank: float, ms_per_step: float) -> float:
     """Whole-job rate of `world` replicas, each doing flops_per_rank per step,
     timed by the slowest rank's ms_per_step."""
@@ -227,7 +242,7 @@ def _timed(fn):
     return out, e0.elapsed_time(e1)
 
 
-def _run_variants(args, n, dev, A_lu, B_lu, A_ch, B_ch):
+def _run_variants(args, n, dev, A_lu, B_lu, A_ch, B_ch, rank=0, world=1):
     """One timed run each of the configurations the headline does not cover:
     the other 16-bit and the split-BF16 updates at N = 32768 (LU and
     Cholesky); the unshifted
@@ -285,33 +300,45 @@ def _run_variants(args, n, dev, A_lu, B_lu, A_ch, B_ch):
         out["lambda_max_est_n%d" % n2] = lam
         del A2, B2
         torch.cuda.empty_cache()
-        out["batched_20000"] = _run_batched(dev)
+        out["batched_20000"] = _run_batched(dev, rank, world)
     return out
 
 
-def _run_batched(dev):
+def _run_batched(dev, rank=0, world=1):
     """The batched configuration: 20,000 matrices, n ~ U{16..512} (numpy
     default_rng(7)), odd index LU of U[-1,1], even index Cholesky of
     G G^T / n + I (formed on the device; torch Philox seed 7); launch
     configuration from the autotuner; each call captured in a CUDA graph and
     timed as a graph replay (FP64 factorization; FP32 factors + FP64
-    refinement with one N(0,1) right-hand side per matrix)."""
+    refinement with one N(0,1) right-hand side per matrix).  With several
+    ranks the matrices are split by LPT on their flops (no exchange; each
+    rank draws its share's values with seed 7 + 1000 rank) and the time is
+    the slowest rank's."""
     import numpy as np
     import torch
     from paper_2108_09337_gb300 import cf
-    sizes = np.random.default_rng(7).integers(16, 513, 20000).tolist()
-    kinds = [0 if i % 2 else 1 for i in range(len(sizes))]
+    sizes_all = np.random.default_rng(7).integers(16, 513, 20000).tolist()
+    kinds_all = [0 if i % 2 else 1 for i in range(len(sizes_all))]
+    fl_all = sum((2.0 if k == 0 else 1.0) * n ** 3 / 3.0 for n, k in zip(sizes_all, kinds_all))
+    if world > 1:
+        costs = [(2.0 if k == 0 else 1.0) * n ** 3 for n, k in zip(sizes_all, kinds_all)]
+        shard = sorted(_lpt_shards(costs, world)[rank])
+        sizes, kinds = [sizes_all[i] for i in shard], [kinds_all[i] for i in shard]
+    else:
+        sizes, kinds = sizes_all, kinds_all
     b = cf.Batch(sizes, kinds=kinds, device=dev)
     g = torch.Generator(device=dev)
-    g.manual_seed(7)
+    g.manual_seed(7 + 1000 * rank)
     b.data.uniform_(-1.0, 1.0, generator=g)
     for i in range(len(sizes)):
         if kinds[i] == 1:
             M = b.matrix(i)
             M.copy_((M @ M.t()) / sizes[i] + torch.eye(sizes[i], device=dev, dtype=torch.float64))
     A0 = b.data.clone()
-    fl = sum((2.0 if k == 0 else 1.0) * n ** 3 / 3.0 for n, k in zip(sizes, kinds))
-    res = {"matrices": len(sizes), "flops": fl}
+    fl = fl_all
+    res = {"matrices": len(sizes_all), "flops": fl}
+    if world > 1:
+        res["matrices_this_rank"] = len(sizes)
     opt_f, ms_tf = cf.batched_autotune(b, mixed=False)
     opt_m, ms_tm = cf.batched_autotune(b, mixed=True)
     res["tuned_factor"] = {"v": opt_f.v, "ctas_per_sm": opt_f.batch_cps, "sample_ms": ms_tf}
@@ -322,6 +349,7 @@ def _run_batched(dev):
     pf.replay()                                     # warm-up
     b.data.copy_(A0)
     _, ms = _timed(pf.replay)
+    ms = _reduce_over_ranks(ms, world, dev, "max")
     res["fp64_factor_ms"] = ms
     res["fp64_factor_tflops"] = fl / (ms * 1e-3) / 1e12
     res["fp64_info_nonzero"] = int((pf.info != 0).sum().item())
@@ -332,6 +360,7 @@ def _run_batched(dev):
     pm.capture()
     pm.replay()
     _, ms = _timed(pm.replay)
+    ms = _reduce_over_ranks(ms, world, dev, "max")
     eta = pm.eta.cpu().numpy()
     res["mixed_solve_ms"] = ms
     res["mixed_solve_tflops"] = fl / (ms * 1e-3) / 1e12
@@ -619,7 +648,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     variants = None
     if not args.no_variants:
         A_lu, B_lu, A_ch, B_ch, _ = _gen_inputs(n, dev)
-        variants = _run_variants(args, n, dev, A_lu, B_lu, A_ch, B_ch)
+        variants = _run_variants(args, n, dev, A_lu, B_lu, A_ch, B_ch, rank, world)
         del A_lu, A_ch
         torch.cuda.empty_cache()
 

@@ -77,3 +77,25 @@ def test_step_stats():
     # t(0.975, 4) * sd / sqrt(5), sd = 0.9618...
     assert s["ci95_mean_ms"] == pytest.approx(2.776 * 0.96176920308356 / 5 ** 0.5, rel=1e-9)
     assert bench._step_stats([1.0])["ci95_mean_ms"] is None
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_lpt_shards_of_the_batched_configuration(world):
+    """The batched configuration shards over ranks by LPT on flops: every
+    matrix on exactly one rank, loads within 0.1% of each other."""
+    import numpy as np
+    sizes = np.random.default_rng(7).integers(16, 513, 20000).tolist()
+    kinds = [0 if i % 2 else 1 for i in range(len(sizes))]
+    costs = [(2.0 if k == 0 else 1.0) * n ** 3 for n, k in zip(sizes, kinds)]
+    shards = bench._lpt_shards(costs, world)
+    assert len(shards) == world
+    assert sorted(i for s in shards for i in s) == list(range(len(sizes)))
+    loads = [sum(costs[i] for i in s) for s in shards]
+    assert max(loads) / (sum(loads) / world) < 1.001
+    assert bench._lpt_shards(costs, world) == shards          # deterministic
+
+
+def test_lpt_shards_small_cases():
+    assert bench._lpt_shards([5.0, 4.0, 3.0, 3.0, 3.0], 2) == [[0, 3], [1, 2, 4]]
+    assert bench._lpt_shards([], 3) == [[], [], []]
+    assert bench._lpt_shards([1.0], 2) == [[0], []]
