@@ -166,6 +166,25 @@ def _job_tflops(world: int, flops_per_rank: float, ms_per_step: float) -> float:
 
 
 # ------------------------------------------------------------------ oracle
+def _host_cpu(cpuinfo: str = "/proc/cpuinfo") -> str:
+    """The host CPU as /proc/cpuinfo names it (x86 'model name'; on Arm the
+    implementer / part codes), with the logical CPU count."""
+    import platform
+    name = None
+    try:
+        fields = {}
+        for line in open(cpuinfo):
+            if ":" in line:
+                k, v = (x.strip() for x in line.split(":", 1))
+                fields.setdefault(k, v)
+        name = fields.get("model name") or fields.get("Model") or (
+            "Arm implementer %s part %s" % (fields["CPU implementer"], fields["CPU part"])
+            if "CPU implementer" in fields and "CPU part" in fields else None)
+    except OSError:
+        pass
+    return "%s, %d logical CPUs" % (name or platform.machine(), os.cpu_count() or 1)
+
+
 def _oracle_sample(n_sample: int):
     """The FP64 oracle as it stands on this host's cores: LU (v = h = 128)
     and Cholesky at n_sample with the same generators.  Returns (TFLOP/s,
@@ -203,7 +222,8 @@ def run_reference(args, rank: int):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "CPU oracle sample of the N=32768 LU/Cholesky workload", "n_sample": n_s},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "host": _host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -657,7 +677,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     cpu = None
     if not args.no_cpu:
         r, dt, threads = _oracle_sample(4096)
-        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "host": _host_cpu(),
                "sample": "FP64 oracle LU (tournament, v=h=128) + Cholesky at N=4096, same generators, "
                          "%.1f s on this host" % dt}
     line = {

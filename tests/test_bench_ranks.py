@@ -99,3 +99,13 @@ def test_lpt_shards_small_cases():
     assert bench._lpt_shards([5.0, 4.0, 3.0, 3.0, 3.0], 2) == [[0, 3], [1, 2, 4]]
     assert bench._lpt_shards([], 3) == [[], [], []]
     assert bench._lpt_shards([1.0], 2) == [[0], []]
+
+
+def test_host_cpu_names(tmp_path):
+    x86 = tmp_path / "x86"
+    x86.write_text("processor\t: 0\nmodel name\t: Some CPU @ 2.70GHz\n\nprocessor\t: 1\nmodel name\t: Some CPU\n")
+    assert bench._host_cpu(str(x86)).startswith("Some CPU @ 2.70GHz, ")
+    arm = tmp_path / "arm"
+    arm.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n")
+    assert bench._host_cpu(str(arm)).startswith("Arm implementer 0x41 part 0xd4f, ")
+    assert "logical CPUs" in bench._host_cpu(str(tmp_path / "missing"))
