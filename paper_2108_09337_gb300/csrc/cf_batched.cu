@@ -1008,9 +1008,9 @@ extern "C" int cf_batched_autotune(int batch, const int *n_host, const int *kind
     CF_CUDA_TRY(cudaMemcpyAsync(d_piv, hP.data(), sizeof(int *) * L.cnt, cudaMemcpyHostToDevice, st));
     CF_CUDA_TRY(cudaStreamSynchronize(st));                      // host vectors go out of scope below
 
-    cudaEvent_t e0, e1;
-    CF_CUDA_TRY(cudaEventCreate(&e0));
-    CF_CUDA_TRY(cudaEventCreate(&e1));
+    ScopedEvent e0, e1;
+    CF_CUDA_TRY(e0.create());
+    CF_CUDA_TRY(e1.create());
     const int vbs[3] = {8, 16, 32};
     const int maxc = mixed ? kMaxCpsMixed : kMaxCpsFactor;
     float best = -1.f;
@@ -1045,8 +1045,6 @@ extern "C" int cf_batched_autotune(int batch, const int *n_host, const int *kind
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     opt->v = best_vb;
     opt->batch_cps = best_cps;
     if (best_ms) *best_ms = best;

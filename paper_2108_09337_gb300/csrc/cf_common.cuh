@@ -33,6 +33,21 @@ void count_launches(long long n);
         CF_CUDA_TRY(cudaGetLastError()); \
     } while (0)
 
+// A CUDA event destroyed when it goes out of scope, so that every error
+// return of a host routine releases it (destroying an event still pending on
+// a stream is allowed: CUDA frees it once it completes).
+struct ScopedEvent {
+    cudaEvent_t e = nullptr;
+    ScopedEvent() = default;
+    ScopedEvent(const ScopedEvent &) = delete;
+    ScopedEvent &operator=(const ScopedEvent &) = delete;
+    ~ScopedEvent() {
+        if (e) cudaEventDestroy(e);
+    }
+    cudaError_t create(unsigned flags = cudaEventDefault) { return cudaEventCreateWithFlags(&e, flags); }
+    operator cudaEvent_t() const { return e; }
+};
+
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

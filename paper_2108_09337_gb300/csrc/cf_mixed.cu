@@ -923,10 +923,10 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     if ((rc = carve_mixed(work, n, nrhs, o, lu, &w))) return rc;
 
     cf_refine_stats S{};
-    cudaEvent_t e0, e1, e2;
-    CF_CUDA_TRY(cudaEventCreate(&e0));
-    CF_CUDA_TRY(cudaEventCreate(&e1));
-    CF_CUDA_TRY(cudaEventCreate(&e2));
+    ScopedEvent e0, e1, e2;
+    CF_CUDA_TRY(e0.create());
+    CF_CUDA_TRY(e1.create());
+    CF_CUDA_TRY(e2.create());
     CF_CUDA_TRY(cudaEventRecord(e0, st));
     CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
 
@@ -1152,9 +1152,6 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     float f_ms = 0, r_ms = 0;
     cudaEventElapsedTime(&f_ms, e0, e1);
     cudaEventElapsedTime(&r_ms, e1, e2);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
     S.iterations = it;
     S.solver = solver;
     S.escalated = escalated ? 1 : 0;
