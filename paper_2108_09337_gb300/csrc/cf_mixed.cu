@@ -599,7 +599,10 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             // A11 restricted to the slab's remaining columns (every row below)
             const int nslab = JE - (k0 + wd);
             float *C = A00 + wd + wd * ld;
-            if (nslab > 0 && (rc = launch_schur_tc(below, nslab, S * kMaxV, w.Ab, S * kMaxV, w.Bb, S * kMaxV, C,
+            // depth: the step's columns rounded up to 64 (the operands are
+            // zero past wd); the split form's three segments sit kMaxV apart
+            const int Kin = split ? S * kMaxV : (wd + 63) / 64 * 64;
+            if (nslab > 0 && (rc = launch_schur_tc(below, nslab, Kin, w.Ab, S * kMaxV, w.Bb, S * kMaxV, C,
                                                    w.ldw, bf16, false, st, 0)))
                 return rc;
         }
@@ -704,7 +707,8 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
                 if ((rc = cvt_rows_split(below, wd, kMaxV, A00 + wd, w.ldw, w.Bb, 3 * kMaxV, kMaxV, 1, st))) return rc;
                 Bop = w.Bb;
             }
-            if ((rc = launch_schur_tc(below, nslab, S * kMaxV, w.Ab, S * kMaxV, Bop, S * kMaxV, A00 + wd + wd * ld,
+            const int Kin = split ? S * kMaxV : (wd + 63) / 64 * 64;   // as in the LU
+            if ((rc = launch_schur_tc(below, nslab, Kin, w.Ab, S * kMaxV, Bop, S * kMaxV, A00 + wd + wd * ld,
                                       w.ldw, bf16, true, st, 0)))
                 return rc;
         }
