@@ -73,3 +73,28 @@ def test_cholesky_3x3():
     assert info == 0
     np.testing.assert_array_equal(L, G["l"])
     assert np.prod(np.diag(L)) ** 2 == G["det"][0]
+
+
+S = load("tournament_9x2_short_leaf.txt")
+
+
+def _sel9(rows):
+    win, _ = oracle.tourn_select(S["panel"][rows], h=int(S["h"][0]), arity=int(S["arity"][0]))
+    return [rows.start + int(i) for i in win]
+
+
+def test_short_leaf_pass_through_and_node_tie():
+    P9 = S["panel"]
+    h, ar = int(S["h"][0]), int(S["arity"][0])
+    leaves = [_sel9(slice(r, min(r + h, 9))) for r in range(0, 9, h)]
+    assert sum(leaves, []) == S["leaf_winners"].astype(int).tolist()
+    level1 = _sel9(slice(0, 4)) + _sel9(slice(4, 8)) + _sel9(slice(8, 9))
+    assert level1 == S["level1_winners"].astype(int).tolist()
+    level2 = _sel9(slice(0, 8)) + _sel9(slice(8, 9))
+    assert level2 == S["level2_winners"].astype(int).tolist()
+    win, gap = oracle.tourn_select(P9, h=h, arity=ar)
+    np.testing.assert_array_equal(win, S["root_winners"].astype(int))
+    assert gap == 0.0                                    # the exact node tie is logged
+    np.testing.assert_array_equal(ex.tourn_select(ex.to_fractions(P9), h, ar), S["root_winners"].astype(int))
+    gepp, _ = oracle.tourn_select(P9, h=9, arity=ar)
+    np.testing.assert_array_equal(gepp, S["gepp_winners"].astype(int))

@@ -63,3 +63,14 @@ def test_lu_and_cholesky_3x3(cf):
     S = dS.cpu().numpy()
     np.testing.assert_array_equal(np.tril(S), C["l"])
     np.testing.assert_array_equal(np.triu(S, 1), np.triu(C["a"], 1))   # upper triangle untouched
+
+
+def test_tournament_short_leaf_and_node_tie_fp64(cf):
+    """A short last leaf passing through two levels and an exact tie at a
+    playoff node (tests/golden/tournament_9x2_short_leaf.txt), FP64."""
+    S = load("tournament_9x2_short_leaf.txt")
+    h, ar = int(S["h"][0]), int(S["arity"][0])
+    win = cf.tourn_select(_dev(S["panel"]), leaf_h=h, arity=ar).cpu().numpy()
+    np.testing.assert_array_equal(win, S["root_winners"].astype(int))
+    win = cf.tourn_select(_dev(S["panel"]), leaf_h=9, arity=ar).cpu().numpy()
+    np.testing.assert_array_equal(win, S["gepp_winners"].astype(int))
