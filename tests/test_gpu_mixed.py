@@ -209,7 +209,8 @@ def test_gesv_mixed_workspace_error(cf):
 # ---------------------------------------------------------- LU-1 in FP32
 @pytest.mark.parametrize("m,w,h,arity", [(128, 128, 128, 2), (1000, 128, 128, 2), (777, 100, 50, 2),
                                          (5000, 128, 256, 2), (300, 17, 128, 2), (50, 128, 128, 2),
-                                         (256, 128, 256, 2), (32768, 128, 128, 2)])
+                                         (256, 128, 256, 2), (32768, 128, 128, 2),
+                                         (32768, 128, 256, 2)])
 def test_tourn_select_f32_gap_audited(cf, m, w, h, arity):
     """FP32 panel values (exact in FP64): where the FP64 oracle's gaps are all
     >= 1e-3 the FP32 elimination must pick the same rows in the same order;
@@ -288,3 +289,28 @@ def test_gesv_mixed_deep_slab(cf, prec):
     X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec=prec, outer_V=2048)
     assert st == cf.CF_OK, stats.as_dict()
     _check_solution(A, B, X.cpu().numpy())
+
+
+@pytest.mark.parametrize("solver", ["gesv", "posv"])
+def test_mixed_solve_full_size(cf, solver):
+    """The benchmark's systems at N = 32768 in the launch configuration it
+    times (LU: A = U[-1,1] + 2 sqrt(N) I, 16 right-hand sides, FP16 updates,
+    leaves of 256 rows; Cholesky: A = G G^T / N + I, 8 right-hand sides,
+    split-BF16 updates): the oracle's compensated residual over every row of
+    a host copy gives eta <= 1e-14."""
+    n = 32768
+    if solver == "gesv":
+        dA = inputs.uniform_pm1_torch(n, seed=0, shift=2.0 * np.sqrt(n), device="cuda")
+        dB = inputs.rhs_normal_torch(n, 16, seed=3, device="cuda")
+        X, info, stats, st = cf.gesv_mixed(dA, dB, prec="f16", leaf_h=256)
+    else:
+        dA = inputs.spd_gram_torch(n, seed=1, alpha=1.0, device="cuda")
+        dB = inputs.rhs_normal_torch(n, 8, seed=4, device="cuda")
+        X, info, stats, st = cf.posv_mixed(dA, dB, prec="bf16x3")
+    torch.cuda.synchronize()
+    assert st == cf.CF_OK and int(info.item()) == 0, stats.as_dict()
+    A = dA.t().cpu().numpy().T                  # column-major host copy, no second copy
+    del dA
+    torch.cuda.empty_cache()
+    eta = oracle.backward_error(A, X.cpu().numpy(), dB.cpu().numpy()).max()
+    assert eta <= 1e-14, eta
