@@ -109,3 +109,22 @@ def test_host_cpu_names(tmp_path):
     arm.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n")
     assert bench._host_cpu(str(arm)).startswith("Arm implementer 0x41 part 0xd4f, ")
     assert "logical CPUs" in bench._host_cpu(str(tmp_path / "missing"))
+
+
+def _line_keys(func_name):
+    """Keys of the dict literal assigned to `line` inside bench.<func_name>."""
+    import ast
+    tree = ast.parse(open(bench.__file__).read())
+    fn = next(n for n in tree.body if isinstance(n, ast.FunctionDef) and n.name == func_name)
+    for node in ast.walk(fn):
+        if (isinstance(node, ast.Assign) and any(isinstance(t, ast.Name) and t.id == "line" for t in node.targets)
+                and isinstance(node.value, ast.Dict)):
+            return {k.value for k in node.value.keys if isinstance(k, ast.Constant)}
+    raise AssertionError("no line = {...} in " + func_name)
+
+
+def test_bench_line_carries_the_contract_keys():
+    base = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "e2e", "cpu_baseline"}
+    assert base | {"clocks", "gpu_launches", "roofline"} <= _line_keys("run_gpu")
+    assert base | {"impl"} <= _line_keys("run_reference")
