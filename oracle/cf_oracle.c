@@ -14,10 +14,12 @@
  * (LAPACK convention).
  *
  * What each function follows:
- *   gepp_select        -- "locally perform the LUP decomposition to choose the
- *                         local v candidate rows" (Sec. 7.3, TournPivot and the
- *                         I/O-cost proof, step 2), realised as unblocked
- *                         Gaussian elimination with partial pivoting.
+ *   gepp_select        -- the local candidate choice of a tournament block:
+ *                         each block runs a pivoted LU on its own rows and
+ *                         keeps the rows it pivots on (Sec. 7.3, TournPivot,
+ *                         and step 2 of the I/O-cost proof), realised as
+ *                         unblocked Gaussian elimination with partial
+ *                         pivoting.
  *   or_tourn_select    -- TournPivot (Alg. 1 step 2, Sec. 7.3): local
  *                         candidates on every leaf, then playoff rounds on
  *                         stacked candidate blocks until v winners remain.
@@ -332,8 +334,9 @@ int or_potrf(int n, double *A, int lda, int *info, long long *n_s3)
         A[IX(k, k, lda)] = lkk;
         for (int i = k + 1; i < n; ++i)                     /* S2 */
             A[IX(i, k, lda)] = A[IX(i, k, lda)] / lkk;
-        /* S3: L(i,j) -= L(i,k) * L(j,k) for k < j <= i; the loop order over
-           (i, j) within one k does not change any element's arithmetic. */
+        /* S3: the trailing lower triangle loses the outer product of the new
+           column, a_ij - l_ik l_jk for k < j <= i; the loop order over (i, j)
+           within one k does not change any element's arithmetic. */
         #pragma omp parallel for schedule(dynamic, 16)
         for (int j = k + 1; j < n; ++j) {
             double ljk = A[IX(j, k, lda)];

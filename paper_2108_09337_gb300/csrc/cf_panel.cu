@@ -2,9 +2,9 @@
 //   LU-3  A10 <- A10 U00^{-1}      (Alg. 1 step 7, "Factorize A10"; Table 2)
 //   LU-4  A01 <- L00^{-1} A01      (Alg. 1 step 9, "Factorize A01")
 //   A00   LU without pivoting of the selected rows (S1/S2 of Fig. "prog_rep",
-//         "computed during TournPivot", Sec. 7.2)
+//         the tournament already yields it, Sec. 7.2)
 //   CH-1  potrf of A00 (Listing "Cholesky Factorization"; Table 2, v^3/6)
-//   CH-2  L10 <- A10 L00^{-T}      (Table 2, "similar to LU")
+//   CH-2  L10 <- A10 L00^{-T}      (Table 2: costed like the LU panel solve)
 //   S-1   the same triangular kernels serve the solves.
 //
 // The v x v triangle lives in shared memory; each CTA streams a chunk of

@@ -4,7 +4,7 @@
 // contiguously), FP32 accumulation in tensor memory.
 //
 // This is Alg. 1 step 11 ("Factorize A11", Table 2's local gemm) and, with
-// `lower`, COnfCHOX's triangular gemmt -- the dominant cost of both methods
+// `lower`, COnfCHOX's triangular gemmt -- where most of both methods' work lies
 // (Sec. 7.5).  Design for sm_103a:
 //   * persistent CTAs, one per SM, walking 128 x 256 output tiles;
 //   * warp 0 issues TMA loads (128-byte swizzle) into a 4-stage ring of
