@@ -128,3 +128,11 @@ def test_bench_line_carries_the_contract_keys():
             "vs_baseline", "dtype", "data", "config", "e2e", "cpu_baseline"}
     assert base | {"clocks", "gpu_launches", "roofline"} <= _line_keys("run_gpu")
     assert base | {"impl"} <= _line_keys("run_reference")
+
+
+def test_forward_error_helper():
+    import torch
+    Xr = torch.tensor([[1.0, -4.0], [2.0, 1.0]], dtype=torch.float64)
+    X = Xr + torch.tensor([[1e-12, 0.0], [0.0, 2e-12]], dtype=torch.float64)
+    # column 0: 1e-12 / 2, column 1: 2e-12 / 4
+    assert bench._fwd_err(X, Xr) == pytest.approx(5e-13, rel=1e-9)
