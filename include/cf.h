@@ -199,7 +199,13 @@ int cf_getrf(int n, double *A, int lda, int *ipiv, int *info, void *work,
  *     capture on that device.
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (other streams, other host threads) race and corrupt each other.  The
- *     arrival counters are cleared at the start of every call. */
+ *     arrival counters are cleared at the start of every call.
+ *   - It always runs the one-stream schedule on `stream` (opt->lookahead is
+ *     ignored): the results equal cf_getrf's, the speed is that of cf_getrf
+ *     with lookahead = 0.
+ *   - The looked-up address is kept for the life of the process: after a
+ *     cudaDeviceReset (or anything else that destroys the device's primary
+ *     context) the next call on that device is invalid. */
 int cf_getrf_noalloc(int n, double *A, int lda, int *ipiv, int *info,
                      const cf_options *opt, cudaStream_t stream);
 

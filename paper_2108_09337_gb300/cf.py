@@ -231,12 +231,16 @@ def getrf_noalloc(A: torch.Tensor, v=None, leaf_h=None, arity=None, ipiv=None, i
     in so that the call itself allocates nothing."""
     assert A.dtype == torch.float64
     n = A.shape[0]
+    assert A.shape == (n, n)
     lda = _ld(A, "A")
     opt = options(v=v, leaf_h=leaf_h, arity=arity)
     if ipiv is None:
         ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
     if info is None:
         info = torch.zeros(1, dtype=torch.int32, device=A.device)
+    # the C ABI writes n int32 pivots and one int32 info through these
+    assert ipiv.dtype == torch.int32 and ipiv.device == A.device and ipiv.is_contiguous() and ipiv.numel() >= n
+    assert info.dtype == torch.int32 and info.device == A.device and info.numel() >= 1
     _check("cf_getrf_noalloc", _lib.cf_getrf_noalloc(n, _ptr(A), lda, _ptr(ipiv), _ptr(info),
                                                      ctypes.byref(opt), _stream()))
     return ipiv[:n], info

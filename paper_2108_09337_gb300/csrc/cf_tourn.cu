@@ -391,11 +391,9 @@ template <typename T, int CL>
 static int launch_tourn_cl(const T *P, int ldp, const TournPlan &plan, const TournWS &ws, const TournEpilogue &ep,
                            cudaStream_t st) {
     const size_t smem = sizeof(TournSmem<T>);
-    static bool attr_done = false;   // per instantiation; idempotent anyway
-    if (!attr_done) {
-        CF_CUDA_TRY(cudaFuncSetAttribute(k_tourn<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_done = true;
-    }
+    // The attribute belongs to the current device: set it on every call (a
+    // flag kept per process would skip it on the second device).
+    CF_CUDA_TRY(cudaFuncSetAttribute(k_tourn<T, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nclusters = ceil_div(plan.nleaves, CL);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nclusters * CL);

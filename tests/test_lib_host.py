@@ -119,3 +119,22 @@ def test_generic_workspace_query_matches_each_call(lib):
     assert L.cf_workspace_size(99, 100, 1, 0, None) == 0
     assert L.cf_workspace_size(0, -1, 0, 0, None) == 0
     assert W("getrf", 100, v=200) == 0
+
+
+def test_noalloc_scratch_limit_matches_documented_sizes(lib):
+    """cf_getrf_noalloc keeps its scratch in a fixed 2 MiB array and needs
+    exactly cf_getrf's workspace: n = 131072 fits with leaf_h = 128 and
+    65536 with leaf_h = 64, twice those sizes do not."""
+    from paper_2108_09337_gb300 import cf
+    lib.cf_getrf_workspace_size.restype = ctypes.c_size_t
+    lib.cf_getrf_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p]
+    limit = 2 << 20
+
+    def need(n, h):
+        o = cf.options(leaf_h=h)
+        return lib.cf_getrf_workspace_size(n, ctypes.cast(ctypes.byref(o), ctypes.c_void_p))
+
+    assert 0 < need(131072, 128) <= limit
+    assert need(262144, 128) > limit
+    assert 0 < need(65536, 64) <= limit
+    assert need(131072, 64) > limit
