@@ -170,6 +170,27 @@ def spd_gram_torch(n: int, seed: int = 1, alpha: float = 1.0, device="cuda"):
     return C.t()  # symmetric: the column-major view holds the same matrix
 
 
+def shift_to_kappa_torch(A, kappa: float, iters: int = 30, seed: int = 5):
+    """Adds alpha I to the symmetric positive semi-definite A (in place) with
+    alpha = lambda_max / (kappa - 1), lambda_max estimated by ``iters`` power
+    iterations from a seeded N(0, 1) start, so that A + alpha I has condition
+    number about kappa when lambda_min(A) ~ 0 (the Gram matrix of a square G).
+    Returns (alpha, lambda_max estimate)."""
+    import torch
+    n = A.shape[0]
+    g = torch.Generator(device=A.device)
+    g.manual_seed(seed)
+    x = torch.randn(n, 1, generator=g, device=A.device, dtype=torch.float64)
+    lam = 0.0
+    for _ in range(iters):
+        y = A @ x
+        lam = float(torch.linalg.vector_norm(y) / torch.linalg.vector_norm(x))
+        x = y / torch.linalg.vector_norm(y)
+    alpha = lam / (kappa - 1.0)
+    A.diagonal().add_(alpha)
+    return alpha, lam
+
+
 def rhs_normal_torch(n: int, nrhs: int, seed: int = 2, device="cuda"):
     import torch
     g = torch.Generator(device=device)

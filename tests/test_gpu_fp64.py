@@ -385,3 +385,70 @@ def test_lookahead_bit_identical(cf, n):
         out[la] = (dA.cpu().numpy(), ipiv.cpu().numpy(), np.tril(dS.cpu().numpy()))
     for a, b in zip(out[0], out[1]):
         np.testing.assert_array_equal(a, b)
+
+
+# ------------------------------------------ config 2 (paper-like sizes)
+def _projection_lu(A, LU, ip):
+    """oracle.lu_random_projection_error for P A = L U on host copies."""
+    n = A.shape[0]
+    p = oracle.perm_from_ipiv(ip, n)
+    Ls = np.tril(LU, -1)
+    U = np.triu(LU)
+    return oracle.lu_random_projection_error(lambda Z: A[p] @ Z, lambda Z: Ls @ Z + Z, lambda Z: U @ Z, n,
+                                             np.linalg.norm(A, "fro"))
+
+
+def _projection_chol(S, L):
+    n = S.shape[0]
+    return oracle.lu_random_projection_error(lambda Z: S @ Z, lambda Z: L @ Z, lambda Z: L.T @ Z, n,
+                                             np.linalg.norm(S, "fro"))
+
+
+@pytest.mark.parametrize("n", [8192])
+def test_config2_fp64_lu_cholesky(cf, n):
+    """The FP64 path at a paper-like size, look-ahead on (LU of U[-1,1] seed 0,
+    Cholesky of G G^T / N + I seed 1, one N(0,1) right-hand side seed 2),
+    checked on host copies by the oracle: the first panel's pivots equal the
+    oracle's selection on the same panel bytes; the probabilistic factorization
+    residual max_z ||(P A - L U) z|| / (||A||_F ||z||) over 4 random z is
+    <= 20 n u (stated as such: the full ||P A - L U|| is O(n^3) on the host at
+    this size); eta of the getrs / potrs solution by the oracle's compensated
+    residual is <= 20 n u."""
+    A = inputs.uniform_pm1(n, seed=0)
+    b = inputs.rhs_normal(n, 1, seed=2)
+    dA = _dev(A)
+    win, _ = oracle.tourn_select(A[:, :128], h=128, arity=2)
+    ipiv, info = cf.getrf(dA, lookahead=1)
+    db = _dev(b)
+    cf.getrs(dA, ipiv, db)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    LU, ip, x = _host(dA), ipiv.cpu().numpy(), _host(db)
+    del dA
+    # LAPACK interchanges of step 0 from the oracle's winners (original panel
+    # rows in pivot order): winner j moves from its current position q to j
+    at, where = np.arange(n), np.arange(n)     # row at each position, and its inverse
+    ip0 = np.zeros(128, dtype=np.int64)
+    for j, r in enumerate(win):
+        q = where[r]
+        ip0[j] = q + 1
+        rj = at[j]
+        at[j], at[q] = r, rj
+        where[r], where[rj] = j, q
+    np.testing.assert_array_equal(ip[:128], ip0)
+    bound = 20 * n * oracle.EPS
+    assert _projection_lu(A, LU, ip) <= bound
+    assert oracle.backward_error(A, x, b).max() <= bound
+    del LU
+
+    S = inputs.spd_gram(n, seed=1)
+    dS = _dev(S)
+    info = cf.potrf(dS, lookahead=1)
+    db = _dev(b)
+    cf.potrs(dS, db)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    L = np.tril(_host(dS))
+    del dS
+    assert _projection_chol(S, L) <= bound
+    assert oracle.backward_error(S, _host(db), b).max() <= bound
