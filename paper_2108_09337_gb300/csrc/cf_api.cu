@@ -41,8 +41,10 @@ int resolve_options(const cf_options *in, Opts *o) {
     o->fp64_residual = in->fp64_residual;
     if (o->fp64_residual < 0 || o->fp64_residual > 1) return CF_ERR_UNSUPPORTED;
     if (o->v < 1 || o->v > kMaxV) return CF_ERR_UNSUPPORTED;
-    if (o->leaf_h < 1 || o->leaf_h > 2 * kMaxV) return CF_ERR_UNSUPPORTED;   // FP64 tournament: <= kMaxV
-    if (o->arity < 2 || o->arity > 4) return CF_ERR_UNSUPPORTED;
+    // the widest shapes any routine takes (FP32 tournament at v <= 64); each
+    // routine checks its own narrower limits (FP64: leaf_h <= kMaxV, arity <= 4)
+    if (o->leaf_h < 1 || o->leaf_h > 4 * kMaxV) return CF_ERR_UNSUPPORTED;
+    if (o->arity < 2 || o->arity > 8) return CF_ERR_UNSUPPORTED;
     if (o->outer_V < 0 || (o->outer_V % o->v) != 0) return CF_ERR_UNSUPPORTED;
     if (o->gmres_restart < 1 || o->gmres_restart > 256) return CF_ERR_UNSUPPORTED;
     if (o->batch_cps < 0 || o->batch_cps > 8) return CF_ERR_UNSUPPORTED;
@@ -135,7 +137,7 @@ extern "C" size_t cf_workspace_size(int op, int n, int nrhs, cf_prec prec, const
 
 extern "C" size_t cf_getrf_workspace_size(int n, const cf_options *opt) {
     Opts o;
-    if (resolve_options(opt, &o) != CF_OK || o.leaf_h > kMaxV) return 0;   // FP64 leaves: <= kMaxV rows
+    if (resolve_options(opt, &o) != CF_OK || !fp64_tourn_shape(o)) return 0;
     return tourn_ws_bytes(n > 0 ? n : 1, o.leaf_h, o.arity);
 }
 
@@ -276,7 +278,7 @@ extern "C" int cf_getrf(int n, double *A, int lda, int *ipiv, int *info, void *w
     Opts o;
     int rc = resolve_options(opt, &o);
     if (rc != CF_OK) return rc;
-    if (o.leaf_h > kMaxV) return CF_ERR_UNSUPPORTED;     // FP64 leaves: <= kMaxV rows
+    if (!fp64_tourn_shape(o)) return CF_ERR_UNSUPPORTED;
     CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
     if (n == 0) return CF_OK;
     if (work == nullptr || lwork < cf_getrf_workspace_size(n, opt)) return CF_ERR_WORKSPACE;

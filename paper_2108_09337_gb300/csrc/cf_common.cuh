@@ -77,6 +77,13 @@ struct Opts {
 };
 // Returns 0 or a negative status for an out-of-range field.
 int resolve_options(const cf_options *in, Opts *out);
+// Tournament shapes of the FP64 routines: leaves of at most kMaxV rows,
+// arity 2..4 (one cluster of `arity` CTAs per playoff node).
+inline bool fp64_tourn_shape(const Opts &o) { return o.leaf_h <= kMaxV && o.arity <= 4; }
+// Tournament shapes of the mixed-precision LU (FP32 panels): v <= 64 with
+// leaves of up to 512 rows and arity up to 8 (arity * v <= 512), or
+// v <= 128 with leaves of up to 256 rows and arity 2.
+bool tourn32_shape_ok(int v, int h, int arity);
 
 // Exactly rounded product and difference (no FMA contraction), so that the
 // tournament, the diagonal-block factorization and the panel solves round

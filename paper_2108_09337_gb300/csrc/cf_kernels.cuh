@@ -82,6 +82,15 @@ int launch_trsm_left(bool lower, bool unit, bool trans, T *X, int ldx, int w, in
 // ---- FP32 panel kernels of the mixed path (cf_tourn32.cu, cf_panel32.cu)
 int launch_tourn32(const float *P, int ldp, int m, int w, int h, int arity, const TournWS &ws, const TournEpilogue &ep,
                    cudaStream_t st);
+// The same rule for panels of w <= 64 columns: leaves of up to 512 rows,
+// arity up to 8 (cf_tourn32w.cu).
+bool tourn32w_supported(int w, int h, int arity);
+int launch_tourn32w(const float *P, int ldp, int m, int w, int h, int arity, const TournWS &ws,
+                    const TournEpilogue &ep, cudaStream_t st);
+// Either FP32 tournament: the wide-node kernel for panels of <= 64 columns
+// when it takes (h, arity), else the v <= 128 kernel (h <= 256, arity 2).
+int launch_tourn32_any(const float *P, int ldp, int m, int w, int h, int arity, const TournWS &ws,
+                       const TournEpilogue &ep, cudaStream_t st);
 int launch_a00_lu32(float *A00, int lda, int w, int kglob, int *info, cudaStream_t st);
 int launch_a00_chol32(float *A00, int lda, int w, int kglob, int *info, cudaStream_t st);
 template <typename LP>
@@ -111,7 +120,7 @@ int trsv_take_status(cudaStream_t st, int *status);
 // itself into the workspace.
 size_t pair_residual_ws_bytes(int m, int n);
 // Elimination flops of one FP32 tournament (cf_tourn32.cu).
-double tourn32_flops(int m, int w, int h);
+double tourn32_flops(int m, int w, int h, int arity = 2);
 int launch_residual_pair(int m, int n, int nrhs, const double *A, int lda, const unsigned long long *amax,
                          const double *X, int ldx, const double *B, int ldb, double *R, int ldr, void *ws,
                          cudaStream_t st);

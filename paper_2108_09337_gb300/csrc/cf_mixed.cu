@@ -528,8 +528,8 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             w.tep.ipiv = w.ipiv;
             w.tep.k0 = k0;
             if (tt && (rc = tt->begin(st))) return rc;
-            if ((rc = launch_tourn32(A00, w.ldw, m, wd, o.leaf_h, o.arity, w.tws, w.tep, st))) return rc;
-            if (tt && (rc = tt->end(st, tourn32_flops(m, wd, o.leaf_h)))) return rc;
+            if ((rc = launch_tourn32_any(A00, w.ldw, m, wd, o.leaf_h, o.arity, w.tws, w.tep, st))) return rc;
+            if (tt && (rc = tt->end(st, tourn32_flops(m, wd, o.leaf_h, o.arity)))) return rc;
             if ((rc = launch_apply_swaps<float>(W, w.ldw, n, k0, w.tep, w.perm, st))) return rc;
             // Fork: the side stream takes the pivot rows' left-looking update
             // (concurrent with the A00 LU) and LU-4 with its operand copies
@@ -1200,6 +1200,7 @@ static size_t mixed_ws_size(int n, int nrhs, cf_prec prec, const cf_options *opt
     (void)prec;
     Opts o;
     if (resolve_options(opt, &o) != CF_OK) return 0;
+    if (lu && !tourn32_shape_ok(o.v, o.leaf_h, o.arity)) return 0;
     MixedWS w;
     if (carve_mixed(nullptr, n > 0 ? n : 1, nrhs > 0 ? nrhs : 1, o, lu, &w) != CF_OK) return 0;
     return w.bytes;
@@ -1212,6 +1213,7 @@ static int mixed_entry(int n, int nrhs, const double *A, int lda, const double *
     if (rc) return rc;
     Opts o;
     if ((rc = resolve_options(opt, &o))) return rc;
+    if (lu && !tourn32_shape_ok(o.v, o.leaf_h, o.arity)) return CF_ERR_UNSUPPORTED;
     if (n == 0 || nrhs == 0) {
         if (stats) { memset(stats, 0, sizeof(*stats)); stats->converged = 1; }
         return CF_OK;

@@ -55,7 +55,7 @@ extern "C" int cf_getrf_noalloc(int n, double *A, int lda, int *ipiv, int *info,
     Opts o;
     int rc = resolve_options(opt, &o);
     if (rc != CF_OK) return rc;
-    if (o.leaf_h > kMaxV) return CF_ERR_UNSUPPORTED;     // FP64 leaves: <= kMaxV rows
+    if (!fp64_tourn_shape(o)) return CF_ERR_UNSUPPORTED;
     // Size check first: it needs no device and touches no memory.
     if (n > 0 && tourn_ws_bytes(n, o.leaf_h, o.arity) > kNoAllocScratchBytes) return CF_ERR_WORKSPACE;
     void *scratch = nullptr;

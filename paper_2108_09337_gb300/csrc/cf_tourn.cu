@@ -338,7 +338,7 @@ k_apply_swaps(T *__restrict__ A, int lda, int ncols, int k0, const int *swap_cnt
 // Host side
 // ---------------------------------------------------------------------------
 int make_tourn_plan(int m, int w, int h, int arity, TournPlan *plan) {
-    if (m < 0 || w < 0 || w > kMaxV || h < 1 || h > 2 * kMaxV || arity < 2 || arity > 4) return CF_ERR_UNSUPPORTED;
+    if (m < 0 || w < 0 || w > kMaxV || h < 1 || h > 4 * kMaxV || arity < 2 || arity > 8) return CF_ERR_UNSUPPORTED;
     TournPlan p{};
     p.m = m; p.w = w; p.h = h; p.arity = arity;
     p.nleaves = m > 0 ? ceil_div(m, h) : 0;
@@ -453,6 +453,7 @@ template int launch_apply_swaps<float>(float *, int, int, int, const TournEpilog
 extern "C" size_t cf_tourn_workspace_size(int m, int w, int leaf_h, int arity) {
     (void)w;
     (void)leaf_h;   // sized for the most leaves (h = 1), valid for every leaf height
+    if (arity > 8) return 0;
     return cf::tourn_ws_bytes(m > 0 ? m : 1, 1, arity < 2 ? 2 : arity);
 }
 

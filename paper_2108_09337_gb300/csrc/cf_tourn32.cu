@@ -355,9 +355,10 @@ k_tourn32(const float *__restrict__ P, int ldp, TournPlan plan, TournWS ws, Tour
 }
 
 // Elimination flops of one FP32 tournament (m x w panel, leaves of h rows,
-// binary tree): per GEPP on r rows x w columns, sum_j (r-j-1)(2(w-j-1) + 1)
-// for j < min(r, w); nodes with one child pass their winners through.
-double tourn32_flops(int m, int w, int h) {
+// `arity` children per playoff node): per GEPP on r rows x w columns,
+// sum_j (r-j-1)(2(w-j-1) + 1) for j < min(r, w); nodes with one child pass
+// their winners through.
+double tourn32_flops(int m, int w, int h, int arity) {
     auto gepp = [w](int r) {
         double f = 0.0;
         const int p = r < w ? r : w;
@@ -372,17 +373,31 @@ double tourn32_flops(int m, int w, int h) {
         f += gepp(r);
         cnt.push_back(r < w ? r : w);
     }
+    if (arity < 2) arity = 2;
     while (cnt.size() > 1) {
         std::vector<int> up;
-        for (size_t i = 0; i < cnt.size(); i += 2) {
-            if (i + 1 == cnt.size()) { up.push_back(cnt[i]); continue; }
-            const int r = cnt[i] + cnt[i + 1];
+        for (size_t i = 0; i < cnt.size(); i += arity) {
+            const size_t e = i + arity < cnt.size() ? i + arity : cnt.size();
+            if (e - i == 1) { up.push_back(cnt[i]); continue; }
+            int r = 0;
+            for (size_t c = i; c < e; ++c) r += cnt[c];
             f += gepp(r);
             up.push_back(r < w ? r : w);
         }
         cnt.swap(up);
     }
     return f;
+}
+
+bool tourn32_shape_ok(int v, int h, int arity) {
+    if (v <= 64) return tourn32w_supported(v, h, arity);
+    return v <= kMaxV && h >= 1 && h <= kT2 && arity == 2;
+}
+
+int launch_tourn32_any(const float *P, int ldp, int m, int w, int h, int arity, const TournWS &ws,
+                       const TournEpilogue &ep, cudaStream_t st) {
+    if (w <= 64 && tourn32w_supported(w, h, arity)) return launch_tourn32w(P, ldp, m, w, h, arity, ws, ep, st);
+    return launch_tourn32(P, ldp, m, w, h, arity, ws, ep, st);
 }
 
 int launch_tourn32(const float *P, int ldp, int m, int w, int h, int arity, const TournWS &ws, const TournEpilogue &ep,
@@ -415,8 +430,8 @@ extern "C" int cf_tourn_select_f32(int m, int w, const float *panel, int ldp, in
     if (w < 0 || w > kMaxV) return -2;
     if (m > 0 && w > 0 && panel == nullptr) return -3;
     if (ldp < (m > 1 ? m : 1)) return -4;
-    if (leaf_h < 1 || leaf_h > 256) return -5;
-    if (arity != 2) return -6;
+    if (leaf_h < 1 || leaf_h > (w <= 64 ? 512 : kT2)) return -5;
+    if (arity < 2 || arity > (w <= 64 ? 8 : 2) || (w <= 64 && !tourn32w_supported(w, leaf_h, arity))) return -6;
     if (m == 0 || w == 0) return CF_OK;
     if (winners == nullptr) return -7;
     if (lwork < cf_tourn_workspace_size(m, w, 1, arity) || work == nullptr) return CF_ERR_WORKSPACE;
@@ -427,5 +442,5 @@ extern "C" int cf_tourn_select_f32(int m, int w, const float *panel, int ldp, in
     ep.ipiv = nullptr;
     CF_CUDA_TRY(cudaMemsetAsync(ws.counter, 0, ws.counter_bytes, stream));
     ws.root_win = winners;
-    return launch_tourn32(panel, ldp, m, w, leaf_h, arity, ws, ep, stream);
+    return launch_tourn32_any(panel, ldp, m, w, leaf_h, arity, ws, ep, stream);
 }

@@ -129,6 +129,32 @@ def prescribed_cond(n: int, cond: float, seed: int, spd: bool = False) -> np.nda
     return np.asfortranarray(A)
 
 
+def typed_panel(m: int, w: int, seed: int, eps: float = 1e-4, ratio: float = 1.004) -> np.ndarray:
+    """An m x w panel (m a multiple of w) on which every argmax of tournament
+    pivoting is separated by about ratio - 1 (relative), whatever the leaf
+    height (a multiple of w) and the arity.  Each block of w consecutive rows
+    holds one row of every "type" j < w (in shuffled order); a row of type j
+    has one entry of magnitude in [1, ratio^(m/w)) at column j (random sign;
+    the values of a type are distinct powers of ratio, shuffled) and entries
+    of magnitude <= eps elsewhere.  Eliminating with a pivot of type j' moves
+    the other rows' entries by O(eps) at most, so column j of every leaf or
+    playoff node picks its largest row of type j, which beats the next one by
+    a factor ratio and every other row by about 1/eps.  Entries are rounded
+    to float32 (exact in both precisions)."""
+    assert m % w == 0
+    rng = _rng(seed)
+    P = eps * (2.0 * rng.random((m, w)) - 1.0)
+    nper = m // w
+    types = np.concatenate([rng.permutation(w) for _ in range(nper)])
+    mags = np.empty(m)
+    for j in range(w):
+        rows = np.nonzero(types == j)[0]
+        mags[rows] = ratio ** rng.permutation(nper)
+    sign = np.where(rng.random(m) < 0.5, -1.0, 1.0)
+    P[np.arange(m), types] = sign * mags
+    return np.asfortranarray(P.astype(np.float32).astype(np.float64))
+
+
 def uniform_pm1_torch(n: int, seed: int = 0, shift: float = 0.0,
                       device="cuda", dtype=None):
     import torch

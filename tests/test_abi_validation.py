@@ -24,7 +24,7 @@ CASES = {
     "cf_tourn_select": ((100, 8, P, 100, 16, 2, P, P, BIG, None),
                         [(1, -1), (2, -1), (2, 129), (3, None), (4, 99), (5, 0), (5, 129), (6, 1), (6, 5), (7, None)]),
     "cf_tourn_select_f32": ((100, 8, P, 100, 16, 2, P, P, BIG, None),
-                            [(1, -1), (2, 129), (3, None), (4, 99), (5, 0), (5, 257), (6, 3), (7, None)]),
+                            [(1, -1), (2, 129), (3, None), (4, 99), (5, 0), (5, 513), (6, 1), (6, 9), (7, None)]),
     "cf_getrf": ((8, P, 8, P, P, P, BIG, None, None),
                  [(1, -1), (2, None), (3, 7), (4, None), (5, None)]),
     "cf_getrf_noalloc": ((8, P, 8, P, P, None, None),
@@ -98,13 +98,30 @@ def test_autotune_argument_checks():
 
 def test_bad_options_are_unsupported_before_any_cuda_call():
     # (a zero in v, leaf_h, arity, tol, max_iter or gmres_restart selects its default)
-    for kw in ({"v": -1}, {"v": 129}, {"leaf_h": -1}, {"leaf_h": 257}, {"arity": 1}, {"arity": 5},
+    for kw in ({"v": -1}, {"v": 129}, {"leaf_h": -1}, {"leaf_h": 513}, {"arity": 1}, {"arity": 9},
                {"outer_V": 100}, {"outer_V": -128}, {"gmres_restart": 257}, {"batch_cps": 9}, {"batch_cps": -1},
                {"fp64_residual": 2}, {"fp64_residual": -1}):
         assert L.cf_getrf(8, P, 8, P, P, P, BIG, _opt(**kw), None) == cf.CF_ERR_UNSUPPORTED, kw
         assert L.cf_potrf(8, P, 8, P, P, BIG, _opt(**kw), None) == cf.CF_ERR_UNSUPPORTED, kw
         assert L.cf_gesv_mixed(8, 2, P, 8, P, 8, P, 8, 3, P, None, P, BIG, _opt(**kw), None) == \
             cf.CF_ERR_UNSUPPORTED, kw
+
+
+def test_tournament_shapes_per_routine():
+    # FP64 routines: leaves <= 128 rows, arity <= 4; the mixed LU: v = 128
+    # with leaves <= 256 and arity 2, or v <= 64 with leaves <= 512 and
+    # arity * v <= 512
+    for kw in ({"arity": 5}, {"leaf_h": 129}):
+        assert L.cf_getrf(8, P, 8, P, P, P, BIG, _opt(**kw), None) == cf.CF_ERR_UNSUPPORTED, kw
+        assert L.cf_getrf_noalloc(8, P, 8, P, P, _opt(**kw), None) == cf.CF_ERR_UNSUPPORTED, kw
+        assert L.cf_getrf_workspace_size(1000, _opt(**kw)) == 0, kw
+    for kw in ({"leaf_h": 257}, {"arity": 3}, {"v": 80, "leaf_h": 300}, {"v": 64, "arity": 8, "leaf_h": 513}):
+        assert L.cf_gesv_mixed(8, 2, P, 8, P, 8, P, 8, 3, P, None, P, BIG, _opt(**kw), None) == \
+            cf.CF_ERR_UNSUPPORTED, kw
+        assert cf.gesv_mixed_workspace_size(1000, 1, "f16", **kw) == 0, kw
+    assert cf.gesv_mixed_workspace_size(1000, 1, "f16", v=64, leaf_h=512, arity=8) > 0
+    assert cf.gesv_mixed_workspace_size(1000, 1, "f16", v=32, leaf_h=512, arity=16) == 0
+    assert cf.posv_mixed_workspace_size(1000, 1, "f16", leaf_h=512, arity=8) > 0   # no tournament
 
 
 def test_fp64_leaves_at_most_128_rows():

@@ -225,6 +225,66 @@ def test_tourn_select_f32_gap_audited(cf, m, w, h, arity):
         np.testing.assert_array_equal(win, win_o)
 
 
+# The wide-node FP32 tournament (panels of <= 64 columns: leaves of up to 512
+# rows, arity up to 8).  Random panels whose FP64-oracle gaps are all >= 1e-3
+# (seeds found by a CPU search of inputs.uniform_pm1(m, seed=1000 s + m + 7 w,
+# m=w)), which exercise the elimination arithmetic at every node.
+@pytest.mark.parametrize("m,w,h,arity,s", [(512, 64, 512, 8, 7), (513, 64, 512, 8, 2), (1024, 64, 512, 2, 27),
+                                           (1100, 64, 512, 3, 100), (700, 64, 100, 4, 149),
+                                           (2048, 32, 256, 8, 46)])
+def test_tourn_select_f32_wide_gap_audited(cf, m, w, h, arity, s):
+    P = inputs.uniform_pm1(m, seed=1000 * s + m + 7 * w, m=w).astype(np.float32).astype(np.float64)
+    win_o, gap = oracle.tourn_select(P, h=h, arity=arity)
+    assert gap >= 1e-3
+    dP = torch.from_numpy(np.ascontiguousarray(P.T.astype(np.float32))).cuda().t()
+    win = cf.tourn_select(dP, leaf_h=h, arity=arity).cpu().numpy()
+    np.testing.assert_array_equal(win, win_o)
+
+
+@pytest.mark.parametrize("m,w,h,arity", [(32768, 64, 512, 8), (40000, 64, 512, 8), (32768, 64, 256, 4),
+                                         (6400, 64, 512, 5), (4096, 64, 128, 4), (2048, 16, 256, 8),
+                                         (32768, 64, 512, 2)])
+def test_tourn_select_f32_wide_typed_panels(cf, m, w, h, arity):
+    """Up to 40000 rows (79 leaves of 512, three playoff levels at arity 8,
+    the last leaf 64 rows) on panels built so that every argmax is separated
+    by 0.4% (inputs.typed_panel, audited by the oracle's gap log): the FP32
+    selection must equal the oracle's."""
+    P = inputs.typed_panel(m, w, seed=m + arity)
+    win_o, gap = oracle.tourn_select(P, h=h, arity=arity)
+    assert gap >= 1e-3
+    dP = torch.from_numpy(np.ascontiguousarray(P.T.astype(np.float32))).cuda().t()
+    win = cf.tourn_select(dP, leaf_h=h, arity=arity).cpu().numpy()
+    np.testing.assert_array_equal(win, win_o)
+
+
+@pytest.mark.parametrize("m,w,h,arity", [(32768, 64, 512, 8), (9999, 61, 333, 7), (300, 64, 512, 8),
+                                         (5000, 1, 512, 8), (64, 64, 512, 8)])
+def test_tourn_select_f32_wide_valid(cf, m, w, h, arity):
+    """Random panels (gaps below 1e-3 somewhere): min(m, w) distinct rows."""
+    P = inputs.uniform_pm1(m, seed=m + w, m=w)
+    dP = torch.from_numpy(np.ascontiguousarray(P.T.astype(np.float32))).cuda().t()
+    win = cf.tourn_select(dP, leaf_h=h, arity=arity).cpu().numpy()
+    assert len(win) == min(m, w) and len(set(win.tolist())) == len(win)
+    assert win.min() >= 0 and win.max() < m
+    if m <= h:                       # a single leaf: GEPP; its first pivot is the column maximum
+        assert abs(P[win[0], 0]) == np.abs(P[:, 0].astype(np.float32)).max()
+
+
+def test_tourn_select_f32_wide_ties_zeros_nan(cf):
+    """The wide kernel on exact-arithmetic panels with ties, zero columns and
+    a NaN (as below, at arity 5 and 8 and leaves of 100 / 512 rows)."""
+    P = np.zeros((1300, 8))
+    P[::3, :] = 1.0
+    P[7, 0] = -1.0
+    P[5, 0] = np.nan
+    P[900, 3] = 2.0
+    dP = torch.from_numpy(np.ascontiguousarray(P.T.astype(np.float32))).cuda().t()
+    for h, arity in ((100, 5), (512, 8), (16, 8)):
+        win_o, _ = oracle.tourn_select(P, h=h, arity=arity)
+        win = cf.tourn_select(dP, leaf_h=h, arity=arity).cpu().numpy()
+        np.testing.assert_array_equal(win, win_o)
+
+
 def test_tourn_select_f32_ties_zeros_nan(cf):
     """Exact ties (ties to the smallest stacked row), zero columns and a NaN
     (ranks below every number) in FP32, with values whose elimination is
@@ -289,6 +349,42 @@ def test_gesv_mixed_deep_slab(cf, prec):
     X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec=prec, outer_V=2048)
     assert st == cf.CF_OK, stats.as_dict()
     _check_solution(A, B, X.cpu().numpy())
+
+
+WIDE = dict(v=64, leaf_h=512, arity=8)
+
+
+@pytest.mark.parametrize("prec,n,V,shift", [("f16", 2048, 0, True), ("bf16", 1000, 256, True),
+                                            ("f16", 777, 128, True), ("bf16x3", 4500, 2048, True),
+                                            ("f16", 4500, 2048, True), ("bf16x3", 2048, 0, False),
+                                            ("f16", 65, 64, True)])
+def test_gesv_mixed_wide_tournament(cf, prec, n, V, shift):
+    """The mixed LU at block size v = 64 with the wide-node tournament (leaves
+    of 512 rows, arity 8): shifted and unshifted uniform matrices (the
+    unshifted one hands over to GMRES-IR), deep and ragged slabs, reach
+    eta <= 1e-14; A and B come back unchanged."""
+    A = inputs.uniform_pm1(n, seed=n + 1, shift=2 * np.sqrt(n) if shift else 0.0)
+    B = inputs.rhs_normal(n, 5, seed=6)
+    dA, dB = _dev(A), _dev(B)
+    X, info, stats, st = cf.gesv_mixed(dA, dB, prec=prec, outer_V=V, **WIDE)
+    assert st == cf.CF_OK and int(info.item()) == 0, stats.as_dict()
+    np.testing.assert_array_equal(dA.cpu().numpy(), A)
+    np.testing.assert_array_equal(dB.cpu().numpy(), B)
+    _check_solution(A, B, X.cpu().numpy())
+
+
+def test_gesv_mixed_shape_checks(cf):
+    """Tournament shapes the mixed LU cannot run are refused before any work
+    (v = 128 takes arity 2 and leaves <= 256; v <= 64 takes arity * v <= 512)."""
+    A = _dev(inputs.uniform_pm1(64, seed=1, shift=16.0))
+    B = _dev(inputs.rhs_normal(64, 1))
+    for kw in (dict(v=128, arity=3), dict(v=128, leaf_h=512), dict(v=64, arity=8, leaf_h=513),
+               dict(v=96, arity=2, leaf_h=300)):
+        with pytest.raises(cf.CfError) as e:
+            cf.gesv_mixed(A, B, **kw)
+        assert e.value.status == cf.CF_ERR_UNSUPPORTED, kw
+    assert cf.gesv_mixed_workspace_size(64, 1, "f16", v=128, arity=3) == 0
+    assert cf.gesv_mixed_workspace_size(64, 1, "f16", **WIDE) > 0
 
 
 @pytest.mark.parametrize("solver", ["gesv", "posv"])
