@@ -267,7 +267,8 @@ def test_tourn_select_f32_wide_valid(cf, m, w, h, arity):
     assert len(win) == min(m, w) and len(set(win.tolist())) == len(win)
     assert win.min() >= 0 and win.max() < m
     if m <= h:                       # a single leaf: GEPP; its first pivot is the column maximum
-        assert abs(P[win[0], 0]) == np.abs(P[:, 0].astype(np.float32)).max()
+        P32 = np.abs(P[:, 0].astype(np.float32))
+        assert P32[win[0]] == P32.max()
 
 
 def test_tourn_select_f32_wide_ties_zeros_nan(cf):
