@@ -310,10 +310,42 @@ int cf_schur_update_fp8(int m, int n, int k, const void *qA, int ldqa,
                         const float *sB, int ldsb, float *C, int ldc,
                         int lower, cudaStream_t stream);
 
-/* Synchronises `stream` and returns, then clears, the status word of the
- * library's bounded device-side waits: CF_OK, or CF_ERR_TIMEOUT if a wait in
- * a tensor-core kernel ran out since the last call. */
+/* Synchronises `stream` and returns, then clears, the status words of the
+ * library's bounded device-side waits: CF_OK, or CF_ERR_TIMEOUT if a wait ran
+ * out since the last call (the tensor-core kernels' waits on their TMA and
+ * MMA barriers, the blocked triangular solves' waits on earlier blocks).  A
+ * wait that runs out ends its kernel early or lets it finish with wrong
+ * values; it never hangs, and the context stays usable.  The mixed solvers
+ * read and clear these words themselves and return CF_ERR_TIMEOUT. */
 int cf_device_status(cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * S-1 with FP32 factors: the blocked triangular solve that the mixed
+ * solvers' refinement runs (paper silent; substitution by 128-row blocks).
+ *   mode  0: X <- L^-1 X, L unit lower (the strictly lower part of T is
+ *         read); 1: X <- U^-1 X, U upper; 2: X <- L^-1 X, L lower non-unit;
+ *         3: X <- L^-T X, L lower non-unit.
+ *   T     n x n FP32, ldt (read only); X n x nrhs FP32, ldx, nrhs <= 16,
+ *         overwritten by the solution.
+ *   work  cf_trsv_f32_workspace_size(n) bytes (inverses of the 128 x 128
+ *         diagonal blocks, block flags).
+ * The launch's CTAs take tickets in launch order and wait (bounded) only for
+ * blocks with earlier tickets.
+ * ------------------------------------------------------------------------ */
+size_t cf_trsv_f32_workspace_size(int n);
+int cf_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, float *X,
+                int ldx, void *work, size_t lwork, cudaStream_t stream);
+
+/* Failure-detection test of the bounded waits (no GPU fault, no hang): the
+ * same solve with the first block withheld -- its ticket is taken before
+ * the launch, so no CTA ever solves block 0 or raises its flag.  Every
+ * CTA's wait for block 0 gives up after spin_limit polls (0 = the library's
+ * limit, 2^22 polls of at least 20 ns), records CF_ERR_TIMEOUT for
+ * cf_device_status, and the CTA goes on, so the kernel ends with X wrong.
+ * Arguments as cf_trsv_f32; spin_limit < 0 returns -8. */
+int cf_trsv_f32_withheld(int mode, int n, int nrhs, const float *T, int ldt,
+                         float *X, int ldx, long long spin_limit, void *work,
+                         size_t lwork, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * BAT-1  Batched uneven factorizations in one persistent launch (an addition

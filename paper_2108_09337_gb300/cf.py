@@ -82,6 +82,9 @@ _SIG = {
     "cf_residual_pair": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _S, _P]),
     "cf_schur_update_lp": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
     "cf_device_status": (_I, [_P]),
+    "cf_trsv_f32_workspace_size": (_S, [_I]),
+    "cf_trsv_f32": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _S, _P]),
+    "cf_trsv_f32_withheld": (_I, [_I, _I, _I, _P, _I, _P, _I, ctypes.c_longlong, _P, _S, _P]),
     "cf_factor_batched_workspace_size": (_S, [_I, _OPT]),
     "cf_factor_batched": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P, _S, _OPT, _P]),
     "cf_getrf_batched_workspace_size": (_S, [_I, _OPT]),
@@ -333,6 +336,32 @@ def schur_update_fp8(qA, sA, qB, sB, C: torch.Tensor, lower: bool = False):
                                                            _ptr(qB), qB.stride(0), _ptr(sB), sB.stride(0), _ptr(C),
                                                            _ld(C, "C"), int(lower), _stream()))
     return C
+
+
+def trsv_f32(T: torch.Tensor, X: torch.Tensor, mode: int):
+    """cf_trsv_f32: X <- M^-1 X in place with the FP32 factor T (mode 0: unit
+    lower, 1: upper, 2: lower, 3: lower transposed); nrhs <= 16."""
+    assert T.dtype == torch.float32 and X.dtype == torch.float32
+    n = T.shape[0]
+    nrhs = X.shape[1] if X.dim() == 2 else 1
+    ws = _workspace(_lib.cf_trsv_f32_workspace_size(n), T.device)
+    _check("cf_trsv_f32", _lib.cf_trsv_f32(mode, n, nrhs, _ptr(T), _ld(T, "T"), _ptr(X), _ld(X, "X"), _ptr(ws),
+                                           ws.numel(), _stream()))
+    return X
+
+
+def trsv_f32_withheld(T: torch.Tensor, X: torch.Tensor, mode: int, spin_limit: int = 0):
+    """cf_trsv_f32_withheld: the same solve with its first block withheld, so
+    that every wait for it runs out (failure-detection test; X comes back
+    wrong and cf_device_status reports CF_ERR_TIMEOUT)."""
+    assert T.dtype == torch.float32 and X.dtype == torch.float32
+    n = T.shape[0]
+    nrhs = X.shape[1] if X.dim() == 2 else 1
+    ws = _workspace(_lib.cf_trsv_f32_workspace_size(n), T.device)
+    _check("cf_trsv_f32_withheld", _lib.cf_trsv_f32_withheld(mode, n, nrhs, _ptr(T), _ld(T, "T"), _ptr(X),
+                                                             _ld(X, "X"), spin_limit, _ptr(ws), ws.numel(),
+                                                             _stream()))
+    return X
 
 
 def device_status() -> int:

@@ -73,34 +73,16 @@ __device__ __forceinline__ float rcp_fast(float x) {
 }
 
 // The largest of the NW warp keys (smallest warp on ties) and the reciprocal
-// published with it: broadcast 16-byte loads and a comparison tree in
-// registers (the right operand wins only when strictly larger).
+// published with it, computed by every warp alike: lane i reads warp i's key,
+// one redux.sync gives the maximum and a ballot its smallest warp, whose
+// reciprocal is one broadcast load.
 template <int NW>
-__device__ __forceinline__ int warp_argmax(const unsigned (&wk)[NW], const float (&wr)[NW], float &rinv) {
-    unsigned k[NW];
-    float f[NW];
-    int id[NW];
-#pragma unroll
-    for (int q = 0; q < NW / 4; ++q) {
-        const uint4 kk = reinterpret_cast<const uint4 *>(wk)[q];
-        const float4 ff = reinterpret_cast<const float4 *>(wr)[q];
-        k[4 * q] = kk.x; k[4 * q + 1] = kk.y; k[4 * q + 2] = kk.z; k[4 * q + 3] = kk.w;
-        f[4 * q] = ff.x; f[4 * q + 1] = ff.y; f[4 * q + 2] = ff.z; f[4 * q + 3] = ff.w;
-    }
-#pragma unroll
-    for (int i = 0; i < NW; ++i) id[i] = i;
-#pragma unroll
-    for (int st = 1; st < NW; st <<= 1) {
-#pragma unroll
-        for (int i = 0; i < NW; i += 2 * st) {
-            const bool c = k[i + st] > k[i];
-            k[i] = c ? k[i + st] : k[i];
-            f[i] = c ? f[i + st] : f[i];
-            id[i] = c ? id[i + st] : id[i];
-        }
-    }
-    rinv = f[0];
-    return id[0];
+__device__ __forceinline__ int warp_argmax(const unsigned (&wk)[NW], const float (&wr)[NW], int lane, float &rinv) {
+    const unsigned k = lane < NW ? wk[lane] : 0u;
+    const unsigned mx = __reduce_max_sync(0xffffffffu, k);
+    const int wb = __ffs(__ballot_sync(0xffffffffu, k == mx)) - 1;
+    rinv = wr[wb];
+    return wb;
 }
 
 template <int U>
@@ -144,7 +126,7 @@ struct BlockStep {
         }
         __syncthreads();
         float ri;
-        const int wb = warp_argmax<NW>(s.wkey[U], s.wrinv[U], ri);
+        const int wb = warp_argmax<NW>(s.wkey[U], s.wrinv[U], lane, ri);
         if (warp == wb && lane == wl) {
             s.order[j] = r;
             used = true;

@@ -246,7 +246,7 @@ __device__ __forceinline__ void trsv_stage_step(float *dst, int step, int s, boo
 template <int SB, int MODE, int NR, typename VT>
 __global__ void __launch_bounds__(256, 1)        // one CTA per SM (shared memory)
 k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *__restrict__ Dinv,
-               const float *__restrict__ Gn, VT *X, int ldx, int *flags, int *ticket) {
+               const float *__restrict__ Gn, VT *X, int ldx, int *flags, int *ticket, long long spin_limit) {
     constexpr int TLD = SB + 4;
     constexpr int RG = SB / 4;                     // row groups of 4
     constexpr int CG = 256 / RG;                   // right-hand-side groups
@@ -328,11 +328,11 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
         if (tid == 0) {
             volatile int *f = flags + cb;
             long long it = 0;
-            while (*f == 0 && it < kFlagSpin) {
+            while (*f == 0 && it < spin_limit) {
                 ++it;
                 if (it > 64) __nanosleep(20);
             }
-            if (it >= kFlagSpin) atomicExch(&g_trsv_status, CF_ERR_TIMEOUT);
+            if (it >= spin_limit) atomicExch(&g_trsv_status, CF_ERR_TIMEOUT);
             __threadfence();
         }
         __syncthreads();
@@ -435,37 +435,41 @@ int launch_diag_inverse64(int mode, int n, const float *T, int ldt, double *Dinv
 
 template <int SB, int MODE, int NR, typename VT>
 static int launch_trsv_nr(int n, int nrhs, const float *T, int ldt, const VT *Dinv, const float *Gn, VT *X, int ldx,
-                          int *flags, int *ticket, cudaStream_t st) {
+                          int *flags, int *ticket, long long spin, cudaStream_t st) {
     const int nb = (n + SB - 1) / SB;
     const size_t smem = trsv_smem_bytes<SB, VT, NR>();
     CF_CUDA_TRY(cudaFuncSetAttribute(k_trsv_blocked<SB, MODE, NR, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    k_trsv_blocked<SB, MODE, NR, VT><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket);
+    k_trsv_blocked<SB, MODE, NR, VT><<<nb, 256, smem, st>>>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, spin);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
 
+// withhold: the first ticket is taken before the launch (failure-detection
+// test: the first block is never solved and every wait for it runs out).
 template <int SB, int MODE, typename VT>
 static int launch_trsv_mode(int n, int nrhs, const float *T, int ldt, const VT *Dinv, const float *Gn, VT *X, int ldx,
-                            int *sync_ws, cudaStream_t st) {
+                            int *sync_ws, bool withhold, long long spin, cudaStream_t st) {
     const int nb = (n + SB - 1) / SB;
     CF_CUDA_TRY(cudaMemsetAsync(sync_ws, 0, sizeof(int) * (size_t)(nb + 1), st));
     int *flags = sync_ws, *ticket = sync_ws + nb;
-    if (nrhs <= 4) return launch_trsv_nr<SB, MODE, 4, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, st);
-    if (nrhs <= 8) return launch_trsv_nr<SB, MODE, 8, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, st);
-    return launch_trsv_nr<SB, MODE, 16, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, st);
+    if (withhold) CF_CUDA_TRY(cudaMemsetAsync(ticket, 1, 1, st));     // ticket = 1 (little-endian low byte)
+    if (nrhs <= 4) return launch_trsv_nr<SB, MODE, 4, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, spin, st);
+    if (nrhs <= 8) return launch_trsv_nr<SB, MODE, 8, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, spin, st);
+    return launch_trsv_nr<SB, MODE, 16, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, flags, ticket, spin, st);
 }
 
 template <int SB, typename VT>
 static int launch_trsv_t(int mode, int n, int nrhs, const float *T, int ldt, const VT *Dinv, const float *Gn, VT *X,
-                         int ldx, int *sync_ws, cudaStream_t st) {
+                         int ldx, int *sync_ws, cudaStream_t st, bool withhold = false,
+                         long long spin = kFlagSpin) {
     if (n <= 0 || nrhs <= 0) return CF_OK;
     if (nrhs > 16) return CF_ERR_UNSUPPORTED;
     switch (mode) {
-        case 0: return launch_trsv_mode<SB, 0, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, st);
-        case 1: return launch_trsv_mode<SB, 1, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, st);
-        case 2: return launch_trsv_mode<SB, 2, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, st);
-        case 3: return launch_trsv_mode<SB, 3, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, st);
+        case 0: return launch_trsv_mode<SB, 0, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, withhold, spin, st);
+        case 1: return launch_trsv_mode<SB, 1, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, withhold, spin, st);
+        case 2: return launch_trsv_mode<SB, 2, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, withhold, spin, st);
+        case 3: return launch_trsv_mode<SB, 3, VT>(n, nrhs, T, ldt, Dinv, Gn, X, ldx, sync_ws, withhold, spin, st);
         default: return CF_ERR_UNSUPPORTED;
     }
 }
@@ -510,6 +514,34 @@ int launch_neighbor_premul(int mode, int n, const float *T, int ldt, const float
     return CF_OK;
 }
 
+// The C-ABI solve and its failure-detection variant: Dinv in work, then the
+// blocked solve (no premultiplied neighbour tiles).
+static size_t trsv_api_ws(int n) {
+    Carver cv(nullptr);
+    cv.take<float>(diag_inverse_floats(n > 0 ? n : 1));
+    cv.take<int>(trsv_ws_bytes(n > 0 ? n : 1) / sizeof(int) + 1);
+    return cv.size();
+}
+
+static int trsv_api(int mode, int n, int nrhs, const float *T, int ldt, float *X, int ldx, bool withhold,
+                    long long spin, void *work, size_t lwork, cudaStream_t st) {
+    if (mode < 0 || mode > 3) return -1;
+    if (n < 0) return -2;
+    if (nrhs < 0 || nrhs > 16) return -3;
+    if (n > 0 && T == nullptr) return -4;
+    if (ldt < (n > 1 ? n : 1)) return -5;
+    if (n > 0 && nrhs > 0 && X == nullptr) return -6;
+    if (ldx < (n > 1 ? n : 1)) return -7;
+    if (n == 0 || nrhs == 0) return CF_OK;
+    if (work == nullptr || lwork < trsv_api_ws(n)) return CF_ERR_WORKSPACE;
+    Carver cv(work);
+    float *Dinv = cv.take<float>(diag_inverse_floats(n));
+    int *sync = cv.take<int>(trsv_ws_bytes(n) / sizeof(int) + 1);
+    int rc = launch_diag_inverse(mode, n, T, ldt, Dinv, st);
+    if (rc != CF_OK) return rc;
+    return launch_trsv_t<kSB32, float>(mode, n, nrhs, T, ldt, Dinv, nullptr, X, ldx, sync, st, withhold, spin);
+}
+
 int trsv_take_status(cudaStream_t st, int *status) {
     int h = 0;
     CF_CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, g_trsv_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
@@ -523,3 +555,18 @@ int trsv_take_status(cudaStream_t st, int *status) {
 }
 
 }  // namespace cf
+
+extern "C" size_t cf_trsv_f32_workspace_size(int n) { return cf::trsv_api_ws(n); }
+
+extern "C" int cf_trsv_f32(int mode, int n, int nrhs, const float *T, int ldt, float *X, int ldx, void *work,
+                           size_t lwork, cudaStream_t stream) {
+    return cf::trsv_api(mode, n, nrhs, T, ldt, X, ldx, false, cf::kFlagSpin, work, lwork, stream);
+}
+
+extern "C" int cf_trsv_f32_withheld(int mode, int n, int nrhs, const float *T, int ldt, float *X, int ldx,
+                                    long long spin_limit, void *work, size_t lwork, cudaStream_t stream) {
+    if (spin_limit < 0) return -8;
+    return cf::trsv_api(mode, n, nrhs, T, ldt, X, ldx, true, spin_limit > 0 ? spin_limit : cf::kFlagSpin, work,
+                        lwork, stream);
+}
+
