@@ -537,7 +537,8 @@ static int trsv_api(int mode, int n, int nrhs, const float *T, int ldt, float *X
     Carver cv(work);
     float *Dinv = cv.take<float>(diag_inverse_floats(n));
     int *sync = cv.take<int>(trsv_ws_bytes(n) / sizeof(int) + 1);
-    int rc = launch_diag_inverse(mode, n, T, ldt, Dinv, st);
+    // mode 3 (L^T) reads the inverses of L's diagonal blocks transposed
+    int rc = launch_diag_inverse(mode == 3 ? 2 : mode, n, T, ldt, Dinv, st);
     if (rc != CF_OK) return rc;
     return launch_trsv_t<kSB32, float>(mode, n, nrhs, T, ldt, Dinv, nullptr, X, ldx, sync, st, withhold, spin);
 }
