@@ -96,8 +96,8 @@ def test_bounded_wait_runs_out_and_recovers(cf, n, spin):
     got = dX.cpu().numpy().astype(np.float64)
     np.testing.assert_array_equal(got[:128], X[:128])    # block 0 was never solved
     ref = _reference(T, X, mode)
-    if n > 128:
-        assert np.abs(got - ref).max() > 1e-3 * np.abs(ref).max()   # and the rest is wrong
+    if n > 128:   # and the rest is wrong (far outside the solve's FP32 error, ~1e-7 here)
+        assert np.abs(got - ref).max() > 1e-5 * np.abs(ref).max()
     # the context is usable: the same solve without the stall is right, and
     # reports no timeout
     dX = _dev32(X)
