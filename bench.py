@@ -43,6 +43,9 @@ TOL = 1e-14
 SOLVER_TOL = 0.9e-14   # asked of the solver: a 10% margin for the independent FP64 check at TOL
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; ~2 DFMA/clk/SM x 152 SMs x 2.07 GHz)
 RESID_TRAFFIC_8192 = 542.2e6   # k_residual_f64 DRAM bytes per launch at N = 8192 (ncu)
+# FP32 tournament DRAM bytes per launch, averaged over an LU's panels, keyed
+# by (N, v, leaf_h, arity), from ncu captures under profiles/
+TOURN_TRAFFIC = {}
 
 
 def _args():
@@ -56,7 +59,9 @@ def _args():
                     help="update precision of the timed Cholesky solve")
     ap.add_argument("--prec", default="f16", choices=["bf16", "f16", "bf16x3"],
                     help="update precision of the timed step (the other 16-bit one runs once as a variant)")
-    ap.add_argument("--leaf-h", type=int, default=256, help="tournament leaf height of the mixed LU")
+    ap.add_argument("--v", type=int, default=64, help="block size of the mixed LU's steps")
+    ap.add_argument("--leaf-h", type=int, default=512, help="tournament leaf height of the mixed LU")
+    ap.add_argument("--arity", type=int, default=8, help="children per playoff node of the mixed LU's tournament")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--fp64-sizes", default="8192,16384,32768",
                     help="sizes of the FP64 path at paper-like sizes (config 2); empty to skip")
@@ -187,16 +192,16 @@ def _host_cpu(cpuinfo: str = "/proc/cpuinfo") -> str:
     return "%s, %d logical CPUs" % (name or platform.machine(), os.cpu_count() or 1)
 
 
-def _oracle_sample(n_sample: int):
-    """The FP64 oracle as it stands on this host's cores: LU (v = h = 128)
-    and Cholesky at n_sample with the same generators.  Returns (TFLOP/s,
-    seconds, threads)."""
+def _oracle_sample(n_sample: int, v: int = 64, h: int = 512, arity: int = 8):
+    """The FP64 oracle as it stands on this host's cores: LU (the mixed LU's
+    tournament shape: v = 64, leaves of 512 rows, arity 8) and Cholesky at
+    n_sample with the same generators.  Returns (TFLOP/s, seconds, threads)."""
     import oracle
     from paper_2108_09337_gb300 import inputs
     A = inputs.uniform_pm1(n_sample, seed=0, shift=2 * math.sqrt(n_sample))
     S = inputs.spd_gram(n_sample, seed=1)
     t0 = time.perf_counter()
-    oracle.getrf(A, v=128, h=128, arity=2)
+    oracle.getrf(A, v=v, h=h, arity=arity)
     oracle.potrf(S)
     dt = time.perf_counter() - t0
     fl = oracle.lu_flops(n_sample) + oracle.chol_flops(n_sample)
@@ -211,14 +216,15 @@ def run_reference(args, rank: int):
         return
     n_s = 2048
     for _ in range(args.warmup):
-        _oracle_sample(n_s)
+        _oracle_sample(n_s, args.v, args.leaf_h, args.arity)
     times, rates = [], []
     for _ in range(args.steps):
-        r, dt, threads = _oracle_sample(n_s)
+        r, dt, threads = _oracle_sample(n_s, args.v, args.leaf_h, args.arity)
         times.append(dt)
         rates.append(r)
     value = statistics.median(rates)
-    sample = "oracle LU (tournament, v=h=128) + Cholesky at N=%d per step, same generators" % n_s
+    sample = ("oracle LU (tournament, v=%d, h=%d, arity %d) + Cholesky at N=%d per step, same generators"
+              % (args.v, args.leaf_h, args.arity, n_s))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
@@ -232,6 +238,11 @@ def run_reference(args, rank: int):
 
 
 # ------------------------------------------------------------------ GPU arm
+def _tourn_kw(args):
+    """Block size and tournament shape of the mixed LU (v, leaf height, arity)."""
+    return {"v": args.v, "leaf_h": args.leaf_h, "arity": args.arity}
+
+
 def _gen_inputs(n, device):
     from paper_2108_09337_gb300 import inputs
     A_lu = inputs.uniform_pm1_torch(n, seed=0, shift=2.0 * math.sqrt(n), device=device)
@@ -279,13 +290,13 @@ def _run_variants(args, n, dev, A_lu, B_lu, A_ch, B_ch, rank=0, world=1):
     lu_fl, ch_fl = 2.0 * n ** 3 / 3.0, n ** 3 / 3.0
     for p in ("bf16", "f16", "bf16x3"):
         if p != args.prec:
-            rec("lu_%s_n%d" % (p, n), lambda: cf.gesv_mixed(A_lu, B_lu, prec=p, leaf_h=args.leaf_h), A_lu, B_lu,
+            rec("lu_%s_n%d" % (p, n), lambda: cf.gesv_mixed(A_lu, B_lu, prec=p, **_tourn_kw(args)), A_lu, B_lu,
                 lu_fl)
         if p != args.chol_prec:
             rec("chol_%s_n%d" % (p, n), lambda: cf.posv_mixed(A_ch, B_ch, prec=p), A_ch, B_ch, ch_fl)
     A0 = inputs.uniform_pm1_torch(n, seed=0, shift=0.0, device=dev)
     for p in ("bf16x3", "bf16", "f16"):
-        rec("lu_s0_%s_n%d" % (p, n), lambda: cf.gesv_mixed(A0, B_lu, prec=p, leaf_h=args.leaf_h), A0, B_lu, lu_fl)
+        rec("lu_s0_%s_n%d" % (p, n), lambda: cf.gesv_mixed(A0, B_lu, prec=p, **_tourn_kw(args)), A0, B_lu, lu_fl)
     del A0
     torch.cuda.empty_cache()
     if n == 32768:
@@ -506,13 +517,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     ch_fl = n ** 3 / 3.0
 
     A_lu, B_lu, A_ch, B_ch, gen_info = _gen_inputs(n, dev)
-    ws_lu = torch.empty(cf.gesv_mixed_workspace_size(n, 16, prec, leaf_h=args.leaf_h), dtype=torch.uint8, device=dev)
+    ws_lu = torch.empty(cf.gesv_mixed_workspace_size(n, 16, prec, **_tourn_kw(args)), dtype=torch.uint8, device=dev)
     cprec = args.chol_prec
     ws_ch = torch.empty(cf.posv_mixed_workspace_size(n, 8, cprec), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
     def step():
-        X1, info1, st1, s1 = cf.gesv_mixed(A_lu, B_lu, prec=prec, work=ws_lu, leaf_h=args.leaf_h, tol=SOLVER_TOL)
+        X1, info1, st1, s1 = cf.gesv_mixed(A_lu, B_lu, prec=prec, work=ws_lu, **_tourn_kw(args), tol=SOLVER_TOL)
         X2, info2, st2, s2 = cf.posv_mixed(A_ch, B_ch, prec=cprec, work=ws_ch, tol=SOLVER_TOL)
         return (X1, st1, s1), (X2, st2, s2)
 
@@ -582,11 +593,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     tourn = kern("tourn_ms", "tourn_launches", sum(s["tourn_flops"] for s, _ in allst))
     bf16_pk = peaks.get("bf16_tflops_sustained") or 1700.0
     cand = {
-        "tourn32": (tourn, "k_tourn32 (LU-1, FP32 tournament pivoting; latency-bound: one barrier per column "
-                           "per tree level)", "alu", fp32_peak,
+        "tourn32": (tourn, ("k_tourn32w (LU-1, FP32 tournament pivoting, v=%d, leaves of %d rows, arity %d; "
+                            "latency-bound: one barrier per column per tree level)" % (args.v, args.leaf_h, args.arity)
+                            if args.v <= 64 else
+                            "k_tourn32 (LU-1, FP32 tournament pivoting; latency-bound: one barrier per column "
+                            "per tree level)"), "alu", fp32_peak,
                     "FP32 FMA nominal: 128 lanes/clk/SM x %d SMs x %.0f MHz x 2 flops" % (n_sm, sm_mhz),
-                    # ncu at N = 8192 (profiles/k_tourn32_n8192.md): DRAM read = the panel's bytes
-                    sum(4.0 * 128 * (n - 128 * i) for i in range(n // 128)) / (n // 128)),
+                    TOURN_TRAFFIC.get((n, args.v, args.leaf_h, args.arity))),
         "residual_f64": (res, "k_residual_f64 (R-1, FP64 r = b - A x)", "alu", FP64_PEAK_TFLOPS,
                          "GB300 FP64 nominal 1.25 TFLOP/s (~2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
                          RESID_TRAFFIC_8192 * (n / 8192.0) ** 2),
@@ -619,8 +632,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     if top == "residual_f64":
         roof["traffic_note"] = "bytes per launch, ncu capture at N=8192 scaled by N^2"
     elif top == "tourn32":
-        roof["traffic_note"] = ("bytes per launch: the panel (m x 128 FP32) averaged over the LU's panels; an ncu "
-                                "capture at N=8192 read exactly the panel")
+        roof["traffic_note"] = ("DRAM bytes per launch averaged over the LU's panels, from ncu captures (the panel "
+                                "is read once); null when no capture of this kernel and shape exists")
     parts = {
         "lu": {"factor_ms": statistics.median(s["factor_ms"] for s in stats_lu),
                "refine_ms": statistics.median(s["refine_ms"] for s in stats_lu),
@@ -685,7 +698,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                 if i + 1 < k:
                     copy_lu(1 - slot)       # its buffer's last reader was step i-1
                 stream.wait_event(lu_in[slot])
-                X1_, _, _, _ = cf.gesv_mixed(dA1[slot], dB1[slot], prec=prec, work=ws_lu, leaf_h=args.leaf_h,
+                X1_, _, _, _ = cf.gesv_mixed(dA1[slot], dB1[slot], prec=prec, work=ws_lu, **_tourn_kw(args),
                                              tol=SOLVER_TOL)
                 lu_free[slot].record(stream)
                 hX1.copy_(X1_, non_blocking=True)
@@ -765,10 +778,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         return
     cpu = None
     if not args.no_cpu:
-        r, dt, threads = _oracle_sample(4096)
+        r, dt, threads = _oracle_sample(4096, args.v, args.leaf_h, args.arity)
         cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "host": _host_cpu(),
-               "sample": "FP64 oracle LU (tournament, v=h=128) + Cholesky at N=4096, same generators, "
-                         "%.1f s on this host" % dt}
+               "sample": "FP64 oracle LU (tournament, v=%d, h=%d, arity %d) + Cholesky at N=4096, same "
+                         "generators, %.1f s on this host" % (args.v, args.leaf_h, args.arity, dt)}
     line = {
         "metric": METRIC, "value": value if ok else 0.0, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -777,7 +790,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "config": {"workload": "mixed LU solve (N=32768, 16 RHS, A=U[-1,1]+2sqrt(N)I, %s tensor-core updates) + "
                                "mixed Cholesky solve (N=32768, 8 RHS, A=GG^T/N+alpha I, kappa~1e2, %s tensor-core "
                                "updates), FP32 accumulation, FP64 refinement to 1e-14" % (prec, cprec),
-                   "n": n, "v": 128, "leaf_h": args.leaf_h, "arity": 2, "outer_V": {"lu": 2048, "chol": 1024},
+                   "n": n, "v": {"lu": args.v, "chol": 128}, "leaf_h": args.leaf_h, "arity": args.arity,
+                   "outer_V": {"lu": 2048, "chol": 1024},
                    "factor_prec": prec,
                    "chol_factor_prec": cprec,
                    "parallelism": "replicas" if world > 1 else "single GPU",

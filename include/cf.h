@@ -57,16 +57,21 @@ typedef enum {
 } cf_prec;
 
 /* Tunables.  Pass NULL for the defaults (in brackets); a field left 0 in v,
- * leaf_h, arity, tol, max_iter or gmres_restart also takes its default.  A
- * value out of range makes the call return CF_ERR_UNSUPPORTED (the size
- * queries return 0) before anything is enqueued.  The pivot sequence is a
- * function of (v, leaf_h, arity) only; the oracle takes the same three. */
+ * leaf_h, arity, tol, max_iter or gmres_restart also takes its default
+ * (cf_default_options leaves v, leaf_h and arity 0, since their defaults
+ * depend on the routine).  A value out of range makes the call return
+ * CF_ERR_UNSUPPORTED (the size queries return 0) before anything is
+ * enqueued.  The pivot sequence is a function of (v, leaf_h, arity) only;
+ * the oracle takes the same three. */
 typedef struct {
-    int v;             /* block size of a step, 1..128 [128] (Sec. 7.2, "Block size v") */
-    int leaf_h;        /* tournament leaf height [128]: 1..128 for the FP64
-                          routines, 1..256 for the mixed solvers (whose FP32
-                          tournament takes arity 2 only) */
-    int arity;         /* children per playoff node, 2..4 [2]; the mixed paths use 2 */
+    int v;             /* block size of a step, 1..128 (Sec. 7.2, "Block size
+                          v") [128; mixed LU: 64] */
+    int leaf_h;        /* tournament leaf height: FP64 routines 1..128 [128];
+                          mixed LU 1..512 with v <= 64 [512], 1..256 with
+                          v > 64 [256] */
+    int arity;         /* children per playoff node: FP64 routines 2..4 [2];
+                          mixed LU with v <= 64: 2..8 and arity * v <= 512
+                          [8], with v > 64: 2 [2] */
     int outer_V;       /* mixed LU/Cholesky: depth of the deferred update,
                           multiple of v [0 = auto: 2048 for LU at n >= 16384,
                           1024 at n >= 8192, 512 below] */

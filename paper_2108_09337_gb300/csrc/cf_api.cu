@@ -29,9 +29,9 @@ int launch_gemm_f64_sub_t(int m, int n, int k, const double *A, int lda, bool tr
 int resolve_options(const cf_options *in, Opts *o) {
     *o = Opts();
     if (in == nullptr) return CF_OK;
-    if (in->v != 0) o->v = in->v;
-    if (in->leaf_h != 0) o->leaf_h = in->leaf_h;
-    if (in->arity != 0) o->arity = in->arity;
+    if (in->v != 0) { o->v = in->v; o->v_set = true; }
+    if (in->leaf_h != 0) { o->leaf_h = in->leaf_h; o->h_set = true; }
+    if (in->arity != 0) { o->arity = in->arity; o->ar_set = true; }
     o->outer_V = in->outer_V;
     o->lookahead = in->lookahead;
     if (in->tol > 0) o->tol = in->tol;
@@ -45,7 +45,9 @@ int resolve_options(const cf_options *in, Opts *o) {
     // routine checks its own narrower limits (FP64: leaf_h <= kMaxV, arity <= 4)
     if (o->leaf_h < 1 || o->leaf_h > 4 * kMaxV) return CF_ERR_UNSUPPORTED;
     if (o->arity < 2 || o->arity > 8) return CF_ERR_UNSUPPORTED;
-    if (o->outer_V < 0 || (o->outer_V % o->v) != 0) return CF_ERR_UNSUPPORTED;
+    // outer_V: a multiple of v (of 64, the smallest default v, when v is left
+    // to the routine; the mixed solvers check it again against their v)
+    if (o->outer_V < 0 || (o->outer_V % (o->v_set ? o->v : 64)) != 0) return CF_ERR_UNSUPPORTED;
     if (o->gmres_restart < 1 || o->gmres_restart > 256) return CF_ERR_UNSUPPORTED;
     if (o->batch_cps < 0 || o->batch_cps > 8) return CF_ERR_UNSUPPORTED;
     return CF_OK;
@@ -82,12 +84,20 @@ __global__ void k_gather_rows(int n, int nrhs, const int *perm, const double *In
 
 using namespace cf;
 
+int cf::mixed_lu_defaults(Opts *o) {
+    if (!o->v_set) o->v = 64;
+    if (!o->h_set) o->leaf_h = o->v <= 64 ? 512 : 256;
+    if (!o->ar_set) o->arity = o->v <= 64 ? (8 * o->v <= 512 ? 8 : 512 / o->v) : 2;
+    if ((o->outer_V % o->v) != 0) return CF_ERR_UNSUPPORTED;
+    return tourn32_shape_ok(o->v, o->leaf_h, o->arity) ? CF_OK : CF_ERR_UNSUPPORTED;
+}
+
 extern "C" void cf_default_options(cf_options *opt) {
     if (opt == nullptr) return;
     Opts o;
-    opt->v = o.v;
-    opt->leaf_h = o.leaf_h;
-    opt->arity = o.arity;
+    opt->v = 0;          // each routine's default (FP64: 128 / 128 / 2; mixed LU: 64 / 512 / 8)
+    opt->leaf_h = 0;
+    opt->arity = 0;
     opt->outer_V = o.outer_V;
     opt->lookahead = o.lookahead;
     opt->tol = o.tol;

@@ -74,9 +74,16 @@ struct Opts {
     int max_iter = 30, gmres_restart = 30;
     int batch_cps = 0;           // batched calls: resident CTAs per SM (0 = as many as fit)
     int fp64_residual = 0;       // mixed solvers: 1 = no pair-arithmetic residuals
+    // whether the caller set v, leaf_h, arity (0 selects the routine's default)
+    bool v_set = false, h_set = false, ar_set = false;
 };
-// Returns 0 or a negative status for an out-of-range field.
+// Returns 0 or a negative status for an out-of-range field.  Fields left 0
+// take the FP64 routines' defaults (v = 128, leaf_h = 128, arity = 2).
 int resolve_options(const cf_options *in, Opts *out);
+// The mixed LU's defaults for the fields the caller left 0: v = 64 with the
+// wide-node tournament (leaves of 512 rows, arity 8); with v > 64 given,
+// leaves of 256 rows and arity 2.  Checks outer_V against the final v.
+int mixed_lu_defaults(Opts *o);
 // Tournament shapes of the FP64 routines: leaves of at most kMaxV rows,
 // arity 2..4 (one cluster of `arity` CTAs per playoff node).
 inline bool fp64_tourn_shape(const Opts &o) { return o.leaf_h <= kMaxV && o.arity <= 4; }

@@ -1200,7 +1200,8 @@ static size_t mixed_ws_size(int n, int nrhs, cf_prec prec, const cf_options *opt
     (void)prec;
     Opts o;
     if (resolve_options(opt, &o) != CF_OK) return 0;
-    if (lu && !tourn32_shape_ok(o.v, o.leaf_h, o.arity)) return 0;
+    if (lu && mixed_lu_defaults(&o) != CF_OK) return 0;
+    if (!lu && (o.outer_V % o.v) != 0) return 0;
     MixedWS w;
     if (carve_mixed(nullptr, n > 0 ? n : 1, nrhs > 0 ? nrhs : 1, o, lu, &w) != CF_OK) return 0;
     return w.bytes;
@@ -1213,7 +1214,8 @@ static int mixed_entry(int n, int nrhs, const double *A, int lda, const double *
     if (rc) return rc;
     Opts o;
     if ((rc = resolve_options(opt, &o))) return rc;
-    if (lu && !tourn32_shape_ok(o.v, o.leaf_h, o.arity)) return CF_ERR_UNSUPPORTED;
+    if (lu && (rc = mixed_lu_defaults(&o))) return rc;
+    if (!lu && (o.outer_V % o.v) != 0) return CF_ERR_UNSUPPORTED;
     if (n == 0 || nrhs == 0) {
         if (stats) { memset(stats, 0, sizeof(*stats)); stats->converged = 1; }
         return CF_OK;

@@ -119,11 +119,17 @@ def test_tournament_shapes_per_routine():
         assert L.cf_getrf(8, P, 8, P, P, P, BIG, _opt(**kw), None) == cf.CF_ERR_UNSUPPORTED, kw
         assert L.cf_getrf_noalloc(8, P, 8, P, P, _opt(**kw), None) == cf.CF_ERR_UNSUPPORTED, kw
         assert L.cf_getrf_workspace_size(1000, _opt(**kw)) == 0, kw
-    for kw in ({"leaf_h": 257}, {"arity": 3}, {"v": 80, "leaf_h": 300}, {"v": 64, "arity": 8, "leaf_h": 513}):
+    for kw in ({"v": 128, "leaf_h": 257}, {"v": 128, "arity": 3}, {"v": 80, "leaf_h": 300},
+               {"v": 64, "arity": 8, "leaf_h": 513}, {"v": 16, "arity": 8, "outer_V": 24}):
         assert L.cf_gesv_mixed(8, 2, P, 8, P, 8, P, 8, 3, P, None, P, BIG, _opt(**kw), None) == \
             cf.CF_ERR_UNSUPPORTED, kw
         assert cf.gesv_mixed_workspace_size(1000, 1, "f16", **kw) == 0, kw
     assert cf.gesv_mixed_workspace_size(1000, 1, "f16", v=64, leaf_h=512, arity=8) > 0
+    # left 0, the mixed LU takes v = 64, leaves of 512 rows, arity 8; v = 128 alone takes 256 / 2
+    assert cf.gesv_mixed_workspace_size(1000, 1, "f16") == cf.gesv_mixed_workspace_size(1000, 1, "f16", v=64,
+                                                                                         leaf_h=512, arity=8)
+    assert cf.gesv_mixed_workspace_size(1000, 1, "f16", v=128) == cf.gesv_mixed_workspace_size(1000, 1, "f16", v=128,
+                                                                                                leaf_h=256, arity=2)
     assert cf.gesv_mixed_workspace_size(1000, 1, "f16", v=32, leaf_h=512, arity=16) == 0
     assert cf.posv_mixed_workspace_size(1000, 1, "f16", leaf_h=512, arity=8) > 0   # no tournament
 

@@ -39,14 +39,15 @@ def _check_solution(A, B, X, eta_tol=1e-14):
     return eta
 
 
+@pytest.mark.parametrize("v", [None, 128])       # None: the default (v = 64, wide tournament)
 @pytest.mark.parametrize("prec", ["bf16", "f16"])
 @pytest.mark.parametrize("n,nrhs,V", [(1, 1, 0), (37, 2, 0), (129, 3, 0), (512, 16, 256), (1000, 4, 256),
                                       (2048, 16, 0)])
-def test_gesv_mixed_well_conditioned(cf, prec, n, nrhs, V):
+def test_gesv_mixed_well_conditioned(cf, prec, n, nrhs, V, v):
     A = inputs.uniform_pm1(n, seed=0, shift=2 * np.sqrt(n))
     B = inputs.rhs_normal(n, nrhs, seed=3)
     dA, dB = _dev(A), _dev(B)
-    X, info, stats, st = cf.gesv_mixed(dA, dB, prec=prec, outer_V=V)
+    X, info, stats, st = cf.gesv_mixed(dA, dB, prec=prec, outer_V=V, v=v)
     assert st == cf.CF_OK, stats.as_dict()
     assert int(info.item()) == 0 and stats.converged == 1
     np.testing.assert_array_equal(dA.cpu().numpy(), A)
@@ -338,8 +339,9 @@ def test_pair_residual_policy(cf, solver):
     assert np.abs(out[0] - out[1]).max() / np.abs(Xs).max() <= 8 * kappa * 1e-14
 
 
+@pytest.mark.parametrize("v", [None, 128])
 @pytest.mark.parametrize("prec", ["f16", "bf16x3"])
-def test_gesv_mixed_deep_slab(cf, prec):
+def test_gesv_mixed_deep_slab(cf, prec, v):
     """Slabs of V = 2048 (the LU default from n = 16384 on) at a size the host
     check affords: two slabs, the second ragged (4500 = 2048 + 2048 + 404),
     left-looking pivot-row updates with K up to 1920, split-BF16 operands
@@ -347,7 +349,7 @@ def test_gesv_mixed_deep_slab(cf, prec):
     n = 4500
     A = inputs.uniform_pm1(n, seed=9, shift=2 * np.sqrt(n))
     B = inputs.rhs_normal(n, 3, seed=10)
-    X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec=prec, outer_V=2048)
+    X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec=prec, outer_V=2048, v=v)
     assert st == cf.CF_OK, stats.as_dict()
     _check_solution(A, B, X.cpu().numpy())
 
@@ -392,7 +394,7 @@ def test_gesv_mixed_shape_checks(cf):
 def test_mixed_solve_full_size(cf, solver):
     """The benchmark's systems at N = 32768 in the launch configuration it
     times (LU: A = U[-1,1] + 2 sqrt(N) I, 16 right-hand sides, FP16 updates,
-    leaves of 256 rows; Cholesky: A = G G^T / N + I, 8 right-hand sides,
+    v = 64 with leaves of 512 rows and arity 8; Cholesky: A = G G^T / N + I, 8 right-hand sides,
     split-BF16 updates; alpha = lambda_max / (kappa - 1) for kappa = 1e2, as
     the benchmark sets it): the oracle's compensated residual over every row
     of a host copy gives eta <= 1e-14."""
@@ -400,7 +402,7 @@ def test_mixed_solve_full_size(cf, solver):
     if solver == "gesv":
         dA = inputs.uniform_pm1_torch(n, seed=0, shift=2.0 * np.sqrt(n), device="cuda")
         dB = inputs.rhs_normal_torch(n, 16, seed=3, device="cuda")
-        X, info, stats, st = cf.gesv_mixed(dA, dB, prec="f16", leaf_h=256)
+        X, info, stats, st = cf.gesv_mixed(dA, dB, prec="f16", v=64, leaf_h=512, arity=8)
     else:
         dA = inputs.spd_gram_torch(n, seed=1, alpha=0.0, device="cuda")
         inputs.shift_to_kappa_torch(dA, 1e2)

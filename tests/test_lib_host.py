@@ -34,7 +34,8 @@ def test_exports_every_declared_function(lib):
 def test_default_options_and_status_strings(lib):
     from paper_2108_09337_gb300 import cf
     o = cf.options()
-    assert (o.v, o.leaf_h, o.arity, o.lookahead, o.max_iter) == (128, 128, 2, 1, 30)
+    # v, leaf_h and arity are left 0: each routine takes its own default
+    assert (o.v, o.leaf_h, o.arity, o.lookahead, o.max_iter) == (0, 0, 0, 1, 30)
     assert o.tol == 1e-14
     lib.cf_status_string.restype = ctypes.c_char_p
     assert lib.cf_status_string(0) == b"ok"
