@@ -79,6 +79,8 @@ _SIG = {
     "cf_potrs": (_I, [_I, _I, _P, _I, _P, _I, _P]),
     "cf_residual": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P]),
     "cf_residual_pair_workspace_size": (_S, [_I, _I, _I]),
+    "cf_residual_tc_workspace_size": (_S, [_I, _I, _I]),
+    "cf_residual_tc": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _S, _P]),
     "cf_residual_pair": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _S, _P]),
     "cf_schur_update_lp": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
     "cf_device_status": (_I, [_P]),
@@ -286,6 +288,19 @@ def residual(A: torch.Tensor, X: torch.Tensor, B: torch.Tensor, R: torch.Tensor 
         R = fortran_empty(m, nrhs, device=A.device)
     _check("cf_residual", _lib.cf_residual(m, n, nrhs, _ptr(A), _ld(A, "A"), _ptr(X), _ld(X, "X"),
                                            _ptr(B), _ld(B, "B"), _ptr(R), _ld(R, "R"), _stream()))
+    return R
+
+
+def residual_tc(A: torch.Tensor, X: torch.Tensor, B: torch.Tensor, R: torch.Tensor | None = None):
+    """R = B - A X at FP64 accuracy on the tensor cores (cf_residual_tc)."""
+    m, n = A.shape
+    nrhs = X.shape[1] if X.dim() == 2 else 1
+    if R is None:
+        R = fortran_empty(m, nrhs, device=A.device)
+    ws = _workspace(_lib.cf_residual_tc_workspace_size(m, n, nrhs), A.device)
+    _check("cf_residual_tc", _lib.cf_residual_tc(m, n, nrhs, _ptr(A), _ld(A, "A"), _ptr(X), _ld(X, "X"),
+                                                 _ptr(B), _ld(B, "B"), _ptr(R), _ld(R, "R"), _ptr(ws), ws.numel(),
+                                                 _stream()))
     return R
 
 

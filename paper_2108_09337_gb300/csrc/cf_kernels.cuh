@@ -126,6 +126,22 @@ int launch_residual_pair(int m, int n, int nrhs, const double *A, int lda, const
                          cudaStream_t st);
 int launch_residual_pair_auto(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
                               const double *B, int ldb, double *R, int ldr, void *ws, cudaStream_t st);
+// R = B - A X at FP64 accuracy on the tensor cores from BF16 digit slices
+// (cf_resid_tc.cu).  resid_tc_prepare cuts A once (resid_tc_a_bytes of wsA,
+// kept while the slices are used); resid_tc_apply forms R for any X
+// (resid_tc_x_bytes of scratch; B null: R = A X).
+struct ResidTC {
+    int m, n, mpad, ldk;
+    void *S;          // 7 digit slices of A, K-major BF16, mpad rows each, pitch ldk
+    int *Ef;          // per-row largest exponent field of A
+};
+ResidTC resid_tc_layout(int m, int n);
+size_t resid_tc_a_bytes(int m, int n);
+size_t resid_tc_x_bytes(int m, int n);
+int resid_tc_prepare(ResidTC *L, const double *A, int lda, void *wsA, cudaStream_t st);
+int resid_tc_apply(const ResidTC &L, int nrhs, const double *X, int ldx, const double *B, int ldb, double *R, int ldr,
+                   void *wsX, cudaStream_t st);
+int rtc_take_status(cudaStream_t st, int *status);
 // R = B - A X for a thin X (nrhs columns).
 int launch_residual_f64(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
                         int ldb, double *R, int ldr, cudaStream_t st);

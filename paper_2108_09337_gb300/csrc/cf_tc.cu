@@ -317,10 +317,11 @@ extern "C" int cf_schur_update_lp(int m, int n, int k, const void *A_lp, int lda
 }
 
 extern "C" int cf_device_status(cudaStream_t stream) {
-    int s = 0, s8 = 0, st = 0;
+    int s = 0, s8 = 0, st = 0, sr = 0;
     int rc = cf::tc_take_status(stream, &s);
     if (rc != CF_OK) return rc;
     if ((rc = cf::fp8_take_status(stream, &s8)) != CF_OK) return rc;
     if ((rc = cf::trsv_take_status(stream, &st)) != CF_OK) return rc;
-    return s != 0 ? s : (s8 != 0 ? s8 : st);
+    if ((rc = cf::rtc_take_status(stream, &sr)) != CF_OK) return rc;
+    return s != 0 ? s : (s8 != 0 ? s8 : (st != 0 ? st : sr));
 }

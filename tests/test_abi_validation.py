@@ -62,6 +62,9 @@ CASES = {
     "cf_gesv_mixed": ((8, 2, P, 8, P, 8, P, 8, 3, P, None, P, BIG, None, None),
                       [(1, -1), (2, -1), (3, None), (4, 7), (5, None), (6, 7), (7, None), (8, 7), (9, 0),
                        (9, 1), (9, 6), (9, 4), (10, None)]),
+    "cf_residual_tc": ((8, 6, 2, P, 8, P, 6, P, 8, P, 8, P, BIG, None),
+                       [(1, -1), (2, -1), (3, -1), (4, None), (5, 7), (6, None), (7, 5), (8, None), (9, 7),
+                        (10, None), (11, 7)]),
     "cf_trsv_f32": ((0, 8, 2, P, 8, P, 8, P, BIG, None),
                     [(1, -1), (1, 4), (2, -1), (3, -1), (3, 17), (4, None), (5, 7), (6, None), (7, 7)]),
     "cf_trsv_f32_withheld": ((0, 8, 2, P, 8, P, 8, 0, P, BIG, None),
