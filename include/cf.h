@@ -86,8 +86,14 @@ typedef struct {
                           Cholesky) or 1..2 (mixed), 0 = as many as fit [0];
                           cf_batched_autotune picks it with v */
     int fp64_residual; /* mixed solvers: 1 = every residual and GMRES product
-                          in FP64 arithmetic; 0 = pair arithmetic (see
-                          cf_residual_pair) where the backward error allows [0] */
+                          in FP64 arithmetic (overrides residual_kind); 0 =
+                          as residual_kind says [0] */
+    int residual_kind; /* mixed solvers' residuals and GMRES products: 0 = on
+                          the tensor cores from digit slices of A
+                          (cf_residual_tc; the workspace holds the slices,
+                          14 n^2 bytes more) [0]; 2 = pair arithmetic
+                          (cf_residual_pair) where the backward error allows
+                          it, FP64 for the residual that decides convergence */
 } cf_options;
 
 void cf_default_options(cf_options *opt /* host */);
@@ -120,6 +126,9 @@ typedef struct {
     int tourn_launches;
     double tourn_flops;     /* their elimination flops: per GEPP on r rows x w
                                columns, sum_j (r-j-1)(2(w-j-1) + 1) */
+    double tc_ms;           /* device time inside the tensor-core residuals and
+                               products (slicing of A included) */
+    int tc_launches;        /* tensor-core products with A */
 } cf_refine_stats;
 
 /* One workspace query for every call that takes (work, lwork): the bytes

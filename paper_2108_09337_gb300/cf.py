@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
     _fields_ = [("v", ctypes.c_int), ("leaf_h", ctypes.c_int), ("arity", ctypes.c_int),
                 ("outer_V", ctypes.c_int), ("lookahead", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("batch_cps", ctypes.c_int),
-                ("fp64_residual", ctypes.c_int)]
+                ("fp64_residual", ctypes.c_int), ("residual_kind", ctypes.c_int)]
 
 
 class RefineStats(ctypes.Structure):
@@ -52,7 +52,8 @@ class RefineStats(ctypes.Structure):
                 ("residual_launches", ctypes.c_int), ("update_launches", ctypes.c_int),
                 ("gmres_iterations", ctypes.c_int), ("escalated", ctypes.c_int),
                 ("pair_ms", ctypes.c_double), ("pair_launches", ctypes.c_int),
-                ("tourn_ms", ctypes.c_double), ("tourn_launches", ctypes.c_int), ("tourn_flops", ctypes.c_double)]
+                ("tourn_ms", ctypes.c_double), ("tourn_launches", ctypes.c_int), ("tourn_flops", ctypes.c_double),
+                ("tc_ms", ctypes.c_double), ("tc_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

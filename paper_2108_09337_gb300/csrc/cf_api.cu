@@ -40,6 +40,8 @@ int resolve_options(const cf_options *in, Opts *o) {
     o->batch_cps = in->batch_cps;
     o->fp64_residual = in->fp64_residual;
     if (o->fp64_residual < 0 || o->fp64_residual > 1) return CF_ERR_UNSUPPORTED;
+    o->residual_kind = in->residual_kind;
+    if (o->residual_kind != 0 && o->residual_kind != 2) return CF_ERR_UNSUPPORTED;
     if (o->v < 1 || o->v > kMaxV) return CF_ERR_UNSUPPORTED;
     // the widest shapes any routine takes (FP32 tournament at v <= 64); each
     // routine checks its own narrower limits (FP64: leaf_h <= kMaxV, arity <= 4)
@@ -105,6 +107,7 @@ extern "C" void cf_default_options(cf_options *opt) {
     opt->gmres_restart = o.gmres_restart;
     opt->batch_cps = o.batch_cps;
     opt->fp64_residual = o.fp64_residual;
+    opt->residual_kind = o.residual_kind;
 }
 
 extern "C" const char *cf_status_string(int s) {

@@ -74,6 +74,7 @@ struct Opts {
     int max_iter = 30, gmres_restart = 30;
     int batch_cps = 0;           // batched calls: resident CTAs per SM (0 = as many as fit)
     int fp64_residual = 0;       // mixed solvers: 1 = no pair-arithmetic residuals
+    int residual_kind = 0;       // mixed solvers: 0 = tensor-core slices, 2 = pair / FP64
     // whether the caller set v, leaf_h, arity (0 selects the routine's default)
     bool v_set = false, h_set = false, ar_set = false;
 };

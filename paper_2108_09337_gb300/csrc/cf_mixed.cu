@@ -324,6 +324,9 @@ struct MixedWS {
     float *sc8 = nullptr;                  // FP8 tile scales: slab (rows/128 x V/128), then one step
     double *Xbest = nullptr;               // best iterate so far
     void *pairws = nullptr;                // pair-arithmetic residual workspace
+    bool use_tc = false;                   // residuals on the tensor cores (digit slices of A)
+    void *rtcA = nullptr, *rtcX = nullptr; // their slices of A, and per-product scratch
+    ResidTC rtc{};
     const unsigned long long *anorm = nullptr;   // bits of ||A||_inf (bound for the pair residual's scaling)
     size_t bytes = 0;
 };
@@ -393,6 +396,11 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
     w->sbits = cv.take<unsigned long long>(nrhs + 1);
     w->Xbest = cv.take<double>(blk + 1);
     w->pairws = cv.take<char>(pair_residual_ws_bytes(n, n));
+    w->use_tc = o.residual_kind == 0 && !o.fp64_residual;
+    if (w->use_tc) {
+        w->rtcA = cv.take<char>(resid_tc_a_bytes(n, n), 1024);
+        w->rtcX = cv.take<char>(resid_tc_x_bytes(n, n), 1024);
+    }
     w->sc8 = cv.take<float>((size_t)(ceil_div(n > 0 ? n : 1, 128) + 1) * (Vp / 128 + 2));
     w->bytes = cv.size();
     return CF_OK;
@@ -818,6 +826,7 @@ static int block_dots(int n, int nrhs, const double *V, int nv, const double *W,
 
 static int gmres_correct(int n, int nrhs, const double *A, int lda, double *X, int ldx, MixedWS &w, bool lu,
                          bool prec_f32, bool pair, double tau, cudaStream_t st, Timer &tres, int *inner) {
+    // products with A: tensor-core slices (w.use_tc), pair arithmetic or FP64
     const size_t blk = (size_t)n * nrhs;
     const int m = w.m;
     int rc;
@@ -850,8 +859,9 @@ static int gmres_correct(int n, int nrhs, const double *A, int lda, double *X, i
         if (all) break;
         const double *Vk = w.V + (size_t)k * blk;
         if ((rc = tres.begin(st))) return rc;
-        rc = pair ? launch_residual_pair(n, n, nrhs, A, lda, w.anorm, Vk, n, nullptr, 0, w.Y, n, w.pairws, st)
-                  : launch_residual_f64(n, n, nrhs, A, lda, Vk, n, nullptr, 0, w.Y, n, st);   // Y = A v_k
+        rc = w.use_tc ? resid_tc_apply(w.rtc, nrhs, Vk, n, nullptr, 0, w.Y, n, w.rtcX, st)   // Y = A v_k
+             : pair   ? launch_residual_pair(n, n, nrhs, A, lda, w.anorm, Vk, n, nullptr, 0, w.Y, n, w.pairws, st)
+                      : launch_residual_f64(n, n, nrhs, A, lda, Vk, n, nullptr, 0, w.Y, n, st);
         if (rc) return rc;
         if ((rc = tres.end(st, 2.0 * n * (double)n * nrhs))) return rc;
         if ((rc = apply_precond(n, nrhs, w.Y, w.Wv, w, lu, prec_f32, st))) return rc;                // w = M^{-1} Y
@@ -935,7 +945,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
 
     // ---- factorization (Cholesky retries with a diagonal shift on breakdown)
-    Timer tupd, tres, tpair, ttourn;
+    Timer tupd, tres, tpair, ttourn, ttc, tprep;
     double shift = 0.0;
     int hinfo = 0;
     bool need_rowsum = true;     // row sums of |A| come with the first W = fl32(A)
@@ -1022,13 +1032,21 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     double eta_prev = HUGE_VAL, eta_pp = HUGE_VAL, eta = HUGE_VAL, eta_best = HUGE_VAL;
     int it = 0, stall = 0, solver = 0, it_limit = o.max_iter;
     bool converged = false, escalated = false;
-    // R = B - A X in pair arithmetic or in FP64
+    // the digit slices of A for the tensor-core residuals, cut once per solve
+    if (w.use_tc) {
+        w.rtc = resid_tc_layout(n, n);
+        if ((rc = tprep.begin(st))) return rc;
+        if ((rc = resid_tc_prepare(&w.rtc, A, lda, w.rtcA, st))) return rc;
+        if ((rc = tprep.end(st, 0.0))) return rc;
+    }
+    // R = B - A X on the tensor cores, in pair arithmetic or in FP64
     auto residual = [&](bool pair) -> int {
-        Timer &t = pair ? tpair : tres;
+        Timer &t = w.use_tc ? ttc : pair ? tpair : tres;
         int rc2 = t.begin(st);
         if (rc2) return rc2;
-        rc2 = pair ? launch_residual_pair(n, n, nrhs, A, lda, w.anorm, X, ldx, B, ldb, w.R, ldr, w.pairws, st)
-                   : launch_residual_f64(n, n, nrhs, A, lda, X, ldx, B, ldb, w.R, ldr, st);
+        rc2 = w.use_tc ? resid_tc_apply(w.rtc, nrhs, X, ldx, B, ldb, w.R, ldr, w.rtcX, st)
+              : pair   ? launch_residual_pair(n, n, nrhs, A, lda, w.anorm, X, ldx, B, ldb, w.R, ldr, w.pairws, st)
+                       : launch_residual_f64(n, n, nrhs, A, lda, X, ldx, B, ldb, w.R, ldr, st);
         if (rc2) return rc2;
         return t.end(st, 2.0 * n * (double)n * nrhs);
     };
@@ -1069,7 +1087,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             const double rate = (it >= 3 && eta_pp < HUGE_VAL && eta_pp > 0.0) ? std::fmin(1.0, eta_prev / eta_pp)
                                                                               : kAssumedRate;
             const double pred = eta_prev < HUGE_VAL ? eta_prev * rate : HUGE_VAL;
-            pair = !o.fp64_residual && !(pred < kPairFloor);
+            pair = !w.use_tc && !o.fp64_residual && !(pred < kPairFloor);
             if ((rc = residual(pair))) return rc;
         }
         if ((rc = measure())) return rc;
@@ -1138,7 +1156,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             const bool prec_f32 = std::is_same<LP, fp8_e4m3>::value && !split;
             const bool gpair = !o.fp64_residual;
             if ((rc = gmres_correct(n, nrhs, A, lda, X, ldx, w, lu, prec_f32, gpair, kGmresTol, st,
-                                    gpair ? tpair : tres, &inner)))
+                                    w.use_tc ? ttc : gpair ? tpair : tres, &inner)))
                 return rc;
             S.gmres_iterations += inner;
         }
@@ -1152,6 +1170,8 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     CF_CUDA_TRY(cudaEventSynchronize(e2));
     int tstat = 0;
     if ((rc = trsv_take_status(st, &tstat))) return rc;
+    if (tstat != 0) return CF_ERR_TIMEOUT;
+    if ((rc = rtc_take_status(st, &tstat))) return rc;
     if (tstat != 0) return CF_ERR_TIMEOUT;
     float f_ms = 0, r_ms = 0;
     cudaEventElapsedTime(&f_ms, e0, e1);
@@ -1167,6 +1187,8 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     S.residual_launches = tres.launches;
     S.pair_ms = tpair.ms();
     S.pair_launches = tpair.launches;
+    S.tc_ms = ttc.ms() + tprep.ms();
+    S.tc_launches = ttc.launches;
     S.tourn_ms = ttourn.ms();
     S.tourn_launches = ttourn.launches;
     S.tourn_flops = ttourn.flops;

@@ -314,29 +314,34 @@ def test_tourn_select_f32_constructed_gepp(cf):
 
 
 @pytest.mark.parametrize("solver", ["gesv", "posv"])
-def test_pair_residual_policy(cf, solver):
-    """Refinement takes its early residuals in pair arithmetic and decides
-    convergence on an FP64 one: with the default options some products are
-    pair-arithmetic and at least one (the last) is FP64; fp64_residual = 1
-    takes none in pair arithmetic.  Both reach eta <= 1e-14 checked on the
-    host, and the answers agree to the refinement's accuracy."""
+def test_residual_policies(cf, solver):
+    """The three residual policies of the refinement: by default every
+    residual runs on the tensor cores (digit slices of A; no FP64 or pair
+    product); residual_kind = 2 takes the early residuals in pair arithmetic
+    and decides convergence on an FP64 one; fp64_residual = 1 takes all of
+    them in FP64.  All reach eta <= 1e-14 checked on the host, and the
+    answers agree to the refinement's accuracy."""
     n, nrhs = 2048, 4
     A = inputs.uniform_pm1(n, seed=2, shift=2 * np.sqrt(n)) if solver == "gesv" else inputs.spd_gram(n, seed=2)
     B = inputs.rhs_normal(n, nrhs, seed=5)
     fn = cf.gesv_mixed if solver == "gesv" else cf.posv_mixed
     out = {}
-    for f64 in (0, 1):
-        X, info, stats, st = fn(_dev(A), _dev(B), prec="f16", fp64_residual=f64)
+    for name, kw in (("tc", {}), ("pair", {"residual_kind": 2}), ("f64", {"fp64_residual": 1})):
+        X, info, stats, st = fn(_dev(A), _dev(B), prec="f16", **kw)
         assert st == cf.CF_OK, stats.as_dict()
-        out[f64] = X.cpu().numpy()
-        _check_solution(A, B, out[f64])
-        if f64:
-            assert stats.pair_launches == 0 and stats.residual_launches >= 1
+        out[name] = X.cpu().numpy()
+        _check_solution(A, B, out[name])
+        d = stats.as_dict()
+        if name == "tc":
+            assert d["tc_launches"] >= 1 and d["pair_launches"] == 0 and d["residual_launches"] == 0, d
+        elif name == "pair":
+            assert d["pair_launches"] >= 1 and d["residual_launches"] >= 1 and d["tc_launches"] == 0, d
         else:
-            assert stats.pair_launches >= 1 and stats.residual_launches >= 1, stats.as_dict()
+            assert d["pair_launches"] == 0 and d["residual_launches"] >= 1 and d["tc_launches"] == 0, d
     Xs = np.linalg.solve(A, B)
     kappa = np.linalg.cond(A, np.inf)
-    assert np.abs(out[0] - out[1]).max() / np.abs(Xs).max() <= 8 * kappa * 1e-14
+    for a in ("tc", "pair"):
+        assert np.abs(out[a] - out["f64"]).max() / np.abs(Xs).max() <= 8 * kappa * 1e-14
 
 
 @pytest.mark.parametrize("v", [None, 128])

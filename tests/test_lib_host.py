@@ -73,22 +73,28 @@ def test_argument_validation_returns_before_any_cuda_call(lib):
 
 def test_mixed_options_and_workspace(lib):
     """The refinement options and workspace queries of the mixed solvers:
-    fp64_residual takes 0 or 1 (anything else is refused by the size query,
-    which returns 0), the default is 0 (pair-arithmetic residuals where
-    allowed), deeper LU slabs from n = 16384 make the LU workspace grow
-    faster than the Cholesky one, and the pair-residual query is host-only
-    and linear in m + n."""
+    fp64_residual takes 0 or 1 and residual_kind 0 or 2 (anything else is
+    refused by the size query, which returns 0); by default the residuals run
+    on the tensor cores, whose digit slices of A (7 n^2 BF16) the workspace
+    holds, and fp64_residual = 1 or residual_kind = 2 drop them; deeper LU
+    slabs from n = 16384 make the LU workspace grow faster than the Cholesky
+    one, and the pair-residual query is host-only and linear in m + n."""
     from paper_2108_09337_gb300 import cf
     L = cf.lib()
     o = cf.options()
-    assert o.fp64_residual == 0
-    ok = cf.gesv_mixed_workspace_size(4096, 4, "f16")
-    assert ok > 0
-    assert cf.gesv_mixed_workspace_size(4096, 4, "f16", fp64_residual=1) == ok
-    assert cf.gesv_mixed_workspace_size(4096, 4, "f16", fp64_residual=2) == 0
-    assert cf.posv_mixed_workspace_size(4096, 4, "f16", fp64_residual=-1) == 0
-    lu16, ch16 = cf.gesv_mixed_workspace_size(16384, 16, "f16"), cf.posv_mixed_workspace_size(16384, 16, "f16")
-    lu8, ch8 = cf.gesv_mixed_workspace_size(8192, 16, "f16"), cf.posv_mixed_workspace_size(8192, 16, "f16")
+    assert o.fp64_residual == 0 and o.residual_kind == 0
+    n = 4096
+    tc = cf.gesv_mixed_workspace_size(n, 4, "f16")
+    ok = cf.gesv_mixed_workspace_size(n, 4, "f16", residual_kind=2)
+    assert ok > 0 and tc - ok >= 14 * n * n
+    assert cf.gesv_mixed_workspace_size(n, 4, "f16", fp64_residual=1) == ok
+    assert cf.gesv_mixed_workspace_size(n, 4, "f16", fp64_residual=2) == 0
+    assert cf.gesv_mixed_workspace_size(n, 4, "f16", residual_kind=1) == 0
+    assert cf.posv_mixed_workspace_size(n, 4, "f16", fp64_residual=-1) == 0
+    kw = dict(residual_kind=2)
+    lu16, ch16 = cf.gesv_mixed_workspace_size(16384, 16, "f16", **kw), cf.posv_mixed_workspace_size(16384, 16, "f16",
+                                                                                                    **kw)
+    lu8, ch8 = cf.gesv_mixed_workspace_size(8192, 16, "f16", **kw), cf.posv_mixed_workspace_size(8192, 16, "f16", **kw)
     assert lu16 - ch16 > 2 * (lu8 - ch8)          # Lb / Ub sized for V = 2048 vs 1024
     p1 = L.cf_residual_pair_workspace_size(1000, 1000, 16)
     p2 = L.cf_residual_pair_workspace_size(2000, 2000, 16)
