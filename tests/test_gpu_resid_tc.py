@@ -57,7 +57,7 @@ def test_fp32_accumulation_of_integer_products_is_exact(cf):
     dA = torch.from_numpy(A.astype(np.float32)).to(torch.bfloat16).cuda()
     dB = torch.from_numpy(B.astype(np.float32)).to(torch.bfloat16).cuda()
     C = torch.zeros((n, m), dtype=torch.float32, device="cuda").t()
-    cf.schur_update_lp(dA, dB, C, prec="bf16")
+    cf.schur_update_lp(dA, dB, C)
     ref = -(A.astype(np.int64) @ B.T.astype(np.int64))
     np.testing.assert_array_equal(C.cpu().numpy().astype(np.int64), ref)
 
