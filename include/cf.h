@@ -91,7 +91,7 @@ typedef struct {
     int residual_kind; /* mixed solvers' residuals and GMRES products: 0 = on
                           the tensor cores from digit slices of A
                           (cf_residual_tc; the workspace holds the slices,
-                          14 n^2 bytes more) [0]; 2 = pair arithmetic
+                          16 n^2 bytes more) [0]; 2 = pair arithmetic
                           (cf_residual_pair) where the backward error allows
                           it, FP64 for the residual that decides convergence */
 } cf_options;
@@ -281,17 +281,17 @@ int cf_residual_pair(int m, int n, int nrhs, const double *A, int lda,
 
 /* R-1 on the tensor cores at FP64 accuracy: R = B - A X (A m x n FP64, lda;
  * X n x nrhs FP64, ldx; B, R m x nrhs FP64; R may alias B; column-major).
- * Every a_ij is rounded to an integer q_ij = round(a_ij 2^(55 - E_i)) with
- * max_j |a_ij| < 2^E_i (X likewise per column) and cut into seven balanced
+ * Every a_ij is rounded to an integer q_ij = round(a_ij 2^(62 - E_i)) with
+ * max_j |a_ij| < 2^E_i (X likewise per column) and cut into eight balanced
  * base-256 digits held exactly in BF16; the products of digit pairs whose
- * weights add to at most 2^-48 below the leading pair are summed by tcgen05
+ * weights are at most 2^-56 below the leading pair are summed by tcgen05
  * MMAs with FP32 accumulation, exact because every 128-term chunk stays
  * below 2^24, then in int64; R is formed from those integer sums in
- * double-double.  Accuracy: a few 2^-56 of max_j |a_ij| ||x_k||_inf per term,
+ * double-double.  Accuracy: a few 2^-63 of max_j |a_ij| ||x_k||_inf per term,
  * below the FP64 product's own rounding (the mixed solvers use it for every
- * residual and GMRES product when their workspace has room for the slices).
- * work: cf_residual_tc_workspace_size(m, n, nrhs) bytes (14 m n bytes of
- * digit slices of A, cut on every call, plus 2 KB per row and 224 bytes per
+ * residual and GMRES product by default).
+ * work: cf_residual_tc_workspace_size(m, n, nrhs) bytes (16 m n bytes of
+ * digit slices of A, cut on every call, plus 1 KB per row and 256 bytes per
  * column of scratch).  Inf / NaN in a row of A (column of X) give NaN in
  * that row (column) of R.  Errors: -k for the k-th argument, CF_ERR_WORKSPACE;
  * a bounded device wait that runs out is reported by cf_device_status. */

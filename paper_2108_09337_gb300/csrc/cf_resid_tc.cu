@@ -6,30 +6,32 @@
 // while the BF16 tensor cores run ~500x faster.  The product is therefore
 // formed exactly from small integers:
 //   * per row i of A, E_i is the exponent with max_j |a_ij| < 2^E_i, and
-//     q_ij = round(a_ij 2^(55 - E_i)) (to nearest, ties away from zero) is an
-//     integer of at most 55 bits; X is cut the same way per column (F_k, p_jk);
-//   * q = sum_s d_s 256^(6-s) in seven balanced base-256 digits (the top one
-//     in [-128, 128], the others in [-128, 127]), each exact in BF16;
-//   * Q_d = sum_{s+t=d} sum_j d_s(q_ij) e_t(p_jk), d = 0..6 (the digit pairs
-//     below 2^-56 of the leading one are dropped): one tcgen05.mma chain per
+//     q_ij = round(a_ij 2^(62 - E_i)) (to nearest, ties away from zero) is an
+//     integer of at most 62 bits; X is cut the same way per column (F_k, p_jk);
+//   * q = sum_s d_s 256^(7-s) in eight balanced base-256 digits (the top one
+//     in [-64, 64], the others in [-128, 127]), each exact in BF16;
+//   * Q_d = sum_{s+t=d} sum_j d_s(q_ij) e_t(p_jk), d = 0..7 (the digit pairs
+//     below 2^-64 of the leading one are dropped): one tcgen05.mma chain per
 //     128-row tile accumulates, for every A digit s, the products with the X
-//     digits t = 0..6-s into the accumulator columns of diagonal s + t, so a
-//     single FP32 accumulator of 7 x 16 columns holds all seven diagonals.
-//     Every product is at most 2^14 and a chunk of 128 consecutive j adds at
-//     most 7 x 128 of them (< 2^24), so the FP32 accumulation of a chunk is
-//     exact in any order; chunks are added in int64 registers and K ranges
-//     in int64 with atomics (integers: exact and order-independent);
-//   * R = B - 2^(E_i + F_k - 62) sum_d Q_d 256^(6-d), combined in
+//     digits t = 0..7-s into the accumulator columns of diagonal s + t, so a
+//     single FP32 accumulator of 8 x 16 columns holds all eight diagonals.
+//     A product is at most 2^14 (2^13 with a top digit) and a chunk of 128
+//     consecutive j adds at most 128 products of each of 8 digit pairs, two
+//     of them with a top digit: at most 7 x 2^21 < 2^24, so the FP32
+//     accumulation of a chunk is exact in any order; chunks are added in int64
+//     registers and K ranges in int64 with atomics (integers: exact and
+//     order-independent);
+//   * R = B - 2^(E_i + F_k - 68) sum_d Q_d 256^(7-d), combined in
 //     double-double.
-// The error is a few 2^-56 of max_j |a_ij| ||x_k|| per term (the rounding of
-// q and p and the dropped pairs), well below the FP64 product's own.  The A
-// slices (7 m n BF16) are cut once and reused for every residual with the
-// same A.  Rows (columns of X) with a non-finite entry give NaN.
+// The error is a few 2^-63 of max_j |a_ij| ||x_k|| per term (the rounding of
+// q and p and the dropped pairs), below the FP64 product's own.  The A slices
+// (8 m n BF16) are cut once and reused for every residual with the same A.
+// Rows (columns of X) with a non-finite entry give NaN.
 //
 // Kernel layout (sm_103a): persistent CTAs over (128-row tile, K range)
-// units; warp 0 issues TMA loads (128-byte swizzle) of the X digits (112 x 64
-// per K block) and of the seven A digit tiles (128 x 64 each), warp 1 issues
-// the MMAs (M = 128, N = 112 - 16 s, K = 16) into one of two TMEM
+// units; warp 0 issues TMA loads (128-byte swizzle) of the X digits (128 x 64
+// per K block) and of the eight A digit tiles (128 x 64 each), warp 1 issues
+// the MMAs (M = 128, N = 128 - 16 s, K = 16) into one of two TMEM
 // accumulators, warps 2-9 read the other accumulator back after each chunk of
 // 128 K and add it to int64 registers.  Every mbarrier wait is bounded.
 #include <cuda.h>
@@ -49,7 +51,8 @@ namespace rtc {
 
 using namespace umma;
 
-constexpr int ND = 7;                 // digits per element
+constexpr int ND = 8;                 // digits per element
+constexpr int QBITS = 8 * ND - 2;     // fixed-point bits of q (top digit <= 64)
 constexpr int NR = 16;                // right-hand sides per launch (zero padded)
 constexpr int NCOL = ND * NR;         // accumulator columns: diagonal d, rhs k at d * NR + k
 constexpr int BM = 128, BK = 64, KC = 128;
@@ -57,7 +60,7 @@ constexpr int XST = 3, AST = 8;       // pipeline depths (X tiles, A digit tiles
 constexpr int UMMA_K = 16;
 constexpr int EPI = 8;                // epilogue warps
 constexpr int kThreads = 64 + 32 * EPI;
-constexpr uint32_t kXBytes = NCOL * BK * 2;   // 14336
+constexpr uint32_t kXBytes = NCOL * BK * 2;   // 16384
 constexpr uint32_t kABytes = BM * BK * 2;     // 16384
 constexpr uint32_t kAccStride = 128;          // TMEM columns per accumulator
 constexpr uint32_t kTmemCols = 256;
@@ -87,14 +90,6 @@ __device__ __forceinline__ void unit_coords(const Problem &p, int u, int &m0, in
     kb0 = kr * p.kb_per_range;
     kb1 = min(p.nkb, kb0 + p.kb_per_range);
 }
-
-#define TMEM_LD16(taddr, r)                                                                                   \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}," \
-                 " [%16];"                                                                                    \
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),        \
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),    \
-                   "=r"(r[14]), "=r"(r[15])                                                                   \
-                 : "r"(taddr))
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_resid_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, Problem p) {
@@ -226,8 +221,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         // ------------------------------------------------ epilogue (warps 2..9)
         const int e = warp - 2;
         const int quarter = warp & 3;             // TMEM lanes 32 * quarter ..
-        const int half = e >> 2;                  // columns 0..63 or 64..111
-        const int ncols = half == 0 ? 64 : NCOL - 64;
+        const int half = e >> 2;                  // columns 0..63 or 64..127
         long long acc[64];
 #pragma unroll
         for (int j = 0; j < 64; ++j) acc[j] = 0;
@@ -250,17 +244,10 @@ k_resid_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 32; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(r[j]));
-                if (half == 0) {
-                    TMEM_LD32(taddr + 32, r);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                TMEM_LD32(taddr + 32, r);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[32 + j] += (long long)__float2int_rn(__uint_as_float(r[j]));
-                } else {
-                    TMEM_LD16(taddr + 32, r);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[32 + j] += (long long)__float2int_rn(__uint_as_float(r[j]));
-                }
+                for (int j = 0; j < 32; ++j) acc[32 + j] += (long long)__float2int_rn(__uint_as_float(r[j]));
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s.acc_empty[b]);
@@ -271,7 +258,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             if (row < p.m) {
 #pragma unroll
                 for (int j = 0; j < 64; ++j)
-                    if (j < ncols && acc[j] != 0)
+                    if (acc[j] != 0)
                         atomicAdd(p.Q + (size_t)(64 * half + j) * p.mpad + row, (unsigned long long)acc[j]);
             }
 #pragma unroll
@@ -319,18 +306,19 @@ __global__ void __launch_bounds__(256) k_col_expmax(int n, int nrhs, const doubl
     if ((threadIdx.x & 31) == 0 && f > 0) atomicMax(Gf + k, f);
 }
 
-// q = round(x 2^(55 - E)), E = max(F, 1) - 1022 for the row's (column's)
-// largest exponent field F, as an integer of at most 55 bits, from the
-// bits of x (ties away from zero); then its seven balanced base-256 digits,
+// q = round(x 2^(62 - E)), E = max(F, 1) - 1022 for the row's (column's)
+// largest exponent field F, as an integer of at most 62 bits, from the
+// bits of x (ties away from zero); then its eight balanced base-256 digits,
 // most significant first.
-__device__ __forceinline__ void digits7(double x, int F, float (&dg)[ND]) {
+__device__ __forceinline__ void digits8(double x, int F, float (&dg)[ND]) {
     const long long bits = __double_as_longlong(x);
     const int f = (int)((bits >> 52) & 0x7FF);
     const long long mant = bits & ((1ll << 52) - 1);
     const long long m53 = f == 0 ? mant : (mant | (1ll << 52));
-    const int sh = (f == 0 ? 1 : f) - (F > 0 ? F : 1) + 2;      // <= 2 (f <= F)
+    // x 2^(62 - E) = m53 2^sh with sh = f - F + (62 - 53): at most 9 (f <= F)
+    const int sh = (f == 0 ? 1 : f) - (F > 0 ? F : 1) + (QBITS - 53);
     long long q;
-    if (sh >= 0) q = m53 << (sh > 2 ? 2 : sh);
+    if (sh >= 0) q = m53 << (sh > QBITS - 53 ? QBITS - 53 : sh);
     else if (-sh >= 60) q = 0;
     else q = (m53 + (1ll << (-sh - 1))) >> (-sh);
     if (bits < 0) q = -q;
@@ -343,7 +331,7 @@ __device__ __forceinline__ void digits7(double x, int F, float (&dg)[ND]) {
     dg[0] = (float)q;
 }
 
-// A (m x n FP64, column-major) -> seven BF16 digit slices, K-major: slice d
+// A (m x n FP64, column-major) -> eight BF16 digit slices, K-major: slice d
 // row i at S[(d * mpad + i) * ldk + j].  Thread: row i, 16 consecutive j.
 __global__ void __launch_bounds__(256) k_slice_a(int m, int n, const double *__restrict__ A, int lda, const int *Ef,
                                                  __nv_bfloat16 *S, int mpad, int ldk) {
@@ -355,7 +343,7 @@ __global__ void __launch_bounds__(256) k_slice_a(int m, int n, const double *__r
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
         const double x = (j0 + c < n) ? A[(size_t)i + (size_t)(j0 + c) * lda] : 0.0;
-        digits7(x, F, dg[c]);
+        digits8(x, F, dg[c]);
     }
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
@@ -377,7 +365,7 @@ __global__ void __launch_bounds__(256) k_slice_x(int n, int nrhs, const double *
     if (j >= n) return;
     float dg[ND];
     if (k < nrhs) {
-        digits7(X[(size_t)j + (size_t)k * ldx], Gf[k], dg);
+        digits8(X[(size_t)j + (size_t)k * ldx], Gf[k], dg);
     } else {
 #pragma unroll
         for (int d = 0; d < ND; ++d) dg[d] = 0.f;
@@ -392,8 +380,8 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
     e = (a - (s - bb)) + (b - bb);
 }
 
-// R = B - 2^(E_i + F_k - 62) sum_d Q_d 256^(6-d) in double-double; sign < 0
-// with B null gives R = A X (the product alone).
+// R = B - 2^(E_i + F_k - 68) sum_d Q_d 256^(7-d) in double-double; with B
+// null, R = A X (the product alone).
 __global__ void __launch_bounds__(256) k_resid_combine(int m, int nrhs, const unsigned long long *Q, int mpad,
                                                        const int *Ef, const int *Gf, const double *B, int ldb,
                                                        double *R, int ldr) {
@@ -416,7 +404,8 @@ __global__ void __launch_bounds__(256) k_resid_combine(int m, int nrhs, const un
             hi = s;
             lo += e;
         }
-        const int sc = ((F > 0 ? F : 1) - 1022) + ((G > 0 ? G : 1) - 1022) - 62;
+        // q p = 2^(2 QBITS - E - F) a x and sum_d Q_d 256^(7-d) = q p / 256^(ND - 1)
+        const int sc = ((F > 0 ? F : 1) - 1022) + ((G > 0 ? G : 1) - 1022) - 2 * QBITS + 8 * (ND - 1);
         hi = ldexp(hi, sc);
         lo = ldexp(lo, sc);
         double s, e;

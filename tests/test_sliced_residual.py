@@ -3,33 +3,34 @@ int64 and Python rationals), against the exact residual.
 
 R = B - A X is formed from integer digit slices:
 * per row i of A, E_i is the exponent with max_j |a_ij| < 2^E_i (frexp);
-  q_ij = round(a_ij 2^(55 - E_i)) (to nearest, ties away from zero), so
-  |q_ij| <= 2^55; per column k of X the same with F_k, giving p_jk;
-* q = sum_s d_s 256^(6 - s) with seven balanced base-256 digits (the six low
-  ones in [-128, 127], the top one in [-128, 128]), likewise p with e_t;
-* Q_d = sum_{s + t = d} sum_j d_s(q_ij) e_t(p_jk) for d = 0..6: every digit
+  q_ij = round(a_ij 2^(62 - E_i)) (to nearest, ties away from zero), so
+  |q_ij| <= 2^62; per column k of X the same with F_k, giving p_jk;
+* q = sum_s d_s 256^(7 - s) with eight balanced base-256 digits (the seven
+  low ones in [-128, 127], the top one in [-64, 64]), likewise p with e_t;
+* Q_d = sum_{s + t = d} sum_j d_s(q_ij) e_t(p_jk) for d = 0..7: every digit
   and every product is an integer exact in BF16 / FP32, and every partial sum
   over a chunk of 128 consecutive j stays below 2^24, so the tensor cores'
   FP32 accumulation of a chunk is exact whatever its order; chunks add up
   exactly in int64;
-* (A X)_ik ~ 2^(E_i + F_k - 62) sum_d Q_d 256^(6 - d) (the digit pairs with
-  s + t > 6 are dropped), and R = B - A X in double-double.
+* (A X)_ik ~ 2^(E_i + F_k - 68) sum_d Q_d 256^(7 - d) (the digit pairs with
+  s + t > 7 are dropped), and R = B - A X in double-double.
 
-The error must stay within a few 2^-53 of ||A||_inf ||x||_inf + ||b||_inf on
-rows that cancel, and the exactness bounds must hold; dropping the digit pairs
-of one more diagonal, or keeping fewer digits, must fail the bound.
+The error must stay within 2^-56 of ||A||_inf ||x||_inf + ||b||_inf on rows
+that cancel (eight times below FP64's unit roundoff), and the exactness
+bounds must hold; dropping the digit pairs of one more diagonal, or keeping
+fewer digits, must fail that bound.
 """
 from fractions import Fraction
 
 import numpy as np
 import pytest
 
-S = 7            # digits per element
-D = 6            # largest digit diagonal kept (s + t <= D)
+S = 8            # digits per element
+D = 7            # largest digit diagonal kept (s + t <= D)
 KC = 128         # K chunk accumulated in FP32 before it is added in int64
 
 
-def _fixed(v, E, bits=8 * S - 1):
+def _fixed(v, E, bits=8 * S - 2):
     """round(v 2^(bits - E)) to nearest, ties away from zero, as int64."""
     w = np.ldexp(v, bits - E)
     a = np.abs(w)
@@ -57,7 +58,7 @@ def _exps(M, axis):
 def sliced_residual(A, X, B, nd=S, dmax=D, kc=KC, stats=None):
     E = _exps(A, 1)
     F = _exps(X, 0)
-    bits = 8 * nd - 1
+    bits = 8 * nd - 2
     dA = _digits(_fixed(A, E[:, None], bits), nd)
     dX = _digits(_fixed(X, F[None, :], bits), nd)
     n = A.shape[1]
@@ -118,33 +119,34 @@ def test_sliced_residual_within_bound(n, nrhs, sa, sx):
     Re = _exact_residual(A, X, B)
     den = np.abs(A).sum(1).max() * np.abs(X).max(0) + np.abs(B).max(0)
     err = (np.abs(R - Re).max(0) / den).max()
-    assert err <= 4 * 2.0 ** -53, err
+    assert err <= 2.0 ** -56, err
     # the exactness arguments
     assert st["max_digit"] <= 128
     assert st["worst_chunk"] < 2 ** 24
-    # worst case of a chunk: 7 digit pairs of 128 x 128, 128 terms each
-    assert 7 * KC * 128 * 128 < 2 ** 24
+    # worst case of a chunk: 128 terms of 6 digit pairs of 128 x 128 and of 2
+    # pairs with a top digit (<= 64)
+    assert KC * (6 * 128 * 128 + 2 * 64 * 128) < 2 ** 24
 
 
 def test_sliced_residual_slips_fail_the_bound():
     A, X, B = _cancelling_system(300, 2, seed=1)
     Re = _exact_residual(A, X, B)
     den = np.abs(A).sum(1).max() * np.abs(X).max(0) + np.abs(B).max(0)
-    for kw in ({"dmax": 5}, {"nd": 5, "dmax": 4}):
+    for kw in ({"dmax": 6}, {"nd": 7, "dmax": 6}):
         R = sliced_residual(A, X, B, **kw)
         err = (np.abs(R - Re).max(0) / den).max()
-        assert err > 16 * 2.0 ** -53, (kw, err)
+        assert err > 2.0 ** -56, (kw, err)
 
 
 def test_digits_reconstruct_and_are_balanced():
     rng = np.random.default_rng(0)
-    q = rng.integers(-(2 ** 55), 2 ** 55, 5000, dtype=np.int64)
-    q[:4] = [2 ** 55, -(2 ** 55), 0, 128]
+    q = rng.integers(-(2 ** 62), 2 ** 62, 5000, dtype=np.int64)
+    q[:4] = [2 ** 62, -(2 ** 62), 0, 128]
     ds = _digits(q)
     back = np.zeros_like(q)
     for d in ds:
         back = back * 256 + d
     np.testing.assert_array_equal(back, q)
-    assert np.abs(ds[0]).max() <= 128
+    assert np.abs(ds[0]).max() <= 64
     for d in ds[1:]:
         assert d.min() >= -128 and d.max() <= 127
