@@ -127,9 +127,11 @@ int launch_residual_pair(int m, int n, int nrhs, const double *A, int lda, const
 int launch_residual_pair_auto(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
                               const double *B, int ldb, double *R, int ldr, void *ws, cudaStream_t st);
 // R = B - A X at FP64 accuracy on the tensor cores from BF16 digit slices
-// (cf_resid_tc.cu).  resid_tc_prepare cuts A once (resid_tc_a_bytes of wsA,
-// kept while the slices are used); resid_tc_apply forms R for any X
-// (resid_tc_x_bytes of scratch; B null: R = A X).
+// (cf_resid_tc.cu).  resid_tc_carve places the slices and the row exponent
+// fields in wsA (resid_tc_a_bytes, kept while the slices are used);
+// resid_tc_prepare cuts A (after computing Ef unless ef_ready: the caller
+// filled Ef with the row maxima of the exponent fields); resid_tc_apply forms
+// R for any X (resid_tc_x_bytes of scratch; B null: R = A X).
 struct ResidTC {
     int m, n, mpad, ldk;
     void *S;          // 7 digit slices of A, K-major BF16, mpad rows each, pitch ldk
@@ -138,7 +140,8 @@ struct ResidTC {
 ResidTC resid_tc_layout(int m, int n);
 size_t resid_tc_a_bytes(int m, int n);
 size_t resid_tc_x_bytes(int m, int n);
-int resid_tc_prepare(ResidTC *L, const double *A, int lda, void *wsA, cudaStream_t st);
+void resid_tc_carve(ResidTC *L, void *wsA);
+int resid_tc_prepare(ResidTC *L, const double *A, int lda, bool ef_ready, cudaStream_t st);
 int resid_tc_apply(const ResidTC &L, int nrhs, const double *X, int ldx, const double *B, int ldb, double *R, int ldr,
                    void *wsX, cudaStream_t st);
 int rtc_take_status(cudaStream_t st, int *status);

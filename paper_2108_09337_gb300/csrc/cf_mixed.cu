@@ -127,12 +127,13 @@ __global__ void k_iota(int n, int *p) {
 constexpr int kCvtCols = 1024;
 __global__ void __launch_bounds__(256) k_to_f32_rowsum(int n, const double *__restrict__ A, int lda,
                                                        float *__restrict__ W, int ldw, double shift, double *rowsum,
-                                                       int vec) {
+                                                       int *ef, int vec) {
     const int i = (blockIdx.x * 256 + threadIdx.x) * 2;
     if (i >= n) return;
     const int j0 = blockIdx.y * kCvtCols, j1 = min(n, j0 + kCvtCols);
     const bool two = i + 1 < n;
     double s0 = 0.0, s1 = 0.0;
+    int f0 = 0, f1 = 0;        // largest exponent fields (the tensor-core residual's row scales)
 #pragma unroll 4
     for (int j = j0; j < j1; ++j) {
         const double *src = A + (size_t)i + (size_t)j * lda;
@@ -147,6 +148,8 @@ __global__ void __launch_bounds__(256) k_to_f32_rowsum(int n, const double *__re
         }
         s0 += fabs(a0);
         s1 += fabs(a1);
+        f0 = max(f0, (int)((__double_as_longlong(a0) >> 52) & 0x7FF));
+        f1 = max(f1, (int)((__double_as_longlong(a1) >> 52) & 0x7FF));
         const float w0 = (i == j && shift != 0.0) ? (float)(a0 + shift) : (float)a0;
         const float w1 = (i + 1 == j && shift != 0.0) ? (float)(a1 + shift) : (float)a1;
         float *dst = W + (size_t)i + (size_t)j * ldw;
@@ -157,15 +160,19 @@ __global__ void __launch_bounds__(256) k_to_f32_rowsum(int n, const double *__re
         atomicAdd(rowsum + i, s0);
         if (two) atomicAdd(rowsum + i + 1, s1);
     }
+    if (ef) {
+        if (f0 > 0) atomicMax(ef + i, f0);
+        if (two && f1 > 0) atomicMax(ef + i + 1, f1);
+    }
 }
 
 static int launch_to_f32_rowsum(int n, const double *A, int lda, float *W, int ldw, double shift, double *rowsum,
-                                cudaStream_t st) {
+                                int *ef, cudaStream_t st) {
     if (n <= 0) return CF_OK;
     if (ldw % 2 != 0 || ((uintptr_t)W & 7)) return CF_ERR_UNSUPPORTED;
     const int vec = (lda % 2 == 0 && ((uintptr_t)A & 15) == 0) ? 1 : 0;
     dim3 g(ceil_div(n, 512), ceil_div(n, kCvtCols));
-    k_to_f32_rowsum<<<g, 256, 0, st>>>(n, A, lda, W, ldw, shift, rowsum, vec);
+    k_to_f32_rowsum<<<g, 256, 0, st>>>(n, A, lda, W, ldw, shift, rowsum, ef, vec);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
@@ -935,6 +942,10 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     if (rc) return rc;
     if (work == nullptr || lwork < w.bytes) return CF_ERR_WORKSPACE;
     if ((rc = carve_mixed(work, n, nrhs, o, lu, &w))) return rc;
+    if (w.use_tc) {
+        w.rtc = resid_tc_layout(n, n);
+        resid_tc_carve(&w.rtc, w.rtcA);
+    }
 
     cf_refine_stats S{};
     ScopedEvent e0, e1, e2;
@@ -960,7 +971,9 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
         for (int attempt = 0; attempt < 4; ++attempt) {
             // W = fl32(A) (+ shift on the diagonal)
             if (need_rowsum) CF_CUDA_TRY(cudaMemsetAsync(w.rowsum, 0, sizeof(double) * (n > 0 ? n : 1), st));
-            rc2 = launch_to_f32_rowsum(n, A, lda, w.W, w.ldw, shift, need_rowsum ? w.rowsum : nullptr, st);
+            if (need_rowsum && w.use_tc) CF_CUDA_TRY(cudaMemsetAsync(w.rtc.Ef, 0, sizeof(int) * (size_t)w.rtc.mpad, st));
+            rc2 = launch_to_f32_rowsum(n, A, lda, w.W, w.ldw, shift, need_rowsum ? w.rowsum : nullptr,
+                                       need_rowsum && w.use_tc ? w.rtc.Ef : nullptr, st);
             if (rc2) return rc2;
             need_rowsum = false;
             CF_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int), st));
@@ -1033,10 +1046,10 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     int it = 0, stall = 0, solver = 0, it_limit = o.max_iter;
     bool converged = false, escalated = false;
     // the digit slices of A for the tensor-core residuals, cut once per solve
+    // (the row exponent fields came with the first W = fl32(A))
     if (w.use_tc) {
-        w.rtc = resid_tc_layout(n, n);
         if ((rc = tprep.begin(st))) return rc;
-        if ((rc = resid_tc_prepare(&w.rtc, A, lda, w.rtcA, st))) return rc;
+        if ((rc = resid_tc_prepare(&w.rtc, A, lda, true, st))) return rc;
         if ((rc = tprep.end(st, 0.0))) return rc;
     }
     // R = B - A X on the tensor cores, in pair arithmetic or in FP64

@@ -322,13 +322,15 @@ __device__ __forceinline__ void digits8(double x, int F, float (&dg)[ND]) {
     else if (-sh >= 60) q = 0;
     else q = (m53 + (1ll << (-sh - 1))) >> (-sh);
     if (bits < 0) q = -q;
+    // the seven low digits are the bytes of q + 128 (1 + 256 + ... + 256^6)
+    // less 128 each, the top one what is left above them (|top| <= 64)
+    const long long t = q + 0x0080808080808080ll;
+    const unsigned lo = (unsigned)t, hi = (unsigned)(t >> 32);
 #pragma unroll
-    for (int t = ND - 1; t >= 1; --t) {
-        const long long d = ((q + 128) & 255) - 128;
-        dg[t] = (float)d;
-        q = (q - d) >> 8;
-    }
-    dg[0] = (float)q;
+    for (int b = 0; b < 4; ++b) dg[ND - 1 - b] = (float)((lo >> (8 * b)) & 255u) - 128.f;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) dg[ND - 5 - b] = (float)((hi >> (8 * b)) & 255u) - 128.f;
+    dg[0] = (float)(t >> 56);
 }
 
 // A (m x n FP64, column-major) -> eight BF16 digit slices, K-major: slice d
@@ -465,18 +467,24 @@ size_t resid_tc_x_bytes(int m, int n) {
     return cv.size();
 }
 
-int resid_tc_prepare(ResidTC *L, const double *A, int lda, void *wsA, cudaStream_t st) {
+void resid_tc_carve(ResidTC *L, void *wsA) {
     Carver cv(wsA);
-    __nv_bfloat16 *S = cv.take<__nv_bfloat16>((size_t)rtc::ND * L->mpad * L->ldk, 1024);
-    L->S = S;
+    L->S = cv.take<__nv_bfloat16>((size_t)rtc::ND * L->mpad * L->ldk, 1024);
     L->Ef = cv.take<int>(L->mpad);
+}
+
+int resid_tc_prepare(ResidTC *L, const double *A, int lda, bool ef_ready, cudaStream_t st) {
     const int m = L->m, n = L->n;
     if (m <= 0 || n <= 0) return CF_OK;
-    CF_CUDA_TRY(cudaMemsetAsync(L->Ef, 0, sizeof(int) * (size_t)L->mpad, st));
-    const int cols_per = 256;
-    rtc::k_row_expmax<<<dim3(ceil_div(m, 256), ceil_div(n, cols_per)), 256, 0, st>>>(m, n, A, lda, cols_per, L->Ef);
-    CF_LAUNCH_CHECK();
-    rtc::k_slice_a<<<dim3(ceil_div(m, 32), ceil_div(n, 128)), 256, 0, st>>>(m, n, A, lda, L->Ef, S, L->mpad, L->ldk);
+    if (!ef_ready) {
+        CF_CUDA_TRY(cudaMemsetAsync(L->Ef, 0, sizeof(int) * (size_t)L->mpad, st));
+        const int cols_per = 256;
+        rtc::k_row_expmax<<<dim3(ceil_div(m, 256), ceil_div(n, cols_per)), 256, 0, st>>>(m, n, A, lda, cols_per,
+                                                                                        L->Ef);
+        CF_LAUNCH_CHECK();
+    }
+    rtc::k_slice_a<<<dim3(ceil_div(m, 32), ceil_div(n, 128)), 256, 0, st>>>(
+        m, n, A, lda, L->Ef, reinterpret_cast<__nv_bfloat16 *>(L->S), L->mpad, L->ldk);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
@@ -584,7 +592,8 @@ extern "C" int cf_residual_tc(int m, int n, int nrhs, const double *A, int lda, 
     void *wa = cv.take<char>(resid_tc_a_bytes(m, n), 1024);
     void *wx = cv.take<char>(resid_tc_x_bytes(m, n), 1024);
     ResidTC L = resid_tc_layout(m, n);
-    int rc = resid_tc_prepare(&L, A, lda, wa, stream);
+    resid_tc_carve(&L, wa);
+    int rc = resid_tc_prepare(&L, A, lda, false, stream);
     if (rc != CF_OK) return rc;
     return resid_tc_apply(L, nrhs, X, ldx, B, ldb, R, ldr, wx, stream);
 }
