@@ -591,7 +591,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     pair = kern("pair_ms", "pair_launches", sum(2.0 * n * n * k * s["pair_launches"] for s, k in allst))
     upd = kern("update_ms", "update_launches", sum(s["update_flops"] for s, _ in allst))
     tourn = kern("tourn_ms", "tourn_launches", sum(s["tourn_flops"] for s, _ in allst))
+    # tensor-core residuals (their time includes cutting A into digit slices
+    # once per solve): algorithmic bytes = the eight BF16 slices of A read per
+    # product, 16 N^2
+    rtc = kern("tc_ms", "tc_launches", sum(16.0 * n * n * s["tc_launches"] for s, _ in allst))
     bf16_pk = peaks.get("bf16_tflops_sustained") or 1700.0
+    hbm_pk = (peaks.get("hbm_gbs") or 6800.0) / 1e3        # TB/s, so that bytes / ms / 1e9 compare
     cand = {
         "tourn32": (tourn, ("k_tourn32w (LU-1, FP32 tournament pivoting, v=%d, leaves of %d rows, arity %d; "
                             "latency-bound: one barrier per column per tree level)" % (args.v, args.leaf_h, args.arity)
@@ -606,15 +611,18 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "residual_pair": (pair, "k_residual_pair (R-1 in FP32 pair arithmetic)", "alu", fp32_peak / 12.0,
                           "FP32 nominal / 12 (12 FP32 operations per term and right-hand side, 2 flops)",
                           None),
+        "residual_tc": (rtc, "k_resid_tc (R-1 on the tensor cores: digit slices of A, exact FP32 chunk sums)",
+                        "hbm", hbm_pk, "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
+                        else "fallback 6.8 TB/s", None),
         "schur_tc_KV": (upd, "k_schur_tc (LU-5/CH-3, K=V tcgen05 update)", "tensor", bf16_pk,
                         "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks
                         else "fallback 1.7 PFLOP/s sustained", None),
     }
     kernels = {}
-    for name, ((ms, cnt, fl), _, _, pk, _, _) in cand.items():
-        t = (fl / (ms * 1e-3) / 1e12) if ms else None
-        kernels[name] = {"ms_per_step": ms / args.steps, "launches_per_step": cnt / args.steps, "tflops": t,
-                         "frac_of_peak": (t / pk) if t else None}
+    for name, ((ms, cnt, fl), _, bound, pk, _, _) in cand.items():
+        t = (fl / (ms * 1e-3) / 1e12) if ms else None      # TFLOP/s, or TB/s for an HBM-bound kernel
+        kernels[name] = {"ms_per_step": ms / args.steps, "launches_per_step": cnt / args.steps,
+                         ("tb_per_s" if bound == "hbm" else "tflops"): t, "frac_of_peak": (t / pk) if t else None}
     # the K = V updates of each solve: algorithmic rate, and the tensor-pipe
     # rate (split BF16 runs three products per algorithmic flop)
     for name, sts, pr in (("schur_tc_KV_lu", stats_lu, prec), ("schur_tc_KV_chol", stats_ch, cprec)):
@@ -627,7 +635,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     top = max(cand, key=lambda k: cand[k][0][0])
     (ms, cnt, fl), label, bound, pk, src, traffic = cand[top]
     ach = (fl / max(cnt, 1)) / (ms / max(cnt, 1) * 1e-3) / 1e12 if cnt else 0.0
-    roof = {"kernel": label, "bound": bound, "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+    if bound == "hbm":            # report GB/s against the measured copy bandwidth
+        ach, pk = ach * 1e3, pk * 1e3
+    roof = {"kernel": label, "bound": bound, "achieved": ach, "peak": pk,
+            "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": ach / pk,
             "traffic": traffic, "peak_source": src, "launches": cnt, "avg_ms": ms / max(cnt, 1)}
     if top == "residual_f64":
         roof["traffic_note"] = "bytes per launch, ncu capture at N=8192 scaled by N^2"

@@ -466,14 +466,17 @@ int cf_batched_autotune(int batch, const int *n_host, const int *kind_host,
  * Refinement: classical (x += M^{-1} r with the FP32 factors M) while each
  * step cuts eta by at least 0.3x; after the first step that does not, GMRES-IR
  * (left-preconditioned GMRES with M, restart opt->gmres_restart) for every
- * remaining step.  Residuals: in pair arithmetic (cf_residual_pair) while
+ * remaining step.  Residuals and GMRES products with A: on the tensor cores
+ * (cf_residual_tc, the digit slices of A cut once per solve) by default;
+ * with opt->residual_kind = 2, in pair arithmetic (cf_residual_pair) while
  * the backward error predicted from the last two steps is at least 1e-12,
- * else in FP64; a pair-arithmetic eta below 1e-12 is recomputed in FP64
- * before it is used, so convergence to tol < 1e-12 is always decided on an
- * FP64 residual.  GMRES products with A: pair arithmetic.
- * opt->fp64_residual = 1 takes every product in FP64.
+ * else in FP64 (a pair-arithmetic eta below 1e-12 is recomputed in FP64
+ * before it is used, so convergence to tol < 1e-12 is decided on an FP64
+ * residual), GMRES products in pair arithmetic; opt->fp64_residual = 1 takes
+ * every product in FP64.
  * If refinement stalls (max_iter steps, a GMRES-IR step that fails to halve
- * eta, or a breakdown of the low-precision factorization), the
+ * eta or, with 16-bit factors, needs 12 or more inner steps to cut it by less
+ * than 100x, or a breakdown of the low-precision factorization), the
  * matrix is refactored once with CF_BF16X3 updates and refinement continues
  * from the best iterate with a fresh step budget (stats->escalated = 1).
  * Returns CF_ERR_NOT_CONVERGED if that also stalls (max_iter more steps, or

@@ -245,6 +245,11 @@ constexpr double kSwitchRate = 0.3;    // classical refinement must cut eta at l
 // backward error is predicted at or above kPairFloor takes one, and an eta
 // below kPairFloor from one is recomputed in FP64.
 constexpr double kPairFloor = 1e-12;
+// A GMRES-IR step with 16-bit factors that needed at least kSlowInner inner
+// iterations and cut eta by less than kSlowGain counts as failed: another
+// such step costs more than refactoring with split BF16 updates.
+constexpr int kSlowInner = 12;
+constexpr double kSlowGain = 1e-2;
 constexpr double kAssumedRate = 1e-2;
 
 // part[(chunk * nv + i) * nrhs + c] = sum over the chunk's rows of V_i[r, c] * W[r, c]
@@ -1043,7 +1048,8 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     std::vector<unsigned long long> hn(3 * nrhs + 2);
     std::vector<double> hscale(nrhs);
     double eta_prev = HUGE_VAL, eta_pp = HUGE_VAL, eta = HUGE_VAL, eta_best = HUGE_VAL;
-    int it = 0, stall = 0, solver = 0, it_limit = o.max_iter;
+    int it = 0, stall = 0, solver = 0, it_limit = o.max_iter, last_inner = 0;
+    bool used_gmres = false;
     bool converged = false, escalated = false;
     // the digit slices of A for the tensor-core residuals, cut once per solve
     // (the row exponent fields came with the first W = fl32(A))
@@ -1126,9 +1132,12 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             solver = 1;
             if ((rc = launch_diag_inverse64(lu ? 0 : 2, n, w.W, w.ldw, w.DinvL64, st))) return rc;
             if (lu && (rc = launch_diag_inverse64(1, n, w.W, w.ldw, w.DinvU64, st))) return rc;
-        } else if (!give_up && solver == 1 && !(eta <= 0.5 * eta_prev)) {
-            // before escalating one failed GMRES-IR step is enough (refactoring
-            // costs about one step); after it, two in a row
+        } else if (!give_up && solver == 1 &&
+                   (!(eta <= 0.5 * eta_prev) ||
+                    (!split && !std::is_same<LP, fp8_e4m3>::value && last_inner >= kSlowInner &&
+                     !(eta <= kSlowGain * eta_prev)))) {
+            // before escalating one failed (or slow) GMRES-IR step is enough
+            // (refactoring costs about one step); after it, two failed in a row
             give_up = ++stall >= (split ? 2 : 1);
         } else {
             stall = 0;
@@ -1150,6 +1159,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             }
             solver = 0;
             stall = 0;
+            last_inner = 0;
             eta_prev = eta_pp = HUGE_VAL;
             it_limit = it + o.max_iter;
             continue;
@@ -1166,12 +1176,14 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
             CF_LAUNCH_CHECK();
         } else {
             int inner = 0;
+            used_gmres = true;
             const bool prec_f32 = std::is_same<LP, fp8_e4m3>::value && !split;
             const bool gpair = !o.fp64_residual;
             if ((rc = gmres_correct(n, nrhs, A, lda, X, ldx, w, lu, prec_f32, gpair, kGmresTol, st,
                                     w.use_tc ? ttc : gpair ? tpair : tres, &inner)))
                 return rc;
             S.gmres_iterations += inner;
+            last_inner = inner;
         }
     }
     if (!converged && eta_best < eta) {   // hand back the best iterate
@@ -1190,7 +1202,7 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     cudaEventElapsedTime(&f_ms, e0, e1);
     cudaEventElapsedTime(&r_ms, e1, e2);
     S.iterations = it;
-    S.solver = solver;
+    S.solver = used_gmres ? 1 : 0;
     S.escalated = escalated ? 1 : 0;
     S.converged = converged ? 1 : 0;
     S.eta = eta;
