@@ -75,10 +75,14 @@ typedef struct {
     int outer_V;       /* mixed LU/Cholesky: depth of the deferred update,
                           multiple of v [0 = auto: 2048 for LU at n >= 16384,
                           1024 at n >= 8192, 512 below] */
-    int lookahead;     /* cf_getrf: 1 = LU-6 look-ahead (TournPivot of step
-                          t+1 on a high-priority stream while the wide update
-                          of step t runs on a low-priority one), 0 = one
-                          stream [1]; the other routines ignore it */
+    int lookahead;     /* LU-6 look-ahead [1]; 0 = one stream.  cf_getrf:
+                          TournPivot of step t+1 on a high-priority stream
+                          while the wide update of step t runs on a
+                          low-priority one; mixed LU: the next panel's
+                          columns are updated first and the rest of the
+                          slab's update runs on a second stream beside
+                          TournPivot of step t+1.  Results do not depend on
+                          it; the other routines ignore it */
     double tol;        /* refinement stop: max backward error [1e-14] */
     int max_iter;      /* refinement iterations [30] */
     int gmres_restart; /* GMRES-IR Krylov dimension per correction, 1..256 [30] */

@@ -524,6 +524,34 @@ struct SideStream {
     }
 };
 
+// LU-6 look-ahead of the mixed LU: the part of a step's in-slab update right
+// of the next panel runs on this stream while TournPivot of the next step
+// (which reads only the next panel's columns, updated first on the main
+// stream) runs; the next step's row swaps wait for it.
+struct LookStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    int open() {
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess)
+            return CF_ERR_CUDA;
+        return CF_OK;
+    }
+    ~LookStream() {
+        if (fork) cudaEventDestroy(fork);
+        if (done) cudaEventDestroy(done);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+static int device_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 148;
+}
+
 template <typename LP>
 static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu, bool split,
                        Timer *tt = nullptr) {
@@ -536,6 +564,10 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
     int rc;
     SideStream ss;
     if ((rc = ss.open())) return rc;
+    LookStream la;
+    if (o.lookahead && (rc = la.open())) return rc;
+    bool la_pending = false;               // the look-ahead stream holds an update the next swaps must wait for
+    const int sms = device_sms();
     k_iota<<<grid_for(n), 256, 0, st>>>(n, w.perm);
     CF_LAUNCH_CHECK();
     CF_CUDA_TRY(cudaMemsetAsync(w.tws.counter, 0, w.tws.counter_bytes, st));
@@ -550,6 +582,10 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             if (tt && (rc = tt->begin(st))) return rc;
             if ((rc = launch_tourn32_any(A00, w.ldw, m, wd, o.leaf_h, o.arity, w.tws, w.tep, st))) return rc;
             if (tt && (rc = tt->end(st, tourn32_flops(m, wd, o.leaf_h, o.arity)))) return rc;
+            if (la_pending) {            // the previous step's update right of this panel
+                CF_CUDA_TRY(cudaStreamWaitEvent(st, la.done, 0));
+                la_pending = false;
+            }
             if ((rc = launch_apply_swaps<float>(W, w.ldw, n, k0, w.tep, w.perm, st))) return rc;
             // Fork: the side stream takes the pivot rows' left-looking update
             // (concurrent with the A00 LU) and LU-4 with its operand copies
@@ -622,9 +658,30 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             // depth: the step's columns rounded up to 64 (the operands are
             // zero past wd); the split form's three segments sit kMaxV apart
             const int Kin = split ? S * kMaxV : (wd + 63) / 64 * 64;
-            if (nslab > 0 && (rc = launch_schur_tc(below, nslab, Kin, w.Ab, S * kMaxV, w.Bb, S * kMaxV, C,
-                                                   w.ldw, bf16, false, st, 0)))
+            if (nslab <= 0) continue;
+            const int wn = v < nslab ? v : nslab;        // the next panel's columns
+            const bool split_la = o.lookahead && nslab > wn;
+            if (split_la) CF_CUDA_TRY(cudaEventRecord(la.fork, st));
+            if ((rc = launch_schur_tc(below, split_la ? wn : nslab, Kin, w.Ab, S * kMaxV, w.Bb, S * kMaxV, C, w.ldw,
+                                      bf16, false, st, 0)))
                 return rc;
+            if (split_la) {
+                // the rest of the slab's columns beside the next TournPivot,
+                // on the SMs its leaves leave free
+                CF_CUDA_TRY(cudaStreamWaitEvent(la.s, la.fork, 0));
+                int cap = sms - ceil_div(below, o.leaf_h);
+                if (cap < sms / 4) cap = sms / 4;
+                if ((rc = launch_schur_tc(below, nslab - wn, Kin, w.Ab, S * kMaxV,
+                                          (const uint16_t *)w.Bb + (size_t)wn * S * kMaxV, S * kMaxV,
+                                          C + (size_t)wn * ld, w.ldw, bf16, false, la.s, cap)))
+                    return rc;
+                CF_CUDA_TRY(cudaEventRecord(la.done, la.s));
+                la_pending = true;
+            }
+        }
+        if (la_pending) {
+            CF_CUDA_TRY(cudaStreamWaitEvent(st, la.done, 0));
+            la_pending = false;
         }
         if (JE < n) {
             // deferred update of everything right of and below the slab

@@ -381,6 +381,24 @@ def test_gesv_mixed_wide_tournament(cf, prec, n, V, shift):
     _check_solution(A, B, X.cpu().numpy())
 
 
+@pytest.mark.parametrize("prec,n,V,v", [("f16", 2048, 0, None), ("bf16x3", 4500, 2048, None), ("f16", 3000, 1024, 128)])
+def test_gesv_mixed_lookahead_identical(cf, prec, n, V, v):
+    """LU-6 look-ahead in the mixed LU (the rest of each step's in-slab
+    update on a second stream beside the next TournPivot) computes exactly
+    what the one-stream schedule computes: the solutions agree bit for bit
+    (so do the pivots and factors they come from), and reach eta <= 1e-14."""
+    A = inputs.uniform_pm1(n, seed=n + 3)
+    B = inputs.rhs_normal(n, 4, seed=9)
+    out = {}
+    for la in (0, 1):
+        X, info, stats, st = cf.gesv_mixed(_dev(A), _dev(B), prec=prec, outer_V=V, v=v, lookahead=la)
+        assert st == cf.CF_OK and int(info.item()) == 0, stats.as_dict()
+        out[la] = (X.cpu().numpy(), stats.iterations, stats.gmres_iterations)
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
+    _check_solution(A, B, out[1][0])
+
+
 def test_gesv_mixed_shape_checks(cf):
     """Tournament shapes the mixed LU cannot run are refused before any work
     (v = 128 takes arity 2 and leaves <= 256; v <= 64 takes arity * v <= 512)."""
