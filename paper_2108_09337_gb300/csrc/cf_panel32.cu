@@ -491,16 +491,18 @@ k_ltrsm32(float *X, int ldx, int w, int cols, const float *__restrict__ L00, int
 }
 
 // ---------------------------------------------------------------------------
+// One thread per row of A00, in whole warps (fewer warps in each barrier for
+// narrow blocks: w = 64 takes two).
 int launch_a00_lu32(float *A00, int lda, int w, int kglob, int *info, cudaStream_t st) {
     if (w <= 0) return CF_OK;
-    k_a00_lu32<<<1, kMaxV, 0, st>>>(A00, lda, w, kglob, info);
+    k_a00_lu32<<<1, (w + 31) / 32 * 32, 0, st>>>(A00, lda, w, kglob, info);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
 
 int launch_a00_chol32(float *A00, int lda, int w, int kglob, int *info, cudaStream_t st) {
     if (w <= 0) return CF_OK;
-    k_a00_chol32<<<1, kMaxV, 0, st>>>(A00, lda, w, kglob, info);
+    k_a00_chol32<<<1, (w + 31) / 32 * 32, 0, st>>>(A00, lda, w, kglob, info);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
