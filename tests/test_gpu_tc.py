@@ -66,3 +66,27 @@ def test_schur_update_many_tiles_persistent(cf):
     """More tiles than SMs: every CTA walks several tiles and reuses both
     TMEM accumulators."""
     _run(cf, 2048, 8192, 128, torch.bfloat16, seed=5)
+
+
+def test_schur_update_slab_depth(cf):
+    """The mixed LU's K = V slab update at its timed depth, M = N = 8192,
+    K = 2048 (FP16 operands, 0.6 GB with C): 4096 sampled entries against the
+    FP64 product of the same operands, within the FP32-accumulation bound."""
+    m = n = 8192
+    k = 2048
+    g = torch.Generator(device="cuda").manual_seed(11)
+    A = torch.randn((m, k), generator=g, device="cuda").to(torch.float16)
+    B = torch.randn((n, k), generator=g, device="cuda").to(torch.float16)
+    C0 = torch.randn((n, m), generator=g, device="cuda", dtype=torch.float32).t()
+    C = C0.clone().t().contiguous().t()
+    cf.schur_update_lp(A, B, C)
+    assert cf.device_status() == 0
+    rng = np.random.default_rng(3)
+    ii, jj = rng.integers(0, m, 4096), rng.integers(0, n, 4096)
+    Ad = A[torch.from_numpy(ii).cuda()].double().cpu().numpy()
+    Bd = B[torch.from_numpy(jj).cuda()].double().cpu().numpy()
+    c0 = C0[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].double().cpu().numpy()
+    got = C[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].double().cpu().numpy()
+    ref = c0 - np.einsum("ik,ik->i", Ad, Bd)
+    bound = 2 * (k + 2) * 2.0 ** -24 * (np.einsum("ik,ik->i", np.abs(Ad), np.abs(Bd)) + np.abs(c0))
+    assert np.all(np.abs(got - ref) <= bound)
