@@ -334,27 +334,55 @@ __device__ __forceinline__ void digits8(double x, int F, float (&dg)[ND]) {
 }
 
 // A (m x n FP64, column-major) -> eight BF16 digit slices, K-major: slice d
-// row i at S[(d * mpad + i) * ldk + j].  Thread: row i, 16 consecutive j.
+// row i at S[(d * mpad + i) * ldk + j].  CTA: a tile of 32 rows x 128
+// columns; thread: row i (lane, so that the loads are coalesced), 16
+// consecutive j (warp).  Each slice's tile goes through shared memory and
+// out as whole 256-byte row segments (two rows per warp store).
+constexpr int kSliceRows = 32, kSliceCols = 128;
+constexpr int kSlicePitch = kSliceCols + 8;      // BF16 per staged row: 272 bytes, fewer bank conflicts
+
 __global__ void __launch_bounds__(256) k_slice_a(int m, int n, const double *__restrict__ A, int lda, const int *Ef,
                                                  __nv_bfloat16 *S, int mpad, int ldk) {
-    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int j0 = (blockIdx.y * 8 + (threadIdx.x >> 5)) * 16;
-    if (i >= m || j0 >= n) return;
-    const int F = Ef[i];
-    float dg[16][ND];
+    __shared__ __align__(16) __nv_bfloat16 tile[kSliceRows * kSlicePitch];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i0 = blockIdx.x * kSliceRows, jt = blockIdx.y * kSliceCols;
+    const int i = i0 + lane;
+    const int j0 = jt + warp * 16;
+    const bool valid = i < m && j0 < n;
+    const int F = valid ? Ef[i] : 0;
+    uint32_t pk[ND][8];                                // the 16 digits of each slice, as BF16 pairs
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-        const double x = (j0 + c < n) ? A[(size_t)i + (size_t)(j0 + c) * lda] : 0.0;
-        digits8(x, F, dg[c]);
+    for (int c = 0; c < 16; c += 2) {
+        float d0[ND], d1[ND];
+        const double x0 = (valid && j0 + c < n) ? A[(size_t)i + (size_t)(j0 + c) * lda] : 0.0;
+        const double x1 = (valid && j0 + c + 1 < n) ? A[(size_t)i + (size_t)(j0 + c + 1) * lda] : 0.0;
+        digits8(x0, F, d0);
+        digits8(x1, F, d1);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(d0[d], d1[d]);
+            pk[d][c / 2] = *reinterpret_cast<const uint32_t *>(&h);
+        }
     }
+    const int rows = min(kSliceRows, m - i0);
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-        __nv_bfloat162 h[8];
+        uint4 *sdst = reinterpret_cast<uint4 *>(tile + lane * kSlicePitch + warp * 16);
+        sdst[0] = make_uint4(pk[d][0], pk[d][1], pk[d][2], pk[d][3]);
+        sdst[1] = make_uint4(pk[d][4], pk[d][5], pk[d][6], pk[d][7]);
+        __syncthreads();
+        // 32 rows x 16 chunks of 8 BF16: two rows per warp store
 #pragma unroll
-        for (int c = 0; c < 8; ++c) h[c] = __floats2bfloat162_rn(dg[2 * c][d], dg[2 * c + 1][d]);
-        uint4 *dst = reinterpret_cast<uint4 *>(S + ((size_t)d * mpad + i) * ldk + j0);
-        dst[0] = *reinterpret_cast<uint4 *>(&h[0]);
-        dst[1] = *reinterpret_cast<uint4 *>(&h[4]);
+        for (int it = 0; it < 2; ++it) {
+            const int c = threadIdx.x + 256 * it;
+            const int r = c >> 4, q = c & 15;
+            const int col = jt + q * 8;
+            if (r < rows && col < ldk) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(tile + r * kSlicePitch + q * 8);
+                *reinterpret_cast<uint4 *>(S + ((size_t)d * mpad + i0 + r) * ldk + col) = v;
+            }
+        }
+        __syncthreads();
     }
 }
 
