@@ -39,21 +39,25 @@ constexpr int kW = 64;                 // row width: columns of a panel, at most
 constexpr int kWP = kW / 2;            // float2 pairs per row
 constexpr int kMaxArity = 8;
 
-template <int NT>
+// NT threads hold RPT rows each: stacked row p = q * NT + thread (q < RPT),
+// so the smallest stacked position is the smallest q, then the smallest
+// thread.
+template <int NT, int RPT>
 struct Smem {
     static constexpr int NW = NT / 32;
     // column U of the current block of 8: each warp's candidate (its eight
-    // in-block values), key and 1 / its value
+    // in-block values), key, 1 / its value and stacked position
     float4 slot[kBlk][NW][2];
     alignas(16) unsigned wkey[kBlk][NW];
     alignas(16) float wrinv[kBlk][NW];
+    alignas(16) unsigned wpos[kBlk][NW];
     // block end: pivot U's row at the block start (columns 8 on, relative to
     // the block; padded stride against bank conflicts) and its multipliers
     // with respect to pivots 0..U-1 of the block
     float4 prow[kBlk][kW / 4 + 1];
     float lmat[kBlk][kBlk];
     int order[kW];
-    int rows[NT];
+    int rows[NT * RPT];
     int ccnt[kMaxArity];
     int nrows;
     int cont;
@@ -70,19 +74,6 @@ __device__ __forceinline__ float rcp_fast(float x) {
     float y;
     asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-// The largest of the NW warp keys (smallest warp on ties) and the reciprocal
-// published with it, computed by every warp alike: lane i reads warp i's key,
-// one redux.sync gives the maximum and a ballot its smallest warp, whose
-// reciprocal is one broadcast load.
-template <int NW>
-__device__ __forceinline__ int warp_argmax(const unsigned (&wk)[NW], const float (&wr)[NW], int lane, float &rinv) {
-    const unsigned k = lane < NW ? wk[lane] : 0u;
-    const unsigned mx = __reduce_max_sync(0xffffffffu, k);
-    const int wb = __ffs(__ballot_sync(0xffffffffu, k == mx)) - 1;
-    rinv = wr[wb];
-    return wb;
 }
 
 template <int U>
@@ -103,70 +94,111 @@ __device__ __forceinline__ void shift_row(float2 (&a)[kWP], int lim) {
     }
 }
 
-template <int NT>
+template <int NT, int RPT>
 struct BlockStep {
     static constexpr int NW = NT / 32;
-    Smem<NT> &s;
-    float2 (&a)[kWP];
-    float (&lb)[kBlk];
-    int w, r, lane, warp, pidx;
-    bool used;
+    Smem<NT, RPT> &s;
+    float2 (&a)[RPT][kWP];
+    float (&lb)[RPT][kBlk];
+    bool (&used)[RPT];
+    int (&pidx)[RPT];
+    int w, tid, lane, warp;
     template <int U>
     __device__ __forceinline__ void step(int j0) {
         const int j = j0 + U;
-        const float aj = elem<U>(a);
-        const unsigned k = key32u(aj, used);
-        const unsigned m = __reduce_max_sync(0xffffffffu, k);
-        const int wl = __ffs(__ballot_sync(0xffffffffu, k == m)) - 1;
+        float aj[RPT];
+        unsigned k[RPT];
+        unsigned kk = 0u;
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            aj[q] = elem<U>(a[q]);
+            k[q] = key32u(aj[q], used[q]);
+            kk = k[q] > kk ? k[q] : kk;
+        }
+        // warp maximum; its smallest stacked position: the first q, then lane
+        const unsigned m = __reduce_max_sync(0xffffffffu, kk);
+        int wq = 0;
+        unsigned bal = __ballot_sync(0xffffffffu, k[0] == m);
+#pragma unroll
+        for (int q = 1; q < RPT; ++q) {
+            const unsigned b = __ballot_sync(0xffffffffu, k[q] == m);
+            if (bal == 0u) { bal = b; wq = q; }
+        }
+        const int wl = __ffs(bal) - 1;
         if (lane == wl) {
-            s.slot[U][warp][0] = make_float4(a[0].x, a[0].y, a[1].x, a[1].y);
-            s.slot[U][warp][1] = make_float4(a[2].x, a[2].y, a[3].x, a[3].y);
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+                if (q == wq) {
+                    s.slot[U][warp][0] = make_float4(a[q][0].x, a[q][0].y, a[q][1].x, a[q][1].y);
+                    s.slot[U][warp][1] = make_float4(a[q][2].x, a[q][2].y, a[q][3].x, a[q][3].y);
+                    s.wrinv[U][warp] = aj[q] != 0.f ? rcp_fast(aj[q]) : 0.f;   // zero pivot: no elimination
+                }
             s.wkey[U][warp] = m;
-            s.wrinv[U][warp] = aj != 0.f ? rcp_fast(aj) : 0.f;   // zero pivot: no elimination
+            s.wpos[U][warp] = (unsigned)(wq * NT + tid);
         }
         __syncthreads();
-        float ri;
-        const int wb = warp_argmax<NW>(s.wkey[U], s.wrinv[U], lane, ri);
-        if (warp == wb && lane == wl) {
-            s.order[j] = r;
-            used = true;
-            pidx = U;
+        // CTA maximum over the warp keys (lane i reads warp i's), then the
+        // smallest stacked position among the warps that hold it
+        const unsigned wk = lane < NW ? s.wkey[U][lane] : 0u;
+        const unsigned M = __reduce_max_sync(0xffffffffu, wk);
+        const unsigned cand = (lane < NW && wk == M) ? s.wpos[U][lane] : 0xffffffffu;
+        const unsigned P = __reduce_min_sync(0xffffffffu, cand);
+        const int pt = (int)(P % NT), pq = (int)(P / NT);
+        const int wb = pt >> 5;
+        const float ri = s.wrinv[U][wb];
+        if (tid == pt) {
+            s.order[j] = (int)P;
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+                if (q == pq) { used[q] = true; pidx[q] = U; }
         }
-        if (!used) {
-            const float l = ri != 0.f ? aj * ri : 0.f;
-            lb[U] = l;
-            if (ri != 0.f) {
+        if (ri != 0.f) {
+            const float4 u0 = s.slot[U][wb][0], u1 = s.slot[U][wb][1];
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                if (used[q]) continue;
+                const float l = aj[q] * ri;
+                lb[q][U] = l;
                 const float2 nl = make_float2(-l, -l);
-                const float4 u0 = s.slot[U][wb][0], u1 = s.slot[U][wb][1];
-                if (1 > U) a[0] = __ffma2_rn(nl, make_float2(u0.x, u0.y), a[0]);
-                if (3 > U) a[1] = __ffma2_rn(nl, make_float2(u0.z, u0.w), a[1]);
-                if (5 > U) a[2] = __ffma2_rn(nl, make_float2(u1.x, u1.y), a[2]);
-                if (7 > U) a[3] = __ffma2_rn(nl, make_float2(u1.z, u1.w), a[3]);
+                if (1 > U) a[q][0] = __ffma2_rn(nl, make_float2(u0.x, u0.y), a[q][0]);
+                if (3 > U) a[q][1] = __ffma2_rn(nl, make_float2(u0.z, u0.w), a[q][1]);
+                if (5 > U) a[q][2] = __ffma2_rn(nl, make_float2(u1.x, u1.y), a[q][2]);
+                if (7 > U) a[q][3] = __ffma2_rn(nl, make_float2(u1.z, u1.w), a[q][3]);
             }
+        } else {
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+                if (!used[q]) lb[q][U] = 0.f;
         }
     }
     // Deferred update of the columns past the block (relative 8 .. w - j0).
     __device__ __forceinline__ void block_end(int j0) {
         const int lim = w - j0;
-        if (pidx >= 0) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            if (pidx[q] < 0) continue;
+            const int pu = pidx[q];
 #pragma unroll
             for (int t = 0; t < kBlk - 1; ++t)
-                if (t < pidx) s.lmat[pidx][t] = lb[t];
-            float4 *dst = s.prow[pidx];
+                if (t < pu) s.lmat[pu][t] = lb[q][t];
+            float4 *dst = s.prow[pu];
 #pragma unroll
             for (int c = 0; c < kW / 32; ++c)
                 if (c * 32 < lim) {
 #pragma unroll
-                    for (int q = c * 8; q < c * 8 + 8; ++q)
-                        if (q >= 2) dst[q] = make_float4(a[2 * q].x, a[2 * q].y, a[2 * q + 1].x, a[2 * q + 1].y);
+                    for (int g = c * 8; g < c * 8 + 8; ++g)
+                        if (g >= 2)
+                            dst[g] = make_float4(a[q][2 * g].x, a[q][2 * g].y, a[q][2 * g + 1].x, a[q][2 * g + 1].y);
                 }
         }
         __syncthreads();
-        if (!used) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            if (used[q]) continue;
             float c[kBlk];
 #pragma unroll
             for (int u = kBlk - 1; u >= 0; --u) {
-                float t = lb[u];
+                float t = lb[q][u];
 #pragma unroll
                 for (int u2 = u + 1; u2 < kBlk; ++u2) t = fmaf(-c[u2], s.lmat[u2][u], t);
                 c[u] = t;
@@ -178,31 +210,42 @@ struct BlockStep {
                 for (int ch = 0; ch < kW / 32; ++ch)
                     if (ch * 32 < lim) {
 #pragma unroll
-                        for (int q = ch * 8; q < ch * 8 + 8; ++q) {
-                            if (q < 2) continue;
-                            const float4 p = s.prow[u][q];
-                            a[2 * q] = __ffma2_rn(nc, make_float2(p.x, p.y), a[2 * q]);
-                            a[2 * q + 1] = __ffma2_rn(nc, make_float2(p.z, p.w), a[2 * q + 1]);
+                        for (int g = ch * 8; g < ch * 8 + 8; ++g) {
+                            if (g < 2) continue;
+                            const float4 p = s.prow[u][g];
+                            a[q][2 * g] = __ffma2_rn(nc, make_float2(p.x, p.y), a[q][2 * g]);
+                            a[q][2 * g + 1] = __ffma2_rn(nc, make_float2(p.z, p.w), a[q][2 * g + 1]);
                         }
                     }
             }
         }
 #pragma unroll
-        for (int u = 0; u < kBlk; ++u) lb[u] = 0.f;
-        pidx = -1;
+        for (int q = 0; q < RPT; ++q) {
+#pragma unroll
+            for (int u = 0; u < kBlk; ++u) lb[q][u] = 0.f;
+            pidx[q] = -1;
+        }
     }
 };
 
 // Masked partial-pivoting selection of npiv pivots among the rows held by
-// this CTA (thread r holds stacked row r if r < s.nrows); s.order[0..npiv)
-// receives the stacked indices of the pivots in pivot order.
-template <int NT>
-__device__ void gepp_select(Smem<NT> &s, float2 (&a)[kWP], int w, int npiv) {
-    const int r = threadIdx.x;
-    float lb[kBlk];
+// this CTA (stacked row p lives in thread p % NT as its row p / NT, valid if
+// p < s.nrows); s.order[0..npiv) receives the stacked indices of the pivots
+// in pivot order.
+template <int NT, int RPT>
+__device__ void gepp_select(Smem<NT, RPT> &s, float2 (&a)[RPT][kWP], int w, int npiv) {
+    const int tid = threadIdx.x;
+    float lb[RPT][kBlk];
+    bool used[RPT];
+    int pidx[RPT];
 #pragma unroll
-    for (int u = 0; u < kBlk; ++u) lb[u] = 0.f;
-    BlockStep<NT> body{s, a, lb, w, r, r & 31, r >> 5, -1, !(r < s.nrows)};
+    for (int q = 0; q < RPT; ++q) {
+#pragma unroll
+        for (int u = 0; u < kBlk; ++u) lb[q][u] = 0.f;
+        used[q] = !(q * NT + tid < s.nrows);
+        pidx[q] = -1;
+    }
+    BlockStep<NT, RPT> body{s, a, lb, used, pidx, w, tid, tid & 31, tid >> 5};
     for (int j0 = 0; j0 < npiv; j0 += kBlk) {
         body.template step<0>(j0);
         if (j0 + 1 < npiv) body.template step<1>(j0);
@@ -214,7 +257,8 @@ __device__ void gepp_select(Smem<NT> &s, float2 (&a)[kWP], int w, int npiv) {
         if (j0 + 7 < npiv) body.template step<7>(j0);
         if (j0 + kBlk >= npiv) break;              // no selection left: skip the update
         body.block_end(j0);
-        shift_row(a, w - j0 - kBlk);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) shift_row(a[q], w - j0 - kBlk);
     }
     __syncthreads();
 }
@@ -223,8 +267,8 @@ __device__ void gepp_select(Smem<NT> &s, float2 (&a)[kWP], int w, int npiv) {
 // (panel rows in pivot order): winner j moves from its current position to
 // k0 + j.  Positions 0..w-1 are the pivot block, w + j stands for winner j's
 // original row when that row lies below the block.
-template <int NT>
-__device__ void root_epilogue(Smem<NT> &s, const int *win, int np, const TournEpilogue &ep) {
+template <int NT, int RPT>
+__device__ void root_epilogue(Smem<NT, RPT> &s, const int *win, int np, const TournEpilogue &ep) {
     if (ep.ipiv == nullptr || threadIdx.x != 0) return;
     const int w = np;
     for (int q = 0; q < 2 * w; ++q) { s.lab_at[q] = q; s.where_[q] = q; }
@@ -250,39 +294,48 @@ __device__ void root_epilogue(Smem<NT> &s, const int *win, int np, const TournEp
     *ep.swap_cnt = cnt;
 }
 
-template <int NT>
+__device__ __forceinline__ void load_row64(float2 (&a)[kWP], const float *__restrict__ P, int ldp, size_t row, int w,
+                                           bool valid) {
+#pragma unroll
+    for (int k = 0; k < kWP; ++k) {
+        const float x = (valid && 2 * k < w) ? P[row + (size_t)(2 * k) * ldp] : 0.f;
+        const float y = (valid && 2 * k + 1 < w) ? P[row + (size_t)(2 * k + 1) * ldp] : 0.f;
+        a[k] = make_float2(x, y);
+    }
+}
+
+template <int NT, int RPT>
 __global__ void __launch_bounds__(NT, 1)
 k_tourn32w(const float *__restrict__ P, int ldp, TournPlan plan, TournWS ws, TournEpilogue ep) {
-    __shared__ Smem<NT> s;
+    __shared__ Smem<NT, RPT> s;
     const int tid = threadIdx.x;
     const int w = plan.w;
     const int ar = plan.arity;
-    float2 a[kWP];
+    float2 a[RPT][kWP];
 
     // ---- leaf: h consecutive rows of the panel
     const int leaf = blockIdx.x;
     {
         const int row0 = leaf * plan.h;
         const int nr = min(plan.h, plan.m - row0);
-        const bool valid = tid < nr;
         if (tid == 0) s.nrows = nr;
-        s.rows[tid] = row0 + tid;
-        const size_t rr = valid ? (size_t)(row0 + tid) : 0;
 #pragma unroll
-        for (int k = 0; k < kWP; ++k) {
-            const float x = (valid && 2 * k < w) ? P[rr + (size_t)(2 * k) * ldp] : 0.f;
-            const float y = (valid && 2 * k + 1 < w) ? P[rr + (size_t)(2 * k + 1) * ldp] : 0.f;
-            a[k] = make_float2(x, y);
-        }
-        if (ws.rows32 != nullptr && valid && plan.nlevels > 1) {   // original rows for the playoff nodes
-            float4 *dst = reinterpret_cast<float4 *>(ws.rows32 + rr * kW);
+        for (int q = 0; q < RPT; ++q) {
+            const int p = q * NT + tid;
+            const bool valid = p < nr;
+            s.rows[p] = row0 + p;
+            const size_t rr = valid ? (size_t)(row0 + p) : 0;
+            load_row64(a[q], P, ldp, rr, w, valid);
+            if (ws.rows32 != nullptr && valid && plan.nlevels > 1) {   // original rows for the playoff nodes
+                float4 *dst = reinterpret_cast<float4 *>(ws.rows32 + rr * kW);
 #pragma unroll
-            for (int q = 0; q < kW / 4; ++q)
-                dst[q] = make_float4(a[2 * q].x, a[2 * q].y, a[2 * q + 1].x, a[2 * q + 1].y);
+                for (int g = 0; g < kW / 4; ++g)
+                    dst[g] = make_float4(a[q][2 * g].x, a[q][2 * g].y, a[q][2 * g + 1].x, a[q][2 * g + 1].y);
+            }
         }
         __syncthreads();
         const int np = min(nr, w);
-        gepp_select<NT>(s, a, w, np);
+        gepp_select<NT, RPT>(s, a, w, np);
         int *dst = ws.node_win + (size_t)(plan.off[0] + leaf) * kMaxV;
         if (tid < np) dst[tid] = s.rows[s.order[tid]];
         if (tid == 0) ws.node_cnt[plan.off[0] + leaf] = np;
@@ -290,7 +343,7 @@ k_tourn32w(const float *__restrict__ P, int ldp, TournPlan plan, TournWS ws, Tou
             __syncthreads();
             if (tid < np) ws.root_win[tid] = dst[tid];
             __syncthreads();
-            root_epilogue<NT>(s, dst, np, ep);
+            root_epilogue<NT, RPT>(s, dst, np, ep);
             return;
         }
     }
@@ -326,36 +379,41 @@ k_tourn32w(const float *__restrict__ P, int ldp, TournPlan plan, TournWS ws, Tou
         } else {
             if (tid < nchild) s.ccnt[tid] = __ldcg(ws.node_cnt + s0 + tid);
             __syncthreads();
-            // stacked row tid: child c, position tid - (counts of children < c)
-            int nr = 0, mine = -1;
+            // stacked row p: child c, position p - (counts of children < c)
+            int nr = 0, mine[RPT];
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) mine[q] = -1;
             for (int c = 0; c < nchild; ++c) {
                 const int cc = s.ccnt[c];
-                if (mine < 0 && tid < nr + cc) mine = __ldcg(ws.node_win + (size_t)(s0 + c) * kMaxV + (tid - nr));
+#pragma unroll
+                for (int q = 0; q < RPT; ++q) {
+                    const int p = q * NT + tid;
+                    if (mine[q] < 0 && p < nr + cc)
+                        mine[q] = __ldcg(ws.node_win + (size_t)(s0 + c) * kMaxV + (p - nr));
+                }
                 nr += cc;
             }
             np = min(nr, w);
-            if (tid < nr) s.rows[tid] = mine;
-            if (tid == 0) s.nrows = nr;
-            if (ws.rows32 != nullptr) {            // contiguous original rows (the leaves' copy)
-                const float4 *src = reinterpret_cast<const float4 *>(ws.rows32 + (size_t)(tid < nr ? mine : 0) * kW);
 #pragma unroll
-                for (int q = 0; q < kW / 4; ++q) {
-                    const float4 v = tid < nr ? __ldcg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    a[2 * q] = make_float2(v.x, v.y);
-                    a[2 * q + 1] = make_float2(v.z, v.w);
-                }
-            } else {
-                const bool valid = tid < nr;
-                const size_t rr = valid ? (size_t)mine : 0;
+            for (int q = 0; q < RPT; ++q) {
+                const int p = q * NT + tid;
+                const bool valid = p < nr;
+                if (valid) s.rows[p] = mine[q];
+                if (ws.rows32 != nullptr) {            // contiguous original rows (the leaves' copy)
+                    const float4 *src = reinterpret_cast<const float4 *>(ws.rows32 + (size_t)(valid ? mine[q] : 0) * kW);
 #pragma unroll
-                for (int k = 0; k < kWP; ++k) {
-                    const float x = (valid && 2 * k < w) ? P[rr + (size_t)(2 * k) * ldp] : 0.f;
-                    const float y = (valid && 2 * k + 1 < w) ? P[rr + (size_t)(2 * k + 1) * ldp] : 0.f;
-                    a[k] = make_float2(x, y);
+                    for (int g2 = 0; g2 < kW / 4; ++g2) {
+                        const float4 v = valid ? __ldcg(src + g2) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        a[q][2 * g2] = make_float2(v.x, v.y);
+                        a[q][2 * g2 + 1] = make_float2(v.z, v.w);
+                    }
+                } else {
+                    load_row64(a[q], P, ldp, valid ? (size_t)mine[q] : 0, w, valid);
                 }
             }
+            if (tid == 0) s.nrows = nr;
             __syncthreads();
-            gepp_select<NT>(s, a, w, np);
+            gepp_select<NT, RPT>(s, a, w, np);
             if (tid < np) dst[tid] = s.rows[s.order[tid]];
             if (tid == 0) ws.node_cnt[node] = np;
         }
@@ -363,7 +421,7 @@ k_tourn32w(const float *__restrict__ P, int ldp, TournPlan plan, TournWS ws, Tou
             __syncthreads();
             if (tid < np) ws.root_win[tid] = dst[tid];
             __syncthreads();
-            root_epilogue<NT>(s, dst, np, ep);
+            root_epilogue<NT, RPT>(s, dst, np, ep);
             return;
         }
     }
@@ -385,13 +443,14 @@ int launch_tourn32w(const float *P, int ldp, int m, int w, int h, int arity, con
     TournPlan plan{};
     int rc = make_tourn_plan(m, w, h, arity, &plan);
     if (rc != CF_OK) return rc;
-    // one thread per candidate row: 256 threads when no leaf or node holds
-    // more than 256 rows
+    // 256 threads: one candidate row each when no leaf or node holds more
+    // than 256 rows, else two (512 rows: half the warps in every barrier and
+    // reduction of the column chain)
     const bool small = h <= 256 && (plan.nlevels == 1 || arity * w <= 256);
     if (small)
-        tw::k_tourn32w<256><<<plan.nleaves, 256, 0, st>>>(P, ldp, plan, ws, ep);
+        tw::k_tourn32w<256, 1><<<plan.nleaves, 256, 0, st>>>(P, ldp, plan, ws, ep);
     else
-        tw::k_tourn32w<512><<<plan.nleaves, 512, 0, st>>>(P, ldp, plan, ws, ep);
+        tw::k_tourn32w<256, 2><<<plan.nleaves, 256, 0, st>>>(P, ldp, plan, ws, ep);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
