@@ -138,11 +138,17 @@ struct BlockStep {
         }
         __syncthreads();
         // CTA maximum over the warp keys (lane i reads warp i's), then the
-        // smallest stacked position among the warps that hold it
+        // smallest stacked position among the warps that hold it (with one
+        // row per thread, the smallest such warp)
         const unsigned wk = lane < NW ? s.wkey[U][lane] : 0u;
         const unsigned M = __reduce_max_sync(0xffffffffu, wk);
-        const unsigned cand = (lane < NW && wk == M) ? s.wpos[U][lane] : 0xffffffffu;
-        const unsigned P = __reduce_min_sync(0xffffffffu, cand);
+        unsigned P;
+        if constexpr (RPT == 1) {
+            P = s.wpos[U][__ffs(__ballot_sync(0xffffffffu, wk == M)) - 1];
+        } else {
+            const unsigned cand = (lane < NW && wk == M) ? s.wpos[U][lane] : 0xffffffffu;
+            P = __reduce_min_sync(0xffffffffu, cand);
+        }
         const int pt = (int)(P % NT), pq = (int)(P / NT);
         const int wb = pt >> 5;
         const float ri = s.wrinv[U][wb];
@@ -443,14 +449,15 @@ int launch_tourn32w(const float *P, int ldp, int m, int w, int h, int arity, con
     TournPlan plan{};
     int rc = make_tourn_plan(m, w, h, arity, &plan);
     if (rc != CF_OK) return rc;
-    // 256 threads: one candidate row each when no leaf or node holds more
-    // than 256 rows, else two (512 rows: half the warps in every barrier and
-    // reduction of the column chain)
+    // one candidate row per thread: 256 threads when no leaf or node holds
+    // more than 256 rows, else 512 (two rows per thread on 256 threads, with
+    // half the warps in each barrier and reduction, measured 9% slower: the
+    // column chain is latency-bound, not issue-bound)
     const bool small = h <= 256 && (plan.nlevels == 1 || arity * w <= 256);
     if (small)
         tw::k_tourn32w<256, 1><<<plan.nleaves, 256, 0, st>>>(P, ldp, plan, ws, ep);
     else
-        tw::k_tourn32w<256, 2><<<plan.nleaves, 256, 0, st>>>(P, ldp, plan, ws, ep);
+        tw::k_tourn32w<512, 1><<<plan.nleaves, 512, 0, st>>>(P, ldp, plan, ws, ep);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
