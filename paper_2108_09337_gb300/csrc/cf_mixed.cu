@@ -763,6 +763,13 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
     const size_t ld = (size_t)w.ldw;
     float *W = w.W;
     int rc;
+    // LU-6 for the Cholesky: the in-slab update of the next panel's columns
+    // first, the rest on the look-ahead stream beside the next A00 Cholesky;
+    // the next panel solve (which rewrites the operand buffers) waits for it
+    LookStream la;
+    if (o.lookahead && (rc = la.open())) return rc;
+    bool la_pending = false;
+    const int sms = device_sms();
     for (int J0 = 0; J0 < n; J0 += V) {
         const int JE = J0 + V < n ? J0 + V : n;
         for (int k0 = J0; k0 < JE; k0 += v) {
@@ -770,6 +777,10 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             const int m = n - k0;
             float *A00 = W + k0 + k0 * ld;
             if ((rc = launch_a00_chol32(A00, w.ldw, wd, k0, info, st))) return rc;
+            if (la_pending) {
+                CF_CUDA_TRY(cudaStreamWaitEvent(st, la.done, 0));
+                la_pending = false;
+            }
             const int below = m - wd;
             if (below <= 0) continue;
             // CH-2: L10 = A10 L00^{-T}, with its K-major low-precision copy
@@ -785,9 +796,28 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
                 Bop = w.Bb;
             }
             const int Kin = split ? S * kMaxV : (wd + 63) / 64 * 64;   // as in the LU
-            if ((rc = launch_schur_tc(below, nslab, Kin, w.Ab, S * kMaxV, Bop, S * kMaxV, A00 + wd + wd * ld,
-                                      w.ldw, bf16, true, st, 0)))
+            const int wn = v < nslab ? v : nslab;                         // the next panel's columns
+            const bool split_la = o.lookahead && nslab > wn;
+            if (split_la) CF_CUDA_TRY(cudaEventRecord(la.fork, st));
+            float *C = A00 + wd + wd * ld;
+            if ((rc = launch_schur_tc(below, split_la ? wn : nslab, Kin, w.Ab, S * kMaxV, Bop, S * kMaxV, C, w.ldw,
+                                      bf16, true, st, 0)))
                 return rc;
+            if (split_la) {
+                // rows and columns from wn on (the lower triangle keeps its diagonal)
+                CF_CUDA_TRY(cudaStreamWaitEvent(la.s, la.fork, 0));
+                const size_t off = (size_t)wn * S * kMaxV;
+                if ((rc = launch_schur_tc(below - wn, nslab - wn, Kin, (const uint16_t *)w.Ab + off, S * kMaxV,
+                                          (const uint16_t *)Bop + off, S * kMaxV, C + wn + (size_t)wn * ld, w.ldw,
+                                          bf16, true, la.s, sms - 1)))
+                    return rc;
+                CF_CUDA_TRY(cudaEventRecord(la.done, la.s));
+                la_pending = true;
+            }
+        }
+        if (la_pending) {
+            CF_CUDA_TRY(cudaStreamWaitEvent(st, la.done, 0));
+            la_pending = false;
         }
         if (JE < n) {
             const int Vs = JE - J0, Vp = (Vs + 63) / 64 * 64, mr = n - JE;

@@ -399,6 +399,21 @@ def test_gesv_mixed_lookahead_identical(cf, prec, n, V, v):
     _check_solution(A, B, out[1][0])
 
 
+@pytest.mark.parametrize("prec,n,V", [("bf16x3", 2048, 0), ("f16", 3000, 1024), ("bf16", 1000, 256)])
+def test_posv_mixed_lookahead_identical(cf, prec, n, V):
+    """LU-6 in the mixed Cholesky (the rest of each step's in-slab update on a
+    second stream beside the next A00 Cholesky) gives bit-identical solutions."""
+    S = inputs.spd_gram(n, seed=n)
+    B = inputs.rhs_normal(n, 3, seed=2)
+    out = {}
+    for la in (0, 1):
+        X, info, stats, st = cf.posv_mixed(_dev(S), _dev(B), prec=prec, outer_V=V, lookahead=la)
+        assert st == cf.CF_OK and int(info.item()) == 0, stats.as_dict()
+        out[la] = X.cpu().numpy()
+    np.testing.assert_array_equal(out[0], out[1])
+    _check_solution(S, B, out[1])
+
+
 def test_gesv_mixed_shape_checks(cf):
     """Tournament shapes the mixed LU cannot run are refused before any work
     (v = 128 takes arity 2 and leaves <= 256; v <= 64 takes arity * v <= 512)."""
