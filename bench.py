@@ -3,14 +3,15 @@
 1e-14 backward error at N = 32768 on one GB300, next to this project's FP64
 path and the CPU oracle.
 
-One step = cf_gesv_mixed (LU with tournament pivoting, FP16 tensor-core
-Schur updates with FP32 accumulation, FP64 refinement; A = U[-1,1] +
-2 sqrt(N) I, 16 right-hand sides) + cf_posv_mixed (Cholesky, split-BF16
-updates: BF16 hi + lo operands, three products accumulated in FP32; FP64
-refinement; A = G G^T / N + alpha I with kappa ~ 1e2, 8 right-hand sides).
-Each system takes the update precision with which it is solved fastest
-(measured: FP16 for this LU, split BF16 for this Cholesky, whose 16
-significant bits save two refinement steps; the others run as variants).
+One step = cf_gesv_mixed (LU with tournament pivoting at v = 64, leaves of
+512 rows, arity 8; FP16 tensor-core Schur updates with FP32 accumulation;
+FP64-accurate refinement with residuals on the tensor cores; A = U[-1,1] +
+2 sqrt(N) I, 16 right-hand sides) + cf_posv_mixed (Cholesky, FP16 updates,
+the same refinement; A = G G^T / N + alpha I with kappa ~ 1e2, 8 right-hand
+sides).  Each system takes the update precision with which it is solved
+fastest (measured: FP16 for both; BF16 needs more refinement steps, split
+BF16 (hi + lo operands, three products) costs more to factor than the steps
+it saves now that a refinement step is cheap; the others run as variants).
 value = (2N^3/3 + N^3/3) / step time.  A step counts only if every
 right-hand side reaches eta <= 1e-14 (checked here with an FP64 residual).
 --prec / --chol-prec choose the precisions; by default the other BF16, FP16
@@ -45,7 +46,8 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; ~2 DFMA/clk/SM x 152 SMs x 2.07
 RESID_TRAFFIC_8192 = 542.2e6   # k_residual_f64 DRAM bytes per launch at N = 8192 (ncu)
 # FP32 tournament DRAM bytes per launch, averaged over an LU's panels, keyed
 # by (N, v, leaf_h, arity), from ncu captures under profiles/
-TOURN_TRAFFIC = {}
+# (profiles/k_tourn32w_n32768.md: the launch reads exactly its panel, m x 64 x 4 bytes)
+TOURN_TRAFFIC = {(32768, 64, 512, 8): sum(4.0 * 64 * (32768 - 64 * i) for i in range(512)) / 512}
 
 
 def _args():
@@ -55,7 +57,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cf", "reference"], default="cf")
     ap.add_argument("--n", type=int, default=32768)
-    ap.add_argument("--chol-prec", default="bf16x3", choices=["bf16", "f16", "bf16x3"],
+    ap.add_argument("--chol-prec", default="f16", choices=["bf16", "f16", "bf16x3"],
                     help="update precision of the timed Cholesky solve")
     ap.add_argument("--prec", default="f16", choices=["bf16", "f16", "bf16x3"],
                     help="update precision of the timed step (the other 16-bit one runs once as a variant)")
