@@ -804,7 +804,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                                "mixed Cholesky solve (N=32768, 8 RHS, A=GG^T/N+alpha I, kappa~1e2, %s tensor-core "
                                "updates), FP32 accumulation, FP64 refinement to 1e-14" % (prec, cprec),
                    "n": n, "v": {"lu": args.v, "chol": 128}, "leaf_h": args.leaf_h, "arity": args.arity,
-                   "outer_V": {"lu": 2048, "chol": 1024},
+                   "outer_V": {"lu": 2048, "chol": 2048},
                    "factor_prec": prec,
                    "chol_factor_prec": cprec,
                    "parallelism": "replicas" if world > 1 else "single GPU",

@@ -73,7 +73,7 @@ typedef struct {
                           mixed LU with v <= 64: 2..8 and arity * v <= 512
                           [8], with v > 64: 2 [2] */
     int outer_V;       /* mixed LU/Cholesky: depth of the deferred update,
-                          multiple of v [0 = auto: 2048 for LU at n >= 16384,
+                          multiple of v [0 = auto: 2048 at n >= 16384,
                           1024 at n >= 8192, 512 below] */
     int lookahead;     /* LU-6 look-ahead [1]; 0 = one stream.  cf_getrf:
                           TournPivot of step t+1 on a high-priority stream

@@ -345,13 +345,14 @@ struct MixedWS {
 
 // Depth V of the slab's deferred K = V update.  Deeper slabs raise the
 // update's arithmetic intensity (its FP32 C is read and written once per
-// slab) and cost more right-looking work inside the slab; measured at
-// N = 32768: V = 2048 runs the LU's update at 1.27 PFLOP/s against 0.76 with
-// V = 1024 (factorization 211 vs 217 ms), while the Cholesky factorization is
-// faster with V = 1024.
+// slab) and cost more right-looking work inside the slab (which the
+// look-ahead stream partly hides); measured at N = 32768: LU 138.7 ms with
+// V = 2048 against 148.0 (V = 1024) and 158.0 (V = 4096); Cholesky with FP16
+// updates 45.0 ms with V = 2048 against 49.6 (V = 1024).
 static int pick_V(int n, const Opts &o, bool lu) {
+    (void)lu;
     if (o.outer_V > 0) return o.outer_V;
-    if (lu && n >= 16384) return 2048;
+    if (n >= 16384) return 2048;
     return n >= 8192 ? 1024 : 512;
 }
 

@@ -76,9 +76,9 @@ def test_mixed_options_and_workspace(lib):
     fp64_residual takes 0 or 1 and residual_kind 0 or 2 (anything else is
     refused by the size query, which returns 0); by default the residuals run
     on the tensor cores, whose digit slices of A (8 n^2 BF16) the workspace
-    holds, and fp64_residual = 1 or residual_kind = 2 drop them; deeper LU
-    slabs from n = 16384 make the LU workspace grow faster than the Cholesky
-    one, and the pair-residual query is host-only and linear in m + n."""
+    holds, and fp64_residual = 1 or residual_kind = 2 drop them; deeper
+    slabs from n = 16384 make the workspace grow, and the pair-residual query
+    is host-only and linear in m + n."""
     from paper_2108_09337_gb300 import cf
     L = cf.lib()
     o = cf.options()
@@ -92,10 +92,11 @@ def test_mixed_options_and_workspace(lib):
     assert cf.gesv_mixed_workspace_size(n, 4, "f16", residual_kind=1) == 0
     assert cf.posv_mixed_workspace_size(n, 4, "f16", fp64_residual=-1) == 0
     kw = dict(residual_kind=2)
-    lu16, ch16 = cf.gesv_mixed_workspace_size(16384, 16, "f16", **kw), cf.posv_mixed_workspace_size(16384, 16, "f16",
-                                                                                                    **kw)
-    lu8, ch8 = cf.gesv_mixed_workspace_size(8192, 16, "f16", **kw), cf.posv_mixed_workspace_size(8192, 16, "f16", **kw)
-    assert lu16 - ch16 > 2 * (lu8 - ch8)          # Lb / Ub sized for V = 2048 vs 1024
+    for fn in (cf.gesv_mixed_workspace_size, cf.posv_mixed_workspace_size):
+        # slabs of V = 2048 from n = 16384 (Lb / Ub hold 3 V columns of each row)
+        deep = fn(16384, 16, "f16", **kw)
+        assert deep == fn(16384, 16, "f16", outer_V=2048, **kw)
+        assert deep - fn(16384, 16, "f16", outer_V=1024, **kw) >= 2 * 3 * 1024 * 16384 * 2
     p1 = L.cf_residual_pair_workspace_size(1000, 1000, 16)
     p2 = L.cf_residual_pair_workspace_size(2000, 2000, 16)
     assert 0 < p1 < p2 <= 2 * p1 + 4096
