@@ -342,6 +342,23 @@ int cf_schur_update_lp(int m, int n, int k, const void *A_lp, int lda_k,
  * in cf_schur_update_lp.  A device wait that expires is reported by
  * cf_device_status.
  * ------------------------------------------------------------------------ */
+/* Split-K form of cf_schur_update_lp (the paper's split of the reduction
+ * dimension over processors, Sec. 7.1-7.2, at the scale of one GPU: when the
+ * output has too few 128 x 256 tiles to occupy every SM, K is cut into
+ * ksplit ranges that run as separate work units).  Each unit writes its FP32
+ * partial product to work; then C -= the sum of the partials, added in range
+ * order, so the result does not depend on the order the units ran in (it
+ * differs from the one-range result by the rounding of the FP32 partial
+ * sums).  ksplit in 1..64 (1: the plain update; more ranges than K blocks of
+ * 64 are merged); work: cf_schur_update_lp_splitk_workspace_size(m, n, k,
+ * ksplit) bytes (0 for ksplit = 1).  Other arguments and errors as
+ * cf_schur_update_lp; -12 for ksplit out of range. */
+size_t cf_schur_update_lp_splitk_workspace_size(int m, int n, int k, int ksplit);
+int cf_schur_update_lp_splitk(int m, int n, int k, const void *A_lp, int lda_k,
+                              const void *B_lp, int ldb_k, float *C, int ldc,
+                              cf_prec prec, int lower, int ksplit, void *work,
+                              size_t lwork, cudaStream_t stream);
+
 int cf_quantize_e4m3(int rows, int k, const float *src, int lds, void *q,
                      int ldq, float *scales, int ld_scales,
                      cudaStream_t stream);

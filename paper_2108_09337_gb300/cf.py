@@ -84,6 +84,8 @@ _SIG = {
     "cf_residual_tc": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _S, _P]),
     "cf_residual_pair": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _S, _P]),
     "cf_schur_update_lp": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P]),
+    "cf_schur_update_lp_splitk_workspace_size": (_S, [_I, _I, _I, _I]),
+    "cf_schur_update_lp_splitk": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _S, _P]),
     "cf_device_status": (_I, [_P]),
     "cf_trsv_f32_workspace_size": (_S, [_I]),
     "cf_trsv_f32": (_I, [_I, _I, _I, _P, _I, _P, _I, _P, _S, _P]),
@@ -327,6 +329,19 @@ def schur_update_lp(A_lp: torch.Tensor, B_lp: torch.Tensor, C: torch.Tensor, low
     _check("cf_schur_update_lp", _lib.cf_schur_update_lp(m, n, k, _ptr(A_lp), A_lp.stride(0), _ptr(B_lp),
                                                          B_lp.stride(0), _ptr(C), _ld(C, "C"), prec,
                                                          int(lower), _stream()))
+    return C
+
+
+def schur_update_lp_splitk(A_lp: torch.Tensor, B_lp: torch.Tensor, C: torch.Tensor, ksplit: int,
+                           lower: bool = False):
+    """cf_schur_update_lp_splitk: the update with K cut into ksplit ranges."""
+    m, k = A_lp.shape
+    n = B_lp.shape[0]
+    prec = {torch.bfloat16: CF_BF16, torch.float16: CF_F16}[A_lp.dtype]
+    ws = _workspace(_lib.cf_schur_update_lp_splitk_workspace_size(m, n, k, ksplit), C.device)
+    _check("cf_schur_update_lp_splitk",
+           _lib.cf_schur_update_lp_splitk(m, n, k, _ptr(A_lp), A_lp.stride(0), _ptr(B_lp), B_lp.stride(0), _ptr(C),
+                                          _ld(C, "C"), prec, int(lower), ksplit, _ptr(ws), ws.numel(), _stream()))
     return C
 
 

@@ -336,6 +336,7 @@ struct MixedWS {
     float *sc8 = nullptr;                  // FP8 tile scales: slab (rows/128 x V/128), then one step
     double *Xbest = nullptr;               // best iterate so far
     void *pairws = nullptr;                // pair-arithmetic residual workspace
+    float *Psk = nullptr;                  // split-K partials of the small K = V updates
     bool use_tc = false;                   // residuals on the tensor cores (digit slices of A)
     void *rtcA = nullptr, *rtcX = nullptr; // their slices of A, and per-product scratch
     ResidTC rtc{};
@@ -415,6 +416,15 @@ static int carve_mixed(void *work, int n, int nrhs, const Opts &o, bool lu, Mixe
         w->rtcX = cv.take<char>(resid_tc_x_bytes(n, n), 1024);
     }
     w->sc8 = cv.take<float>((size_t)(ceil_div(n > 0 ? n : 1, 128) + 1) * (Vp / 128 + 2));
+    // split-K partials: at most (SMs / tiles) ranges of the tiles of an
+    // update that fills fewer than half the SMs (a triangle counts half)
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+        w->Psk = cv.take<float>((size_t)2 * sms * 128 * 256, 1024);
+    }
     w->bytes = cv.size();
     return CF_OK;
 }
@@ -693,8 +703,10 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
                 return rc;
             }
             if (tu && (rc = tu->begin(st))) return rc;
-            if ((rc = launch_schur_tc(mr, mr, S * Vp, w.Lb, S * Vp, w.Ub, S * Vpad, W + JE + JE * ld, w.ldw, bf16,
-                                      false, st, 0)))
+            // the last slabs' updates have few tiles: split K over the SMs
+            const int ks = schur_tc_splitk(mr, mr, S * Vp, false);
+            if ((rc = launch_schur_tc_splitk(mr, mr, S * Vp, w.Lb, S * Vp, w.Ub, S * Vpad, W + JE + JE * ld, w.ldw,
+                                             bf16, false, ks, w.Psk, st, 0)))
                 return rc;
             if (tu && (rc = tu->end(st, 2.0 * mr * (double)mr * Vs))) return rc;
         }
@@ -831,8 +843,9 @@ static int mixed_potrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
                 Bop = w.Ub;
             }
             if (tu && (rc = tu->begin(st))) return rc;
-            if ((rc = launch_schur_tc(mr, mr, S * Vp, w.Lb, S * Vp, Bop, S * Vp, W + JE + JE * ld, w.ldw, bf16, true,
-                                      st, 0)))
+            const int ks = schur_tc_splitk(mr, mr, S * Vp, true);
+            if ((rc = launch_schur_tc_splitk(mr, mr, S * Vp, w.Lb, S * Vp, Bop, S * Vp, W + JE + JE * ld, w.ldw, bf16,
+                                             true, ks, w.Psk, st, 0)))
                 return rc;
             // algorithmic flops of the triangular update: m (m + 1) K
             if (tu && (rc = tu->end(st, (double)mr * (mr + 1.0) * Vs))) return rc;

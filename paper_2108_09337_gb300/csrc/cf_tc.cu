@@ -58,6 +58,12 @@ struct Problem {
     int ldc;
     int lower;
     int tiles_m, tiles_n, ntiles;
+    // split-K: work unit u is tile u % ntiles over K blocks
+    // [s kps, (s + 1) kps), s = u / ntiles; with P set, each unit writes its
+    // accumulator to P[(s ntiles + tile) BM BN + col BM + row] instead of
+    // updating C (k_splitk_reduce then subtracts the partials in order)
+    int ksplit, kps, nunits;
+    float *P;
 };
 
 // Tile t -> (bm, bn), M fastest so consecutive CTAs share a B tile in L2.
@@ -80,6 +86,12 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = p.k / BK;
+    auto unit_k = [&](int u, int &t, int &kb0, int &kb1) {
+        t = u % p.ntiles;
+        const int sp = u / p.ntiles;
+        kb0 = sp * p.kps;
+        kb1 = min(nkb, kb0 + p.kps);
+    };
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) { mbar_init(&s.full[i], 1); mbar_init(&s.empty[i], 1); }
@@ -105,10 +117,11 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-                int m0, n0;
+            for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
+                int t, kb0, kb1, m0, n0;
+                unit_k(u, t, kb0, kb1);
                 if (!tile_coords(p, t, m0, n0)) continue;
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int st = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                     if (!wait_bounded(&s.empty[st], ph ^ 1u, abort_flag, &g_tc_status)) { ok = false; break; }
@@ -131,15 +144,16 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         if (lane == 0) {
             int it = 0, tcount = 0;
             bool ok = true, issued = false;
-            for (int t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-                int m0, n0;
+            for (int u = blockIdx.x; u < p.nunits && ok; u += gridDim.x) {
+                int t, kb0, kb1, m0, n0;
+                unit_k(u, t, kb0, kb1);
                 if (!tile_coords(p, t, m0, n0)) continue;
                 const int b = tcount & 1;
                 const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
                 if (!wait_bounded(&s.acc_empty[b], aph ^ 1u, abort_flag, &g_tc_status)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int st = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                     if (!wait_bounded(&s.full[st], ph, abort_flag, &g_tc_status)) { ok = false; break; }
@@ -150,7 +164,7 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     for (int kk = 0; kk < BK / UMMA_K; ++kk) {
                         // advance 16 elements = 32 bytes inside the swizzled row
                         umma_f16(d_tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                                 (kb > kb0 || kk > 0) ? 1u : 0u);
                     }
                     issued = true;
                     umma_commit(&s.empty[st]);
@@ -169,8 +183,9 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         // ------------------------------------------------ epilogue (warps 2..5)
         const int quarter = warp & 3;                 // TMEM lanes 32*quarter ..
         int tcount = 0;
-        for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
-            int m0, n0;
+        for (int u = blockIdx.x; u < p.nunits; u += gridDim.x) {
+            int t, kb0, kb1, m0, n0;
+            unit_k(u, t, kb0, kb1);
             if (!tile_coords(p, t, m0, n0)) continue;
             const int b = tcount & 1;
             const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
@@ -179,6 +194,24 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_fence_after();
+            if (p.P != nullptr) {
+                // split-K partial: the whole 128 x 256 accumulator, column-major
+                float *dst = p.P + ((size_t)(u / p.ntiles) * p.ntiles + t) * (BM * BN) + quarter * 32 + lane;
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    uint32_t r[32];
+                    const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0);
+                    TMEM_LD32(taddr, r);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) dst[(size_t)(c0 + j) * BM] = __uint_as_float(r[j]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s.acc_empty[b]);
+                ++tcount;
+                continue;
+            }
             const int row = m0 + quarter * 32 + lane;
             const bool row_ok = row < p.m;
             float *crow = p.C + row;
@@ -215,6 +248,22 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
                      : "memory");
+    }
+}
+
+// C -= sum_s P_s over the split-K partials of every tile, in the order
+// s = 0, 1, ...: a deterministic sum, whatever order the units ran in.
+__global__ void __launch_bounds__(256) k_splitk_reduce(Problem p) {
+    const int t = blockIdx.y;
+    const int m0 = (t % p.tiles_m) * BM, n0 = (t / p.tiles_m) * BN;
+    if (p.lower && n0 > m0 + BM - 1) return;
+    for (int e = blockIdx.x * 256 + threadIdx.x; e < BM * BN; e += gridDim.x * 256) {
+        const int row = m0 + e % BM, col = n0 + e / BM;
+        if (row >= p.m || col >= p.n || (p.lower && row < col)) continue;
+        float acc = 0.f;
+        for (int sp = 0; sp < p.ksplit; ++sp) acc += p.P[((size_t)sp * p.ntiles + t) * (BM * BN) + e];
+        float *c = p.C + row + (size_t)col * p.ldc;
+        *c = *c - acc;
     }
 }
 
@@ -261,8 +310,32 @@ static int num_sms() {
     return sms;
 }
 
+int schur_tc_splitk(int m, int n, int k, bool lower) {
+    // enough K ranges to fill the SMs when the output has too few tiles, each
+    // range at least 4 K blocks, at most 8 ranges
+    const int tiles = ceil_div(m, tc::BM) * ceil_div(n, tc::BN);
+    const int eff = lower ? (tiles + ceil_div(m, tc::BM)) / 2 : tiles;     // about half the tiles of a triangle
+    const int sms = num_sms();
+    if (m <= 0 || n <= 0 || eff * 2 > sms) return 1;
+    int ks = sms / (eff > 0 ? eff : 1);
+    const int maxk = (k / tc::BK) / 4;
+    if (ks > maxk) ks = maxk;
+    if (ks > 8) ks = 8;
+    return ks < 2 ? 1 : ks;
+}
+
+size_t schur_tc_splitk_bytes(int m, int n, int ksplit) {
+    if (ksplit <= 1 || m <= 0 || n <= 0) return 0;
+    return sizeof(float) * (size_t)ksplit * ceil_div(m, tc::BM) * ceil_div(n, tc::BN) * tc::BM * tc::BN;
+}
+
 int launch_schur_tc(int m, int n, int k, const void *A, int lda_k, const void *B, int ldb_k, float *C, int ldc,
                     bool bf16, bool lower, cudaStream_t st, int max_ctas) {
+    return launch_schur_tc_splitk(m, n, k, A, lda_k, B, ldb_k, C, ldc, bf16, lower, 1, nullptr, st, max_ctas);
+}
+
+int launch_schur_tc_splitk(int m, int n, int k, const void *A, int lda_k, const void *B, int ldb_k, float *C, int ldc,
+                           bool bf16, bool lower, int ksplit, float *P, cudaStream_t st, int max_ctas) {
     if (m <= 0 || n <= 0 || k <= 0) return CF_OK;
     if (k % tc::BK != 0 || lda_k % 8 != 0 || ldb_k % 8 != 0 || lda_k < k || ldb_k < k) return CF_ERR_UNSUPPORTED;
     if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return CF_ERR_UNSUPPORTED;
@@ -276,13 +349,24 @@ int launch_schur_tc(int m, int n, int k, const void *A, int lda_k, const void *B
     p.tiles_m = ceil_div(m, tc::BM);
     p.tiles_n = ceil_div(n, tc::BN);
     p.ntiles = p.tiles_m * p.tiles_n;
+    const int nkb = k / tc::BK;
+    if (ksplit < 1 || P == nullptr) ksplit = 1;
+    if (ksplit > nkb) ksplit = nkb;
+    p.kps = ceil_div(nkb, ksplit);
+    p.ksplit = ceil_div(nkb, p.kps);          // every range non-empty
+    p.nunits = p.ntiles * p.ksplit;
+    p.P = p.ksplit > 1 ? P : nullptr;
     const size_t smem = 1024 + tc::STAGES * tc::kStageBytes + sizeof(tc::Smem);
     CF_CUDA_TRY(cudaFuncSetAttribute(tc::k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int grid = num_sms();
     if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
-    if (grid > p.ntiles) grid = p.ntiles;
+    if (grid > p.nunits) grid = p.nunits;
     tc::k_schur_tc<<<grid, tc::kThreads, smem, st>>>(ta, tb, p, tc::make_idesc(bf16, tc::BM, tc::BN));
     CF_LAUNCH_CHECK();
+    if (p.P != nullptr) {
+        tc::k_splitk_reduce<<<dim3(8, p.ntiles), 256, 0, st>>>(p);
+        CF_LAUNCH_CHECK();
+    }
     return CF_OK;
 }
 
@@ -314,6 +398,31 @@ extern "C" int cf_schur_update_lp(int m, int n, int k, const void *A_lp, int lda
     if (ldc < (m > 1 ? m : 1)) return -9;
     if (prec != CF_BF16 && prec != CF_F16) return -10;
     return cf::launch_schur_tc(m, n, k, A_lp, lda_k, B_lp, ldb_k, C, ldc, prec == CF_BF16, lower != 0, stream, 0);
+}
+
+extern "C" size_t cf_schur_update_lp_splitk_workspace_size(int m, int n, int k, int ksplit) {
+    (void)k;
+    return cf::schur_tc_splitk_bytes(m, n, ksplit);
+}
+
+extern "C" int cf_schur_update_lp_splitk(int m, int n, int k, const void *A_lp, int lda_k, const void *B_lp, int ldb_k,
+                                         float *C, int ldc, cf_prec prec, int lower, int ksplit, void *work,
+                                         size_t lwork, cudaStream_t stream) {
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (k < 0 || k % 64 != 0) return -3;
+    if (m > 0 && k > 0 && A_lp == nullptr) return -4;
+    if (lda_k < k || lda_k % 8 != 0) return -5;
+    if (n > 0 && k > 0 && B_lp == nullptr) return -6;
+    if (ldb_k < k || ldb_k % 8 != 0) return -7;
+    if (m > 0 && n > 0 && C == nullptr) return -8;
+    if (ldc < (m > 1 ? m : 1)) return -9;
+    if (prec != CF_BF16 && prec != CF_F16) return -10;
+    if (ksplit < 1 || ksplit > 64) return -12;
+    if (m == 0 || n == 0 || k == 0) return CF_OK;
+    if (ksplit > 1 && (work == nullptr || lwork < cf::schur_tc_splitk_bytes(m, n, ksplit))) return CF_ERR_WORKSPACE;
+    return cf::launch_schur_tc_splitk(m, n, k, A_lp, lda_k, B_lp, ldb_k, C, ldc, prec == CF_BF16, lower != 0, ksplit,
+                                      (float *)work, stream, 0);
 }
 
 extern "C" int cf_device_status(cudaStream_t stream) {

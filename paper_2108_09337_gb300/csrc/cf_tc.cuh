@@ -17,6 +17,16 @@ int get_encoder();
 // column-major.  lower: only i >= j.  max_ctas > 0 caps the persistent grid.
 int launch_schur_tc(int m, int n, int k, const void *A, int lda_k, const void *B, int ldb_k, float *C, int ldc,
                     bool bf16, bool lower, cudaStream_t st, int max_ctas);
+// Split-K form (the paper's split of the reduction dimension, Sec. 7.1-7.2,
+// for outputs with too few tiles to fill the SMs): ksplit K ranges run as
+// separate work units that write their FP32 partials to P
+// (schur_tc_splitk_bytes), then C -= sum of the partials in range order
+// (deterministic).  ksplit <= 1 or P null: the plain update.
+int launch_schur_tc_splitk(int m, int n, int k, const void *A, int lda_k, const void *B, int ldb_k, float *C, int ldc,
+                           bool bf16, bool lower, int ksplit, float *P, cudaStream_t st, int max_ctas);
+// The number of K ranges the mixed solvers use for an update (1: none).
+int schur_tc_splitk(int m, int n, int k, bool lower);
+size_t schur_tc_splitk_bytes(int m, int n, int ksplit);
 
 // Synchronises st, returns (and clears) the device status word of the
 // BF16/FP16 tensor-core kernel: 0 or CF_ERR_TIMEOUT (fp8_take_status: the

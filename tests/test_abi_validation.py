@@ -44,6 +44,9 @@ CASES = {
     "cf_schur_update_lp": ((256, 256, 128, P, 128, P, 128, P, 256, 2, 0, None),
                            [(1, -1), (2, -1), (3, -64), (3, 100), (4, None), (5, 64), (5, 132), (6, None),
                             (7, 64), (7, 130), (8, None), (9, 255), (10, 0), (10, 4)]),
+    "cf_schur_update_lp_splitk": ((256, 256, 128, P, 128, P, 128, P, 256, 2, 0, 2, P, BIG, None),
+                                  [(1, -1), (2, -1), (3, -64), (3, 100), (4, None), (5, 64), (6, None), (7, 64),
+                                   (8, None), (9, 255), (10, 0), (12, 0), (12, 65)]),
     "cf_quantize_e4m3": ((256, 200, P, 256, P, 256, P, 2, None),
                          [(1, -1), (2, -1), (3, None), (4, 255), (5, None), (6, 128), (6, 264), (7, None),
                           (8, 1)]),

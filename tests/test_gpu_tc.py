@@ -90,3 +90,41 @@ def test_schur_update_slab_depth(cf):
     ref = c0 - np.einsum("ik,ik->i", Ad, Bd)
     bound = 2 * (k + 2) * 2.0 ** -24 * (np.einsum("ik,ik->i", np.abs(Ad), np.abs(Bd)) + np.abs(c0))
     assert np.all(np.abs(got - ref) <= bound)
+
+
+def _run_splitk(cf, m, n, k, ksplit, lower=False, seed=0):
+    g = torch.Generator().manual_seed(seed)
+    A = torch.randn((m, k), generator=g).to(torch.bfloat16)
+    B = torch.randn((n, k), generator=g).to(torch.bfloat16)
+    C = torch.randn((m, n), generator=g, dtype=torch.float32)
+    outs = []
+    for _ in range(2):
+        dC = C.t().contiguous().cuda().t()
+        cf.schur_update_lp_splitk(A.cuda(), B.cuda(), dC, ksplit, lower=lower)
+        assert cf.device_status() == 0
+        outs.append(dC.cpu().double().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])             # deterministic
+    got = outs[0]
+    Ad, Bd, Cd = A.double().numpy(), B.double().numpy(), C.double().numpy()
+    ref = Cd - Ad @ Bd.T
+    # ksplit FP32 partial sums of k / ksplit products, added in FP32, then subtracted
+    bound = 2 * (k + ksplit + 2) * 2.0 ** -24 * (np.abs(Ad) @ np.abs(Bd).T + np.abs(Cd))
+    if lower:
+        il = np.tril(np.ones((m, n), dtype=bool))
+        assert np.all(np.abs(got - ref)[il] <= bound[il])
+        assert np.array_equal(got[~il], Cd[~il])
+    else:
+        assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("m,n,k,ksplit,lower", [(256, 256, 2048, 4, False), (300, 500, 1024, 3, False),
+                                                (1000, 700, 4096, 8, False), (129, 257, 640, 16, False),
+                                                (512, 512, 2048, 6, True), (1000, 1000, 1024, 2, True),
+                                                (64, 64, 128, 1, False)])
+def test_schur_update_splitk(cf, m, n, k, ksplit, lower):
+    """Split-K (K cut into ksplit ranges run as separate work units, partials
+    added in range order): within the FP32 bound of the FP64 product,
+    bit-identical over two calls, the strict upper triangle untouched in the
+    lower form; more ranges than K blocks are merged (640 = 10 blocks, 16
+    ranges asked)."""
+    _run_splitk(cf, m, n, k, ksplit, lower=lower, seed=m + k)
