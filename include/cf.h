@@ -69,7 +69,7 @@ typedef struct {
     int leaf_h;        /* tournament leaf height: FP64 routines 1..128 [128];
                           mixed LU 1..512 with v <= 64 [512], 1..256 with
                           v > 64 [256] */
-    int arity;         /* children per playoff node: FP64 routines 2..4 [2];
+    int arity;         /* children per playoff node: FP64 routines 2..8 [2];
                           mixed LU with v <= 64: 2..8 and arity * v <= 512
                           [8], with v > 64: 2 [2] */
     int outer_V;       /* mixed LU/Cholesky: depth of the deferred update,
@@ -175,7 +175,8 @@ long long cf_kernel_launches(void);
  * Leaves are leaf_h consecutive rows; each playoff node stacks the winners
  * of `arity` adjacent children (original panel values) and keeps min(rows, w)
  * by partial-pivoting elimination; ties go to the smallest stacked position.
- * w <= 128, 1 <= leaf_h <= 128, 2 <= arity <= 4.
+ * w <= 128, 1 <= leaf_h <= 128, 2 <= arity <= 8 (a playoff node is a
+ * thread-block cluster of `arity` CTAs).
  * ------------------------------------------------------------------------ */
 size_t cf_tourn_workspace_size(int m, int w, int leaf_h, int arity);
 int cf_tourn_select(int m, int w, const double *panel, int ldp, int leaf_h,
@@ -184,8 +185,9 @@ int cf_tourn_select(int m, int w, const double *panel, int ldp, int leaf_h,
 
 /* The same selection on an FP32 panel, as the mixed-precision solvers run
  * it (elimination in FP32 with fused multiply-add; one register row per
- * thread).  Same arguments and workspace as cf_tourn_select, except that
- * 1 <= leaf_h <= 256 and arity must be 2. */
+ * thread).  Same arguments and workspace as cf_tourn_select, except the
+ * shapes: w <= 64 with 1 <= leaf_h <= 512, 2 <= arity <= 8 and
+ * arity * w <= 512; or w <= 128 with 1 <= leaf_h <= 256 and arity 2. */
 int cf_tourn_select_f32(int m, int w, const float *panel, int ldp, int leaf_h,
                         int arity, int *winners, void *work, size_t lwork,
                         cudaStream_t stream);

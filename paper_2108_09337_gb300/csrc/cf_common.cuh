@@ -86,8 +86,8 @@ int resolve_options(const cf_options *in, Opts *out);
 // leaves of 256 rows and arity 2.  Checks outer_V against the final v.
 int mixed_lu_defaults(Opts *o);
 // Tournament shapes of the FP64 routines: leaves of at most kMaxV rows,
-// arity 2..4 (one cluster of `arity` CTAs per playoff node).
-inline bool fp64_tourn_shape(const Opts &o) { return o.leaf_h <= kMaxV && o.arity <= 4; }
+// arity 2..8 (one cluster of `arity` CTAs per playoff node).
+inline bool fp64_tourn_shape(const Opts &o) { return o.leaf_h <= kMaxV && o.arity <= 8; }
 // Tournament shapes of the mixed-precision LU (FP32 panels): v <= 64 with
 // leaves of up to 512 rows and arity up to 8 (arity * v <= 512), or
 // v <= 128 with leaves of up to 256 rows and arity 2.

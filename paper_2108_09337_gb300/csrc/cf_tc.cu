@@ -311,16 +311,19 @@ static int num_sms() {
 }
 
 int schur_tc_splitk(int m, int n, int k, bool lower) {
-    // enough K ranges to fill the SMs when the output has too few tiles, each
-    // range at least 4 K blocks, at most 8 ranges
+    // Only outputs with too few tiles to occupy half the SMs, and only ranges
+    // at least 2048 deep, at most 4 of them.  Measured on GB300 (FP16, one
+    // launch): M = 512..1024 at K = 8192 and M = 256..1024 at K = 16384 run
+    // 1.5-2.3x faster in 4 ranges; every shape at K <= 2048 runs slower split
+    // (the partial-sum round trip and the second launch cost more than the
+    // idle SMs), so the mixed solvers' K = V <= 2048 updates never split.
     const int tiles = ceil_div(m, tc::BM) * ceil_div(n, tc::BN);
     const int eff = lower ? (tiles + ceil_div(m, tc::BM)) / 2 : tiles;     // about half the tiles of a triangle
     const int sms = num_sms();
     if (m <= 0 || n <= 0 || eff * 2 > sms) return 1;
     int ks = sms / (eff > 0 ? eff : 1);
-    const int maxk = (k / tc::BK) / 4;
-    if (ks > maxk) ks = maxk;
-    if (ks > 8) ks = 8;
+    if (ks > k / 2048) ks = k / 2048;
+    if (ks > 4) ks = 4;
     return ks < 2 ? 1 : ks;
 }
 

@@ -424,6 +424,10 @@ int launch_tourn(const T *P, int ldp, int m, int w, int h, int arity, const Tour
         case 2: return launch_tourn_cl<T, 2>(P, ldp, plan, ws, ep, st);
         case 3: return launch_tourn_cl<T, 3>(P, ldp, plan, ws, ep, st);
         case 4: return launch_tourn_cl<T, 4>(P, ldp, plan, ws, ep, st);
+        case 5: return launch_tourn_cl<T, 5>(P, ldp, plan, ws, ep, st);
+        case 6: return launch_tourn_cl<T, 6>(P, ldp, plan, ws, ep, st);
+        case 7: return launch_tourn_cl<T, 7>(P, ldp, plan, ws, ep, st);
+        case 8: return launch_tourn_cl<T, 8>(P, ldp, plan, ws, ep, st);
         default: return CF_ERR_UNSUPPORTED;
     }
 }
@@ -465,7 +469,7 @@ extern "C" int cf_tourn_select(int m, int w, const double *panel, int ldp, int l
     if (m > 0 && w > 0 && panel == nullptr) return -3;
     if (ldp < (m > 1 ? m : 1)) return -4;
     if (leaf_h < 1 || leaf_h > kMaxV) return -5;
-    if (arity < 2 || arity > 4) return -6;
+    if (arity < 2 || arity > 8) return -6;
     if (m == 0 || w == 0) return CF_OK;
     if (winners == nullptr) return -7;
     if (lwork < cf_tourn_workspace_size(m, w, leaf_h, arity) || work == nullptr) return CF_ERR_WORKSPACE;

@@ -145,17 +145,35 @@ __device__ __forceinline__ void stage_tile(float *St, const float *T, int ldt, i
     }
 }
 
-// Row length of the staged right-hand sides: every thread reads columns
-// cg + CG t for t < CPT, which may pass NR (those are never written back).
+// Thread layout of the blocked solves (256 threads, 8 warps).  A thread
+// holds 4 rows x 2 right-hand sides of its block's accumulator.  The lanes
+// of a warp cover LR = 32 / LC row quads and LC = NR / 2 column pairs, so
+// that per k one warp reads one 16-byte word of the tile per row quad and
+// one 8-byte pair of Y per column pair (a single shared-memory wavefront
+// each).  WR warps cover the block's rows; the KS = 8 / WR warp groups split
+// k of every tile (partial sums, added once per block before its last
+// step).
 template <int SB, int NR>
-__host__ __device__ constexpr int trsv_yld() {
-    return (256 / (SB / 4)) * ((NR + (256 / (SB / 4)) - 1) / (256 / (SB / 4))) + 1;
-}
+struct TrsvMap {
+    static constexpr int LC = NR / 2;            // lanes along columns
+    static constexpr int LR = 32 / LC;           // lanes along rows (row quads)
+    static constexpr int RW = 4 * LR;            // rows per warp
+    static constexpr int WR = SB / RW;           // warps over the rows
+    static constexpr int KS = 8 / WR;            // k split
+    static constexpr int KW = SB / KS;           // k per split
+    static constexpr int YLD = NR + 4;           // staged Y row: 16-byte aligned rows
+    static_assert(NR == 4 || NR == 8 || NR == 16, "right-hand-side classes");
+    static_assert(WR >= 1 && WR <= 8 && WR * RW == SB && KS * WR == 8, "thread layout");
+    static_assert(KW % 4 == 0, "k per split: whole vectors");
+};
 
 template <int SB, typename VT, int NR>
 __host__ __device__ constexpr size_t trsv_smem_bytes() {
-    return sizeof(float) * 2 * (size_t)SB * (SB + 4) +
-           sizeof(VT) * ((size_t)SB * (SB + 4) + (size_t)SB * trsv_yld<SB, NR>());
+    using M = TrsvMap<SB, NR>;
+    return sizeof(float) * 2 * (size_t)SB * (SB + 4) +                 // two tile buffers
+           sizeof(VT) * ((size_t)SB * (SB + 4) +                       // inverse of the diagonal block
+                         (size_t)SB * M::YLD +                         // staged Y
+                         (size_t)(M::KS - 1) * SB * NR);               // partial sums of the k split
 }
 
 // Four consecutive 16-byte-aligned shared-memory values as VT.
@@ -172,53 +190,61 @@ __device__ __forceinline__ void load4(float (&m)[4], const float *p) {
     const float4 v = *reinterpret_cast<const float4 *>(p);
     m[0] = v.x; m[1] = v.y; m[2] = v.z; m[3] = v.w;
 }
+__device__ __forceinline__ void load2(float (&y)[2], const float *p) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    y[0] = v.x; y[1] = v.y;
+}
+__device__ __forceinline__ void load2(double (&y)[2], const double *p) {
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    y[0] = v.x; y[1] = v.y;
+}
 
-// Row r (0..3) of a thread's four: 4 rg + r (consecutive), or rg + RG r
-// (STRIDED, used by the transposed solve so that the lanes of a warp read
-// consecutive rows of a row-major tile without bank conflicts).
-template <bool STRIDED, int RG>
-__device__ __forceinline__ int trow(int rg, int r) { return STRIDED ? rg + RG * r : 4 * rg + r; }
+// Row r (0..3) of a thread: rb + r (consecutive; column-major tiles are
+// read as one vector per k), or rb + LR r (strided: the transposed solve,
+// whose row-major tiles are read as one vector per four k, so that the
+// lanes of a warp read consecutive rows without bank conflicts), where rb
+// is the thread's base row.
+template <bool STRIDED, int LR>
+__device__ __forceinline__ int trow(int rbase, int r) { return STRIDED ? rbase + LR * r : rbase + r; }
 
-// acc[r][t] += sign * sum_kk Mt(row(r), kk) * Ys[kk][cg + CG t] for one staged
-// tile; Mt(i, kk) = Tt[kk * LD + i] (COLMAJ) or Tt[i * LD + kk].  Column-major
-// tiles with consecutive rows are read as one 16-byte vector per kk;
-// row-major ones (strided rows) as one vector per four kk; the right-hand
-// sides are broadcast within a warp.
-template <int SB, int NR, int CPT, int CG, bool COLMAJ, bool STRIDED, typename MT, typename VT>
-__device__ __forceinline__ void tile_update(VT (&acc)[4][CPT], const MT *Tt, int LD, const VT *Ys, int YLD, int rg,
-                                            int cg, VT sign) {
-    constexpr int RG = SB / 4;
+// acc[r][t] += sign * sum_{k0 <= kk < k1} Mt(row(r), kk) * Ys[kk * YLD + c + t]
+// for one staged tile; Mt(i, kk) = Tt[kk * LD + i] (COLMAJ) or
+// Tt[i * LD + kk].  Every Y pair is one 8- or 16-byte vector.
+template <int LR, bool COLMAJ, bool STRIDED, typename MT, typename VT>
+__device__ __forceinline__ void tile_mac(VT (&acc)[4][2], const MT *Tt, int LD, const VT *Ys, int YLD, int rbase,
+                                         int c, int k0, int k1, VT sign) {
     if (COLMAJ) {
 #pragma unroll 4
-        for (int kk = 0; kk < SB; ++kk) {
+        for (int kk = k0; kk < k1; ++kk) {
             VT m[4];
             if (!STRIDED) {
-                load4(m, Tt + kk * LD + 4 * rg);
+                load4(m, Tt + kk * LD + rbase);
             } else {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) m[r] = (VT)Tt[kk * LD + trow<true, RG>(rg, r)];
+                for (int r = 0; r < 4; ++r) m[r] = (VT)Tt[kk * LD + trow<true, LR>(rbase, r)];
             }
+            VT y[2];
+            load2(y, Ys + kk * YLD + c);
 #pragma unroll
-            for (int t = 0; t < CPT; ++t) {
-                const VT y = Ys[kk * YLD + cg + CG * t];
+            for (int t = 0; t < 2; ++t)
 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc[r][t] = fma(sign * m[r], y, acc[r][t]);
-            }
+                for (int r = 0; r < 4; ++r) acc[r][t] = fma(sign * m[r], y[t], acc[r][t]);
         }
     } else {
 #pragma unroll 2
-        for (int k4 = 0; k4 < SB; k4 += 4) {
+        for (int k4 = k0; k4 < k1; k4 += 4) {
             VT m[4][4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) load4(m[r], Tt + trow<STRIDED, RG>(rg, r) * LD + k4);
+            for (int r = 0; r < 4; ++r) load4(m[r], Tt + trow<STRIDED, LR>(rbase, r) * LD + k4);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) {
+                VT y[2];
+                load2(y, Ys + (k4 + u) * YLD + c);
 #pragma unroll
-                for (int t = 0; t < CPT; ++t) {
-                    const VT y = Ys[(k4 + u) * YLD + cg + CG * t];
+                for (int t = 0; t < 2; ++t)
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) acc[r][t] = fma(sign * m[r][u], y, acc[r][t]);
-                }
+                    for (int r = 0; r < 4; ++r) acc[r][t] = fma(sign * m[r][u], y[t], acc[r][t]);
+            }
         }
     }
 }
@@ -237,39 +263,47 @@ __device__ __forceinline__ void trsv_stage_step(float *dst, int step, int s, boo
     const int ti = (MODE == 3) ? cb * SB : r0, tj = (MODE == 3) ? r0 : cb * SB;
     stage_tile<SB>(dst, T, ldt, n, ti, tj, aligned && ti + SB <= n && tj + SB <= n);
 }
-
-// VT: arithmetic and right-hand-side type (float, or double for FP64
-// solves with the FP32 factor); the factor tiles stay FP32 in shared memory.
-// Thread = (row group rg = tid % (SB / 4): rows 4 rg .. 4 rg + 3, or
-// rg + (SB / 4) r for the transposed solve; right-hand-side group
-// cg = tid / (SB / 4): columns cg + CG t).
+// Block solve of one ticket.  VT: arithmetic and right-hand-side type
+// (float, or double for FP64 solves with the FP32 factor); the factor tiles
+// stay FP32 in shared memory.
+//
+// Per step (one finished block's tile): the tile of the next step is
+// prefetched with cp.async; the flags of later blocks are polled a warp at
+// a time (up to 64 per poll), so for blocks that finished long ago neither
+// the flag nor the data costs a dependent round trip: the Y block of the
+// next step is loaded into registers while this step's tile product runs.
+// Only the first unfinished block is waited for (bounded).
 template <int SB, int MODE, int NR, typename VT>
 __global__ void __launch_bounds__(256, 1)        // one CTA per SM (shared memory)
 k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *__restrict__ Dinv,
                const float *__restrict__ Gn, VT *X, int ldx, int *flags, int *ticket, long long spin_limit) {
+    using Map = TrsvMap<SB, NR>;
     constexpr int TLD = SB + 4;
-    constexpr int RG = SB / 4;                     // row groups of 4
-    constexpr int CG = 256 / RG;                   // right-hand-side groups
-    constexpr int CPT = (NR + CG - 1) / CG;        // right-hand sides per thread
-    constexpr int YLD = trsv_yld<SB, NR>();
-    static_assert(YLD >= CG * CPT + 1, "staged right-hand-side rows too short");
+    constexpr int LR = Map::LR, RW = Map::RW, WR = Map::WR, KS = Map::KS, KW = Map::KW, YLD = Map::YLD;
+    constexpr int YPT = SB * NR / 256;             // Y values per thread of one block
+    static_assert(SB * NR % 256 == 0, "Y block: whole values per thread");
     constexpr bool STR = (MODE == 3);              // strided rows (see trow)
     extern __shared__ __align__(16) float sm[];
     float *St0 = sm;                               // two tile buffers
     float *St1 = sm + SB * TLD;
     VT *Ds = reinterpret_cast<VT *>(sm + 2 * SB * TLD);     // inverse of the diagonal block
     VT *Ys = Ds + SB * TLD;                                 // [SB][YLD]
-    __shared__ int s_ticket;
+    VT *Red = Ys + SB * YLD;                                // [KS - 1][SB][NR] partial sums
+    __shared__ int s_ticket, s_upto;
     constexpr bool fwd = (MODE == 0 || MODE == 2);
     const int nb = (n + SB - 1) / SB;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) s_ticket = atomicAdd(ticket, 1);
     __syncthreads();
     const int s = s_ticket;
     if (s >= nb) return;
     const int b = fwd ? s : nb - 1 - s;
     const int r0 = b * SB, rb = min(SB, n - r0);
-    const int rg = tid % RG, cg = tid / RG;
+    const int wr = warp % WR, kp = warp / WR;      // row warp, k part
+    const int lr = lane % LR, lc = lane / LR;
+    const int rbase = wr * RW + (STR ? lr : 4 * lr);
+    const int c = 2 * lc;                          // first of the thread's two right-hand sides
+    const int k0 = kp * KW, k1 = k0 + KW;
     const bool aligned = ((ldt & 3) == 0) && ((((uintptr_t)T) & 15) == 0);
     // the diagonal block's inverse does not depend on anyone: fetch it now
     // (Ds[kk * TLD + ii] = (Dinv_b)(ii, kk); MODE 3 uses (L_bb^{-1})^T)
@@ -280,13 +314,14 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
             Ds[kk * TLD + ii] = (MODE == 3) ? D[kk + SB * ii] : D[ii + SB * kk];
         }
     }
-    VT acc[4][CPT];
+    // the right-hand side lives in the k-part-0 threads; the others sum from 0
+    VT acc[4][2];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int t = 0; t < CPT; ++t) {
-            const int i = trow<STR, RG>(rg, r), c = cg + CG * t;
-            acc[r][t] = (i < rb && c < nrhs) ? X[(size_t)(r0 + i) + (size_t)c * ldx] : VT(0);
+        for (int t = 0; t < 2; ++t) {
+            const int i = trow<STR, LR>(rbase, r);
+            acc[r][t] = (kp == 0 && i < rb && c + t < nrhs) ? X[(size_t)(r0 + i) + (size_t)(c + t) * ldx] : VT(0);
         }
     // With Gn (the neighbour block's tile premultiplied by this block's
     // diagonal inverse, G_b = Dinv_b M(b, b -+ 1)), the last step, which waits
@@ -298,90 +333,161 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
         trsv_stage_step<SB, MODE>(St0, 0, s, pre, Gb, T, ldt, n, nb, r0, aligned);
         cp_async_commit();
     }
+    // Y block of a step: value e = tid + 256 j is (row e % SB, column e / SB)
+    auto load_y = [&](VT (&v)[YPT], int step) {
+        const int cb = fwd ? step : nb - 1 - step;
+        const int c0 = cb * SB, cbk = min(SB, n - c0);
+#pragma unroll
+        for (int j = 0; j < YPT; ++j) {
+            const int e = tid + 256 * j, kk = e % SB, cc = e / SB;
+            v[j] = (kk < cbk && cc < nrhs) ? __ldcg(X + (size_t)(c0 + kk) + (size_t)cc * ldx) : VT(0);
+        }
+    };
+    auto store_y = [&](const VT (&v)[YPT]) {
+#pragma unroll
+        for (int j = 0; j < YPT; ++j) {
+            const int e = tid + 256 * j;
+            Ys[(e % SB) * YLD + e / SB] = v[j];
+        }
+    };
+    // Warp 0: waits (bounded) for the flag of step `from`, then extends the
+    // run of finished steps as far as the next unset flag (at most 64
+    // more); s_upto = the first step past the run.  The fence orders the
+    // flag reads before every later read of the solution blocks.
+    auto poll = [&](int from) {
+        if (warp == 0) {
+            if (lane == 0) {
+                volatile int *f = flags + (fwd ? from : nb - 1 - from);
+                long long it = 0;
+                while (*f == 0 && it < spin_limit) {
+                    ++it;
+                    if (it > 64) __nanosleep(20);
+                }
+                if (it >= spin_limit) atomicExch(&g_trsv_status, CF_ERR_TIMEOUT);
+            }
+            __syncwarp();
+            int u = from + 1;
+#pragma unroll 1
+            for (int chunk = 0; chunk < 2 && u < s; ++chunk) {
+                const int idx = u + lane;
+                const int fl = (idx < s) ? *(volatile int *)(flags + (fwd ? idx : nb - 1 - idx)) : 1;
+                const unsigned unset = ~__ballot_sync(0xffffffffu, fl != 0);
+                if (unset == 0u) {
+                    u = min(s, u + 32);
+                } else {
+                    u = min(s, u + __ffs(unset) - 1);
+                    break;
+                }
+            }
+            __threadfence();
+            if (lane == 0) s_upto = u;
+        }
+    };
+    int upto = 0;                                  // steps [0, upto) are known finished
+    bool have = false;                             // this step's Y block is in yv
+    VT yv[YPT];
     for (int step = 0; step < s; ++step) {
         float *St = (step & 1) ? St1 : St0;
         if (step + 1 < s)                          // prefetch the next tile
             trsv_stage_step<SB, MODE>((step & 1) ? St0 : St1, step + 1, s, pre, Gb, T, ldt, n, nb, r0, aligned);
         cp_async_commit();
-        const int cb = fwd ? step : nb - 1 - step;
-        const int c0 = cb * SB, cbk = min(SB, n - c0);
-        const bool last_pre = pre && step == s - 1;
-        if (last_pre) {                            // acc <- Dinv_b acc before the neighbour's wait
+        const bool last = (step == s - 1);
+        if (last) {
+            // partial sums of the k split into the k-part-0 threads (fixed order)
+            if (KS > 1) {
+                if (kp > 0) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int t = 0; t < CPT; ++t)
-                    if (cg + CG * t < NR) Ys[trow<STR, RG>(rg, r) * YLD + cg + CG * t] = acc[r][t];
-            __syncthreads();
-            VT z[4][CPT];
+                        for (int t = 0; t < 2; ++t)
+                            Red[((kp - 1) * SB + trow<STR, LR>(rbase, r)) * NR + c + t] = acc[r][t];
+                }
+                __syncthreads();
+                if (kp == 0) {
+#pragma unroll 1
+                    for (int q = 0; q < KS - 1; ++q)
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                        for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int t = 0; t < CPT; ++t) z[r][t] = VT(0);
-            tile_update<SB, NR, CPT, CG, true, STR>(z, Ds, TLD, Ys, YLD, rg, cg, VT(1));
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int t = 0; t < CPT; ++t) acc[r][t] = z[r][t];
-            __syncthreads();
-        }
-        if (tid == 0) {
-            volatile int *f = flags + cb;
-            long long it = 0;
-            while (*f == 0 && it < spin_limit) {
-                ++it;
-                if (it > 64) __nanosleep(20);
+                            for (int t = 0; t < 2; ++t)
+                                acc[r][t] += Red[(q * SB + trow<STR, LR>(rbase, r)) * NR + c + t];
+                }
             }
-            if (it >= spin_limit) atomicExch(&g_trsv_status, CF_ERR_TIMEOUT);
-            __threadfence();
+            if (pre) {                             // acc <- Dinv_b acc before the neighbour's wait
+                if (kp == 0) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int t = 0; t < 2; ++t) Ys[trow<STR, LR>(rbase, r) * YLD + c + t] = acc[r][t];
+                }
+                __syncthreads();
+                VT z[4][2] = {};
+                if (kp == 0) tile_mac<LR, true, STR>(z, Ds, TLD, Ys, YLD, rbase, c, 0, SB, VT(1));
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) acc[r][t] = z[r][t];
+                __syncthreads();
+            }
         }
-        __syncthreads();
-        for (int e = tid; e < SB * NR; e += 256) {
-            const int kk = e % SB, c = e / SB;
-            Ys[kk * YLD + c] = (kk < cbk && c < nrhs) ? __ldcg(X + (size_t)(c0 + kk) + (size_t)c * ldx) : VT(0);
+        // this step's Y block
+        if (have) {
+            store_y(yv);
+        } else {
+            if (step >= upto) poll(step);
+            __syncthreads();
+            upto = s_upto;
+            VT v[YPT];
+            load_y(v, step);
+            store_y(v);
         }
+        // the next step's Y block into registers while this step computes
+        have = (step + 1 < upto);
+        if (have) load_y(yv, step + 1);
         cp_async_wait<1>();                        // this step's tile has landed
         __syncthreads();
         // M(i, kk) = St[kk * TLD + i], or St[i * TLD + kk] for MODE 3; G_b
         // is staged column-major in every mode
-        if (last_pre) tile_update<SB, NR, CPT, CG, true, STR>(acc, St, TLD, Ys, YLD, rg, cg, VT(-1));
-        else tile_update<SB, NR, CPT, CG, MODE != 3, STR>(acc, St, TLD, Ys, YLD, rg, cg, VT(-1));
+        if (!last) {
+            tile_mac<LR, MODE != 3, STR>(acc, St, TLD, Ys, YLD, rbase, c, k0, k1, VT(-1));
+        } else if (kp == 0) {
+            if (pre) tile_mac<LR, true, STR>(acc, St, TLD, Ys, YLD, rbase, c, 0, SB, VT(-1));
+            else tile_mac<LR, MODE != 3, STR>(acc, St, TLD, Ys, YLD, rbase, c, 0, SB, VT(-1));
+        }
         __syncthreads();
     }
     cp_async_wait<0>();
+    VT y[4][2];
     if (pre) {                                     // acc already holds y_b
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int t = 0; t < CPT; ++t) {
-                const int i = trow<STR, RG>(rg, r), c = cg + CG * t;
-                if (i < rb && c < nrhs) X[(size_t)(r0 + i) + (size_t)c * ldx] = acc[r][t];
-            }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) atomicExch(flags + b, 1);
-        return;
-    }
-    // y_b = Dinv_b acc
+            for (int t = 0; t < 2; ++t) y[r][t] = acc[r][t];
+    } else {
+        // y_b = Dinv_b acc (acc complete in the k-part-0 threads: the last
+        // step added the partial sums; with no step, only they hold any)
+        if (kp == 0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int t = 0; t < CPT; ++t)
-            if (cg + CG * t < NR) Ys[trow<STR, RG>(rg, r) * YLD + cg + CG * t] = acc[r][t];
-    __syncthreads();
-    VT y[4][CPT];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int t = 0; t < CPT; ++t) y[r][t] = VT(0);
-    tile_update<SB, NR, CPT, CG, true, STR>(y, Ds, TLD, Ys, YLD, rg, cg, VT(1));
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int t = 0; t < CPT; ++t) {
-            const int i = trow<STR, RG>(rg, r), c = cg + CG * t;
-            if (i < rb && c < nrhs) X[(size_t)(r0 + i) + (size_t)c * ldx] = y[r][t];
+                for (int t = 0; t < 2; ++t) Ys[trow<STR, LR>(rbase, r) * YLD + c + t] = acc[r][t];
         }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int t = 0; t < 2; ++t) y[r][t] = VT(0);
+        if (kp == 0) tile_mac<LR, true, STR>(y, Ds, TLD, Ys, YLD, rbase, c, 0, SB, VT(1));
+    }
+    if (kp == 0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int i = trow<STR, LR>(rbase, r);
+                if (i < rb && c + t < nrhs) X[(size_t)(r0 + i) + (size_t)(c + t) * ldx] = y[r][t];
+            }
+    }
     __threadfence();
     __syncthreads();
     if (tid == 0) atomicExch(flags + b, 1);

@@ -22,7 +22,7 @@ def _opt(**kw):
 # name: (valid-looking arguments, [(1-based position, invalid value), ...])
 CASES = {
     "cf_tourn_select": ((100, 8, P, 100, 16, 2, P, P, BIG, None),
-                        [(1, -1), (2, -1), (2, 129), (3, None), (4, 99), (5, 0), (5, 129), (6, 1), (6, 5), (7, None)]),
+                        [(1, -1), (2, -1), (2, 129), (3, None), (4, 99), (5, 0), (5, 129), (6, 1), (6, 9), (7, None)]),
     "cf_tourn_select_f32": ((100, 8, P, 100, 16, 2, P, P, BIG, None),
                             [(1, -1), (2, 129), (3, None), (4, 99), (5, 0), (5, 513), (6, 1), (6, 9), (7, None)]),
     "cf_getrf": ((8, P, 8, P, P, P, BIG, None, None),
@@ -118,10 +118,10 @@ def test_bad_options_are_unsupported_before_any_cuda_call():
 
 
 def test_tournament_shapes_per_routine():
-    # FP64 routines: leaves <= 128 rows, arity <= 4; the mixed LU: v = 128
+    # FP64 routines: leaves <= 128 rows, arity <= 8; the mixed LU: v = 128
     # with leaves <= 256 and arity 2, or v <= 64 with leaves <= 512 and
     # arity * v <= 512
-    for kw in ({"arity": 5}, {"leaf_h": 129}):
+    for kw in ({"leaf_h": 129}, {"leaf_h": 512, "arity": 8}):
         assert L.cf_getrf(8, P, 8, P, P, P, BIG, _opt(**kw), None) == cf.CF_ERR_UNSUPPORTED, kw
         assert L.cf_getrf_noalloc(8, P, 8, P, P, _opt(**kw), None) == cf.CF_ERR_UNSUPPORTED, kw
         assert L.cf_getrf_workspace_size(1000, _opt(**kw)) == 0, kw

@@ -55,7 +55,8 @@ def _pivots_agree(ip_gpu, ip_or, gaps, v):
 @pytest.mark.parametrize("m,w,h,arity", [
     (128, 128, 128, 2), (1, 1, 128, 2), (50, 128, 128, 2), (1000, 128, 128, 2),
     (777, 100, 50, 3), (300, 17, 128, 4), (5000, 128, 128, 2), (4099, 64, 7, 2),
-    (2000, 128, 128, 4), (129, 128, 128, 3)])
+    (2000, 128, 128, 4), (129, 128, 128, 3), (2000, 128, 128, 8), (5000, 128, 100, 5), (1500, 128, 64, 6),
+    (9000, 128, 128, 7), (130, 128, 128, 8), (40000, 128, 128, 8)])
 def test_tourn_select_bit_identical(cf, m, w, h, arity):
     P = inputs.uniform_pm1(m, seed=m + w, m=w)
     win_o, _ = oracle.tourn_select(P, h=h, arity=arity)
@@ -73,18 +74,20 @@ def test_tourn_select_ties_and_zeros(cf):
     np.testing.assert_array_equal(win.cpu().numpy(), win_o)
 
 
-def test_tourn_select_full_height_panel(cf):
+@pytest.mark.parametrize("arity", [2, 8])
+def test_tourn_select_full_height_panel(cf, arity):
     """The first panel of the N = 32768 LU workload (32768 x 128)."""
     m, w = 32768, 128
     P = inputs.uniform_pm1(m, seed=0, m=w)
-    win_o, _ = oracle.tourn_select(P, h=128, arity=2)
-    win = cf.tourn_select(_dev(P), leaf_h=128, arity=2)
+    win_o, _ = oracle.tourn_select(P, h=128, arity=arity)
+    win = cf.tourn_select(_dev(P), leaf_h=128, arity=arity)
     np.testing.assert_array_equal(win.cpu().numpy(), win_o)
 
 
 # ------------------------------------------------------------------- LU
 LU_CASES = [(1, 128, 128, 2), (2, 128, 128, 2), (5, 2, 3, 2), (127, 128, 128, 2), (128, 128, 128, 2),
-            (129, 128, 128, 2), (300, 64, 40, 3), (515, 128, 128, 2), (700, 100, 128, 4), (1000, 128, 17, 2)]
+            (129, 128, 128, 2), (300, 64, 40, 3), (515, 128, 128, 2), (700, 100, 128, 4), (1000, 128, 17, 2),
+            (1000, 128, 128, 8), (2048, 128, 128, 8), (1200, 64, 32, 6)]
 
 
 @pytest.mark.parametrize("n,v,h,arity", LU_CASES)

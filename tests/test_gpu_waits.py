@@ -65,12 +65,15 @@ def _dev32(A):
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
-@pytest.mark.parametrize("n,nrhs", [(1, 1), (200, 3), (1000, 8), (3000, 16)])
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (200, 3), (1000, 8), (2100, 5), (3000, 16), (5000, 1), (4100, 12)])
 def test_trsv_f32_matches_fp64_substitution(cf, mode, n, nrhs):
+    """Ragged last blocks (200, 2100, 3000, 4100, 5000 rows), one-block
+    solves, every right-hand-side width class (<= 4, <= 8, <= 16)."""
     T = _tri(n, mode, seed=n + mode)
     X = inputs.rhs_normal(n, nrhs, seed=mode).astype(np.float32).astype(np.float64)
     dX = _dev32(X)
     cf.trsv_f32(_dev32(T), dX, mode)
+    assert cf.device_status() == cf.CF_OK
     ref = _reference(T, X, mode)
     got = dX.cpu().numpy().astype(np.float64)
     assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()

@@ -66,7 +66,7 @@ def test_argument_validation_returns_before_any_cuda_call(lib):
     assert L.cf_potrf(-2, null, 1, null, null, 0, None, null) == -1
     assert L.cf_tourn_select(10, 200, ctypes.c_void_p(16), 10, 128, 2, null, null, 0, null) == -2
     assert L.cf_tourn_select(10, 4, ctypes.c_void_p(16), 10, 0, 2, null, null, 0, null) == -5
-    assert L.cf_tourn_select(10, 4, ctypes.c_void_p(16), 10, 8, 7, null, null, 0, null) == -6
+    assert L.cf_tourn_select(10, 4, ctypes.c_void_p(16), 10, 8, 9, null, null, 0, null) == -6
     assert L.cf_residual(-1, 1, 1, null, 1, null, 1, null, 1, null, 1, null) == -1
     assert L.cf_getrs(4, 1, ctypes.c_void_p(16), 2, null, null, 4, null, 0, null) == -4
 
