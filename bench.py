@@ -593,10 +593,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     pair = kern("pair_ms", "pair_launches", sum(2.0 * n * n * k * s["pair_launches"] for s, k in allst))
     upd = kern("update_ms", "update_launches", sum(s["update_flops"] for s, _ in allst))
     tourn = kern("tourn_ms", "tourn_launches", sum(s["tourn_flops"] for s, _ in allst))
-    # tensor-core residuals (their time includes cutting A into digit slices
-    # once per solve): algorithmic bytes = the eight BF16 slices of A read per
-    # product, 16 N^2
+    # tensor-core residuals: algorithmic bytes = the eight BF16 slices of A
+    # read per product, 16 N^2; cutting A into its slices (once per solve):
+    # A read in FP64 and the slices written, 24 N^2
     rtc = kern("tc_ms", "tc_launches", sum(16.0 * n * n * s["tc_launches"] for s, _ in allst))
+    prep_ms = sum(s["tc_prep_ms"] for s, _ in allst)
+    prep_cnt = sum(1 for s, _ in allst if s["tc_prep_ms"] > 0)
+    prep = (prep_ms, prep_cnt, 24.0 * n * n * prep_cnt)
     bf16_pk = peaks.get("bf16_tflops_sustained") or 1700.0
     hbm_pk = (peaks.get("hbm_gbs") or 6800.0) / 1e3        # TB/s, so that bytes / ms / 1e9 compare
     cand = {
@@ -616,6 +619,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "residual_tc": (rtc, "k_resid_tc (R-1 on the tensor cores: digit slices of A, exact FP32 chunk sums)",
                         "hbm", hbm_pk, "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
                         else "fallback 6.8 TB/s", None),
+        "slice_a": (prep, "k_slice_a (A cut into eight BF16 digit slices for the tensor-core residuals)", "hbm",
+                    hbm_pk, "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s", None),
         "schur_tc_KV": (upd, "k_schur_tc (LU-5/CH-3, K=V tcgen05 update)", "tensor", bf16_pk,
                         "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks
                         else "fallback 1.7 PFLOP/s sustained", None),

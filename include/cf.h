@@ -69,7 +69,7 @@ typedef struct {
     int leaf_h;        /* tournament leaf height: FP64 routines 1..128 [128];
                           mixed LU 1..512 with v <= 64 [512], 1..256 with
                           v > 64 [256] */
-    int arity;         /* children per playoff node: FP64 routines 2..8 [2];
+    int arity;         /* children per playoff node: FP64 routines 2..8 [8];
                           mixed LU with v <= 64: 2..8 and arity * v <= 512
                           [8], with v > 64: 2 [2] */
     int outer_V;       /* mixed LU/Cholesky: depth of the deferred update,
@@ -131,8 +131,10 @@ typedef struct {
     double tourn_flops;     /* their elimination flops: per GEPP on r rows x w
                                columns, sum_j (r-j-1)(2(w-j-1) + 1) */
     double tc_ms;           /* device time inside the tensor-core residuals and
-                               products (slicing of A included) */
+                               products with A */
     int tc_launches;        /* tensor-core products with A */
+    double tc_prep_ms;      /* device time cutting A into its digit slices
+                               (once per solve) */
 } cf_refine_stats;
 
 /* One workspace query for every call that takes (work, lwork): the bytes
@@ -211,9 +213,10 @@ int cf_getrf(int n, double *A, int lda, int *ipiv, int *info, void *work,
  * Same arguments, results and kernels as cf_getrf, but the tournament
  * scratch lives in a 2 MiB array that the library places on every GPU that
  * loads it and holds until the process exits; nothing is allocated.
- *   - The scratch needed grows like n / leaf_h: n up to 131072 fits with
- *     leaf_h = 128 and arity 2 (65536 with leaf_h = 64).  Larger requests
- *     return CF_ERR_WORKSPACE before anything is enqueued.
+ *   - The scratch needed grows like n / leaf_h: n up to 393216 fits with
+ *     leaf_h = 128 and the default arity 8 (196608 with leaf_h = 64; with
+ *     arity 2, 131072 and 65536).  Larger requests return CF_ERR_WORKSPACE
+ *     before anything is enqueued.
  *   - The first call on a device looks up the array's device address (once,
  *     with that device current); make that first call before any stream
  *     capture on that device.

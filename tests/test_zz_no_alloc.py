@@ -55,7 +55,7 @@ def test_noalloc_matches_getrf_two_calls(cf, call):
         LU, LUr = dA.cpu().numpy(), dA_ref.cpu().numpy()
         np.testing.assert_array_equal(LU, LUr)
         # against the oracle (same v, leaf height and arity as the defaults)
-        LUo, ipo, info_o, gaps, _ = oracle.getrf(A, v=128, h=128, arity=2)
+        LUo, ipo, info_o, gaps, _ = oracle.getrf(A, v=128, h=128, arity=8)   # the FP64 defaults
         assert info_o == 0
         div = np.nonzero(ip != ipo)[0]
         if div.size:
