@@ -160,14 +160,20 @@ __global__ void __launch_bounds__(256) k_to_f32_rowsum(int n, const double *__re
             t1 += fabsf(a1f);
             f0 = max(f0, (int)((__double_as_longlong(a0) >> 52) & 0x7FF));
             f1 = max(f1, (int)((__double_as_longlong(a1) >> 52) & 0x7FF));
-            const float w0 = (i == j && shift != 0.0) ? (float)(a0 + shift) : a0f;
-            const float w1 = (i + 1 == j && shift != 0.0) ? (float)(a1 + shift) : a1f;
             float *dst = W + (size_t)i + (size_t)j * ldw;
-            if (two) *reinterpret_cast<float2 *>(dst) = make_float2(w0, w1);
-            else dst[0] = w0;
+            if (two) *reinterpret_cast<float2 *>(dst) = make_float2(a0f, a1f);
+            else dst[0] = a0f;
         }
         s0 += (double)t0;
         s1 += (double)t1;
+    }
+    // the shifted diagonal, rewritten by the thread that wrote it (the FP64
+    // addition stays out of the element loop: selected per element, it was
+    // computed for every element)
+    if (shift != 0.0) {
+        if (i >= j0 && i < j1) W[(size_t)i + (size_t)i * ldw] = (float)(A[(size_t)i + (size_t)i * lda] + shift);
+        if (two && i + 1 >= j0 && i + 1 < j1)
+            W[(size_t)(i + 1) + (size_t)(i + 1) * ldw] = (float)(A[(size_t)(i + 1) + (size_t)(i + 1) * lda] + shift);
     }
     if (rowsum) {
         atomicAdd(rowsum + i, s0);
@@ -530,13 +536,15 @@ static int cvt_cols_split(int k, int cols, int kpad, const float *src, int lds, 
 // A second stream for the parts of a panel step that do not depend on each
 // other (released when its work completes).
 struct SideStream {
-    cudaStream_t s = nullptr;
-    cudaEvent_t swapped = nullptr, a00_done = nullptr, side_done = nullptr;
+    cudaStream_t s = nullptr, bg = nullptr;
+    cudaEvent_t swapped = nullptr, a00_done = nullptr, side_done = nullptr, bg_done = nullptr;
     int open() {
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&bg, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&swapped, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&a00_done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&side_done, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&side_done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&bg_done, cudaEventDisableTiming) != cudaSuccess)
             return CF_ERR_CUDA;
         return CF_OK;
     }
@@ -544,7 +552,9 @@ struct SideStream {
         if (swapped) cudaEventDestroy(swapped);
         if (a00_done) cudaEventDestroy(a00_done);
         if (side_done) cudaEventDestroy(side_done);
+        if (bg_done) cudaEventDestroy(bg_done);
         if (s) cudaStreamDestroy(s);
+        if (bg) cudaStreamDestroy(bg);
     }
 };
 
@@ -611,63 +621,78 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
                 la_pending = false;
             }
             if ((rc = launch_apply_swaps<float>(W, w.ldw, n, k0, w.tep, w.perm, st))) return rc;
-            // Fork: the side stream takes the pivot rows' left-looking update
-            // (concurrent with the A00 LU) and LU-4 with its operand copies
-            // (concurrent with LU-3); the main stream joins before the slab
-            // update, which reads both solves' operands.
+            // Fork: the side stream takes LU-4 on the slab's columns with
+            // their operand copy (concurrent with LU-3); the main stream joins
+            // before the next panel's update, which reads both solves'
+            // operands.  The background stream takes what only the slab's
+            // deferred update needs: the pivot rows' left-looking update
+            // right of the slab, LU-4 there and its K-major copy; the main
+            // stream joins it at the slab's end.  It writes only this step's
+            // pivot rows right of the slab, which no later step of the slab
+            // reads before it (the next steps' swaps move rows below them;
+            // the next steps' background work follows in stream order).
             CF_CUDA_TRY(cudaEventRecord(ss.swapped, st));
-            CF_CUDA_TRY(cudaStreamWaitEvent(ss.s, ss.swapped, 0));
+            CF_CUDA_TRY(cudaStreamWaitEvent(ss.bg, ss.swapped, 0));
             if ((rc = launch_a00_lu32(A00, w.ldw, wd, k0, info, st))) return rc;
             CF_CUDA_TRY(cudaEventRecord(ss.a00_done, st));
+            CF_CUDA_TRY(cudaStreamWaitEvent(ss.s, ss.a00_done, 0));
             const int below = m - wd, right = n - k0 - wd;
             const int off = k0 - J0, nout = n - JE;
+            const int rslab = right - nout;              // columns right of the panel inside the slab
             // The part of the new pivot rows right of the slab has not yet
             // received this slab's earlier steps (they are deferred for every
             // row still below, and a pivot row may have come from anywhere
             // below): apply them now, A[k0:k0+wd, JE:] -= L[k0:k0+wd, J0:k0]
             // U[J0:k0, JE:] (left-looking, K = off; operand in Lb, which is
             // free until the slab's deferred update).
+            // (background)
             if (off > 0 && nout > 0) {
                 const int Kp = (off + 63) / 64 * 64;
                 float *Cp = W + k0 + JE * ld;
                 if (!split) {
-                    if ((rc = cvt_rows<LP>(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Lb, Kp, ss.s))) return rc;
-                    if ((rc = launch_schur_tc(wd, nout, Kp, w.Lb, Kp, w.Ub, Vpad, Cp, w.ldw, bf16, false, ss.s, 0)))
+                    if ((rc = cvt_rows<LP>(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Lb, Kp, ss.bg))) return rc;
+                    if ((rc = launch_schur_tc(wd, nout, Kp, w.Lb, Kp, w.Ub, Vpad, Cp, w.ldw, bf16, false, ss.bg, 0)))
                         return rc;
                 } else {
                     // segments (hi, hi, lo) x (hi, lo, hi): three K = off products
-                    if ((rc = cvt_rows_split(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Lb, 3 * Kp, Kp, 0, ss.s)))
+                    if ((rc = cvt_rows_split(wd, off, Kp, W + k0 + J0 * ld, w.ldw, w.Lb, 3 * Kp, Kp, 0, ss.bg)))
                         return rc;
                     for (int sg = 0; sg < 3; ++sg)
                         if ((rc = launch_schur_tc(wd, nout, Kp, (const __nv_bfloat16 *)w.Lb + (size_t)sg * Kp, 3 * Kp,
                                                   (const __nv_bfloat16 *)w.Ub + (size_t)sg * Vpad, 3 * Vpad, Cp,
-                                                  w.ldw, true, false, ss.s, 0)))
+                                                  w.ldw, true, false, ss.bg, 0)))
                             return rc;
                 }
             }
-            // LU-4 (side) after the A00 LU; it also writes the K-major
-            // low-precision operand of the updates inside the slab (split
-            // form: converted after), and the U rows of this step right of
-            // the slab go to the K-major operand of the slab's deferred update
-            // (K rows off .. off + wd, zeros up to the next multiple of 64).
-            CF_CUDA_TRY(cudaStreamWaitEvent(ss.s, ss.a00_done, 0));
-            if ((rc = launch_ltrsm32<LP>(A00 + wd * ld, w.ldw, wd, right, A00, w.ldw, split ? nullptr : (LP *)w.Bb,
+            // LU-4 (side) after the A00 LU on the slab's columns; it also
+            // writes the K-major low-precision operand of the updates inside
+            // the slab (split form: converted after).
+            if ((rc = launch_ltrsm32<LP>(A00 + wd * ld, w.ldw, wd, rslab, A00, w.ldw, split ? nullptr : (LP *)w.Bb,
                                          kMaxV, kMaxV, ss.s)))
                 return rc;
-            if (split && (rc = cvt_cols_split(wd, right, kMaxV, A00 + wd * ld, w.ldw, w.Bb, 3 * kMaxV, kMaxV, 1,
+            if (split && (rc = cvt_cols_split(wd, rslab, kMaxV, A00 + wd * ld, w.ldw, w.Bb, 3 * kMaxV, kMaxV, 1,
                                               ss.s)))
                 return rc;
+            CF_CUDA_TRY(cudaEventRecord(ss.side_done, ss.s));
+            // LU-4 right of the slab (background, after the left-looking
+            // update); those U rows go to the K-major operand of the slab's
+            // deferred update (K rows off .. off + wd, zeros up to the next
+            // multiple of 64).
             if (nout > 0) {
+                CF_CUDA_TRY(cudaStreamWaitEvent(ss.bg, ss.a00_done, 0));
+                if ((rc = launch_ltrsm32<LP>(W + k0 + JE * ld, w.ldw, wd, nout, A00, w.ldw, nullptr, kMaxV, kMaxV,
+                                             ss.bg)))
+                    return rc;
                 const int kp = (off + wd + 63) / 64 * 64 - off;
                 if (!split) {
-                    if ((rc = cvt_cols<LP>(wd, nout, kp, W + k0 + JE * ld, w.ldw, (LP *)w.Ub + off, Vpad, ss.s)))
+                    if ((rc = cvt_cols<LP>(wd, nout, kp, W + k0 + JE * ld, w.ldw, (LP *)w.Ub + off, Vpad, ss.bg)))
                         return rc;
                 } else if ((rc = cvt_cols_split(wd, nout, kp, W + k0 + JE * ld, w.ldw,
-                                                (__nv_bfloat16 *)w.Ub + off, 3 * Vpad, Vpad, 1, ss.s))) {
+                                                (__nv_bfloat16 *)w.Ub + off, 3 * Vpad, Vpad, 1, ss.bg))) {
                     return rc;
                 }
             }
-            CF_CUDA_TRY(cudaEventRecord(ss.side_done, ss.s));
+            CF_CUDA_TRY(cudaEventRecord(ss.bg_done, ss.bg));
             // LU-3 (main)
             if ((rc = launch_rtrsm32<LP>(A00 + wd, w.ldw, below, wd, A00, w.ldw, false,
                                          split ? nullptr : (LP *)w.Ab, kMaxV, kMaxV, nullptr, st)))
@@ -707,6 +732,7 @@ static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t
             CF_CUDA_TRY(cudaStreamWaitEvent(st, la.done, 0));
             la_pending = false;
         }
+        CF_CUDA_TRY(cudaStreamWaitEvent(st, ss.bg_done, 0));    // the slab's pivot rows right of it
         if (JE < n) {
             // deferred update of everything right of and below the slab
             const int Vs = JE - J0, Vp = (Vs + 63) / 64 * 64, mr = n - JE;
