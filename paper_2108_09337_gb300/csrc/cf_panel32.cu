@@ -1,20 +1,22 @@
 // cf_panel32.cu -- FP32 block routines of the mixed-precision path, built for
 // latency (they sit on the chain of dependent work of every step):
 //
-//   k_a00_lu32      LU of A00 without pivoting (S1/S2 of Fig. "prog_rep" on
-//                   the rows TournPivot selected; Sec. 7.2)
+//   k_a00_lu_q32,   LU of A00 without pivoting (S1/S2 of Fig. "prog_rep" on
+//   k_a00_lu32      the rows TournPivot selected; Sec. 7.2)
 //   k_a00_chol32    Cholesky of A00 (Listing "Cholesky Factorization"; CH-1)
 //   k_rtrsm32       LU-3  A10 <- A10 U00^{-1}  /  CH-2  L10 <- A10 L00^{-T}
 //   k_ltrsm32       LU-4  A01 <- L00^{-1} A01
 //
-// Each thread holds one row (or, for LU-4, one column) of its tile in
-// registers, indexed relative to the current block of 8 columns so that all
-// register indices are compile-time constants; the v x v triangle is read
-// from shared memory as float4 rows.  A00 kernels need one barrier per
-// column; the panel solves need none, hold the row as float2 pairs updated
-// with packed FMAs and write their results straight from registers (no
-// staging), so three of their CTAs fit on an SM.  The solve kernels also
-// write the BF16/FP16 K-major copies that the tensor-core update reads.
+// The A00 kernels: one thread per row (four lanes per row for LU blocks of
+// up to 64 rows), the row in registers with compile-time indices, one
+// barrier per column.
+// The panel solves: one thread per row (LU-3, CH-2) or column (LU-4), held
+// as float2 pairs updated with packed FMAs, no barrier, results written
+// straight from registers, three CTAs per SM; they also write the BF16/FP16
+// K-major copies that the tensor-core update reads.  (Four or eight lanes
+// per row, each with a quarter of it, measured slower at N = 32768: the
+// full-size solves are bound by issue, and the quartered form issues about
+// twice the instructions.)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -30,6 +32,84 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 lp_from<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 template <>
 __device__ __forceinline__ __half lp_from<__half>(float x) { return __float2half_rn(x); }
+
+// ---------------------------------------------------------------------------
+// A00 LU of blocks of up to 64 rows, four lanes per row: lane q of row r
+// holds the row's columns 16q .. 16q + 15, one barrier per column.  With one
+// thread per row (below) a 64 x 64 LU issued ~10,000 instructions per warp
+// on two warps (ncu: 24 us per launch, 19% issue active, 1.8 cycles of
+// fixed-latency wait per issue); split four ways over eight warps it takes
+// 18.7 us against 26.2 (measured alone).  For 128 rows the quartered rows
+// (32 columns a lane, the column loop unrolled 32 times) measured slower
+// than one thread per row (83 against 53 us), and so did the same form of
+// the Cholesky (108 against 51 us at 128 rows): those keep the kernels
+// below.
+//
+// LU without pivoting (S1/S2 of Fig. "prog_rep" on the rows TournPivot
+// selected, Sec. 7.2), in place: for every column k, row k (final from
+// column k on) is published in shared memory; every row r > k takes
+// l = a(r, k) / a(k, k) (its lane holding column k divides and hands l to
+// the other three) and does a(r, j) -= l a(k, j) for j > k.  A zero pivot
+// is reported in info and its column is not divided (LAPACK dgetf2); the
+// elimination then goes on with the undivided column.
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(4 * R, 1) k_a00_lu_q32(float *A00, int lda, int w, int kglob, int *info) {
+    constexpr int T = 4, C = R / T;
+    __shared__ __align__(16) float prow[2][R];
+    const int tid = threadIdx.x, r = tid / T, q = tid % T, lane = tid & 31;
+    const int base = lane - q, c0 = q * C;
+    const bool row_live = r < w;
+    float a[C];
+#pragma unroll
+    for (int jl = 0; jl < C; ++jl) a[jl] = (row_live && c0 + jl < w) ? A00[(size_t)r + (size_t)(c0 + jl) * lda] : 0.f;
+    if (r == 0) {
+#pragma unroll
+        for (int g = 0; g < C / 4; ++g)
+            *reinterpret_cast<float4 *>(&prow[0][c0 + 4 * g]) =
+                make_float4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]);
+    }
+    __syncthreads();
+    for (int qo = 0; qo < T; ++qo) {
+        if (qo * C >= w) break;
+#pragma unroll
+        for (int kl = 0; kl < C; ++kl) {
+            const int k = qo * C + kl;
+            if (k >= w) break;
+            const float *u = prow[k & 1];
+            const float piv = u[k];
+            const bool upd = row_live && r > k;
+            float l = 0.f;
+            if (upd && q == qo) l = (piv != 0.f) ? a[kl] / piv : a[kl];
+            l = __shfl_sync(0xffffffffu, l, base + qo);
+            if (upd) {
+                if (q == qo) a[kl] = l;                           // L(r, k)
+                float m[C];
+#pragma unroll
+                for (int g = 0; g < C / 4; ++g) {
+                    const float4 v = *reinterpret_cast<const float4 *>(u + c0 + 4 * g);
+                    m[4 * g] = v.x; m[4 * g + 1] = v.y; m[4 * g + 2] = v.z; m[4 * g + 3] = v.w;
+                }
+#pragma unroll
+                for (int jl = 0; jl < C; ++jl)
+                    if (q > qo || (q == qo && jl > kl)) a[jl] = fmaf(-l, m[jl], a[jl]);
+            }
+            if (r == k + 1 && k + 1 < w) {                         // the next pivot row, final from k + 1 on
+#pragma unroll
+                for (int g = 0; g < C / 4; ++g)
+                    *reinterpret_cast<float4 *>(&prow[(k + 1) & 1][c0 + 4 * g]) =
+                        make_float4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]);
+            }
+            if (tid == 0 && piv == 0.f) atomicCAS(info, 0, kglob + k + 1);
+            __syncthreads();
+        }
+    }
+    if (row_live) {
+#pragma unroll
+        for (int jl = 0; jl < C; ++jl)
+            if (c0 + jl < w) A00[(size_t)r + (size_t)(c0 + jl) * lda] = a[jl];
+    }
+}
 
 // ---------------------------------------------------------------------------
 // A00 = L00 U00, no pivoting, in place (w <= 128).  Thread r owns row r as a
@@ -491,17 +571,20 @@ k_ltrsm32(float *X, int ldx, int w, int cols, const float *__restrict__ L00, int
 }
 
 // ---------------------------------------------------------------------------
-// One thread per row of A00, in whole warps (fewer warps in each barrier for
-// narrow blocks: w = 64 takes two).
+// One CTA: four lanes per row for LU blocks of up to 64 rows (256 threads),
+// else one thread per row in whole warps.
 int launch_a00_lu32(float *A00, int lda, int w, int kglob, int *info, cudaStream_t st) {
     if (w <= 0) return CF_OK;
-    k_a00_lu32<<<1, (w + 31) / 32 * 32, 0, st>>>(A00, lda, w, kglob, info);
+    if (w > kMaxV) return CF_ERR_UNSUPPORTED;
+    if (w <= 64) k_a00_lu_q32<64><<<1, 256, 0, st>>>(A00, lda, w, kglob, info);
+    else k_a00_lu32<<<1, (w + 31) / 32 * 32, 0, st>>>(A00, lda, w, kglob, info);
     CF_LAUNCH_CHECK();
     return CF_OK;
 }
 
 int launch_a00_chol32(float *A00, int lda, int w, int kglob, int *info, cudaStream_t st) {
     if (w <= 0) return CF_OK;
+    if (w > kMaxV) return CF_ERR_UNSUPPORTED;
     k_a00_chol32<<<1, (w + 31) / 32 * 32, 0, st>>>(A00, lda, w, kglob, info);
     CF_LAUNCH_CHECK();
     return CF_OK;
