@@ -143,15 +143,20 @@ struct BlockStep {
         const unsigned wk = lane < NW ? s.wkey[U][lane] : 0u;
         const unsigned M = __reduce_max_sync(0xffffffffu, wk);
         unsigned P;
+        int wb;
         if constexpr (RPT == 1) {
-            P = s.wpos[U][__ffs(__ballot_sync(0xffffffffu, wk == M)) - 1];
+            // the winning warp is the first that holds M: its position, 1 /
+            // pivot and in-block values are loaded together
+            wb = __ffs(__ballot_sync(0xffffffffu, wk == M)) - 1;
+            P = s.wpos[U][wb];
         } else {
             const unsigned cand = (lane < NW && wk == M) ? s.wpos[U][lane] : 0xffffffffu;
             P = __reduce_min_sync(0xffffffffu, cand);
+            wb = (int)(P % NT) >> 5;
         }
-        const int pt = (int)(P % NT), pq = (int)(P / NT);
-        const int wb = pt >> 5;
         const float ri = s.wrinv[U][wb];
+        const float4 u0 = s.slot[U][wb][0], u1 = s.slot[U][wb][1];
+        const int pt = (int)(P % NT), pq = (int)(P / NT);
         if (tid == pt) {
             s.order[j] = (int)P;
 #pragma unroll
@@ -159,7 +164,6 @@ struct BlockStep {
                 if (q == pq) { used[q] = true; pidx[q] = U; }
         }
         if (ri != 0.f) {
-            const float4 u0 = s.slot[U][wb][0], u1 = s.slot[U][wb][1];
 #pragma unroll
             for (int q = 0; q < RPT; ++q) {
                 if (used[q]) continue;
