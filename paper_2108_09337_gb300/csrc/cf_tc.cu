@@ -64,6 +64,10 @@ struct Problem {
     // updating C (k_splitk_reduce then subtracts the partials in order)
     int ksplit, kps, nunits;
     float *P;
+    // MMA width: 64 or 128 when the whole output is that narrow (the B
+    // box, the MMA and the epilogue cover only those columns), else BN
+    int nmma;
+    uint32_t bbytes;       // bytes of one B stage as loaded: nmma x BK x 2
 };
 
 // Tile t -> (bm, bn), M fastest so consecutive CTAs share a B tile in L2.
@@ -74,6 +78,11 @@ __device__ __forceinline__ bool tile_coords(const Problem &p, int t, int &m0, in
     return true;
 }
 
+// NARROW: outputs of at most 128 columns (p.nmma = 64 or 128: the B box, the
+// MMA and the epilogue cover only those); the wide form keeps compile-time
+// 256-column loops (measured 7-20% faster for wide outputs than the same
+// loops with run-time bounds).
+template <bool NARROW>
 __global__ void __launch_bounds__(kThreads, 1)
 k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Problem p,
            uint32_t idesc) {
@@ -125,7 +134,7 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     const int st = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                     if (!wait_bounded(&s.empty[st], ph ^ 1u, abort_flag, &g_tc_status)) { ok = false; break; }
-                    mbar_arrive_expect_tx(&s.full[st], kStageBytes);
+                    mbar_arrive_expect_tx(&s.full[st], NARROW ? kStageA + p.bbytes : kStageBytes);
                     tma_load_2d(stageA + st * kStageA, &tmA, &s.full[st], kb * BK, m0);
                     tma_load_2d(stageB + st * kStageB, &tmB, &s.full[st], kb * BK, n0);
                 }
@@ -194,11 +203,18 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_fence_after();
+            // narrow outputs: the columns of this tile that exist (and, for the
+            // lower form, reach the diagonal of the tile's last row)
+            int cmax = BN;
+            if constexpr (NARROW) {
+                cmax = min(p.nmma, p.n - n0);
+                if (p.lower) cmax = min(cmax, m0 + BM - n0);
+            }
             if (p.P != nullptr) {
-                // split-K partial: the whole 128 x 256 accumulator, column-major
+                // split-K partial: the accumulator's live columns, column-major
                 float *dst = p.P + ((size_t)(u / p.ntiles) * p.ntiles + t) * (BM * BN) + quarter * 32 + lane;
 #pragma unroll 1
-                for (int c0 = 0; c0 < BN; c0 += 32) {
+                for (int c0 = 0; c0 < (NARROW ? cmax : BN); c0 += 32) {
                     uint32_t r[32];
                     const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0);
                     TMEM_LD32(taddr, r);
@@ -216,7 +232,7 @@ k_schur_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             const bool row_ok = row < p.m;
             float *crow = p.C + row;
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            for (int c0 = 0; c0 < (NARROW ? cmax : BN); c0 += 32) {
                 const int colbase = n0 + c0;
                 float cv[32];
 #pragma unroll
@@ -344,10 +360,15 @@ int launch_schur_tc_splitk(int m, int n, int k, const void *A, int lda_k, const 
     if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return CF_ERR_UNSUPPORTED;
     int rc = get_encoder();
     if (rc) return rc;
+    // narrow outputs (a panel's next columns): the MMA, the B box and the
+    // epilogue cover only 64 or 128 columns instead of 256
+    const int nmma = n <= 64 ? 64 : n <= 128 ? 128 : tc::BN;
     CUtensorMap ta, tb;
     if ((rc = make_operand_map(&ta, A, m, k, lda_k, tc::BM))) return rc;
-    if ((rc = make_operand_map(&tb, B, n, k, ldb_k, tc::BN))) return rc;
+    if ((rc = make_operand_map(&tb, B, n, k, ldb_k, nmma))) return rc;
     tc::Problem p;
+    p.nmma = nmma;
+    p.bbytes = (uint32_t)nmma * tc::BK * 2;
     p.m = m; p.n = n; p.k = k; p.C = C; p.ldc = ldc; p.lower = lower ? 1 : 0;
     p.tiles_m = ceil_div(m, tc::BM);
     p.tiles_n = ceil_div(n, tc::BN);
@@ -360,11 +381,16 @@ int launch_schur_tc_splitk(int m, int n, int k, const void *A, int lda_k, const 
     p.nunits = p.ntiles * p.ksplit;
     p.P = p.ksplit > 1 ? P : nullptr;
     const size_t smem = 1024 + tc::STAGES * tc::kStageBytes + sizeof(tc::Smem);
-    CF_CUDA_TRY(cudaFuncSetAttribute(tc::k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int grid = num_sms();
     if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
     if (grid > p.nunits) grid = p.nunits;
-    tc::k_schur_tc<<<grid, tc::kThreads, smem, st>>>(ta, tb, p, tc::make_idesc(bf16, tc::BM, tc::BN));
+    if (nmma < tc::BN) {
+        CF_CUDA_TRY(cudaFuncSetAttribute(tc::k_schur_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tc::k_schur_tc<true><<<grid, tc::kThreads, smem, st>>>(ta, tb, p, tc::make_idesc(bf16, tc::BM, nmma));
+    } else {
+        CF_CUDA_TRY(cudaFuncSetAttribute(tc::k_schur_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tc::k_schur_tc<false><<<grid, tc::kThreads, smem, st>>>(ta, tb, p, tc::make_idesc(bf16, tc::BM, nmma));
+    }
     CF_LAUNCH_CHECK();
     if (p.P != nullptr) {
         tc::k_splitk_reduce<<<dim3(8, p.ntiles), 256, 0, st>>>(p);
