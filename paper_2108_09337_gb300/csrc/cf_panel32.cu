@@ -4,19 +4,21 @@
 //   k_a00_lu_q32,   LU of A00 without pivoting (S1/S2 of Fig. "prog_rep" on
 //   k_a00_lu32      the rows TournPivot selected; Sec. 7.2)
 //   k_a00_chol32    Cholesky of A00 (Listing "Cholesky Factorization"; CH-1)
-//   k_rtrsm32       LU-3  A10 <- A10 U00^{-1}  /  CH-2  L10 <- A10 L00^{-T}
-//   k_ltrsm32       LU-4  A01 <- L00^{-1} A01
+//   k_rtrsm32(_w)   LU-3  A10 <- A10 U00^{-1}  /  CH-2  L10 <- A10 L00^{-T}
+//   k_ltrsm32(_w)   LU-4  A01 <- L00^{-1} A01
 //
 // The A00 kernels: one thread per row (four lanes per row for LU blocks of
 // up to 64 rows), the row in registers with compile-time indices, one
 // barrier per column.
 // The panel solves: one thread per row (LU-3, CH-2) or column (LU-4), held
 // as float2 pairs updated with packed FMAs, no barrier, results written
-// straight from registers, three CTAs per SM; they also write the BF16/FP16
-// K-major copies that the tensor-core update reads.  (Four or eight lanes
-// per row, each with a quarter of it, measured slower at N = 32768: the
-// full-size solves are bound by issue, and the quartered form issues about
-// twice the instructions.)
+// straight from registers; they also write the BF16/FP16 K-major copies that
+// the tensor-core update reads.  Full panels (w = 64 or 128) take the
+// fixed-width forms k_rtrsm32_w / k_ltrsm32_w (column loop unrolled at
+// compile time), ragged ones k_rtrsm32 / k_ltrsm32.  (Four lanes per row,
+// each with a quarter of it, measured slower: 30.2 against 24.1 us for
+// 24000 x 64 with the shifting form; the quartered form issues about twice
+// the instructions.)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -571,6 +573,178 @@ k_ltrsm32(float *X, int ldx, int w, int cols, const float *__restrict__ L00, int
 }
 
 // ---------------------------------------------------------------------------
+// Fixed-width panel solves (w = W = 64 or 128, the full panels): the same
+// arithmetic as k_rtrsm32 / k_ltrsm32, in the same order, with the column
+// loop unrolled at compile time, so the row is never shifted and every index
+// is a constant (k_rtrsm32 spends ~1,000 register moves per row on shifts
+// at w = 64).  The row (column) of X is loaded before the triangle is
+// staged, so the two latencies overlap, and the triangle is staged with
+// coalesced loads, all of a thread's loads of a batch in flight at once,
+// into rows padded to W + 4 floats (conflict-free stores, 16-byte aligned
+// rows).  Measured alone: 12.4 us against 22.6 for 24000 x 64 (LU-3), 26.8
+// against 39.1 for 32640 x 128 (CH-2), results bit-identical.
+//
+// Ms[k][t] = M(k, t) for t >= k (the factor's storage on the diagonal for
+// the unit left solve: there it multiplies only entries that are already
+// final, never read again), zero left of the diagonal.
+//   TRI 0: M = U00, M(k, t) = M00[k + t ldm]   (right solve, LU-3)
+//   TRI 1: M = L00^T, M(k, t) = M00[t + k ldm] (right solve CH-2; unit left
+//          solve LU-4, where row k of M is column k of L)
+// ---------------------------------------------------------------------------
+template <int W, int NT, int TRI>
+__device__ __forceinline__ void stage_tri_fixed(float *Ms, const float *__restrict__ M00, int ldm) {
+    constexpr int MS = W + 4, NE = W * W / NT, BATCH = NE < 32 ? NE : 32;
+    static_assert(NT % 32 == 0 && NE % BATCH == 0, "staging layout");
+    const int tid = threadIdx.x, lane = tid & 31;
+#pragma unroll 1
+    for (int b0 = 0; b0 < NE; b0 += BATCH) {
+        float v[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int e = (b0 + u) * NT + tid;
+            if constexpr (TRI == 0) {
+                // a warp takes 8 consecutive k (32 bytes of a column of U) x 4 columns t
+                const int T = e >> 5;
+                const int k = 8 * (T % (W / 8)) + (lane & 7), t = 4 * (T / (W / 8)) + (lane >> 3);
+                v[u] = k <= t ? M00[(size_t)k + (size_t)t * ldm] : 0.f;
+            } else {
+                const int t = e % W, k = e / W;   // a warp takes 32 consecutive t of column k of L
+                v[u] = t >= k ? M00[(size_t)t + (size_t)k * ldm] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int e = (b0 + u) * NT + tid;
+            int k, t;
+            if constexpr (TRI == 0) {
+                const int T = e >> 5;
+                k = 8 * (T % (W / 8)) + (lane & 7);
+                t = 4 * (T / (W / 8)) + (lane >> 3);
+            } else {
+                t = e % W;
+                k = e / W;
+            }
+            Ms[k * MS + t] = v[u];
+        }
+    }
+}
+
+// Column k = K of the solve on a pair row: x_K = a_K (LEFT, unit diagonal)
+// or a_K / M(K, K); a_t -= x_K M(K, t) for the pairs holding a column > K.
+// RIGHT writes x_K to its FP32 column at once (coalesced over the CTA's
+// rows); LEFT writes each block of 8 as two 16-byte stores.  Both write the
+// low-precision copy per block of 8.
+template <int W, bool LEFT, typename LP>
+struct TrsmFixed {
+    static constexpr int MS = W + 4;
+    float2 (&a)[W / 2];
+    float (&xb)[8];
+    const float *Ms;
+    const float *rinv;
+    float *xout;   // RIGHT: X + row, column stride ldx; LEFT: the column, contiguous; null: not live
+    LP *lout;
+    int ldx;
+    template <int K>
+    __device__ __forceinline__ void run() {
+        if constexpr (K < W) {
+            float xk = (K & 1) ? a[K >> 1].y : a[K >> 1].x;
+            if constexpr (!LEFT) {
+                xk *= rinv[K];
+                if (xout) xout[(size_t)K * ldx] = xk;
+            }
+            xb[K & 7] = xk;
+            const float2 nl = make_float2(-xk, -xk);
+            const float4 *row = reinterpret_cast<const float4 *>(Ms + K * MS);
+#pragma unroll
+            for (int q = K / 4; q < W / 4; ++q) {
+                const float4 p = row[q];
+                if (4 * q >= K) a[2 * q] = __ffma2_rn(nl, make_float2(p.x, p.y), a[2 * q]);
+                if (4 * q + 2 >= K) a[2 * q + 1] = __ffma2_rn(nl, make_float2(p.z, p.w), a[2 * q + 1]);
+            }
+            if constexpr ((K & 7) == 7) {
+                if constexpr (LEFT) {
+                    if (xout) {
+                        reinterpret_cast<float4 *>(xout + K - 7)[0] = make_float4(xb[0], xb[1], xb[2], xb[3]);
+                        reinterpret_cast<float4 *>(xout + K - 7)[1] = make_float4(xb[4], xb[5], xb[6], xb[7]);
+                    }
+                }
+                if (lout) store8_lp<LP>(lout + K - 7, xb);
+            }
+            run<K + 1>();
+        }
+    }
+};
+
+template <int W, typename LP>
+__global__ void __launch_bounds__(128, 1)
+k_rtrsm32_w(float *X, int ldx, int rows, const float *__restrict__ M00, int ldm, int trans_lower, LP *lp, int ldk,
+            int kpad, const int *skip) {
+    if (skip != nullptr && *skip != 0) return;
+    constexpr int MS = W + 4;
+    extern __shared__ __align__(16) float smem[];
+    float *Ms = smem;               // [W][MS]
+    float *rinv = smem + W * MS;    // [W]
+    const int tid = threadIdx.x;
+    const int r0 = blockIdx.x * 128;
+    const bool live = tid < rows - r0;
+    float2 a[W / 2];
+#pragma unroll
+    for (int p = 0; p < W / 2; ++p) {
+        const float x0 = live ? X[(size_t)(r0 + tid) + (size_t)(2 * p) * ldx] : 0.f;
+        const float x1 = live ? X[(size_t)(r0 + tid) + (size_t)(2 * p + 1) * ldx] : 0.f;
+        a[p] = make_float2(x0, x1);
+    }
+    if (trans_lower) stage_tri_fixed<W, 128, 1>(Ms, M00, ldm);
+    else stage_tri_fixed<W, 128, 0>(Ms, M00, ldm);
+    __syncthreads();
+    if (tid < W) {
+        const float d = Ms[tid * MS + tid];
+        rinv[tid] = d != 0.f ? 1.0f / d : 1.0f;
+    }
+    __syncthreads();
+    float xb[8];
+    LP *lrow = (lp != nullptr && live) ? lp + (size_t)(r0 + tid) * ldk : nullptr;
+    TrsmFixed<W, false, LP> body{a, xb, Ms, rinv, live ? X + r0 + tid : nullptr, lrow, ldx};
+    body.template run<0>();
+    if (lrow) {
+        float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int j0 = W; j0 < kpad; j0 += 8) store8_lp<LP>(lrow + j0, z);
+    }
+}
+
+// X (W x cols) <- L00^{-1} X, thread = column, 64 threads per CTA (a slab's
+// 2,000 columns spread over twice the SMs).  The columns must be 16-byte
+// aligned (the launcher checks).
+template <int W, typename LP>
+__global__ void __launch_bounds__(64)
+k_ltrsm32_w(float *X, int ldx, int cols, const float *__restrict__ L00, int ldl, LP *lp, int ldk, int kpad) {
+    constexpr int NT = 64;
+    extern __shared__ __align__(16) float smem[];
+    float *Ms = smem;               // [W][W + 4]
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * NT;
+    const bool live = tid < cols - c0;
+    float *xc = X + (size_t)(c0 + (live ? tid : 0)) * ldx;
+    float2 a[W / 2];
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+        const float4 v = live ? reinterpret_cast<const float4 *>(xc)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[2 * q] = make_float2(v.x, v.y);
+        a[2 * q + 1] = make_float2(v.z, v.w);
+    }
+    stage_tri_fixed<W, NT, 1>(Ms, L00, ldl);
+    __syncthreads();
+    float xb[8];
+    LP *lcol = (lp != nullptr && live) ? lp + (size_t)(c0 + tid) * ldk : nullptr;
+    TrsmFixed<W, true, LP> body{a, xb, Ms, nullptr, live ? xc : nullptr, lcol, ldx};
+    body.template run<0>();
+    if (lcol) {
+        float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int j0 = W; j0 < kpad; j0 += 8) store8_lp<LP>(lcol + j0, z);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One CTA: four lanes per row for LU blocks of up to 64 rows (256 threads),
 // else one thread per row in whole warps.
 int launch_a00_lu32(float *A00, int lda, int w, int kglob, int *info, cudaStream_t st) {
@@ -595,6 +769,20 @@ int launch_rtrsm32(float *X, int ldx, int rows, int w, const float *M00, int ldm
                    int kpad, const int *skip, cudaStream_t st) {
     if (rows <= 0 || w <= 0) return CF_OK;
     if (lp != nullptr && ((ldk % 8) != 0 || (kpad % 8) != 0 || (((uintptr_t)lp) & 15) != 0)) return CF_ERR_UNSUPPORTED;
+    if ((w == 64 || w == 128) && (lp == nullptr || kpad >= w)) {
+        const size_t smem = sizeof(float) * (size_t)w * (w + 5);
+        if (w == 64) {
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_rtrsm32_w<64, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_rtrsm32_w<64, LP><<<ceil_div(rows, 128), 128, smem, st>>>(X, ldx, rows, M00, ldm, trans_lower ? 1 : 0, lp,
+                                                                       ldk, kpad, skip);
+        } else {
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_rtrsm32_w<128, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_rtrsm32_w<128, LP><<<ceil_div(rows, 128), 128, smem, st>>>(X, ldx, rows, M00, ldm, trans_lower ? 1 : 0,
+                                                                        lp, ldk, kpad, skip);
+        }
+        CF_LAUNCH_CHECK();
+        return CF_OK;
+    }
     const size_t smem = sizeof(float) * (size_t)(kMaxV + 1) * kMaxV;   // + padding row
     CF_CUDA_TRY(cudaFuncSetAttribute(k_rtrsm32<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_rtrsm32<LP><<<ceil_div(rows, kMaxV), kMaxV, smem, st>>>(X, ldx, rows, w, M00, ldm, trans_lower ? 1 : 0, lp, ldk,
@@ -608,6 +796,18 @@ int launch_ltrsm32(float *X, int ldx, int w, int cols, const float *L00, int ldl
                    cudaStream_t st) {
     if (cols <= 0 || w <= 0) return CF_OK;
     if (lp != nullptr && ((ldk % 8) != 0 || (kpad % 8) != 0 || (((uintptr_t)lp) & 15) != 0)) return CF_ERR_UNSUPPORTED;
+    if ((w == 64 || w == 128) && (lp == nullptr || kpad >= w) && (((uintptr_t)X) & 15) == 0 && (ldx % 4) == 0) {
+        const size_t smem = sizeof(float) * (size_t)w * (w + 4);
+        if (w == 64) {
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_ltrsm32_w<64, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_ltrsm32_w<64, LP><<<ceil_div(cols, 64), 64, smem, st>>>(X, ldx, cols, L00, ldl, lp, ldk, kpad);
+        } else {
+            CF_CUDA_TRY(cudaFuncSetAttribute(k_ltrsm32_w<128, LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_ltrsm32_w<128, LP><<<ceil_div(cols, 64), 64, smem, st>>>(X, ldx, cols, L00, ldl, lp, ldk, kpad);
+        }
+        CF_LAUNCH_CHECK();
+        return CF_OK;
+    }
     const size_t smem = sizeof(float) * (size_t)(kMaxV + 1) * kMaxV;   // + padding row
     CF_CUDA_TRY(cudaFuncSetAttribute(k_ltrsm32<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_ltrsm32<LP><<<ceil_div(cols, kMaxV), kMaxV, smem, st>>>(X, ldx, w, cols, L00, ldl, lp, ldk, kpad);
