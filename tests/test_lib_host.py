@@ -55,6 +55,23 @@ def test_workspace_sizes_are_host_only(lib):
     assert L.cf_getrf_workspace_size(100, ctypes.byref(bad)) == 0
 
 
+def test_noalloc_scratch_limit(lib):
+    """cf_getrf_noalloc keeps the tournament scratch in a fixed 2 MiB array:
+    the sizes include/cf.h promises fit (n up to 393216 with leaf_h = 128 and
+    arity 8, 196608 with leaf_h = 64; 131072 and 65536 with arity 2), the
+    scratch grows with n, and a far larger request does not fit (the entry
+    point refuses it with CF_ERR_WORKSPACE)."""
+    from paper_2108_09337_gb300 import cf
+    L = cf.lib()
+    L.cf_getrf_workspace_size.restype = ctypes.c_size_t
+    limit = 2 << 20
+    for leaf_h, arity, n_max in ((128, 8, 393216), (64, 8, 196608), (128, 2, 131072), (64, 2, 65536)):
+        o = cf.options(leaf_h=leaf_h, arity=arity)
+        sizes = [L.cf_getrf_workspace_size(n, ctypes.byref(o)) for n in (1024, n_max // 4, n_max)]
+        assert 0 < sizes[0] <= sizes[1] <= sizes[2] <= limit, (leaf_h, arity, sizes)
+        assert L.cf_getrf_workspace_size(4 * n_max, ctypes.byref(o)) > limit
+
+
 def test_argument_validation_returns_before_any_cuda_call(lib):
     from paper_2108_09337_gb300 import cf
     L = cf.lib()

@@ -4,8 +4,9 @@ framework that owns all device memory).  It keeps its tournament scratch in
 a fixed array inside the library, so these tests check, through the C ABI,
 that it returns what cf_getrf returns with a caller-provided work buffer, on
 two calls in a row (the second call reuses the array the first one left
-behind), that both agree with the CPU oracle's LU, and that a request too
-large for the array is refused.
+behind), that both agree with the CPU oracle's LU, that a call captured
+into a CUDA graph and replayed gives the same factors and pivots, and that
+a request too large for the array is refused.
 
 Tolerance: the same as the other LU parity tests (pivots identical to the
 oracle's except after a step where the oracle logged an argmax gap below
@@ -65,6 +66,36 @@ def test_noalloc_matches_getrf_two_calls(cf, call):
         assert oracle.lu_residual(A, LU, ip) <= 20.0
         results.append(n)
     assert results == [700, 1029]
+
+
+def test_noalloc_captured_in_cuda_graph(cf):
+    """The case the entry point exists for: one warm-up call, then the call
+    captured into a CUDA graph (stream capture refuses device allocations)
+    and replayed twice on fresh copies of A; each replay's pivots, info and
+    factors equal cf_getrf's with a work buffer."""
+    n = 700
+    A = inputs.uniform_pm1(n, seed=21)
+    dA_ref = _dev(A)
+    ipiv_ref, info_ref = cf.getrf(dA_ref)
+    A0 = _dev(A)
+    dA = _dev(A)
+    ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cf.getrf_noalloc(dA, ipiv=ipiv, info=info)           # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        cf.getrf_noalloc(dA, ipiv=ipiv, info=info)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        dA.copy_(A0)
+        ipiv.fill_(-1)
+        info.fill_(-1)                                   # the call itself resets info to 0
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ipiv.cpu().numpy(), ipiv_ref.cpu().numpy())
+        assert int(info.item()) == int(info_ref.item()) == 0
+        np.testing.assert_array_equal(dA.cpu().numpy(), dA_ref.cpu().numpy())
 
 
 def test_noalloc_rejects_oversized_request(cf):
