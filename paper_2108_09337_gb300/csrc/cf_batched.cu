@@ -343,10 +343,11 @@ __device__ int cta_potrf(BSmem<T> &s, T *A, int n, int lda, int *info, int vb) {
     return 0;
 }
 
-// Per-CTA scratch of the mixed solve: the n x n factors (FP64 room), r, d
-// and the pivots, rounded to 1 KiB.
+// Per-CTA scratch of the mixed solve: the n x n factors (FP64 room), r and
+// the pivots, rounded to 1 KiB (the corrections' right-hand side lives in
+// shared memory).
 __host__ __device__ constexpr size_t batched_scratch_bytes_per_cta() {
-    return ((sizeof(double) * ((size_t)kBMaxN * kBMaxN + 2 * kBMaxN) + sizeof(int) * kBMaxN) + 1023) / 1024 * 1024;
+    return ((sizeof(double) * ((size_t)kBMaxN * kBMaxN + kBMaxN) + sizeof(int) * kBMaxN) + 1023) / 1024 * 1024;
 }
 
 struct BatchArgs {
@@ -442,43 +443,83 @@ __device__ double cta_residual_eta(int n, const double *A, int lda, const double
 }
 
 // x += (P^T L U)^{-1} r (kind 0) or (L L^T)^{-1} r (kind 1), the solve in the
-// factor precision T on r scaled by 1/||r||_inf; serial substitution with the
-// inner updates spread over the CTA.
+// factor precision T on r scaled by 1/||r||_inf.  The right-hand side d lives
+// in shared memory (sd; spiv holds the pivots for the interchanges) and the
+// substitutions go by blocks of 32 rows: one warp solves the block's
+// triangle with the row in a register, each column's value handed to the
+// other lanes by a shuffle (no CTA barrier), then the CTA applies the
+// block's columns to the rows not yet solved: two barriers per block of 32
+// rows instead of two per row, and no round trip through global memory per
+// row.  Every row receives the same fused multiply-adds, with the same
+// operands, in the same order as in a row-by-row substitution (columns in
+// increasing order for L, decreasing for U / L^T), so the result is the
+// same to the bit.
 template <typename T>
-__device__ void cta_correct(int kind, int n, const T *W, const int *piv, const double *r, T *d, double *x,
-                            double *s_red) {
-    const int tid = threadIdx.x;
+__device__ void cta_correct(int kind, int n, const T *W, const int *piv, const double *r, T *sd, int *spiv,
+                            double *x, double *s_red) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double rn = 0.0;
     for (int row = tid; row < n; row += kBT) rn = fmax(rn, fabs(r[row]));
     rn = cta_max(rn, s_red);
     const double sc = rn > 0.0 ? rn : 1.0;
-    for (int row = tid; row < n; row += kBT) d[row] = (T)(r[row] / sc);
+    for (int row = tid; row < n; row += kBT) sd[row] = (T)(r[row] / sc);
+    if (kind == 0)
+        for (int j = tid; j < n; j += kBT) spiv[j] = piv[j];
     __syncthreads();
     if (kind == 0 && tid == 0) {
         for (int j = 0; j < n; ++j) {                // row interchanges, in order
-            const int p = piv[j] - 1;
-            if (p != j) { const T t = d[j]; d[j] = d[p]; d[p] = t; }
+            const int p = spiv[j] - 1;
+            if (p != j) { const T t = sd[j]; sd[j] = sd[p]; sd[p] = t; }
         }
     }
     __syncthreads();
-    for (int k = 0; k < n; ++k) {                    // L y = d (unit diagonal for LU)
-        if (kind == 1 && tid == 0) d[k] = d[k] / W[k + (size_t)k * n];
+    // L y = d (unit diagonal for LU), blocks from the top
+    for (int b0 = 0; b0 < n; b0 += 32) {
+        const int bw = min(32, n - b0);
+        if (warp == 0) {
+            T v = lane < bw ? sd[b0 + lane] : T(0);
+            for (int k = 0; k < bw; ++k) {
+                if (kind == 1 && lane == k) v = v / W[(size_t)(b0 + k) * n + b0 + k];
+                const T dk = __shfl_sync(0xffffffffu, v, k);
+                if (lane > k && lane < bw) v = fma(-W[(size_t)(b0 + k) * n + b0 + lane], dk, v);
+            }
+            if (lane < bw) sd[b0 + lane] = v;
+        }
         __syncthreads();
-        const T dk = d[k];
-        for (int row = k + 1 + tid; row < n; row += kBT) d[row] = fma(-W[row + (size_t)k * n], dk, d[row]);
-        __syncthreads();
-    }
-    for (int k = n - 1; k >= 0; --k) {               // U z = y (LU) or L^T z = y (Cholesky)
-        if (tid == 0) d[k] = d[k] / W[k + (size_t)k * n];
-        __syncthreads();
-        const T dk = d[k];
-        for (int row = tid; row < k; row += kBT) {
-            const T u = (kind == 0) ? W[row + (size_t)k * n] : W[k + (size_t)row * n];
-            d[row] = fma(-u, dk, d[row]);
+        for (int row = b0 + bw + tid; row < n; row += kBT) {
+            T acc = sd[row];
+            for (int k = 0; k < bw; ++k) acc = fma(-W[(size_t)(b0 + k) * n + row], sd[b0 + k], acc);
+            sd[row] = acc;
         }
         __syncthreads();
     }
-    for (int row = tid; row < n; row += kBT) x[row] += sc * (double)d[row];
+    // U z = y (LU) or L^T z = y (Cholesky), blocks from the bottom
+    for (int be = n; be > 0; be -= 32) {
+        const int b0 = be > 32 ? be - 32 : 0, bw = be - b0;
+        if (warp == 0) {
+            T v = lane < bw ? sd[b0 + lane] : T(0);
+            for (int k = bw - 1; k >= 0; --k) {
+                if (lane == k) v = v / W[(size_t)(b0 + k) * n + b0 + k];
+                const T dk = __shfl_sync(0xffffffffu, v, k);
+                if (lane < k) {
+                    const T u = (kind == 0) ? W[(size_t)(b0 + k) * n + b0 + lane] : W[(size_t)(b0 + lane) * n + b0 + k];
+                    v = fma(-u, dk, v);
+                }
+            }
+            if (lane < bw) sd[b0 + lane] = v;
+        }
+        __syncthreads();
+        for (int row = tid; row < b0; row += kBT) {
+            T acc = sd[row];
+            for (int k = bw - 1; k >= 0; --k) {
+                const T u = (kind == 0) ? W[(size_t)(b0 + k) * n + row] : W[(size_t)row * n + b0 + k];
+                acc = fma(-u, sd[b0 + k], acc);
+            }
+            sd[row] = acc;
+        }
+        __syncthreads();
+    }
+    for (int row = tid; row < n; row += kBT) x[row] += sc * (double)sd[row];
     __syncthreads();
 }
 
@@ -504,14 +545,14 @@ __device__ int cta_factor_copy(unsigned char *smem_raw, int kind, int n, const d
 // residual of x on entry and on exit.
 template <typename T>
 __device__ int cta_refine(int kind, int n, const double *A, int lda, const double *b, double *x, const T *W,
-                          const int *piv, double *r, T *d, double an, double bn, double tol, int &it, int it_end,
-                          double &eta, double *s_red) {
+                          const int *piv, double *r, T *sd, int *spiv, double an, double bn, double tol, int &it,
+                          int it_end, double &eta, double *s_red) {
     double prev = -1.0;
     while (true) {
         if (eta <= tol) return 0;
         if (it >= it_end) return 1;
         if (prev >= 0.0 && !(eta <= 0.5 * prev)) return 1;      // stalled (or NaN)
-        cta_correct<T>(kind, n, W, piv, r, d, x, s_red);
+        cta_correct<T>(kind, n, W, piv, r, sd, spiv, x, s_red);
         ++it;
         prev = eta;
         eta = cta_residual_eta(n, A, lda, b, x, r, an, bn, s_red);
@@ -527,8 +568,7 @@ __global__ void __launch_bounds__(kBT, MINB) k_solve_batched_mixed(BatchArgs a) 
     unsigned char *base = reinterpret_cast<unsigned char *>(a.scratch) + batched_scratch_bytes_per_cta() * blockIdx.x;
     void *W = base;                                                          // n x n, FP32 or FP64
     double *r = reinterpret_cast<double *>(base + sizeof(double) * kBMaxN * kBMaxN);
-    void *d = r + kBMaxN;                                                    // kBMaxN of FP32 or FP64
-    int *piv = reinterpret_cast<int *>(r + 2 * kBMaxN);
+    int *piv = reinterpret_cast<int *>(r + kBMaxN);
     const int tid = threadIdx.x;
     while (true) {
         if (tid == 0) s_idx = atomicAdd(a.queue, 1);
@@ -566,9 +606,13 @@ __global__ void __launch_bounds__(kBT, MINB) k_solve_batched_mixed(BatchArgs a) 
         double eta = cta_residual_eta(n, A, lda, b, x, r, an, bn, s_red);
         int it = 0;
         int bad = cta_factor_copy<float>(smem_raw, kind, n, A, lda, static_cast<float *>(W), piv, &s_info, a.vb);
+        // the right-hand side of the corrections and the pivots in shared
+        // memory: the panel copy and the label array of the factorization,
+        // free until the next matrix
+        BSmem<float> &sf = *reinterpret_cast<BSmem<float> *>(smem_raw);
         if (!bad)
-            bad = cta_refine<float>(kind, n, A, lda, b, x, static_cast<const float *>(W), piv, r,
-                                    static_cast<float *>(d), an, bn, a.tol, it, a.max_iter, eta, s_red);
+            bad = cta_refine<float>(kind, n, A, lda, b, x, static_cast<const float *>(W), piv, r, bsmem_panel(sf),
+                                    sf.lab, an, bn, a.tol, it, a.max_iter, eta, s_red);
         if (bad) {
             // FP64 factors; refinement resumes from the current iterate unless
             // it is not finite
@@ -581,8 +625,9 @@ __global__ void __launch_bounds__(kBT, MINB) k_solve_batched_mixed(BatchArgs a) 
             if (cta_factor_copy<double>(smem_raw, kind, n, A, lda, static_cast<double *>(W), piv, &s_info, a.vb)) {
                 if (tid == 0) a.info[i] = s_info;
             } else {
-                cta_refine<double>(kind, n, A, lda, b, x, static_cast<const double *>(W), piv, r,
-                                   static_cast<double *>(d), an, bn, a.tol, it, it + a.max_iter, eta, s_red);
+                BSmem<double> &sdb = *reinterpret_cast<BSmem<double> *>(smem_raw);
+                cta_refine<double>(kind, n, A, lda, b, x, static_cast<const double *>(W), piv, r, bsmem_panel(sdb),
+                                   sdb.lab, an, bn, a.tol, it, it + a.max_iter, eta, s_red);
             }
         }
         if (tid == 0) { a.iters[i] = it; a.eta[i] = eta; }
