@@ -36,8 +36,8 @@ constexpr int kBMaxV = 32;              // largest block size
 template <typename T>
 struct BSmem {
     T D[kBMaxV * (kBMaxV + 1)];         // diagonal block
-    T redv[kBT / 32];
-    int redi[kBT / 32];
+    T redv2[2][kBT / 32];               // the pivot search's warp maxima, alternating by column
+    int redi2[2][kBT / 32];
     int used[kBMaxN];
     int order[kBMaxV];
     int lab[kBMaxN];
@@ -69,9 +69,12 @@ __device__ __forceinline__ void bbetter(T &bv, int &bi, T ov, int oi) {
     if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
 }
 
-// CTA-wide argmax (value, index) with the tie rule of the tournament.
+// CTA-wide argmax (value, index) with the tie rule of the tournament, one
+// barrier: the warp maxima go to buffer buf (alternating from one call to
+// the next, so the next call's writes never meet this call's reads) and
+// every thread reduces the eight itself.
 template <typename T>
-__device__ void cta_argmax(BSmem<T> &s, T &bv, int &bi) {
+__device__ __forceinline__ void cta_argmax_1bar(BSmem<T> &s, T &bv, int &bi, int buf) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -79,13 +82,12 @@ __device__ void cta_argmax(BSmem<T> &s, T &bv, int &bi) {
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         bbetter(bv, bi, ov, oi);
     }
-    if (lane == 0) { s.redv[warp] = bv; s.redi[warp] = bi; }
+    if (lane == 0) { s.redv2[buf][warp] = bv; s.redi2[buf][warp] = bi; }
     __syncthreads();
-    bv = s.redv[0];
-    bi = s.redi[0];
+    bv = s.redv2[buf][0];
+    bi = s.redi2[buf][0];
 #pragma unroll
-    for (int q = 1; q < kBT / 32; ++q) bbetter(bv, bi, s.redv[q], s.redi[q]);
-    __syncthreads();
+    for (int q = 1; q < kBT / 32; ++q) bbetter(bv, bi, s.redv2[buf][q], s.redi2[buf][q]);
 }
 
 // C (mm x nn, ldc) -= A (mm x kk, lda) * B (kk x nn, ldb), kk <= kBMaxV; if
@@ -154,14 +156,18 @@ __device__ void cta_getrf(BSmem<T> &s, T *A, int n, int lda, int *ipiv, int *inf
         }
         for (int r = tid; r < m; r += kBT) s.used[r] = 0;
         __syncthreads();
+        // One barrier per column: a thread reads and writes only its own
+        // rows (r = tid mod kBT) and marks its own row when it wins; the
+        // pivot row, final since its owner's update of the previous column,
+        // is read by all after the column's barrier and written by no one.
         for (int j = 0; j < w; ++j) {
             T bv = T(-1);
             int bi = INT_MAX;
             for (int r = tid; r < m; r += kBT)
                 if (!s.used[r]) bbetter(bv, bi, bkey(P[j * m + r]), r);
-            cta_argmax(s, bv, bi);
-            if (tid == 0) { s.order[j] = bi; s.used[bi] = 1; }
-            __syncthreads();
+            cta_argmax_1bar(s, bv, bi, j & 1);
+            if (tid == 0) s.order[j] = bi;
+            if (bi % kBT == tid) s.used[bi] = 1;
             const T piv = P[j * m + bi];
             if (piv != T(0)) {
                 for (int r = tid; r < m; r += kBT) {
@@ -170,11 +176,12 @@ __device__ void cta_getrf(BSmem<T> &s, T *A, int n, int lda, int *ipiv, int *inf
                     for (int c = j + 1; c < w; ++c) P[c * m + r] = P[c * m + r] - l * P[c * m + bi];
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
         // ---- LU-2: interchanges (positions of the winners, as cf_getrf)
+        for (int r = tid; r < m; r += kBT) { s.lab[r] = r; s.where_[r] = r; }
+        __syncthreads();
         if (tid == 0) {
-            for (int r = 0; r < m; ++r) { s.lab[r] = r; s.where_[r] = r; }
             for (int j = 0; j < w; ++j) {
                 const int lab = s.order[j], p = s.where_[lab];
                 ipiv[k0 + j] = k0 + p + 1;
