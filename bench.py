@@ -426,7 +426,7 @@ def _run_fp64_config2(dev, sizes):
     side (seed 2).  Each factorization is timed alone with CUDA events, then
     solved (cf_getrs / cf_potrs, untimed) and checked in torch FP64: eta of
     the solution and the probabilistic factorization residual over 4 random
-    z, each also divided by n u (the benchmark spec's bound is 20 n u)."""
+    z, each also divided by n u (the bound the FP64 path is held to is 20 n u)."""
     import torch
     from paper_2108_09337_gb300 import cf, inputs
     u = 2.0 ** -53

@@ -168,7 +168,7 @@ int cf_last_cuda_error(void);   /* last cudaError_t seen by the library */
 long long cf_kernel_launches(void);
 
 /* ------------------------------------------------------------------------
- * LU-1  TournPivot on one panel (Alg. 1 step 2; Sec. 7.3, "Tournament
+ * LU-1  TournPivot on one panel (Alg. 1; Sec. 7.3, "Tournament
  * Pivoting" / "Pivoting in COnfLUX").  Exposed for testing the selection
  * rule alone.
  *   panel   m x w FP64, ld ldp (read only)

@@ -9,10 +9,10 @@ out the plain definitions of the error measures.
 
 Functions and the passages they follow:
 
-* :func:`tourn_select` -- TournPivot (Alg. 1 step 2; Sec. 7.3 "Tournament
-  Pivoting" and "Pivoting in COnfLUX"; step 2 of the I/O-cost proof).
-* :func:`getrf` -- COnfLUX LU (Alg. 1, Sec. 7.2 routines, Table 2; statements
-  S1/S2 of Fig. "prog_rep").
+* :func:`tourn_select` -- TournPivot (Alg. 1; Sec. 7.3 "Tournament
+  Pivoting" and "Pivoting in COnfLUX"; the pivot selection in the I/O-cost proof).
+* :func:`getrf` -- COnfLUX LU (Alg. 1, Sec. 7.2 routines, Table 2; the
+  in-place LU of Fig. "prog_rep").
 * :func:`potrf` -- COnfCHOX's factorization, Listing "Cholesky Factorization"
   (Sec. 6.2), lower triangle.
 * :func:`getrs`, :func:`potrs` -- substitution with the factors (paper
@@ -101,8 +101,9 @@ def tourn_select(panel: np.ndarray, h: int = 128, arity: int = 2):
 
 def getrf(A: np.ndarray, v: int = 128, h: int = 128, arity: int = 2):
     """COnfLUX LU with tournament pivoting.  Returns (LU, ipiv, info, gaps,
-    n_s2): the in-place factors, 1-based LAPACK ipiv, info, the smallest
-    tournament gap of each step and the number of S2 statements executed.
+    n_upd): the in-place factors, 1-based LAPACK ipiv, info, the smallest
+    tournament gap of each step and the number of updates
+    A[i,j] -= A[i,k] A[k,j] executed.
     h >= n gives Gaussian elimination with partial pivoting."""
     LU = _fortran(A).copy(order="F")
     n = LU.shape[0]
@@ -111,28 +112,28 @@ def getrf(A: np.ndarray, v: int = 128, h: int = 128, arity: int = 2):
     info = ctypes.c_int(0)
     nsteps = max((n + v - 1) // v, 1)
     gaps = np.ones(nsteps, dtype=np.float64)
-    ns2 = ctypes.c_longlong(0)
+    nupd = ctypes.c_longlong(0)
     rc = _load().or_getrf(n, _ptr(LU), max(n, 1), int(v), int(h), int(arity),
                           _ptr(ipiv), ctypes.byref(info), _ptr(gaps),
-                          ctypes.byref(ns2))
+                          ctypes.byref(nupd))
     if rc != 0:
         raise ValueError("or_getrf: bad argument")
-    return LU, ipiv[:n].copy(), info.value, gaps[:(n + v - 1) // v], ns2.value
+    return LU, ipiv[:n].copy(), info.value, gaps[:(n + v - 1) // v], nupd.value
 
 
 def potrf(A: np.ndarray):
-    """Cholesky (lower).  Returns (L, info, n_s3); the strict upper triangle
+    """Cholesky (lower).  Returns (L, info, n_upd); the strict upper triangle
     of L is zeroed."""
     L = _fortran(A).copy(order="F")
     n = L.shape[0]
     info = ctypes.c_int(0)
-    ns3 = ctypes.c_longlong(0)
+    nupd = ctypes.c_longlong(0)
     rc = _load().or_potrf(n, _ptr(L), max(n, 1), ctypes.byref(info),
-                          ctypes.byref(ns3))
+                          ctypes.byref(nupd))
     if rc != 0:
         raise ValueError("or_potrf: bad argument")
     L = np.tril(L)
-    return np.asfortranarray(L), info.value, ns3.value
+    return np.asfortranarray(L), info.value, nupd.value
 
 
 def getrs(LU: np.ndarray, ipiv: np.ndarray, B: np.ndarray) -> np.ndarray:
@@ -236,24 +237,26 @@ def lu_random_projection_error(apply_pa, apply_l, apply_u, n, norm_a,
 # --------------------------------------------------------------------------
 # Closed forms.
 # --------------------------------------------------------------------------
-def lu_s2_count(n: int) -> int:
-    """Executions of S2 in the in-place LU of Fig. "prog_rep":
+def lu_update_count(n: int) -> int:
+    """Executions of the update A[i,j] -= A[i,k] A[k,j] in the in-place LU of
+    Fig. "prog_rep":
     sum_k (n-k-1)^2 = (n-1) n (2n-1) / 6."""
     return (n - 1) * n * (2 * n - 1) // 6
 
 
-def chol_s3_count(n: int) -> int:
-    """Executions of S3 in the Cholesky listing: sum_k (n-k-1)(n-k)/2."""
+def chol_update_count(n: int) -> int:
+    """Executions of the trailing update A[i,j] -= A[i,k] A[j,k] (j <= i) in
+    the Cholesky listing: sum_k (n-k-1)(n-k)/2."""
     return (n - 1) * n * (n + 1) // 6
 
 
 def lu_flops(n: int) -> float:
-    """Flop convention of the metric: 2 n^3 / 3 (leading term of 2 * S2)."""
+    """Flop convention of the metric: 2 n^3 / 3 (leading term of twice the update count)."""
     return 2.0 * n ** 3 / 3.0
 
 
 def chol_flops(n: int) -> float:
-    """n^3 / 3 (leading term of 2 * S3)."""
+    """n^3 / 3 (leading term of twice the update count)."""
     return n ** 3 / 3.0
 
 

@@ -17,20 +17,21 @@
  *   gepp_select        -- the local candidate choice of a tournament block:
  *                         each block runs a pivoted LU on its own rows and
  *                         keeps the rows it pivots on (Sec. 7.3, TournPivot,
- *                         and step 2 of the I/O-cost proof), realised as
+ *                         and the pivot selection in the I/O-cost proof), realised as
  *                         unblocked Gaussian elimination with partial
  *                         pivoting.
- *   or_tourn_select    -- TournPivot (Alg. 1 step 2, Sec. 7.3): local
+ *   or_tourn_select    -- TournPivot (Alg. 1, Sec. 7.3): local
  *                         candidates on every leaf, then playoff rounds on
  *                         stacked candidate blocks until v winners remain.
  *   or_getrf           -- COnfLUX (Alg. 1): per step, TournPivot, then
  *                         Factorize A00 / A10 / A01 / A11 (Sec. 7.2, Table 2),
- *                         i.e. the statements S1 (A[i,k] /= A[k,k]) and S2
- *                         (A[i,j] -= A[i,k]*A[k,j]) of the in-place LU
+ *                         i.e. the column scaling A[i,k] /= A[k,k] and the
+ *                         update A[i,j] -= A[i,k]*A[k,j] of the in-place LU
  *                         (Fig. "prog_rep", Sec. 6.1) applied to the
  *                         row-permuted matrix.
- *   or_potrf           -- Listing "Cholesky Factorization" (Sec. 6.2): S1
- *                         sqrt, S2 scale, S3 update on the lower triangle.
+ *   or_potrf           -- Listing "Cholesky Factorization" (Sec. 6.2): the
+ *                         pivot's square root, the column scaling and the
+ *                         trailing update, on the lower triangle.
  *   or_getrs/or_potrs  -- forward and back substitution with the factors
  *                         (the paper is silent; plain textbook definition).
  *   or_residual        -- R = B - A*X with the compensated dot product Dot2 of
@@ -217,15 +218,15 @@ static void swap_rows(int n, double *A, int lda, int r1, int r2)
 /*   ipiv[0..n-1]: row i was interchanged with row ipiv[i]-1, i = 0..n-1.    */
 /*   *info: 0, or the 1-based column of the first exactly-zero pivot.        */
 /*   step_gap[t] (optional, ceil(n/v) entries): smallest tournament gap of   */
-/*   step t.  *n_s2 (optional): number of executed S2 statements.            */
+/*   step t.  *n_upd (optional): number of updates A[i,j] -= A[i,k]A[k,j]. */
 /* Returns 0, or -1 on a bad argument.                                       */
 /* ------------------------------------------------------------------------ */
 int or_getrf(int n, double *A, int lda, int v, int h, int arity, int *ipiv,
-             int *info, double *step_gap, long long *n_s2)
+             int *info, double *step_gap, long long *n_upd)
 {
     if (n < 0 || lda < (n > 1 ? n : 1) || v < 1) return -1;
     *info = 0;
-    long long s2 = 0;
+    long long nupd = 0;
     int *win = (int *)malloc(sizeof(int) * (size_t)(v + 1));
     int *rowat = (int *)malloc(sizeof(int) * (size_t)(n + 1));
     int *where = (int *)malloc(sizeof(int) * (size_t)(n + 1));
@@ -255,7 +256,7 @@ int or_getrf(int n, double *A, int lda, int v, int h, int arity, int *ipiv,
         }
 
         int ke = k0 + w;
-        /* Factorize A00: S1/S2 inside the w x w diagonal block. */
+        /* Factorize A00: scaling and update inside the w x w diagonal block. */
         for (int k = k0; k < ke; ++k) {
             double piv = A[IX(k, k, lda)];
             if (piv == 0.0) {
@@ -269,9 +270,9 @@ int or_getrf(int n, double *A, int lda, int v, int h, int arity, int *ipiv,
                 for (int i = k + 1; i < ke; ++i)
                     A[IX(i, j, lda)] = A[IX(i, j, lda)] - A[IX(i, k, lda)] * akj;
             }
-            s2 += (long long)(ke - k - 1) * (ke - k - 1);
+            nupd += (long long)(ke - k - 1) * (ke - k - 1);
         }
-        /* Factorize A10: A10 <- A10 * U00^{-1} (S1 and S2 on rows below). */
+        /* Factorize A10: A10 <- A10 * U00^{-1} (scaling and update, rows below). */
         #pragma omp parallel for schedule(static)
         for (int i = ke; i < n; ++i) {
             for (int k = k0; k < ke; ++k) {
@@ -282,7 +283,7 @@ int or_getrf(int n, double *A, int lda, int v, int h, int arity, int *ipiv,
                     A[IX(i, j, lda)] = A[IX(i, j, lda)] - lik * A[IX(k, j, lda)];
             }
         }
-        /* Factorize A01: A01 <- L00^{-1} * A01 (S2 on the pivot rows). */
+        /* Factorize A01: A01 <- L00^{-1} * A01 (update on the pivot rows). */
         #pragma omp parallel for schedule(static)
         for (int j = ke; j < n; ++j) {
             for (int k = k0; k < ke; ++k) {
@@ -291,7 +292,7 @@ int or_getrf(int n, double *A, int lda, int v, int h, int arity, int *ipiv,
                     A[IX(i, j, lda)] = A[IX(i, j, lda)] - A[IX(i, k, lda)] * akj;
             }
         }
-        /* Factorize A11: A11 <- A11 - A10 * A01 (S2 on the trailing block,
+        /* Factorize A11: A11 <- A11 - A10 * A01 (update on the trailing block,
            one k at a time in increasing order, as in the unblocked loop). */
         #pragma omp parallel for schedule(static)
         for (int j = ke; j < n; ++j) {
@@ -302,13 +303,13 @@ int or_getrf(int n, double *A, int lda, int v, int h, int arity, int *ipiv,
             }
         }
         for (int k = k0; k < ke; ++k)
-            s2 += (long long)(n - ke) * (ke - k - 1) * 2   /* A10 and A01 */
-                + (long long)(n - ke) * (n - ke);          /* A11 */
+            nupd += (long long)(n - ke) * (ke - k - 1) * 2   /* A10 and A01 */
+                  + (long long)(n - ke) * (n - ke);          /* A11 */
     }
     free(where);
     free(rowat);
     free(win);
-    if (n_s2) *n_s2 = s2;
+    if (n_upd) *n_upd = nupd;
     return 0;
 }
 
@@ -317,24 +318,24 @@ int or_getrf(int n, double *A, int lda, int v, int h, int arity, int *ipiv,
 /* Only the lower triangle (i >= j) is read and written.                     */
 /* *info: 0, or k+1 for the first k whose pivot is <= 0 or NaN (the         */
 /* factorization stops there, as LAPACK dpotrf does).                        */
-/* *n_s3 (optional): number of executed S3 statements.                       */
+/* *n_upd (optional): number of trailing updates A[i,j] -= A[i,k]A[j,k].    */
 /* ------------------------------------------------------------------------ */
-int or_potrf(int n, double *A, int lda, int *info, long long *n_s3)
+int or_potrf(int n, double *A, int lda, int *info, long long *n_upd)
 {
     if (n < 0 || lda < (n > 1 ? n : 1)) return -1;
     *info = 0;
-    long long s3 = 0;
+    long long nupd = 0;
     for (int k = 0; k < n; ++k) {
         double d = A[IX(k, k, lda)];
         if (!(d > 0.0)) {               /* also catches NaN */
             *info = k + 1;
             break;
         }
-        double lkk = sqrt(d);                               /* S1 */
+        double lkk = sqrt(d);                               /* pivot */
         A[IX(k, k, lda)] = lkk;
-        for (int i = k + 1; i < n; ++i)                     /* S2 */
+        for (int i = k + 1; i < n; ++i)                     /* scaling */
             A[IX(i, k, lda)] = A[IX(i, k, lda)] / lkk;
-        /* S3: the trailing lower triangle loses the outer product of the new
+        /* Update: the trailing lower triangle loses the outer product of the new
            column, a_ij - l_ik l_jk for k < j <= i; the loop order over (i, j)
            within one k does not change any element's arithmetic. */
         #pragma omp parallel for schedule(dynamic, 16)
@@ -343,9 +344,9 @@ int or_potrf(int n, double *A, int lda, int *info, long long *n_s3)
             for (int i = j; i < n; ++i)
                 A[IX(i, j, lda)] = A[IX(i, j, lda)] - A[IX(i, k, lda)] * ljk;
         }
-        s3 += (long long)(n - k - 1) * (n - k) / 2;
+        nupd += (long long)(n - k - 1) * (n - k) / 2;
     }
-    if (n_s3) *n_s3 = s3;
+    if (n_upd) *n_upd = nupd;
     return 0;
 }
 

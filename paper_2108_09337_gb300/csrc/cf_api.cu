@@ -6,8 +6,8 @@
 // interchanges (LU-2; the paper masks rows instead because its matrix is
 // replicated over c layers -- a single copy swaps in O(vN) per step), the LU
 // of the selected rows A00, the two triangular solves (LU-3, LU-4) and the
-// Schur update of A11 (LU-5).  The paper's scatters and reductions between
-// ranks (steps 1, 3-6, 8, 10) have no counterpart on one device.
+// Schur update of A11 (LU-5).  The paper's scatters, broadcasts and
+// reductions between ranks have no counterpart on one device.
 #include <atomic>
 #include <cstring>
 

@@ -1,7 +1,7 @@
 // cf_gemm64.cu -- SIMT Schur-complement update (FP64; FP32 for the solves of
 // the mixed path) and the FP64 residual.
 //
-//   LU-5 (FP64 path)  A11 <- A11 - A10 A01      (Alg. 1 step 11; Table 2 gemm)
+//   LU-5 (FP64 path)  A11 <- A11 - A10 A01      (Alg. 1; Table 2 gemm)
 //   CH-3 (FP64 path)  A11 <- A11 - L10 L10^T    (Table 2 gemmt, lower only)
 //   S-1               block updates of the triangular solves
 //   R-1               R = B - A X

@@ -49,7 +49,7 @@ template <typename T>
 int launch_apply_swaps(T *A, int lda, int ncols, int k0, const TournEpilogue &ep, int *perm, cudaStream_t st);
 
 // ---- panel kernels (cf_panel.cu)
-// LU of the w x w diagonal block without pivoting (S1/S2 of Fig. "prog_rep").
+// LU of the w x w diagonal block without pivoting (Fig. "prog_rep").
 template <typename T>
 int launch_getf2_nopiv(T *A00, int lda, int w, int kglob, int *info, cudaStream_t st);
 // A10 <- A10 * U^{-1}: rows x w block X, U upper non-unit w x w (or, with

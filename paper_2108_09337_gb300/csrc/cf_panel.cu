@@ -1,7 +1,7 @@
 // cf_panel.cu -- the per-step block routines around the Schur update:
-//   LU-3  A10 <- A10 U00^{-1}      (Alg. 1 step 7, "Factorize A10"; Table 2)
-//   LU-4  A01 <- L00^{-1} A01      (Alg. 1 step 9, "Factorize A01")
-//   A00   LU without pivoting of the selected rows (S1/S2 of Fig. "prog_rep",
+//   LU-3  A10 <- A10 U00^{-1}      (Alg. 1, "Factorize A10"; Table 2)
+//   LU-4  A01 <- L00^{-1} A01      (Alg. 1, "Factorize A01")
+//   A00   LU without pivoting of the selected rows (Fig. "prog_rep",
 //         the tournament already yields it, Sec. 7.2)
 //   CH-1  potrf of A00 (Listing "Cholesky Factorization"; Table 2, v^3/6)
 //   CH-2  L10 <- A10 L00^{-T}      (Table 2: costed like the LU panel solve)
@@ -83,11 +83,11 @@ k_potf2(T *A, int lda, int w, int kglob, int *info) {
             kdone = k;
             break;
         }
-        const T lkk = sqrt(d);                                  // S1
-        if (half == 0 && r > k && r < w) t[k * kLdT + r] = div_rn(t[k * kLdT + r], lkk);   // S2
+        const T lkk = sqrt(d);                                  // the pivot
+        if (half == 0 && r > k && r < w) t[k * kLdT + r] = div_rn(t[k * kLdT + r], lkk);   // column scaling
         __syncthreads();
         if (tid == 0) t[k * kLdT + k] = lkk;
-        if (r > k && r < w) {                                   // S3, j in (k, r]
+        if (r > k && r < w) {                                   // trailing update, j in (k, r]
             const T lik = t[k * kLdT + r];
             for (int j = k + 1 + half; j <= r; j += 2)
                 t[j * kLdT + r] = sub_rn(t[j * kLdT + r], mul_rn(lik, t[k * kLdT + j]));

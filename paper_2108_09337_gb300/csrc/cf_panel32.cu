@@ -1,7 +1,7 @@
 // cf_panel32.cu -- FP32 block routines of the mixed-precision path, built for
 // latency (they sit on the chain of dependent work of every step):
 //
-//   k_a00_lu_q32,   LU of A00 without pivoting (S1/S2 of Fig. "prog_rep" on
+//   k_a00_lu_q32,   LU of A00 without pivoting (Fig. "prog_rep" on
 //   k_a00_lu32      the rows TournPivot selected; Sec. 7.2)
 //   k_a00_chol32    Cholesky of A00 (Listing "Cholesky Factorization"; CH-1)
 //   k_rtrsm32(_w)   LU-3  A10 <- A10 U00^{-1}  /  CH-2  L10 <- A10 L00^{-T}
@@ -47,7 +47,7 @@ __device__ __forceinline__ __half lp_from<__half>(float x) { return __float2half
 // the Cholesky (108 against 51 us at 128 rows): those keep the kernels
 // below.
 //
-// LU without pivoting (S1/S2 of Fig. "prog_rep" on the rows TournPivot
+// LU without pivoting (Fig. "prog_rep" on the rows TournPivot
 // selected, Sec. 7.2), in place: for every column k, row k (final from
 // column k on) is published in shared memory; every row r > k takes
 // l = a(r, k) / a(k, k) (its lane holding column k divides and hands l to

@@ -3,7 +3,7 @@
 // with A and B in BF16 or FP16, K-major (row i of A holds its k values
 // contiguously), FP32 accumulation in tensor memory.
 //
-// This is Alg. 1 step 11 ("Factorize A11", Table 2's local gemm) and, with
+// This is Alg. 1 ("Factorize A11", Table 2's local gemm) and, with
 // `lower`, COnfCHOX's triangular gemmt -- where most of both methods' work lies
 // (Sec. 7.5).  Design for sm_103a:
 //   * persistent CTAs, one per SM, walking 128 x 256 output tiles;

@@ -1,5 +1,5 @@
-// cf_tourn.cu -- LU-1: TournPivot (Alg. 1 step 2; Sec. 7.3 "Tournament
-// Pivoting" and "Pivoting in COnfLUX"; step 2 of the I/O-cost proof) and
+// cf_tourn.cu -- LU-1: TournPivot (Alg. 1; Sec. 7.3 "Tournament
+// Pivoting" and "Pivoting in COnfLUX"; the pivot selection in the I/O-cost proof) and
 // LU-2: the row interchanges that bring the winners to the top.
 //
 // GPU design.  One launch runs a whole tournament.  A thread-block cluster of

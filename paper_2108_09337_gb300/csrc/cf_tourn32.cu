@@ -1,4 +1,4 @@
-// cf_tourn32.cu -- LU-1 (TournPivot, Alg. 1 step 2; Sec. 7.3) for the FP32
+// cf_tourn32.cu -- LU-1 (TournPivot, Alg. 1; Sec. 7.3) for the FP32
 // panels of the mixed-precision path.
 //
 // Same rule as the FP64 tournament (leaves of h consecutive rows, binary

@@ -1,6 +1,6 @@
 """Exact-rational restatement of the tournament-pivoting LU rule, used only to
 pin the C oracle (tests).  Written independently of oracle/cf_oracle.c, in
-Python ``fractions``, from the same reading of TournPivot (Alg. 1 step 2,
+Python ``fractions``, from the same reading of TournPivot (Alg. 1,
 Sec. 7.3): leaves of h consecutive panel rows choose their local candidates
 by partial-pivoting elimination; playoff nodes stack the candidates of
 ``arity`` adjacent children (original panel values) and choose again; the

@@ -10,8 +10,8 @@
 
 int or_tourn_select(int m, int w, const double *P, int ldp, int h, int arity, int *winners, double *min_gap);
 int or_getrf(int n, double *A, int lda, int v, int h, int arity, int *ipiv, int *info, double *step_gap,
-             long long *n_s2);
-int or_potrf(int n, double *A, int lda, int *info, long long *n_s3);
+             long long *n_upd);
+int or_potrf(int n, double *A, int lda, int *info, long long *n_upd);
 int or_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, double *B, int ldb);
 int or_potrs(int n, int nrhs, const double *L, int lda, double *B, int ldb);
 int or_residual(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B, int ldb,
@@ -62,8 +62,8 @@ int main(void) {
         for (size_t i = 0; i < (size_t)lda * n; ++i) A0[i] = A[i];
         int *ipiv = (int *)malloc(sizeof(int) * (size_t)n), info = -1;
         double *gaps = (double *)malloc(sizeof(double) * (size_t)steps);
-        long long ns2 = 0;
-        CHECK(or_getrf(n, A, lda, v, h, ar, ipiv, &info, gaps, &ns2) == 0);
+        long long nupd = 0;
+        CHECK(or_getrf(n, A, lda, v, h, ar, ipiv, &info, gaps, &nupd) == 0);
         for (int i = 0; i < n; ++i) CHECK(ipiv[i] >= i + 1 && ipiv[i] <= n);
         double *B = mat(n, nrhs, ldb), *X = (double *)malloc(sizeof(double) * (size_t)ldb * nrhs);
         double *R = (double *)malloc(sizeof(double) * (size_t)(n + 4) * nrhs);
@@ -102,8 +102,8 @@ int main(void) {
             }
         for (int i = 0; i < n; ++i) A[i + i * lda] += n;     /* diagonally dominant: SPD */
         int info = -1;
-        long long ns3 = 0;
-        CHECK(or_potrf(n, A, lda, &info, &ns3) == 0);
+        long long nupd = 0;
+        CHECK(or_potrf(n, A, lda, &info, &nupd) == 0);
         CHECK(info == 0);
         double *B = mat(n, nrhs, n);
         CHECK(or_potrs(n, nrhs, A, lda, B, n) == 0);

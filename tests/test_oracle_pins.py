@@ -283,17 +283,17 @@ def test_compensated_residual_is_nearly_exact():
 @pytest.mark.parametrize("n", [1, 2, 17, 100])
 def test_statement_counts_match_closed_forms(n):
     A = inputs.uniform_pm1(n, seed=1)
-    _, _, _, _, ns2 = oracle.getrf(A, v=7, h=5)
-    assert ns2 == oracle.lu_s2_count(n)
+    _, _, _, _, nupd = oracle.getrf(A, v=7, h=5)
+    assert nupd == oracle.lu_update_count(n)
     S = inputs.spd_gram(n, seed=1)
-    _, _, ns3 = oracle.potrf(S)
-    assert ns3 == oracle.chol_s3_count(n)
+    _, _, nupd = oracle.potrf(S)
+    assert nupd == oracle.chol_update_count(n)
 
 
 def test_flop_conventions_are_leading_terms():
     n = 10 ** 5
-    assert 2 * oracle.lu_s2_count(n) / oracle.lu_flops(n) == pytest.approx(1, rel=1e-4)
-    assert 2 * oracle.chol_s3_count(n) / oracle.chol_flops(n) == pytest.approx(1, rel=1e-4)
+    assert 2 * oracle.lu_update_count(n) / oracle.lu_flops(n) == pytest.approx(1, rel=1e-4)
+    assert 2 * oracle.chol_update_count(n) / oracle.chol_flops(n) == pytest.approx(1, rel=1e-4)
     # Sec. 6.1 counts |V2| = N(N-1)(N-2)/3 with its own index convention;
     # its double sum sum_k (N-k)(N-k-1) gives exactly that value.
     N = 50
