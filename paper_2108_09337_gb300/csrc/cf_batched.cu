@@ -674,15 +674,7 @@ struct BatchWS {
     size_t bytes;
 };
 
-static int sm_count_b() {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
-        cudaGetLastError();
-        sms = 148;
-    }
-    return sms;
-}
+static int sm_count_b() { return device_sm_count(); }
 
 // Launch configuration: block size vb and resident CTAs per SM (cps).  The
 // kernel variant compiled for cps resident CTAs is used; cps = 0 asks for

@@ -1,6 +1,8 @@
 // cf_common.cuh -- shared definitions of the libcf CUDA sources (sm_103a).
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -49,6 +51,27 @@ struct ScopedEvent {
 };
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// SM count of the current device (148 if the query fails), queried once per
+// device and kept in an atomic slot, so concurrent calls from several host
+// threads never race on it.
+inline int device_sm_count() {
+    constexpr int kDevs = 64;
+    static std::atomic<int> cache[kDevs];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 148;
+    }
+    int n = (dev >= 0 && dev < kDevs) ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 148;
+    }
+    if (dev >= 0 && dev < kDevs) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Carves aligned sub-buffers out of a caller-provided workspace; with a null

@@ -304,16 +304,7 @@ static int make_map_u8(CUtensorMap *map, const void *ptr, int rows, int k, int l
     return r == CUDA_SUCCESS ? CF_OK : CF_ERR_CUDA;
 }
 
-static int num_sms_fp8() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
-    return sms;
-}
+static int num_sms_fp8() { return device_sm_count(); }
 
 int launch_schur_fp8(int m, int n, int k, const void *qA, int ldqa, const float *sA, int ldsa, const void *qB,
                      int ldqb, const float *sB, int ldsb, float *C, int ldc, bool lower, cudaStream_t st) {

@@ -176,16 +176,7 @@ k_residual_f64(int m, int n, int nrhs, const double *__restrict__ A, int lda, co
     }
 }
 
-static int sm_count() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
-    return sms;
-}
+static int sm_count() { return device_sm_count(); }
 
 template <int NR, int RG>
 static int launch_residual_rg(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,

@@ -579,12 +579,7 @@ struct LookStream {
     }
 };
 
-static int device_sms() {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 148;
-}
+static int device_sms() { return device_sm_count(); }
 
 template <typename LP>
 static int mixed_getrf(int n, MixedWS &w, int *info, const Opts &o, cudaStream_t st, Timer *tu, bool split,

@@ -300,27 +300,20 @@ __global__ void __launch_bounds__(256) k_mat_absmax(int m, int n, const double *
 
 namespace {
 
-int sm_count_pair() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
-    return sms;
-}
+int sm_count_pair() { return device_sm_count(); }
 
 template <int NR>
 int resident_ctas() {
-    static int occ = 0;
-    if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual_pair<NR>, kPairThreads,
-                                                          pair_smem_bytes<NR>()) !=
-                cudaSuccess ||
-            occ <= 0)
-            occ = 1;
-    }
+    static const int occ = [] {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_residual_pair<NR>, kPairThreads,
+                                                          pair_smem_bytes<NR>()) != cudaSuccess ||
+            o <= 0) {
+            cudaGetLastError();
+            o = 1;
+        }
+        return o;
+    }();
     return occ;
 }
 

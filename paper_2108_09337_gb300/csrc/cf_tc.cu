@@ -315,16 +315,7 @@ static int make_operand_map(CUtensorMap *map, const void *ptr, int rows, int k, 
     return r == CUDA_SUCCESS ? CF_OK : CF_ERR_CUDA;
 }
 
-static int num_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
-    return sms;
-}
+static int num_sms() { return device_sm_count(); }
 
 int schur_tc_splitk(int m, int n, int k, bool lower) {
     // Only outputs with too few tiles to occupy half the SMs, and only ranges
