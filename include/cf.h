@@ -23,7 +23,12 @@
  *    the factorization stops there).
  *  - Return value (host): CF_OK, -i when argument i (1-based) is invalid, or
  *    one of the CF_ERR_* codes below.
- *  - Not thread-safe for concurrent calls that share a work buffer.
+ *  - Calls from several host threads, or overlapping on several streams,
+ *    are safe when each has its own work buffer, with two device-wide
+ *    exceptions: cf_getrf_noalloc's fixed scratch (such calls must not
+ *    overlap on the GPU), and the status words of the bounded device waits
+ *    (cf_device_status): a wait that runs out in one call may be reported,
+ *    and cleared, by whichever call reads them next.
  */
 #ifndef CF_H
 #define CF_H
