@@ -185,6 +185,7 @@ __device__ void cta_getrf(BSmem<T> &s, T *A, int n, int lda, int *ipiv, int *inf
             for (int j = 0; j < w; ++j) {
                 const int lab = s.order[j], p = s.where_[lab];
                 ipiv[k0 + j] = k0 + p + 1;
+                s.order[j] = p;                          // the swap partner, for the column loop
                 if (p != j) {
                     const int lj = s.lab[j];
                     s.lab[j] = lab; s.where_[lab] = j;
@@ -196,7 +197,7 @@ __device__ void cta_getrf(BSmem<T> &s, T *A, int n, int lda, int *ipiv, int *inf
         for (int c = tid; c < n; c += kBT) {
             T *col = A + (size_t)c * lda;
             for (int j = 0; j < w; ++j) {
-                const int p = ipiv[k0 + j] - 1;
+                const int p = k0 + s.order[j];
                 if (p != k0 + j) { const T t = col[k0 + j]; col[k0 + j] = col[p]; col[p] = t; }
             }
         }
@@ -227,24 +228,48 @@ __device__ void cta_getrf(BSmem<T> &s, T *A, int n, int lda, int *ipiv, int *inf
             const int r = e % w, c = e / w;
             A00[r + (size_t)c * lda] = s.D[c * (kBMaxV + 1) + r];
         }
-        // ---- LU-3: A10 <- A10 U00^{-1} (one row per thread)
+        // ---- LU-3: A10 <- A10 U00^{-1} (one row per thread, held in registers:
+        // every element gets the same operations in the same order as in
+        // place, without a trip through memory per multiply-add)
         for (int r = w + tid; r < m; r += kBT) {
             T *row = A00 + r;
-            for (int k = 0; k < w; ++k) {
-                const T ukk = s.D[k * (kBMaxV + 1) + k];
-                T x = row[(size_t)k * lda];
-                if (ukk != T(0)) x = x / ukk;
-                row[(size_t)k * lda] = x;
-                for (int j = k + 1; j < w; ++j) row[(size_t)j * lda] -= x * s.D[j * (kBMaxV + 1) + k];
+            T v[kBMaxV];
+#pragma unroll
+            for (int k = 0; k < kBMaxV; ++k) v[k] = k < w ? row[(size_t)k * lda] : T(0);
+#pragma unroll
+            for (int k = 0; k < kBMaxV; ++k) {
+                if (k < w) {
+                    const T ukk = s.D[k * (kBMaxV + 1) + k];
+                    T x = v[k];
+                    if (ukk != T(0)) x = x / ukk;
+                    v[k] = x;
+#pragma unroll
+                    for (int j = k + 1; j < kBMaxV; ++j)
+                        if (j < w) v[j] -= x * s.D[j * (kBMaxV + 1) + k];
+                }
             }
+#pragma unroll
+            for (int k = 0; k < kBMaxV; ++k)
+                if (k < w) row[(size_t)k * lda] = v[k];
         }
-        // ---- LU-4: A01 <- L00^{-1} A01 (one column per thread)
+        // ---- LU-4: A01 <- L00^{-1} A01 (one column per thread, in registers)
         for (int c = w + tid; c < m; c += kBT) {
             T *col = A00 + (size_t)c * lda;
-            for (int k = 0; k < w; ++k) {
-                const T xk = col[k];
-                for (int i = k + 1; i < w; ++i) col[i] -= s.D[k * (kBMaxV + 1) + i] * xk;
+            T v[kBMaxV];
+#pragma unroll
+            for (int i = 0; i < kBMaxV; ++i) v[i] = i < w ? col[i] : T(0);
+#pragma unroll
+            for (int k = 0; k < kBMaxV; ++k) {
+                if (k < w) {
+                    const T xk = v[k];
+#pragma unroll
+                    for (int i = k + 1; i < kBMaxV; ++i)
+                        if (i < w) v[i] -= s.D[k * (kBMaxV + 1) + i] * xk;
+                }
             }
+#pragma unroll
+            for (int i = 0; i < kBMaxV; ++i)
+                if (i < w) col[i] = v[i];
         }
         __syncthreads();
         // ---- LU-5: A11 <- A11 - A10 A01
@@ -292,14 +317,25 @@ __device__ int cta_potrf(BSmem<T> &s, T *A, int n, int lda, int *info, int vb) {
             const int r = e % w, c = e / w;
             if (r >= c) A00[r + (size_t)c * lda] = s.D[c * (kBMaxV + 1) + r];
         }
-        // CH-2: L10 <- A10 L00^{-T} (one row per thread)
+        // CH-2: L10 <- A10 L00^{-T} (one row per thread, held in registers)
         for (int r = w + tid; r < m; r += kBT) {
             T *row = A00 + r;
-            for (int k = 0; k < w; ++k) {
-                T x = row[(size_t)k * lda] / s.D[k * (kBMaxV + 1) + k];
-                row[(size_t)k * lda] = x;
-                for (int j = k + 1; j < w; ++j) row[(size_t)j * lda] -= x * s.D[k * (kBMaxV + 1) + j];
+            T v[kBMaxV];
+#pragma unroll
+            for (int k = 0; k < kBMaxV; ++k) v[k] = k < w ? row[(size_t)k * lda] : T(0);
+#pragma unroll
+            for (int k = 0; k < kBMaxV; ++k) {
+                if (k < w) {
+                    const T x = v[k] / s.D[k * (kBMaxV + 1) + k];
+                    v[k] = x;
+#pragma unroll
+                    for (int j = k + 1; j < kBMaxV; ++j)
+                        if (j < w) v[j] -= x * s.D[k * (kBMaxV + 1) + j];
+                }
             }
+#pragma unroll
+            for (int k = 0; k < kBMaxV; ++k)
+                if (k < w) row[(size_t)k * lda] = v[k];
         }
         __syncthreads();
         // CH-3: A11 <- A11 - L10 L10^T (lower); B operand = L10^T read from A
